@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs: stencil matrices in CSR form and right-hand sides.
+
+This module is the one place that both the CUDA path's tests/benchmark and the
+oracle's tests draw their inputs from.  It holds none of the solver's
+arithmetic (no SpMV, factorisation, level scheduling or Krylov step); it only
+assembles matrices and vectors from a documented recipe with numpy's PCG64
+generator (``numpy.random.default_rng(seed)``).
+
+The workloads stand in for the paper's test matrices (Section 3: the
+3D_Poisson 150^3 matrix of Table 2, and reservoir-like diffusion systems):
+
+* ``poisson2d_5pt(N)`` / ``poisson3d_7pt(N)`` -- constant-coefficient Poisson,
+  unscaled (diagonal 4 / 6, off-diagonals -1), Dirichlet boundary, natural
+  lexicographic order with x fastest.
+* ``diffusion2d_5pt_lognormal`` / ``diffusion3d_7pt_lognormal`` -- cell-centred
+  finite-volume diffusion with one coefficient kappa_f = exp(sigma * g),
+  g ~ N(0, 1), per cell face (boundary faces included).  A_ij = -kappa_f for the
+  face shared by cells i and j; A_ii = sum of the kappa of all faces of cell i
+  (a boundary face acts as a Dirichlet face).  The result is symmetric, an
+  M-matrix and positive definite.
+* ``stencil27_irregular`` -- 27-point stencil with off-diagonals -1, plus a
+  fraction of rows that receive extra random off-diagonal entries (values
+  N(0, variance)), with the diagonal set to a multiple of the off-diagonal
+  absolute row sum (strictly diagonally dominant).
+* ``rhs_uniform(n, seed)`` -- right-hand side uniform on [-1, 1].
+
+All matrices come back as ``(row_ptr int32[n+1], col int32[nnz], val
+float64[nnz])`` with strictly ascending column indices in every row and the
+diagonal present.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "CSR",
+    "poisson2d_5pt",
+    "poisson3d_7pt",
+    "diffusion2d_5pt_lognormal",
+    "diffusion3d_7pt_lognormal",
+    "stencil27_irregular",
+    "rhs_uniform",
+    "tridiagonal",
+    "random_sparse",
+]
+
+
+class CSR:
+    """A square CSR matrix: ``row_ptr`` (int32, n+1), ``col`` (int32), ``val`` (float64)."""
+
+    __slots__ = ("n", "row_ptr", "col", "val")
+
+    def __init__(self, row_ptr, col, val):
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+        self.n = int(self.row_ptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        d[rows, self.col] = self.val
+        return d
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+def _assemble(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -> CSR:
+    """Sort (row, col) pairs and build CSR.  Pairs must be unique."""
+    order = np.lexsort((cols, rows))
+    rows = rows[order]
+    cols = cols[order]
+    vals = vals[order]
+    counts = np.bincount(rows, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32 indices")
+    return CSR(row_ptr.astype(np.int32), cols.astype(np.int32), vals)
+
+
+def _stencil_csr(dims, offsets, weights) -> CSR:
+    """Constant-coefficient stencil on a box grid (x fastest), Dirichlet.
+
+    ``offsets`` are per-axis displacement tuples (dx, dy[, dz]); ``weights``
+    the matrix value for each.  Offsets are visited in ascending linear
+    order so columns come out sorted without a sort.
+    """
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    nd = len(dims)
+    strides = [1]
+    for d in dims[:-1]:
+        strides.append(strides[-1] * d)
+    lin = [sum(o[a] * strides[a] for a in range(nd)) for o in offsets]
+    order = np.argsort(lin, kind="stable")
+    coords = np.unravel_index(np.arange(n), dims[::-1])[::-1]  # coords[a] for axis a (x first)
+    rows_l, cols_l, vals_l = [], [], []
+    idx = np.arange(n, dtype=np.int64)
+    for oi in order:
+        o = offsets[oi]
+        mask = np.ones(n, dtype=bool)
+        for a in range(nd):
+            c = coords[a] + o[a]
+            mask &= (c >= 0) & (c < dims[a])
+        r = idx[mask]
+        rows_l.append(r)
+        cols_l.append(r + lin[oi])
+        vals_l.append(np.full(r.shape[0], weights[oi], dtype=np.float64))
+    rows = np.concatenate(rows_l)
+    cols = np.concatenate(cols_l)
+    vals = np.concatenate(vals_l)
+    return _assemble(n, rows, cols, vals)
+
+
+def poisson2d_5pt(N: int) -> CSR:
+    """2D 5-point Poisson on an N x N grid: n = N^2, nnz = 5N^2 - 4N."""
+    offs = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)]
+    w = [4.0, -1.0, -1.0, -1.0, -1.0]
+    return _stencil_csr((N, N), offs, w)
+
+
+def poisson3d_7pt(N: int) -> CSR:
+    """3D 7-point Poisson on an N^3 grid: n = N^3, nnz = 7N^3 - 6N^2."""
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    w = [6.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0]
+    return _stencil_csr((N, N, N), offs, w)
+
+
+def _face_assembly(dims, faces) -> CSR:
+    """Finite-volume assembly from per-axis face coefficient arrays.
+
+    ``faces[a]`` has the grid shape (z, y, x order, reversed dims) with axis
+    a extended by one: face index f along axis a sits between cells f-1 and
+    f; faces 0 and dims[a] are boundary faces.
+    """
+    dims = tuple(int(d) for d in dims)
+    nd = len(dims)
+    n = int(np.prod(dims))
+    shape = dims[::-1]  # numpy shape, slowest axis first
+    diag = np.zeros(shape, dtype=np.float64)
+    rows_l, cols_l, vals_l = [], [], []
+    idx = np.arange(n, dtype=np.int64).reshape(shape)
+    for a in range(nd):
+        ax = nd - 1 - a  # numpy axis for grid axis a
+        k = faces[a]
+        lo = [slice(None)] * nd
+        hi = [slice(None)] * nd
+        lo[ax] = slice(0, dims[a])
+        hi[ax] = slice(1, dims[a] + 1)
+        diag += k[tuple(lo)] + k[tuple(hi)]
+        inner = [slice(None)] * nd
+        inner[ax] = slice(1, dims[a])
+        kin = k[tuple(inner)]  # faces between cell f-1 and f, f = 1..dims-1
+        left = [slice(None)] * nd
+        right = [slice(None)] * nd
+        left[ax] = slice(0, dims[a] - 1)
+        right[ax] = slice(1, dims[a])
+        il = idx[tuple(left)].ravel()
+        ir = idx[tuple(right)].ravel()
+        kv = kin.ravel()
+        rows_l += [il, ir]
+        cols_l += [ir, il]
+        vals_l += [-kv, -kv]
+    rows_l.append(idx.ravel())
+    cols_l.append(idx.ravel())
+    vals_l.append(diag.ravel())
+    return _assemble(n, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(vals_l))
+
+
+def diffusion2d_5pt_lognormal(N: int, sigma: float, seed: int, Ny: int | None = None) -> CSR:
+    """2D 5-point diffusion, log-normal(0, sigma) face coefficients.
+
+    Draw order from ``default_rng(seed)``: x-faces (shape Ny x (N+1)), then
+    y-faces ((Ny+1) x N), each as standard normals scaled by sigma.
+    """
+    Nx, Ny = int(N), int(N if Ny is None else Ny)
+    rng = np.random.default_rng(seed)
+    fx = np.exp(sigma * rng.standard_normal((Ny, Nx + 1)))
+    fy = np.exp(sigma * rng.standard_normal((Ny + 1, Nx)))
+    return _face_assembly((Nx, Ny), [fx, fy])
+
+
+def diffusion3d_7pt_lognormal(N: int, sigma: float, seed: int) -> CSR:
+    """3D 7-point diffusion on N^3 with log-normal(0, sigma) face coefficients.
+
+    Draw order from ``default_rng(seed)``: x-faces (N, N, N+1), y-faces
+    (N, N+1, N), z-faces (N+1, N, N), numpy shapes in (z, y, x) order.
+    n = N^3, nnz = 7N^3 - 6N^2.
+    """
+    rng = np.random.default_rng(seed)
+    fx = np.exp(sigma * rng.standard_normal((N, N, N + 1)))
+    fy = np.exp(sigma * rng.standard_normal((N, N + 1, N)))
+    fz = np.exp(sigma * rng.standard_normal((N + 1, N, N)))
+    return _face_assembly((N, N, N), [fx, fy, fz])
+
+
+def stencil27_irregular(N: int, struct_seed: int, value_seed: int, frac: float = 0.02,
+                        extra_min: int = 30, extra_max: int = 120, variance: float = 0.01,
+                        diag_factor: float = 1.1) -> CSR:
+    """3D 27-point stencil (off-diagonals -1) on N^3 plus irregular rows.
+
+    ``round(frac * n)`` rows, chosen uniformly without replacement with
+    ``default_rng(struct_seed)``, each receive U{extra_min..extra_max} extra
+    distinct off-diagonal columns drawn uniformly among the columns the row
+    does not hold yet.  Their values are N(0, variance) from
+    ``default_rng(value_seed)`` (variance, i.e. standard deviation
+    sqrt(variance)).  The diagonal is diag_factor times the off-diagonal
+    absolute row sum.
+    """
+    offs, w = [], []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                offs.append((dx, dy, dz))
+                w.append(0.0 if (dx, dy, dz) == (0, 0, 0) else -1.0)
+    base = _stencil_csr((N, N, N), offs, w)
+    n = base.n
+    srng = np.random.default_rng(struct_seed)
+    vrng = np.random.default_rng(value_seed)
+    nrows = int(round(frac * n))
+    chosen = np.sort(srng.choice(n, size=nrows, replace=False))
+    counts = srng.integers(extra_min, extra_max + 1, size=nrows)
+    ex_rows, ex_cols = [], []
+    for r, c in zip(chosen.tolist(), counts.tolist()):
+        have = set(base.col[base.row_ptr[r]:base.row_ptr[r + 1]].tolist())
+        picked: list[int] = []
+        while len(picked) < c:
+            cand = srng.integers(0, n, size=2 * c)
+            for j in cand.tolist():
+                if j not in have:
+                    have.add(j)
+                    picked.append(j)
+                    if len(picked) == c:
+                        break
+        ex_rows.append(np.full(c, r, dtype=np.int64))
+        ex_cols.append(np.asarray(picked, dtype=np.int64))
+    ex_rows = np.concatenate(ex_rows) if ex_rows else np.zeros(0, np.int64)
+    ex_cols = np.concatenate(ex_cols) if ex_cols else np.zeros(0, np.int64)
+    ex_vals = vrng.normal(0.0, np.sqrt(variance), size=ex_rows.shape[0])
+    brows = np.repeat(np.arange(n, dtype=np.int64), np.diff(base.row_ptr))
+    rows = np.concatenate([brows, ex_rows])
+    cols = np.concatenate([base.col.astype(np.int64), ex_cols])
+    vals = np.concatenate([base.val, ex_vals])
+    offdiag = rows != cols
+    absrow = np.bincount(rows[offdiag], weights=np.abs(vals[offdiag]), minlength=n)
+    vals = np.where(offdiag, vals, diag_factor * absrow[rows])
+    return _assemble(n, rows, cols, vals)
+
+
+def rhs_uniform(n: int, seed: int) -> np.ndarray:
+    """Right-hand side with entries uniform on [-1, 1] from ``default_rng(seed)``."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
+
+
+def tridiagonal(n: int, seed: int) -> CSR:
+    """Random strictly diagonally dominant tridiagonal matrix (nonsymmetric)."""
+    rng = np.random.default_rng(seed)
+    lo = rng.uniform(-1.0, 1.0, n - 1)
+    up = rng.uniform(-1.0, 1.0, n - 1)
+    d = 2.5 + rng.uniform(0.0, 1.0, n)
+    rows = np.concatenate([np.arange(1, n), np.arange(n), np.arange(n - 1)])
+    cols = np.concatenate([np.arange(n - 1), np.arange(n), np.arange(1, n)])
+    vals = np.concatenate([lo, d, up])
+    return _assemble(n, rows.astype(np.int64), cols.astype(np.int64), vals)
+
+
+def random_sparse(n: int, density: float, seed: int, dominance: float = 1.5,
+                  integer: bool = False) -> CSR:
+    """Random nonsymmetric sparse matrix with full diagonal.
+
+    Off-diagonal positions are Bernoulli(density); values uniform on [-1, 1]
+    (or integers in [-3, 3] \\ {0} if ``integer``).  The diagonal is
+    ``dominance`` times the off-diagonal absolute row sum plus one, so every
+    ILU(k) of it has nonzero pivots.
+    """
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n, n)) < density
+    np.fill_diagonal(mask, False)
+    r, c = np.nonzero(mask)
+    if integer:
+        v = rng.integers(1, 4, size=r.shape[0]) * rng.choice([-1.0, 1.0], size=r.shape[0])
+    else:
+        v = rng.uniform(-1.0, 1.0, size=r.shape[0])
+    absrow = np.bincount(r, weights=np.abs(v), minlength=n)
+    d = np.floor(dominance * absrow) + 1.0 if integer else dominance * absrow + 1.0
+    rows = np.concatenate([r, np.arange(n)])
+    cols = np.concatenate([c, np.arange(n)])
+    vals = np.concatenate([v, d])
+    return _assemble(n, rows.astype(np.int64), cols.astype(np.int64), vals.astype(np.float64))

@@ -1,0 +1,490 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-types an oracle formula: each compares the oracle with
+a closed form, a brute-force literal execution on tiny inputs, a textbook or
+library routine in a case where the method reduces to it exactly, or an
+invariant.  They run without a GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_1606_00545_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- helpers
+def dense_iluk_literal(Ad, pattern, k):
+    """Algorithm 2 executed literally on dense arrays (brute force, O(n^3)).
+
+    Levels follow Eq. 9 (0 on the pattern, infinity elsewhere) and Eq. 10;
+    after the p loop of row i the positions with level > k are zeroed and
+    their level reset to infinity.
+    """
+    A = Ad.astype(np.float64).copy()
+    n = A.shape[0]
+    L = np.where(pattern, 0.0, np.inf)
+    for i in range(1, n):
+        for p in range(i):
+            if L[i, p] <= k:
+                A[i, p] = A[i, p] / A[p, p]
+                A[i, p + 1:] = A[i, p + 1:] - A[i, p] * A[p, p + 1:]
+                L[i, p + 1:] = np.minimum(L[i, p + 1:], L[i, p] + L[p, p + 1:] + 1)
+        drop = L[i, :] > k
+        A[i, drop] = 0.0
+        L[i, drop] = np.inf
+    return A, L
+
+
+def pattern_of(A):
+    P = np.zeros((A.n, A.n), dtype=bool)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    P[rows, A.col] = True
+    return P
+
+
+def fixpoint_levels(n, row_ptr, col, upper):
+    """Brute force for Eq. 11: sweep in the *wrong* order until nothing changes."""
+    lev = np.zeros(n, dtype=np.int64)
+    changed = True
+    sweeps = 0
+    while changed:
+        changed = False
+        sweeps += 1
+        order = range(n) if upper else range(n - 1, -1, -1)
+        for i in order:
+            cols = col[row_ptr[i]:row_ptr[i + 1]]
+            deps = cols[cols > i] if upper else cols[cols < i]
+            new = 1 + (lev[deps].max() if deps.size else 0)
+            if new != lev[i]:
+                lev[i] = new
+                changed = True
+        assert sweeps <= n + 2
+    return lev
+
+
+def lu_nopivot_checked(D):
+    """scipy LU; asserts that no row exchange happened (so it is Doolittle LU)."""
+    P, L, U = sla.lu(D)
+    assert np.array_equal(P, np.eye(D.shape[0]))
+    return L, U
+
+
+# --------------------------------------------------------------------------- generator vs Table 2
+def test_table2_poisson_sizes_match_paper():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table2_poisson_sizes.txt"))
+            if l.strip() and not l.startswith("#")]
+    for name, side, n, nnz, mib in rows:
+        side, n, nnz = int(side), int(n), int(nnz)
+        # n and nnz of the 7-point stencil: count without building the 3.4M-row matrix
+        assert side ** 3 == n
+        assert 7 * side ** 3 - 6 * side ** 2 == nnz
+        if mib != "-":
+            assert round((nnz * 12 + (n + 1) * 4) / 2 ** 20) == int(mib)
+    small = synth.poisson3d_7pt(12)
+    assert small.nnz == 7 * 12 ** 3 - 6 * 12 ** 2
+
+
+# --------------------------------------------------------------------------- O1: SpMV
+@pytest.mark.parametrize("N", [7, 12])
+def test_spmv_poisson2d_eigenpairs(orc, N):
+    A = synth.poisson2d_5pt(N)
+    x = np.arange(1, N + 1)
+    h = np.pi / (N + 1)
+    for p, q in [(1, 1), (2, 3), (N, 1), (N - 1, N)]:
+        v = np.outer(np.sin(q * h * x), np.sin(p * h * x)).ravel()  # (y, x) with x fastest
+        lam = 4 - 2 * np.cos(p * h) - 2 * np.cos(q * h)
+        Av = orc.spmv(A, v)
+        assert np.max(np.abs(Av - lam * v)) <= 1e-12 * max(1.0, lam)
+
+
+def test_spmv_poisson3d_eigenpairs(orc):
+    N = 6
+    A = synth.poisson3d_7pt(N)
+    x = np.arange(1, N + 1)
+    h = np.pi / (N + 1)
+    for p, q, r in [(1, 1, 1), (2, 5, 3), (6, 6, 6)]:
+        v = np.einsum("k,j,i->kji", np.sin(r * h * x), np.sin(q * h * x), np.sin(p * h * x)).ravel()
+        lam = 6 - 2 * (np.cos(p * h) + np.cos(q * h) + np.cos(r * h))
+        assert np.max(np.abs(orc.spmv(A, v) - lam * v)) <= 1e-12 * lam
+
+
+def test_spmv_integer_exact_and_epilogue(orc):
+    A = synth.random_sparse(150, 0.05, seed=11, integer=True)
+    rng = np.random.default_rng(3)
+    x = rng.integers(-5, 6, size=A.n).astype(np.float64)
+    y = rng.integers(-5, 6, size=A.n).astype(np.float64)
+    Ai = A.to_dense().astype(np.int64)
+    exact = 2 * (Ai @ x.astype(np.int64)) - 3 * y.astype(np.int64)
+    got = orc.spmv(A, x, alpha=2.0, beta=-3.0, y=y)
+    assert np.array_equal(got, exact.astype(np.float64))
+
+
+def test_spmv_diffusion_rowsum_is_boundary_flux(orc):
+    # A 1 = sum of the boundary-face coefficients of each cell (interior faces cancel)
+    N, sigma, seed = 5, 2.0, 9
+    A = synth.diffusion3d_7pt_lognormal(N, sigma, seed)
+    rng = np.random.default_rng(seed)
+    fx = np.exp(sigma * rng.standard_normal((N, N, N + 1)))
+    fy = np.exp(sigma * rng.standard_normal((N, N + 1, N)))
+    fz = np.exp(sigma * rng.standard_normal((N + 1, N, N)))
+    bnd = np.zeros((N, N, N))
+    bnd[:, :, 0] += fx[:, :, 0]
+    bnd[:, :, -1] += fx[:, :, -1]
+    bnd[:, 0, :] += fy[:, 0, :]
+    bnd[:, -1, :] += fy[:, -1, :]
+    bnd[0, :, :] += fz[0, :, :]
+    bnd[-1, :, :] += fz[-1, :, :]
+    got = orc.spmv(A, np.ones(A.n))
+    assert np.allclose(got, bnd.ravel(), rtol=1e-12, atol=1e-12 * np.abs(A.val).max())
+
+
+def test_vector_ops_exact(orc):
+    rng = np.random.default_rng(5)
+    x = rng.integers(-9, 10, 1000).astype(np.float64)
+    y = rng.integers(-9, 10, 1000).astype(np.float64)
+    assert orc.dot(x, y) == float(np.sum(x.astype(np.int64) * y.astype(np.int64)))
+    assert orc.nrm2(np.array([3.0, 4.0])) == 5.0
+    assert np.array_equal(orc.axpby(2.0, x, -1.0, y), 2 * x - y)
+    assert np.array_equal(orc.waxpby(-3.0, x, 4.0, y), -3 * x + 4 * y)
+
+
+# --------------------------------------------------------------------------- O2/O3: ILU(k)
+def _check_against_literal(orc, A, k):
+    F = orc.iluk(A, k)
+    Ad = A.to_dense()
+    D, Lev = dense_iluk_literal(Ad, pattern_of(A), k)
+    keep = np.isfinite(Lev)
+    rows = np.repeat(np.arange(A.n), np.diff(F.row_ptr))
+    got_pat = np.zeros_like(keep)
+    got_pat[rows, F.col] = True
+    assert np.array_equal(got_pat, keep), "fill pattern differs from literal Algorithm 2"
+    assert np.array_equal(F.lev, Lev[rows, F.col].astype(np.int32)), "fill levels differ"
+    assert np.array_equal(F.val, D[rows, F.col]), "values differ from literal Algorithm 2"
+    return F
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_iluk_matches_literal_algorithm2_random(orc, k, seed):
+    A = synth.random_sparse(90, 0.04, seed=seed)
+    _check_against_literal(orc, A, k)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_iluk_matches_literal_algorithm2_stencils(orc, k):
+    _check_against_literal(orc, synth.poisson2d_5pt(9), k)
+    _check_against_literal(orc, synth.diffusion3d_7pt_lognormal(4, 2.0, 1), k)
+    _check_against_literal(orc, synth.stencil27_irregular(4, 1, 2, frac=0.1, extra_min=3,
+                                                          extra_max=8), k)
+
+
+def test_ilu0_reproduces_A_on_its_pattern(orc):
+    for A in (synth.random_sparse(120, 0.05, seed=4), synth.diffusion3d_7pt_lognormal(5, 2.0, 3)):
+        F = orc.iluk(A, 0)
+        (Lrp, Lc, Lv), (Urp, Uc, Uv) = F.split()
+        Ld = np.eye(A.n)
+        Ud = np.zeros((A.n, A.n))
+        Ld[np.repeat(np.arange(A.n), np.diff(Lrp)), Lc] = Lv
+        Ud[np.repeat(np.arange(A.n), np.diff(Urp)), Uc] = Uv
+        Ad = A.to_dense()
+        P = pattern_of(A)
+        assert np.array_equal(np.repeat(np.arange(A.n), np.diff(F.row_ptr)),
+                              np.repeat(np.arange(A.n), np.diff(A.row_ptr)))
+        LU = Ld @ Ud
+        scale = np.abs(Ad).max()
+        assert np.max(np.abs(LU[P] - Ad[P])) <= 1e-13 * scale
+
+
+def test_ilu0_tridiagonal_equals_dense_lu(orc):
+    A = synth.tridiagonal(200, seed=8)
+    F = orc.iluk(A, 0)
+    L, U = lu_nopivot_checked(A.to_dense())
+    D = F.to_dense()
+    assert np.allclose(np.tril(D, -1), np.tril(L, -1), rtol=0, atol=1e-14)
+    assert np.allclose(np.triu(D), U, rtol=0, atol=1e-14 * np.abs(U).max())
+
+
+def test_iluk_high_level_equals_dense_lu(orc):
+    # 2D Poisson N x N: full LU fills inside the band |i-j| <= N; a level beyond
+    # the maximum fill level reproduces exact LU (pattern and values).
+    N = 6
+    A = synth.poisson2d_5pt(N)
+    L, U = lu_nopivot_checked(A.to_dense())
+    F = orc.iluk(A, 3 * N)
+    D = F.to_dense()
+    band = np.abs(np.subtract.outer(np.arange(A.n), np.arange(A.n))) <= N
+    rows = np.repeat(np.arange(A.n), np.diff(F.row_ptr))
+    pat = np.zeros((A.n, A.n), bool)
+    pat[rows, F.col] = True
+    lu_nz = (np.tril(L, -1) + U) != 0
+    assert np.all(pat[lu_nz]) and not np.any(pat & ~band)
+    # the same result as any larger level
+    assert np.array_equal(orc.iluk(A, 5 * N).to_dense(), D)
+    assert np.allclose(np.tril(D, -1), np.tril(L, -1), atol=1e-13)
+    assert np.allclose(np.triu(D), U, atol=1e-13)
+
+
+def test_iluk_fill_offsets_2d_and_3d(orc):
+    N = 8
+    A = synth.poisson2d_5pt(N)
+    F = orc.iluk(A, 1)
+    rows = np.repeat(np.arange(A.n), np.diff(F.row_ptr))
+    offs = set(np.unique(F.col - rows).tolist())
+    assert offs == {-N, -(N - 1), -1, 0, 1, N - 1, N}
+    fill = F.lev == 1
+    assert set(np.unique((F.col - rows)[fill]).tolist()) == {-(N - 1), N - 1}
+    assert F.row_ptr[-1] == A.nnz + 2 * (N - 1) ** 2
+    M = 5
+    B = synth.poisson3d_7pt(M)
+    G = orc.iluk(B, 1)
+    rows = np.repeat(np.arange(B.n), np.diff(G.row_ptr))
+    fill_offs = set(np.unique((G.col - rows)[G.lev == 1]).tolist())
+    assert fill_offs == {-(M - 1), M - 1, -(M * M - 1), M * M - 1, -(M * M - M), M * M - M}
+    assert G.lev.max() == 1
+
+
+def test_iluk_zero_pivot_and_invalid(orc):
+    A = synth.CSR(np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([0.0, 1.0, 1.0, 0.0]))
+    with pytest.raises(orc.OracleError) as e:
+        orc.iluk(A, 0)
+    assert e.value.status == orc.ERR_ZERO_PIVOT
+    B = synth.CSR(np.array([0, 2, 3]), np.array([1, 0, 1]), np.array([1.0, 2.0, 3.0]))
+    with pytest.raises(orc.OracleError) as e:
+        orc.iluk(B, 0)
+    assert e.value.status == orc.ERR_INVALID
+
+
+# --------------------------------------------------------------------------- O5: levels
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_levels_match_fixpoint(orc, k):
+    for A in (synth.random_sparse(150, 0.03, seed=21), synth.stencil27_irregular(
+            5, 3, 4, frac=0.05, extra_min=2, extra_max=6)):
+        F = orc.iluk(A, k)
+        for upper in (False, True):
+            lev, nlev = orc.levels(F.n, F.row_ptr, F.col, upper)
+            ref = fixpoint_levels(F.n, F.row_ptr, F.col, upper)
+            assert np.array_equal(lev, ref)
+            assert nlev == ref.max()
+
+
+def test_levels_closed_forms(orc):
+    N = 9
+    F = orc.iluk(synth.poisson2d_5pt(N), 0)
+    lev, nlev = orc.levels(F.n, F.row_ptr, F.col, False)
+    y, x = np.divmod(np.arange(N * N), N)
+    assert nlev == 2 * N - 1
+    assert np.array_equal(lev, x + y + 1)
+    ulev, unlev = orc.levels(F.n, F.row_ptr, F.col, True)
+    assert unlev == 2 * N - 1
+    assert np.array_equal(ulev, (N - 1 - x) + (N - 1 - y) + 1)
+    M = 5
+    G = orc.iluk(synth.poisson3d_7pt(M), 0)
+    lev, nlev = orc.levels(G.n, G.row_ptr, G.col, False)
+    z, r = np.divmod(np.arange(M ** 3), M * M)
+    y, x = np.divmod(r, M)
+    assert nlev == 3 * M - 2
+    assert np.array_equal(lev, x + y + z + 1)
+    # diagonal -> 1 level, bidiagonal -> n levels
+    n = 10
+    lev, nlev = orc.levels(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), False)
+    assert nlev == 1 and np.all(lev == 1)
+    rp = np.concatenate([[0], 1 + 2 * np.arange(n)]).astype(np.int32)
+    col = np.concatenate([[0]] + [[i - 1, i] for i in range(1, n)]).astype(np.int32)
+    lev, nlev = orc.levels(n, rp, col, False)
+    assert nlev == n and np.array_equal(lev, np.arange(1, n + 1))
+
+
+def test_level_sets_are_canonical(orc):
+    F = orc.iluk(synth.random_sparse(80, 0.05, seed=2), 1)
+    lev, nlev = orc.levels(F.n, F.row_ptr, F.col, False)
+    ptr, rows = orc.level_sets(lev, nlev)
+    assert ptr[-1] == F.n and np.all(np.diff(ptr) > 0)
+    for l in range(nlev):
+        seg = rows[ptr[l]:ptr[l + 1]]
+        assert np.all(np.diff(seg) > 0) and np.all(lev[seg] == l + 1)
+
+
+# --------------------------------------------------------------------------- O6: triangular solves
+def test_triangular_solves_vs_scipy(orc):
+    A = synth.random_sparse(200, 0.03, seed=6)
+    F = orc.iluk(A, 1)
+    D = F.to_dense()
+    b = synth.rhs_uniform(A.n, 3)
+    y = orc.lsolve_unit(F, b)
+    yr = sla.solve_triangular(np.tril(D, -1) + np.eye(A.n), b, lower=True, unit_diagonal=True)
+    assert np.max(np.abs(y - yr)) <= 1e-13 * np.abs(yr).max()
+    z = orc.usolve(F, y)
+    zr = sla.solve_triangular(np.triu(D), y, lower=False)
+    assert np.max(np.abs(z - zr)) <= 1e-13 * np.abs(zr).max()
+
+
+# --------------------------------------------------------------------------- O4: RAS
+def test_ras_single_block_is_plain_ilu(orc):
+    A = synth.diffusion3d_7pt_lognormal(6, 2.0, 5)
+    r = synth.rhs_uniform(A.n, 1)
+    M = orc.RAS(A, 1, 1, 0)
+    F = orc.iluk(A, 1)
+    assert np.array_equal(M.apply(r), orc.usolve(F, orc.lsolve_unit(F, r)))
+
+
+def test_ras_block_diagonal_equals_global_ilu(orc):
+    blocks = [synth.random_sparse(40, 0.08, seed=s) for s in range(4)]
+    n = 160
+    rows, cols, vals = [], [], []
+    for b, B in enumerate(blocks):
+        rr = np.repeat(np.arange(40), np.diff(B.row_ptr)) + 40 * b
+        rows.append(rr)
+        cols.append(B.col + 40 * b)
+        vals.append(B.val)
+    A = synth._assemble(n, np.concatenate(rows).astype(np.int64),
+                        np.concatenate(cols).astype(np.int64), np.concatenate(vals))
+    r = synth.rhs_uniform(n, 2)
+    F = orc.iluk(A, 2)
+    ref = orc.usolve(F, orc.lsolve_unit(F, r))
+    for ov in (0, 1, 3):
+        assert np.array_equal(orc.RAS(A, 2, 4, ov).apply(r), ref)
+
+
+def test_ras_large_overlap_equals_global_ilu(orc):
+    A = synth.poisson2d_5pt(8)
+    r = synth.rhs_uniform(A.n, 4)
+    F = orc.iluk(A, 0)
+    ref = orc.usolve(F, orc.lsolve_unit(F, r))
+    M = orc.RAS(A, 0, 4, 2 * 8)  # overlap >= graph diameter: every block is the whole matrix
+    for b in range(4):
+        assert M.block(b)[0].shape[0] == A.n
+    assert np.array_equal(M.apply(r), ref)
+
+
+def test_ras_apply_is_the_schwarz_sum(orc):
+    # z = sum_b R0_b (L_b U_b)^{-1} R_b r computed with dense algebra
+    A = synth.random_sparse(120, 0.03, seed=9)
+    M = orc.RAS(A, 1, 5, 1)
+    r = synth.rhs_uniform(A.n, 5)
+    z = np.full(A.n, np.nan)
+    owned = np.zeros(A.n, int)
+    for b in range(5):
+        rows, lo, hi, F = M.block(b)
+        D = F.to_dense()
+        Lb = np.tril(D, -1) + np.eye(rows.shape[0])
+        Ub = np.triu(D)
+        zb = np.linalg.solve(Lb @ Ub, r[rows])
+        sel = (rows >= lo) & (rows < hi)
+        z[rows[sel]] = zb[sel]
+        owned[rows[sel]] += 1
+    assert np.all(owned == 1)
+    got = M.apply(r)
+    assert np.max(np.abs(got - z)) <= 1e-10 * np.abs(z).max()
+
+
+def test_ras_overlap_sets_closed_form(orc):
+    # 7-point stencil, N^3 grid, nb = N/2 blocks of 2 z-planes, overlap 1:
+    # V_b = planes 2b-1 .. 2b+2 (clipped to the grid)
+    N = 6
+    A = synth.poisson3d_7pt(N)
+    nb = N // 2
+    M = orc.RAS(A, 1, nb, 1)
+    P = N * N
+    for b in range(nb):
+        rows, lo, hi, F = M.block(b)
+        assert (lo, hi) == (2 * b * P, (2 * b + 2) * P)
+        z0, z1 = max(0, 2 * b - 1), min(N, 2 * b + 3)
+        assert np.array_equal(rows, np.arange(z0 * P, z1 * P))
+
+
+def test_ras_every_owned_row_written_once(orc):
+    A = synth.stencil27_irregular(6, 1, 2, frac=0.05, extra_min=3, extra_max=10)
+    M = orc.RAS(A, 0, 7, 1)
+    z = M.apply(np.ones(A.n))
+    assert np.all(np.isfinite(z))
+    covered = np.zeros(A.n, int)
+    for b in range(7):
+        rows, lo, hi, F = M.block(b)
+        covered[lo:hi] += 1
+    assert np.all(covered == 1)
+
+
+# --------------------------------------------------------------------------- O7: BiCGSTAB
+def test_bicgstab_exact_preconditioner_one_iteration(orc):
+    A = synth.tridiagonal(300, seed=3)
+    b = synth.rhs_uniform(A.n, 1)
+    x, info = orc.bicgstab(A, b, M=orc.RAS(A, 0, 1, 0), tol=1e-12)
+    assert info.status == orc.OK and info.iters == 1 and info.rel_resid <= 1e-12
+    B = synth.poisson2d_5pt(7)
+    b = synth.rhs_uniform(B.n, 2)
+    x, info = orc.bicgstab(B, b, M=orc.RAS(B, 100, 1, 0), tol=1e-12)
+    assert info.iters == 1 and info.rel_resid <= 1e-12
+
+
+@pytest.mark.parametrize("nb,ov,k", [(1, 0, 0), (4, 1, 1), (3, 0, 2)])
+def test_bicgstab_manufactured_solution(orc, nb, ov, k):
+    A = synth.diffusion2d_5pt_lognormal(24, 1.0, seed=4)
+    xs = synth.rhs_uniform(A.n, 7)
+    b = orc.spmv(A, xs)
+    x, info = orc.bicgstab(A, b, M=orc.RAS(A, k, nb, ov), tol=1e-10, maxit=500)
+    assert info.status == orc.OK and info.rel_resid <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
+    xd = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-6
+
+
+def test_bicgstab_unpreconditioned_and_breakdown(orc):
+    A = synth.random_sparse(100, 0.05, seed=12)
+    b = synth.rhs_uniform(A.n, 3)
+    x, info = orc.bicgstab(A, b, tol=1e-10)
+    assert info.status == orc.OK
+    assert np.allclose(x, np.linalg.solve(A.to_dense(), b), atol=1e-8)
+    # skew-symmetric: (r0, A r0) = 0, so alpha is undefined at the first step
+    S = synth.CSR(np.array([0, 1, 2]), np.array([1, 0]), np.array([1.0, -1.0]))
+    S = synth.CSR(np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([0.0, 1.0, -1.0, 0.0]))
+    x, info = orc.bicgstab(S, np.array([1.0, 2.0]), tol=1e-10)
+    assert info.status == orc.BREAKDOWN
+
+
+def test_bicgstab_zero_rhs(orc):
+    A = synth.poisson2d_5pt(4)
+    x, info = orc.bicgstab(A, np.zeros(A.n), x0=np.ones(A.n))
+    assert info.iters == 0 and np.all(x == 0)
+
+
+# --------------------------------------------------------------------------- O8: GMRES
+def test_gmres_finite_termination(orc):
+    A = synth.poisson2d_5pt(6)
+    b = synth.rhs_uniform(A.n, 1)
+    x, info = orc.gmres(A, b, tol=1e-10, maxit=A.n, restart=A.n)
+    assert info.status == orc.OK and info.iters <= A.n and info.rel_resid <= 1e-10
+    # an exact LU preconditioner solves in one Arnoldi step
+    x, info = orc.gmres(A, b, M=orc.RAS(A, 100, 1, 0), tol=1e-12, restart=5)
+    assert info.iters == 1 and info.rel_resid <= 1e-12
+
+
+def test_gmres_givens_estimate_is_true_residual(orc):
+    A = synth.diffusion2d_5pt_lognormal(16, 1.0, seed=2)
+    b = synth.rhs_uniform(A.n, 9)
+    for M in (None, orc.RAS(A, 0, 2, 1)):
+        x, info = orc.gmres(A, b, M=M, tol=1e-6, maxit=400, restart=400)
+        assert info.restarts == 1
+        assert abs(info.est_resid - info.rel_resid) <= 1e-9
+
+
+@pytest.mark.parametrize("restart", [5, 30])
+def test_gmres_manufactured_solution(orc, restart):
+    A = synth.random_sparse(150, 0.04, seed=15)
+    xs = synth.rhs_uniform(A.n, 2)
+    b = orc.spmv(A, xs)
+    x, info = orc.gmres(A, b, M=orc.RAS(A, 0, 3, 1), tol=1e-10, maxit=600, restart=restart)
+    assert info.status == orc.OK and info.rel_resid <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+    if restart == 5:
+        assert info.restarts > 1
+
+
+def test_gmres_maxit(orc):
+    A = synth.diffusion2d_5pt_lognormal(20, 2.0, seed=1)
+    b = synth.rhs_uniform(A.n, 1)
+    x, info = orc.gmres(A, b, tol=1e-14, maxit=7, restart=3)
+    assert info.status == orc.MAXIT and info.iters == 7
