@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark: preconditioned Krylov iterations per second on one GB300.
+
+Workload (one "step" = one full solve, every row of the hot path):
+  3D 7-point variable-coefficient diffusion on 128^3 (n = 2,097,152, nnz =
+  14,581,760), face coefficients log-normal(0, sigma = 2) from seed 2, FP64;
+  ILU(1) on 64 RAS blocks with overlap 1; BiCGSTAB (Algorithm 4) from x0 = 0
+  to relative residual 1e-8; right-hand side uniform[-1, 1] from seed 3.
+  The matrix and factors (about 0.8 GB) exceed the 129 MB L2, so no flush is
+  needed between steps.
+
+Output: one JSON line (rank 0).  ``value`` = iterations/s of the whole job
+(device-resident inputs); ``e2e`` = the same through the C ABI with host
+buffers (copies inside the timed region); ``roofline`` = the dominant kernel
+(the level-scheduled RAS triangular solve) against the measured HBM peak;
+``cpu_baseline`` = the FP64 oracle timed on a bounded sample on host cores.
+``--impl reference`` times the oracle alone as the reference arm.
+Under torchrun with N > 1 every rank solves its own copy (replicas; the
+method needs no exchange on one device) and ``value`` sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1606_00545_gb300 import synth  # noqa: E402
+
+N_GRID = 128
+SIGMA = 2.0
+COEF_SEED = 2
+RHS_SEED = 3
+K_FILL = 1
+NBLOCKS = 64
+OVERLAP = 1
+TOL = 1e-8
+MAXIT = 20000
+WORKLOAD = "diffusion3d_7pt_128^3_lognormal_sigma2_ilu1_ras64_ov1_bicgstab_tol1e-8_fp64"
+METRIC = "BiCGSTAB iterations/s (ILU(1)+RAS 64 blocks overlap 1, 128^3 7-pt log-normal diffusion, FP64, to 1e-8)"
+CPU_SAMPLE_ITERS = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["trsv", "spmv"], default=None,
+                    help="profiling mode: set up the workload, then launch only this kernel "
+                         "--steps times (few launches before it, for ncu -k/-s/-c)")
+    return ap.parse_args()
+
+
+def run_kernel_only(args, local_rank):
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu as H
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    A, b = workload()
+    Ah = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(Ah, K_FILL, NBLOCKS, OVERLAP)
+    H.level_schedule(P)
+    r = torch.tensor(b, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(args.steps):
+        if args.kernel == "trsv":
+            H.hec_precond_apply(P, r, z)
+        else:
+            H.hec_spmv(Ah, 1.0, r, 0.0, None, z)
+    torch.cuda.synchronize()
+    if args.kernel == "trsv":
+        assert H.hec_precond_status(P) == H.OK
+    print(json.dumps({"kernel": args.kernel, "launches": args.steps,
+                      "apply_bytes": P.info()["apply_bytes"],
+                      "spmv_bytes": A.nnz * 12 + A.n * 16}))
+
+
+def workload():
+    A = synth.diffusion3d_7pt_lognormal(N_GRID, SIGMA, COEF_SEED)
+    b = synth.rhs_uniform(A.n, RHS_SEED)
+    return A, b
+
+
+def base_config(A, extra=None):
+    cfg = {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "ilu_k": K_FILL, "ras_blocks": NBLOCKS,
+           "overlap": OVERLAP, "tol": TOL, "solver": "bicgstab",
+           "l2": "inputs larger than L2 (matrix + factors ~0.8 GB > 129 MB), no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bad_clocks(c):
+    if c["sm_mhz"] is None:
+        return False
+    if set(c["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    return c["sm_mhz"] < 0.6 * c["sm_max_mhz"] and not c["reasons"]
+
+
+# ------------------------------------------------------------------ peaks / profiles
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("k_trsv.cu", "kernels.cuh", "hec_setup.cpp"):
+        with open(os.path.join(ROOT, "paper_1606_00545_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the triangular-solve kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "trsv_ras_c2.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    sha = bytes_ = None
+    for line in txt.splitlines():
+        if line.startswith("source_sha256_16:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                bytes_ = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                pass
+    if sha == kernel_source_sha() and bytes_:
+        return bytes_
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_sample(A, b, iters):
+    import oracle
+    t0 = time.perf_counter()
+    R = oracle.RAS(A, K_FILL, NBLOCKS, OVERLAP)
+    setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = oracle.bicgstab(A, b, M=R, tol=TOL, maxit=iters)
+    dt = time.perf_counter() - t0
+    return info.iters / dt, info.iters, dt, setup_s
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    A, b = workload()
+    import oracle
+    R = oracle.RAS(A, K_FILL, NBLOCKS, OVERLAP)
+    per_step = 4
+    rates, times = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        x, info = oracle.bicgstab(A, b, M=R, tol=TOL, maxit=per_step)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            rates.append(info.iters)
+    value = sum(rates) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": base_config(A, {"sample": "%d BiCGSTAB iterations per step from x0 = 0"
+                                      % per_step}),
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of %d BiCGSTAB iterations of the full workload"
+                                       % (args.steps, per_step)},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu as H
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    H.load_library()
+    H.use_torch_allocator()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    A, b = workload()
+    t0 = time.perf_counter()
+    Ah = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(Ah, K_FILL, NBLOCKS, OVERLAP)
+    H.level_schedule(P)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    pinf = P.info()
+    stream = torch.cuda.current_stream()
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+
+    def solve():
+        return H.krylov_solve(Ah, P, bd, x, tol=TOL, maxit=MAXIT, method=H.BICGSTAB,
+                              flags=H.X0_ZERO)
+
+    for _ in range(max(3, args.warmup)):
+        info = solve()
+    assert info["status"] == H.OK, info
+    iters = info["iters"]
+
+    def timed(fn, steps):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = [fn() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, out
+
+    for attempt in range(2):
+        with ClockSampler(local_rank) as cs:
+            ms, infos = timed(solve, args.steps)
+        clocks = cs.summary()
+        if not bad_clocks(clocks):
+            break
+    tot_iters = sum(i["iters"] for i in infos)
+    launches = sum(i["kernel_launches"] for i in infos)
+    value = world * tot_iters / (ms * 1e-3)
+    rel_resid = max(i["rel_resid"] for i in infos)
+
+    # e2e: host (pinned) b and x through the C ABI, copies inside the region
+    bh = torch.tensor(b).pin_memory()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    bh_np, xh_np = bh.numpy(), xh.numpy()
+
+    def solve_host():
+        return H.krylov_solve(Ah, P, bh_np, xh_np, tol=TOL, maxit=MAXIT, method=H.BICGSTAB,
+                              flags=H.X0_ZERO)
+
+    solve_host()
+    ms_e2e, infos_e2e = timed(solve_host, max(1, args.steps // 2))
+    e2e_value = world * sum(i["iters"] for i in infos_e2e) / (ms_e2e * 1e-3)
+    xg = xh.numpy().copy()
+
+    # dominant kernel: level-scheduled RAS triangular solve, timed alone
+    r = torch.tensor(synth.rhs_uniform(A.n, 7), device=dev)
+    z = torch.empty_like(r)
+    for _ in range(5):
+        H.hec_precond_apply(P, r, z)
+    reps = 50
+    ms_apply, _ = timed(lambda: H.hec_precond_apply(P, r, z), reps)
+    assert H.hec_precond_status(P) == H.OK
+    apply_s = ms_apply * 1e-3 / reps
+    peak, peak_kind = measured_peaks()
+    achieved = pinf["apply_bytes"] / apply_s / 1e9
+    # SpMV alone (second kernel of the path)
+    y = torch.empty_like(r)
+    for _ in range(5):
+        H.hec_spmv(Ah, 1.0, r, 0.0, None, y)
+    ms_spmv, _ = timed(lambda: H.hec_spmv(Ah, 1.0, r, 0.0, None, y), reps)
+    spmv_bytes = A.nnz * 12 + A.n * 16
+    spmv_gbs = spmv_bytes / (ms_spmv * 1e-3 / reps) / 1e9
+
+    # GMRES(30) on the same system (Arnoldi/Givens rows of the path)
+    xg30 = torch.zeros_like(bd)
+    H.krylov_solve(Ah, P, bd, xg30, tol=TOL, maxit=MAXIT, restart=30, method=H.GMRES,
+                   flags=H.X0_ZERO)
+    ms_g, ig = timed(lambda: H.krylov_solve(Ah, P, bd, xg30, tol=TOL, maxit=MAXIT, restart=30,
+                                            method=H.GMRES, flags=H.X0_ZERO), 1)
+    gm = ig[0]
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, it, dt, cpu_setup = cpu_sample(A, b, CPU_SAMPLE_ITERS)
+        cpu = {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle",
+               "sample": "%d BiCGSTAB iterations of the full 128^3 workload from x0 = 0 "
+                         "(%.1f s; RAS/ILU(1) setup %.1f s untimed)" % (it, dt, cpu_setup)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": base_config(A, {"iters_per_solve": iters, "rel_resid": rel_resid,
+                                  "setup_s": round(setup_s, 3),
+                                  "parallelism": "replicas" if world > 1 else "single"}),
+        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": 8 * A.n,
+                "d2h_bytes_per_step": 8 * A.n},
+        "gpu_launches": launches,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "roofline": {"bound": "hbm", "kernel": "k_trsv_ras (RAS L+U level-scheduled solve)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "alg_bytes_per_launch": pinf["apply_bytes"],
+                     "launch_ms": apply_s * 1e3},
+        "spmv": {"achieved": spmv_gbs, "unit": "GB/s", "frac": spmv_gbs / peak,
+                 "alg_bytes_per_launch": spmv_bytes, "launch_ms": ms_spmv / reps},
+        "gmres30": {"iters": gm["iters"], "restarts": gm["restarts"],
+                    "iters_per_s": gm["iters"] / (ms_g * 1e-3), "rel_resid": gm["rel_resid"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.kernel:
+        run_kernel_only(args, local_rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

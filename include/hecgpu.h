@@ -1,0 +1,241 @@
+/*
+ * hecgpu.h -- C ABI of the GB300 (sm_103a) ILU(k)/RAS-preconditioned Krylov
+ * library.  The operations follow Yang, Liu and Chen, "Development of Krylov
+ * and AMG linear solvers for large-scale sparse matrices on GPUs":
+ *   hec_build       HEC matrix format (Section 2.1): a column-major ELL slab
+ *                   plus a CSR tail for the entries that do not fit.
+ *   hec_spmv        SpMV on HEC (Section 2.2, Algorithm 1, Eqs. 1-2).
+ *   hec_axpby ...   vector operations (Section 2.3, Eqs. 3-6).
+ *   ilu_k_setup     ILU(k) (Section 2.4, Eqs. 8-10, Algorithm 2) on every
+ *                   block of a restricted additive Schwarz partition
+ *                   (Section 2.5).
+ *   level_schedule  level sets of every L_b and U_b (Section 2.6, Eq. 11,
+ *                   Algorithm 3) and the device layout the solver streams.
+ *   hec_precond_apply  z = M^{-1} r, M the RAS/ILU(k) preconditioner
+ *                   (Eq. 7), by level-scheduled triangular solves.
+ *   krylov_solve    preconditioned BiCGSTAB (Section 2.7, Algorithm 4) or
+ *                   restarted GMRES(m) (Section 2.7).
+ *
+ * Conventions
+ *   - Every call returns int: 0 (HEC_OK), a negative error code, or a
+ *     positive solver outcome (HEC_MAXIT, HEC_BREAKDOWN).  No exception
+ *     crosses the ABI.  hec_last_error() returns a message for the calling
+ *     thread's last failure.
+ *   - Indices are 0-based int32.  A CSR matrix must be square, with strictly
+ *     ascending column indices in every row (else HEC_ERR_UNSORTED_CSR);
+ *     ilu_k_setup also needs every diagonal entry stored.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is ordered on it; calls that return host data
+ *     (queries, krylov_solve's info) synchronise it.
+ *   - Handles own their device memory.  It comes from the allocator set with
+ *     hec_set_allocator (default: cudaMalloc / cudaFree).  Vectors passed in
+ *     (x, y, r, z, b) are owned by the caller and only borrowed for the call.
+ *   - Values are FP64.  There is no CPU fallback: a call that needs the
+ *     device fails with HEC_ERR_CUDA when no CUDA device is present.
+ */
+#ifndef HECGPU_H
+#define HECGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define HEC_OK 0
+#define HEC_ERR_INVALID (-1)      /* bad argument or handle state            */
+#define HEC_ERR_OOM (-2)          /* the allocator returned NULL             */
+#define HEC_ERR_ZERO_PIVOT (-3)   /* ILU(k) met a pivot equal to zero        */
+#define HEC_ERR_UNSORTED_CSR (-4) /* columns not strictly ascending / range  */
+#define HEC_ERR_CUDA (-5)         /* a CUDA runtime call failed              */
+#define HEC_ERR_TIMEOUT (-6)      /* a bounded device wait ran out           */
+#define HEC_MAXIT 1               /* solver stopped at maxit                 */
+#define HEC_BREAKDOWN 2           /* BiCGSTAB rho = 0, (r0,v) = 0, omega = 0  */
+
+/* ---------------------------------------------------------------- types */
+typedef struct hec_matrix_s *hec_matrix_t;   /* HEC matrix on the device     */
+typedef struct hec_precond_s *hec_precond_t; /* RAS blocks, ILU(k) factors   */
+
+/* A CSR matrix, borrowed for the call (copied). */
+typedef struct {
+    int32_t n;              /* rows = columns, >= 1                          */
+    int32_t nnz;            /* row_ptr[n]                                    */
+    const int32_t *row_ptr; /* n + 1 entries                                 */
+    const int32_t *col;     /* nnz entries                                   */
+    const double *val;      /* nnz entries                                   */
+    int32_t on_device;      /* 0: the three arrays are host memory; 1: device */
+} hec_csr_t;
+
+/* Options of hec_build.  A zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+    int32_t ell_width;    /* K, entries per row kept in the ELL slab; 0 = auto
+                             (largest K that at least a third of the rows
+                             reach); the rest of a longer row goes to the CSR
+                             tail                                           */
+    int32_t ell_ld_align; /* slab leading dimension = n rounded up to this
+                             multiple of 32; 0 = 256 (Section 2.1)           */
+    int32_t flags;        /* HEC_HOST_ONLY: keep the host structure only (no
+                             device memory; queries work, compute calls
+                             return HEC_ERR_INVALID)                        */
+    int32_t reserved;
+} hec_opts_t;
+
+#define HEC_HOST_ONLY 1
+
+typedef struct {
+    int32_t n, nnz;
+    int32_t ell_width;  /* K                                                  */
+    int32_t ell_ld;     /* slab leading dimension                             */
+    int32_t tail_rows;  /* rows with more than K entries                      */
+    int32_t tail_nnz;   /* entries stored in the CSR tail                     */
+    int64_t device_bytes;
+} hec_matrix_info_t;
+
+typedef struct {
+    int32_t nblocks, overlap, k;
+    int32_t scheduled;       /* level_schedule has run                        */
+    int64_t rows_total;      /* sum over blocks of |V_b|                      */
+    int64_t factor_nnz;      /* sum over blocks of nnz(L_b) + nnz(U_b)        */
+    int32_t max_levels_L;    /* largest level count of an L_b                 */
+    int32_t max_levels_U;    /* largest level count of a U_b                  */
+    int64_t apply_bytes;     /* algorithmic bytes one hec_precond_apply moves  */
+    int64_t device_bytes;
+    int32_t ring_slots;      /* shared-memory window of solved values          */
+    int32_t global_passes;   /* (block, factor) solves whose dependencies do
+                                not fit the window and are read from global
+                                memory instead                                */
+} hec_precond_info_t;
+
+#define HEC_GMRES 0
+#define HEC_BICGSTAB 1
+
+typedef struct {
+    int32_t method;     /* HEC_GMRES or HEC_BICGSTAB                          */
+    int32_t flags;      /* HEC_X0_ZERO: ignore the content of x, start at 0   */
+    int64_t spin_limit; /* polls of a device wait before HEC_ERR_TIMEOUT;
+                           0 = default (about a second)                      */
+} hec_solve_opts_t;
+
+#define HEC_X0_ZERO 1
+
+typedef struct {
+    int32_t iters;          /* BiCGSTAB passes / GMRES Arnoldi steps          */
+    int32_t restarts;       /* GMRES cycles started                           */
+    int32_t status;         /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN or an error   */
+    int32_t reserved;
+    double rel_resid;       /* true ||b - A x|| / ||b|| recomputed at the end */
+    double est_resid;       /* GMRES: last Givens estimate / ||b||; BiCGSTAB:
+                               last recursive residual / ||b||                */
+    int64_t kernel_launches;/* library kernels the solve ran                  */
+    int64_t h2d_bytes;      /* host->device bytes copied (host b / x)         */
+    int64_t d2h_bytes;      /* device->host bytes copied (host x)             */
+} hec_solve_info_t;
+
+/* ---------------------------------------------------------------- misc */
+const char *hec_status_string(int status);
+/* Message describing the calling thread's last failing call ("" if none). */
+const char *hec_last_error(void);
+/* Device allocator for every handle and workspace allocation: alloc(bytes,
+ * stream, ctx) returns device memory or NULL; free(ptr, stream, ctx).  NULL
+ * functions restore cudaMalloc / cudaFree.  Affects later allocations only;
+ * memory is always returned through the allocator that produced it. */
+int hec_set_allocator(void *(*alloc_fn)(size_t bytes, void *stream, void *ctx),
+                      void (*free_fn)(void *ptr, void *stream, void *ctx), void *ctx);
+
+/* ---------------------------------------------------------------- HEC matrix */
+/* Section 2.1: convert A to HEC (ELL slab + CSR tail) and upload it.  The
+ * slab is column-major, entry k of row i at [k * ell_ld + i]; short rows are
+ * padded with value 0 and their own row index as column. */
+int hec_build(const hec_csr_t *A, const hec_opts_t *opts, void *stream, hec_matrix_t *out);
+int hec_matrix_info(hec_matrix_t A, hec_matrix_info_t *info);
+/* Host copies of the HEC arrays (each pointer may be NULL to skip it):
+ * ell_col/ell_val: K * ell_ld entries; tail_rows: tail_rows entries;
+ * tail_ptr: tail_rows + 1; tail_col/tail_val: tail_nnz. */
+int hec_matrix_export(hec_matrix_t A, int32_t *ell_col, double *ell_val, int32_t *tail_rows,
+                      int32_t *tail_ptr, int32_t *tail_col, double *tail_val);
+void hec_matrix_destroy(hec_matrix_t A);
+
+/* Eq. 2 (Algorithm 1): y_out = alpha * A x + beta * y_in on the device.
+ * y_in may equal y_out; it is not read when beta == 0; x must not overlap y_out.  x, y_in, y_out:
+ * device arrays of n doubles.  When dots != NULL (device, 2 doubles) the
+ * reductions of the result are fused into the same launch:
+ * dots[0] = (w, y_out) (w: device array of n doubles; NULL means y_out) and
+ * dots[1] = (y_out, y_out), each summed in a fixed order (deterministic). */
+int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const double *y_in,
+             double *y_out, const double *w, double *dots, void *stream);
+
+/* ---------------------------------------------------------------- vector ops */
+/* Eqs. 3-6 on device arrays of n doubles.  hec_dot / hec_nrm2 write their
+ * result to *result (device, 1 double), summed in a fixed order. */
+int hec_axpby(int32_t n, double a, const double *x, double b, double *y, void *stream);
+int hec_waxpby(int32_t n, double a, const double *x, double b, const double *y, double *z,
+               void *stream);
+int hec_dot(int32_t n, const double *x, const double *y, double *result, void *stream);
+int hec_nrm2(int32_t n, const double *x, double *result, void *stream);
+/* Arnoldi projection: h[i] = (V_i, w) for i < k, V column-major with leading
+ * dimension ldv (>= n), h: device array of k doubles. */
+int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const double *w, double *h,
+                 void *stream);
+
+/* ---------------------------------------------------------------- preconditioner */
+/* Sections 2.4-2.5: partition the rows into nblocks contiguous owned ranges
+ * W_b = [floor(b n / nblocks), floor((b+1) n / nblocks)), grow each by
+ * `overlap` layers of matrix-graph neighbours (V_b), and factorise every
+ * A[V_b, V_b] by ILU(k).  Factors are computed on the host and kept there
+ * until level_schedule uploads them.  Returns HEC_ERR_ZERO_PIVOT if a pivot
+ * is zero, HEC_ERR_INVALID if a diagonal entry is missing. */
+int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
+                hec_precond_t *out);
+/* Section 2.6 (Eq. 11, Algorithm 3): level of every row of every L_b and
+ * U_b, and the level-major device layout of the factors.  Idempotent. */
+int level_schedule(hec_precond_t M, void *stream);
+int hec_precond_info(hec_precond_t M, hec_precond_info_t *info);
+/* Block b: |V_b| (*nv), the owned range, and the global row ids of V_b in
+ * ascending order (rows may be NULL). */
+int hec_precond_get_block(hec_precond_t M, int32_t b, int32_t *nv, int32_t *own_lo,
+                          int32_t *own_hi, int32_t *rows);
+/* Block b: the combined ILU(k) factor of A[V_b, V_b] in local indices (L
+ * strictly below the diagonal, unit diagonal implied; U on and above),
+ * host copies; any array may be NULL, *nnz is always set. */
+int hec_precond_get_factor(hec_precond_t M, int32_t b, int32_t *nnz, int32_t *row_ptr,
+                           int32_t *col, double *val, int32_t *lev);
+#define HEC_FACTOR_L 0
+#define HEC_FACTOR_U 1
+/* Block b, factor L or U: number of levels (Eq. 11) and the level sets,
+ * level_ptr (nlev + 1) and level_rows (local row ids, ascending inside each
+ * level); arrays may be NULL. */
+int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *nlev,
+                           int32_t *level_ptr, int32_t *level_rows);
+/* z = M^{-1} r (Eq. 7 with M = the RAS combination of L_b U_b): every block
+ * gathers r on V_b, solves L_b then U_b level by level, and writes z on its
+ * owned rows only.  r, z: device arrays of n doubles, r != z.  Needs
+ * level_schedule.  Waits are bounded by spin_limit polls (0 = default); a
+ * wait that runs out is reported by hec_precond_status. */
+int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit,
+                      void *stream);
+/* Synchronise the stream and return (and clear) the device error word of
+ * the preconditioner: HEC_OK or HEC_ERR_TIMEOUT. */
+int hec_precond_status(hec_precond_t M, void *stream);
+void hec_precond_destroy(hec_precond_t M);
+
+/* ---------------------------------------------------------------- Krylov */
+/* Section 2.7: solve A x = b with the right-preconditioned BiCGSTAB of
+ * Algorithm 4 or restarted GMRES(restart), M == NULL meaning no
+ * preconditioner.  Convergence: ||r|| <= tol ||b|| (BiCGSTAB: the recursive
+ * residual of Algorithm 4; GMRES: the true residual checked at every cycle
+ * end).  b and x are device or host arrays of n doubles (host arrays are
+ * staged through device memory; the byte counts are reported in info);
+ * x holds x0 on entry unless HEC_X0_ZERO, and the solution on exit.  The
+ * whole iteration runs on the device as one CUDA graph with a device-side
+ * loop condition; the call synchronises the stream at the end.  Returns
+ * HEC_OK, HEC_MAXIT, HEC_BREAKDOWN or an error; info may be NULL. */
+int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, double tol,
+                 int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
+                 hec_solve_info_t *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1228 @@
+// hec_lib.cu -- the C ABI declared in include/hecgpu.h: handles, device memory,
+// launches, and the CUDA-graph drivers of BiCGSTAB (Algorithm 4) and
+// restarted GMRES(m) (Section 2.7).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstddef>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hecgpu.h"
+#include "hec_setup.h"
+#include "kernels.cuh"
+
+using namespace hec;
+
+// ====================================================================== errors
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define HEC_CK(call)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(HEC_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                        __LINE__);                                                                \
+    } while (0)
+
+#define HEC_TRY(expr)                                                                             \
+    do {                                                                                          \
+        int r_ = (expr);                                                                          \
+        if (r_ != HEC_OK)                                                                         \
+            return r_;                                                                            \
+    } while (0)
+
+int check_launch(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(HEC_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return HEC_OK;
+}
+
+// ====================================================================== allocator
+struct AllocFns {
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*free_)(void *, void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocFns g_alloc;
+
+// One device allocation, returned through the allocator that made it.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    AllocFns fns;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (!p)
+            return;
+        if (fns.free_)
+            fns.free_(p, nullptr, fns.ctx);
+        else
+            cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t nbytes, cudaStream_t s)
+    {
+        release();
+        if (nbytes == 0)
+            nbytes = 16;
+        {
+            std::lock_guard<std::mutex> lk(g_alloc_mu);
+            fns = g_alloc;
+        }
+        if (fns.alloc) {
+            p = fns.alloc(nbytes, (void *)s, fns.ctx);
+            if (!p)
+                return fail(HEC_ERR_OOM, "allocator returned NULL for %zu bytes", nbytes);
+        } else {
+            cudaError_t e = cudaMalloc(&p, nbytes);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? HEC_ERR_OOM : HEC_ERR_CUDA,
+                            "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
+            }
+        }
+        bytes = nbytes;
+        return HEC_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <class T>
+int upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s)
+{
+    HEC_TRY(d.alloc(h.size() * sizeof(T), s));
+    if (!h.empty())
+        HEC_CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return HEC_OK;
+}
+
+int device_sms()
+{
+    static int sms = -1;
+    if (sms < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    return sms;
+}
+
+inline int grid_for(int64_t items, int per_cta, int ctas_per_sm)
+{
+    int64_t need = (items + per_cta - 1) / per_cta;
+    int64_t cap = (int64_t)device_sms() * ctas_per_sm;
+    return (int)std::max<int64_t>(1, std::min(need, cap));
+}
+
+// Reduction scratch: partials sized for every reducing launch of the library.
+struct Reducer {
+    DevBuf partials, ticket;
+    RedScratch r{};
+    int init(cudaStream_t s)
+    {
+        const int cap = std::max(device_sms() * 8 * kMaxDots, device_sms() * 4 * (kMaxRestart + 1));
+        HEC_TRY(partials.alloc((size_t)cap * sizeof(double), s));
+        HEC_TRY(ticket.alloc(sizeof(unsigned), s));
+        HEC_CK(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
+        r.partials = partials.as<double>();
+        r.ticket = ticket.as<unsigned>();
+        r.capacity = cap;
+        return HEC_OK;
+    }
+};
+
+std::atomic<uint64_t> g_next_id(1);
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+} // namespace
+
+// ====================================================================== handles
+struct Solver;
+
+struct hec_matrix_s {
+    uint64_t id = 0;
+    bool host_only = false;
+    HostCSR csr;
+    HecHost hec;
+    DevBuf ell_col, ell_val, tail_rows, tail_ptr, tail_col, tail_val, tile_tail;
+    Reducer red;
+    std::vector<std::unique_ptr<Solver>> solvers; // solves without a preconditioner
+    int64_t device_bytes() const
+    {
+        return (int64_t)(ell_col.bytes + ell_val.bytes + tail_rows.bytes + tail_ptr.bytes +
+                         tail_col.bytes + tail_val.bytes + tile_tail.bytes + red.partials.bytes);
+    }
+    ~hec_matrix_s();
+};
+
+struct hec_precond_s {
+    uint64_t matrix_id = 0;
+    int n = 0, k = 0, nblocks = 0, overlap = 0;
+    bool host_only = false, scheduled = false;
+    std::vector<BlockFactor> blocks;
+    TrsvPack pack;
+    DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc, d_err;
+    int stage_bytes = 32768, nstages = 4;
+    std::vector<std::unique_ptr<Solver>> solvers;
+    int64_t device_bytes() const
+    {
+        return (int64_t)(d_pack.bytes + d_chunks.bytes + d_blocks.bytes + d_ysc.bytes +
+                         d_zsc.bytes + d_err.bytes);
+    }
+    ~hec_precond_s();
+};
+
+namespace {
+
+constexpr long long kDefaultSpin = 1ll << 24;
+constexpr int kMaxRing = 8192; // shared-memory ring slots (doubles)
+
+// ---------------------------------------------------------------- launch helpers
+SpmvArgs spmv_args(const hec_matrix_s *A)
+{
+    SpmvArgs a{};
+    a.n = A->hec.n;
+    a.ld = A->hec.ld;
+    a.K = A->hec.K;
+    a.ntiles = (A->hec.n + kSpmvTile - 1) / kSpmvTile;
+    a.ell_col = A->ell_col.as<int>();
+    a.ell_val = A->ell_val.as<double>();
+    a.tail_rows = A->tail_rows.as<int>();
+    a.tail_ptr = A->tail_ptr.as<int>();
+    a.tail_col = A->tail_col.as<int>();
+    a.tail_val = A->tail_val.as<double>();
+    a.tile_tail = A->tile_tail.as<int>();
+    a.alpha = 1.0;
+    a.beta = 0.0;
+    a.op = FIN_STORE;
+    return a;
+}
+
+int spmv_grid(const hec_matrix_s *A) { return grid_for((A->hec.n + kSpmvTile - 1) / kSpmvTile, 1, 8); }
+
+int run_spmv(const hec_matrix_s *A, SpmvArgs a, int mode, int ndot, cudaStream_t s)
+{
+    if (launch_spmv(a, mode, ndot, !A->hec.tail_rows.empty(), spmv_grid(A), s) != 0)
+        return fail(HEC_ERR_INVALID, "no SpMV variant for mode %d ndot %d", mode, ndot);
+    return check_launch("spmv");
+}
+
+int vec_grid(int64_t n) { return grid_for(n, kThreads, 8); }
+
+int run_vec(VecOp op, const VecArgs &a, cudaStream_t s)
+{
+    if (launch_vec(op, a, vec_grid(a.n), s) != 0)
+        return fail(HEC_ERR_INVALID, "bad vector op");
+    return check_launch("vector op");
+}
+
+TrsvArgs trsv_args(const hec_precond_s *M, long long spin)
+{
+    TrsvArgs a{};
+    a.nblocks = M->nblocks;
+    a.blocks = M->d_blocks.as<TrsvBlock>();
+    a.chunks = M->d_chunks.as<uint2>();
+    a.pack = M->d_pack.as<unsigned char>();
+    a.ysc = M->d_ysc.as<double>();
+    a.zsc = M->pack.zsz ? M->d_zsc.as<double>() : nullptr;
+    a.ring_mask = M->pack.ring_slots - 1;
+    a.stage_bytes = M->stage_bytes;
+    a.nstages = M->nstages;
+    a.spin_limit = spin;
+    a.err = M->d_err.as<int>();
+    return a;
+}
+
+int run_trsv(const TrsvArgs &a, cudaStream_t s)
+{
+    if (launch_trsv(a, s) != 0)
+        return fail(HEC_ERR_CUDA, "cannot configure the triangular-solve kernel");
+    return check_launch("trsv");
+}
+
+// Global reducer for the stand-alone vector calls (one per process).
+std::mutex g_red_mu;
+std::unique_ptr<Reducer> g_red;
+int global_reducer(cudaStream_t s, RedScratch &out)
+{
+    std::lock_guard<std::mutex> lk(g_red_mu);
+    if (!g_red) {
+        std::unique_ptr<Reducer> r(new Reducer());
+        HEC_TRY(r->init(s));
+        g_red = std::move(r);
+    }
+    out = g_red->r;
+    return HEC_OK;
+}
+
+} // namespace
+
+// ====================================================================== solver (graphs)
+struct Solver {
+    uint64_t matrix_id = 0;
+    int method = 0, restart = 0;
+    int n = 0;
+    int64_t ldv = 0;
+    DevBuf ws, st_buf;
+    Reducer red;
+    SolverState *st = nullptr;
+    double *b = nullptr, *x = nullptr, *r = nullptr, *r0 = nullptr, *p = nullptr, *ps = nullptr;
+    double *v = nullptr, *s = nullptr, *ss = nullptr, *t = nullptr;
+    double *V = nullptr, *z = nullptr, *w = nullptr, *u = nullptr, *zu = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle h_while = 0, h_if = 0;
+    int64_t init_launches = 0;
+    ~Solver()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (graph)
+            cudaGraphDestroy(graph);
+    }
+};
+
+hec_matrix_s::~hec_matrix_s() { solvers.clear(); }
+hec_precond_s::~hec_precond_s() { solvers.clear(); }
+
+namespace {
+
+// Address of a member of the device-resident solver state.
+template <class T>
+T *dev_field(SolverState *st, size_t off)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(st) + off);
+}
+
+// Capture helper: begin capturing launches into `g` after `deps`.
+int begin_capture(cudaStream_t cs, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps)
+{
+    HEC_CK(cudaStreamBeginCaptureToGraph(cs, g, deps, nullptr, ndeps,
+                                         cudaStreamCaptureModeRelaxed));
+    return HEC_OK;
+}
+
+// End the capture and return the node(s) the next node must follow.
+int end_capture(cudaStream_t cs, std::vector<cudaGraphNode_t> &tail)
+{
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    HEC_CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &nd));
+    tail.assign(deps, deps + nd);
+    cudaGraph_t g = nullptr;
+    HEC_CK(cudaStreamEndCapture(cs, &g));
+    return HEC_OK;
+}
+
+int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                    cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    cudaGraphNode_t &node, cudaGraph_t &body)
+{
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    HEC_CK(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                            &np));
+    body = np.conditional.phGraph_out[0];
+    return HEC_OK;
+}
+
+// --- launch sequences (used while capturing) --------------------------------
+
+int seq_precond(const hec_precond_s *M, Solver &S, const double *in, double *out, int from_j,
+                cudaStream_t cs)
+{
+    TrsvArgs a = trsv_args(M, kDefaultSpin);
+    a.r = in;
+    a.z = out;
+    a.st = S.st;
+    a.r_from_j = from_j;
+    a.ldv = S.ldv;
+    return run_trsv(a, cs);
+}
+
+int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    const int n = S.n;
+    HEC_CK(cudaGraphCreate(&S.graph, 0));
+    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> tail;
+    // init: ||b||; r = b - A x0, rho = (r, r); r0 = r; loop condition
+    HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
+    VecArgs va{};
+    va.n = n;
+    va.st = S.st;
+    va.red = S.red.r;
+    va.x = S.b;
+    va.op = FIN_NRM_B;
+    HEC_TRY(run_vec(V_NRM2SQ, va, cs));
+    SpmvArgs sa = spmv_args(A);
+    sa.st = S.st;
+    sa.red = S.red.r;
+    sa.x = S.x;
+    sa.alpha = -1.0;
+    sa.beta = 1.0;
+    sa.y_in = S.b;
+    sa.y_out = S.r;
+    sa.w0 = nullptr;
+    sa.op = FIN_BICG_INIT;
+    HEC_TRY(run_spmv(A, sa, 2, 1, cs));
+    VecArgs cp{};
+    cp.n = n;
+    cp.st = S.st;
+    cp.x = S.r;
+    cp.z = S.r0;
+    HEC_TRY(run_vec(V_COPY, cp, cs));
+    if (launch_loopcond(S.st, cs) != 0)
+        return fail(HEC_ERR_CUDA, "loopcond");
+    HEC_TRY(check_launch("loopcond"));
+    S.init_launches = 4;
+    HEC_TRY(end_capture(cs, tail));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
+
+    // body: one pass of Algorithm 4
+    HEC_TRY(begin_capture(cs, body, nullptr, 0));
+    {
+        VecArgs pa{};
+        pa.n = n;
+        pa.st = S.st;
+        pa.x = S.r;
+        pa.y = S.v;
+        pa.z = S.p;
+        HEC_TRY(run_vec(V_BICG_P, pa, cs)); // p = r + beta (p - omega v)
+        if (M)
+            HEC_TRY(seq_precond(M, S, S.p, S.ps, 0, cs)); // M p* = p
+        SpmvArgs v = spmv_args(A);
+        v.st = S.st;
+        v.red = S.red.r;
+        v.x = M ? S.ps : S.p;
+        v.y_out = S.v;
+        v.w0 = S.r0;
+        v.op = FIN_BICG_ALPHA;
+        HEC_TRY(run_spmv(A, v, 0, 1, cs)); // v = A p*, (r0, v) -> alpha
+        VecArgs sv{};
+        sv.n = n;
+        sv.st = S.st;
+        sv.red = S.red.r;
+        sv.x = S.r;
+        sv.y = S.v;
+        sv.z = S.s;
+        sv.op = FIN_BICG_S;
+        HEC_TRY(run_vec(V_BICG_S, sv, cs)); // s = r - alpha v, ||s||
+        if (M)
+            HEC_TRY(seq_precond(M, S, S.s, S.ss, 0, cs)); // M s* = s
+        SpmvArgs t = spmv_args(A);
+        t.st = S.st;
+        t.red = S.red.r;
+        t.x = M ? S.ss : S.s;
+        t.y_out = S.t;
+        t.w0 = S.s;
+        t.w1 = nullptr;
+        t.op = FIN_BICG_OMEGA;
+        HEC_TRY(run_spmv(A, t, 0, 2, cs)); // t = A s*, (t, s), (t, t) -> omega
+        VecArgs xr{};
+        xr.n = n;
+        xr.st = S.st;
+        xr.red = S.red.r;
+        xr.w = S.x;
+        xr.u = M ? S.ps : S.p;
+        xr.v = M ? S.ss : S.s;
+        xr.q = S.t;
+        xr.x = S.s;
+        xr.y = S.r0;
+        xr.z = S.r;
+        xr.op = FIN_BICG_XR;
+        HEC_TRY(run_vec(V_BICG_XR, xr, cs)); // x, r updates; tests; loop condition
+    }
+    HEC_TRY(end_capture(cs, tail));
+
+    // exit: x = 0 if b = 0; true residual
+    HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
+    VecArgs zx{};
+    zx.n = n;
+    zx.st = S.st;
+    zx.z = S.x;
+    HEC_TRY(run_vec(V_ZERO_IF_ST, zx, cs));
+    SpmvArgs fr = spmv_args(A);
+    fr.st = S.st;
+    fr.red = S.red.r;
+    fr.x = S.x;
+    fr.alpha = -1.0;
+    fr.beta = 1.0;
+    fr.y_in = S.b;
+    fr.y_out = S.r;
+    fr.op = FIN_TRUE_RESID;
+    HEC_TRY(run_spmv(A, fr, 2, 1, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
+    return HEC_OK;
+}
+
+// cycle start: r = b - A x, beta, v_1 = r / beta
+int seq_gmres_cycle(hec_matrix_s *A, Solver &S, cudaStream_t cs)
+{
+    SpmvArgs sa = spmv_args(A);
+    sa.st = S.st;
+    sa.red = S.red.r;
+    sa.x = S.x;
+    sa.alpha = -1.0;
+    sa.beta = 1.0;
+    sa.y_in = S.b;
+    sa.y_out = S.r;
+    sa.op = FIN_GMRES_CYCLE;
+    HEC_TRY(run_spmv(A, sa, 2, 1, cs));
+    VecArgs sc{};
+    sc.n = S.n;
+    sc.st = S.st;
+    sc.x = S.r;
+    sc.z = S.V; // column 0
+    sc.guard = 2;
+    HEC_TRY(run_vec(V_SCALE_ST, sc, cs));
+    return HEC_OK;
+}
+
+int build_gmres(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    const int n = S.n, m = S.restart;
+    HEC_CK(cudaGraphCreate(&S.graph, 0));
+    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> tail;
+    HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
+    VecArgs va{};
+    va.n = n;
+    va.st = S.st;
+    va.red = S.red.r;
+    va.x = S.b;
+    va.op = FIN_NRM_B;
+    HEC_TRY(run_vec(V_NRM2SQ, va, cs));
+    HEC_TRY(seq_gmres_cycle(A, S, cs));
+    if (launch_loopcond(S.st, cs) != 0)
+        return fail(HEC_ERR_CUDA, "loopcond");
+    HEC_TRY(check_launch("loopcond"));
+    HEC_TRY(end_capture(cs, tail));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
+    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_if, body, 0, cudaGraphCondAssignDefault));
+
+    // body: one Arnoldi step with CGS2
+    HEC_TRY(begin_capture(cs, body, nullptr, 0));
+    {
+        if (M) {
+            HEC_TRY(seq_precond(M, S, S.V, S.z, 1, cs)); // z = M^{-1} v_j
+        } else {
+            VecArgs c{};
+            c.n = n;
+            c.st = S.st;
+            c.x = S.V;
+            c.x_from_j = 1;
+            c.ldv = S.ldv;
+            c.z = S.z;
+            HEC_TRY(run_vec(V_COPY, c, cs));
+        }
+        SpmvArgs w = spmv_args(A);
+        w.st = S.st;
+        w.red = S.red.r;
+        w.x = S.z;
+        w.y_out = S.w;
+        w.op = FIN_GMRES_W0;
+        HEC_TRY(run_spmv(A, w, 0, 1, cs)); // w = A z, ||w||
+        const int mdgrid = grid_for(n, kThreads, 2);
+        BasisArgs h{};
+        h.n = n;
+        h.k = m + 1;
+        h.k_from_st = 1;
+        h.V = S.V;
+        h.ldv = S.ldv;
+        h.w = S.w;
+        h.red = S.red.r;
+        h.st = S.st;
+        h.op = FIN_GMRES_H1;
+        launch_multidot(h, mdgrid, cs); // h1 = V^T w
+        HEC_TRY(check_launch("multidot"));
+        BasisArgs up = h;
+        up.coef = dev_field<double>(S.st, offsetof(SolverState, h1));
+        up.wout = S.w;
+        launch_basis_update(up, false, vec_grid(n), cs); // w -= V h1
+        HEC_TRY(check_launch("basis update"));
+        BasisArgs h2 = h;
+        h2.op = FIN_GMRES_H2;
+        launch_multidot(h2, mdgrid, cs); // h2 = V^T w
+        HEC_TRY(check_launch("multidot"));
+        BasisArgs up2 = h;
+        up2.coef = dev_field<double>(S.st, offsetof(SolverState, h2));
+        up2.wout = S.w;
+        up2.op = FIN_GMRES_STEP;
+        launch_basis_update(up2, true, vec_grid(n), cs); // w -= V h2, ||w||, Givens
+        HEC_TRY(check_launch("basis update"));
+        VecArgs sc{};
+        sc.n = n;
+        sc.st = S.st;
+        sc.x = S.w;
+        sc.z = S.V;
+        sc.z_from_j = 1; // j already advanced when the cycle goes on
+        sc.ldv = S.ldv;
+        sc.guard = 1;
+        HEC_TRY(run_vec(V_SCALE_ST, sc, cs)); // v_{j+1} = w / h_{j+1,j}
+    }
+    HEC_TRY(end_capture(cs, tail));
+    cudaGraphNode_t ifnode;
+    cudaGraph_t ifbody;
+    HEC_TRY(add_conditional(body, tail, S.h_if, cudaGraphCondTypeIf, ifnode, ifbody));
+    // cycle end: y = R^{-1} g; x += M^{-1} V y; next cycle start
+    HEC_TRY(begin_capture(cs, ifbody, nullptr, 0));
+    {
+        if (launch_gmres_lsq(S.st, cs) != 0)
+            return fail(HEC_ERR_CUDA, "lsq");
+        HEC_TRY(check_launch("lsq"));
+        BasisArgs cb{};
+        cb.n = n;
+        cb.k = m;
+        cb.k_from_st = 2;
+        cb.V = S.V;
+        cb.ldv = S.ldv;
+        cb.coef = dev_field<double>(S.st, offsetof(SolverState, y));
+        cb.wout = S.u;
+        cb.st = S.st;
+        launch_basis_combine(cb, vec_grid(n), cs); // u = V y
+        HEC_TRY(check_launch("basis combine"));
+        if (M)
+            HEC_TRY(seq_precond(M, S, S.u, S.zu, 0, cs)); // zu = M^{-1} u
+        VecArgs ax{};
+        ax.n = n;
+        ax.st = S.st;
+        ax.x = M ? S.zu : S.u;
+        ax.z = S.x;
+        HEC_TRY(run_vec(V_AXPY_ST1, ax, cs)); // x += zu
+        HEC_TRY(seq_gmres_cycle(A, S, cs));
+    }
+    HEC_TRY(end_capture(cs, tail));
+    HEC_TRY(begin_capture(cs, body, &ifnode, 1));
+    if (launch_loopcond(S.st, cs) != 0)
+        return fail(HEC_ERR_CUDA, "loopcond");
+    HEC_TRY(check_launch("loopcond"));
+    HEC_TRY(end_capture(cs, tail));
+
+    HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
+    VecArgs zx{};
+    zx.n = n;
+    zx.st = S.st;
+    zx.z = S.x;
+    HEC_TRY(run_vec(V_ZERO_IF_ST, zx, cs));
+    SpmvArgs fr = spmv_args(A);
+    fr.st = S.st;
+    fr.red = S.red.r;
+    fr.x = S.x;
+    fr.alpha = -1.0;
+    fr.beta = 1.0;
+    fr.y_in = S.b;
+    fr.y_out = S.r;
+    fr.op = FIN_TRUE_RESID;
+    HEC_TRY(run_spmv(A, fr, 2, 1, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
+    return HEC_OK;
+}
+
+int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cudaStream_t s,
+                Solver *&out)
+{
+    auto &cache = M ? M->solvers : A->solvers;
+    for (auto &p : cache)
+        if (p->matrix_id == A->id && p->method == method &&
+            (method == HEC_BICGSTAB || p->restart == restart)) {
+            out = p.get();
+            return HEC_OK;
+        }
+    std::unique_ptr<Solver> S(new Solver());
+    S->matrix_id = A->id;
+    S->method = method;
+    S->restart = restart;
+    S->n = A->hec.n;
+    S->ldv = ((int64_t)S->n + 31) / 32 * 32;
+    const int64_t nv = S->ldv;
+    const int nvec = method == HEC_BICGSTAB ? 10 : (restart + 1) + 7;
+    HEC_TRY(S->ws.alloc((size_t)nvec * nv * sizeof(double), s));
+    HEC_CK(cudaMemsetAsync(S->ws.p, 0, S->ws.bytes, s));
+    HEC_TRY(S->st_buf.alloc(sizeof(SolverState), s));
+    HEC_CK(cudaMemsetAsync(S->st_buf.p, 0, sizeof(SolverState), s));
+    HEC_TRY(S->red.init(s));
+    S->st = S->st_buf.as<SolverState>();
+    double *base = S->ws.as<double>();
+    auto vec = [&](int i) { return base + (int64_t)i * nv; };
+    if (method == HEC_BICGSTAB) {
+        S->b = vec(0);
+        S->x = vec(1);
+        S->r = vec(2);
+        S->r0 = vec(3);
+        S->p = vec(4);
+        S->ps = vec(5);
+        S->v = vec(6);
+        S->s = vec(7);
+        S->ss = vec(8);
+        S->t = vec(9);
+    } else {
+        S->b = vec(0);
+        S->x = vec(1);
+        S->r = vec(2);
+        S->z = vec(3);
+        S->w = vec(4);
+        S->u = vec(5);
+        S->zu = vec(6);
+        S->V = vec(7);
+    }
+    HEC_CK(cudaStreamSynchronize(s));
+    cudaStream_t cs;
+    HEC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = method == HEC_BICGSTAB ? build_bicgstab(A, M, *S, cs) : build_gmres(A, M, *S, cs);
+    cudaStreamDestroy(cs);
+    if (rc != HEC_OK)
+        return rc;
+    out = S.get();
+    cache.push_back(std::move(S));
+    return HEC_OK;
+}
+
+int upload_matrix(hec_matrix_s *A, cudaStream_t s)
+{
+    const HecHost &H = A->hec;
+    HEC_TRY(upload(A->ell_col, H.ell_col, s));
+    HEC_TRY(upload(A->ell_val, H.ell_val, s));
+    HEC_TRY(upload(A->tail_rows, H.tail_rows, s));
+    HEC_TRY(upload(A->tail_ptr, H.tail_ptr, s));
+    HEC_TRY(upload(A->tail_col, H.tail_col, s));
+    HEC_TRY(upload(A->tail_val, H.tail_val, s));
+    HEC_TRY(upload(A->tile_tail, H.tile_tail, s));
+    HEC_TRY(A->red.init(s));
+    HEC_CK(cudaStreamSynchronize(s));
+    return HEC_OK;
+}
+
+} // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *hec_status_string(int status)
+{
+    switch (status) {
+    case HEC_OK: return "ok";
+    case HEC_ERR_INVALID: return "invalid argument";
+    case HEC_ERR_OOM: return "out of device memory";
+    case HEC_ERR_ZERO_PIVOT: return "zero pivot in ILU(k)";
+    case HEC_ERR_UNSORTED_CSR: return "CSR columns not strictly ascending or out of range";
+    case HEC_ERR_CUDA: return "CUDA error";
+    case HEC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case HEC_MAXIT: return "iteration limit reached";
+    case HEC_BREAKDOWN: return "solver breakdown";
+    default: return "unknown status";
+    }
+}
+
+const char *hec_last_error(void) { return g_last_error.c_str(); }
+
+int hec_set_allocator(void *(*alloc_fn)(size_t, void *, void *), void (*free_fn)(void *, void *, void *),
+                      void *ctx)
+{
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return fail(HEC_ERR_INVALID, "allocator needs both functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc_fn;
+    g_alloc.free_ = free_fn;
+    g_alloc.ctx = ctx;
+    return HEC_OK;
+}
+
+int hec_build(const hec_csr_t *Ain, const hec_opts_t *opts, void *stream, hec_matrix_t *out)
+{
+    if (!Ain || !out)
+        return fail(HEC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    hec_opts_t o{};
+    if (opts)
+        o = *opts;
+    const int align = o.ell_ld_align ? o.ell_ld_align : 256;
+    if (align < 32 || align % 32 != 0)
+        return fail(HEC_ERR_INVALID, "ell_ld_align must be a positive multiple of 32");
+    if (o.ell_width < 0)
+        return fail(HEC_ERR_INVALID, "ell_width must be >= 0");
+    const int n = Ain->n, nnz = Ain->nnz;
+    if (n < 1 || nnz < 0)
+        return fail(HEC_ERR_INVALID, "bad sizes n=%d nnz=%d", n, nnz);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<hec_matrix_s> A(new hec_matrix_s());
+    A->id = g_next_id++;
+    A->host_only = (o.flags & HEC_HOST_ONLY) != 0;
+    HostCSR &C = A->csr;
+    C.n = n;
+    C.rp.resize(n + 1);
+    C.ci.resize(nnz);
+    C.va.resize(nnz);
+    if (Ain->on_device) {
+        HEC_CK(cudaMemcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+        if (nnz) {
+            HEC_CK(cudaMemcpy(C.ci.data(), Ain->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+            HEC_CK(cudaMemcpy(C.va.data(), Ain->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+        }
+    } else {
+        if (!Ain->row_ptr || (nnz && (!Ain->col || !Ain->val)))
+            return fail(HEC_ERR_INVALID, "null CSR array");
+        std::memcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1));
+        if (nnz) {
+            std::memcpy(C.ci.data(), Ain->col, sizeof(int) * nnz);
+            std::memcpy(C.va.data(), Ain->val, sizeof(double) * nnz);
+        }
+    }
+    std::string msg;
+    int rc = check_csr(n, C.rp.data(), C.ci.data(), nnz, false, msg);
+    if (rc != HEC_OK)
+        return fail(rc, "%s", msg.c_str());
+    const int K = o.ell_width ? o.ell_width : ell_width_auto(C);
+    build_hec(C, K, align, A->hec);
+    if (!A->host_only)
+        HEC_TRY(upload_matrix(A.get(), s));
+    *out = A.release();
+    return HEC_OK;
+}
+
+int hec_matrix_info(hec_matrix_t A, hec_matrix_info_t *info)
+{
+    if (!A || !info)
+        return fail(HEC_ERR_INVALID, "null argument");
+    info->n = A->hec.n;
+    info->nnz = (int32_t)A->csr.ci.size();
+    info->ell_width = A->hec.K;
+    info->ell_ld = A->hec.ld;
+    info->tail_rows = (int32_t)A->hec.tail_rows.size();
+    info->tail_nnz = (int32_t)A->hec.tail_col.size();
+    info->device_bytes = A->device_bytes();
+    return HEC_OK;
+}
+
+int hec_matrix_export(hec_matrix_t A, int32_t *ell_col, double *ell_val, int32_t *tail_rows,
+                      int32_t *tail_ptr, int32_t *tail_col, double *tail_val)
+{
+    if (!A)
+        return fail(HEC_ERR_INVALID, "null matrix");
+    const HecHost &H = A->hec;
+    auto cp = [](void *dst, const void *src, size_t bytes) {
+        if (dst && bytes)
+            std::memcpy(dst, src, bytes);
+    };
+    cp(ell_col, H.ell_col.data(), H.ell_col.size() * sizeof(int));
+    cp(ell_val, H.ell_val.data(), H.ell_val.size() * sizeof(double));
+    cp(tail_rows, H.tail_rows.data(), H.tail_rows.size() * sizeof(int));
+    cp(tail_ptr, H.tail_ptr.data(), H.tail_ptr.size() * sizeof(int));
+    cp(tail_col, H.tail_col.data(), H.tail_col.size() * sizeof(int));
+    cp(tail_val, H.tail_val.data(), H.tail_val.size() * sizeof(double));
+    return HEC_OK;
+}
+
+void hec_matrix_destroy(hec_matrix_t A) { delete A; }
+
+int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const double *y_in,
+             double *y_out, const double *w, double *dots, void *stream)
+{
+    if (!A || !x || !y_out)
+        return fail(HEC_ERR_INVALID, "null argument");
+    if (A->host_only)
+        return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
+    if (beta != 0.0 && !y_in)
+        return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
+    if (x == y_out)
+        return fail(HEC_ERR_INVALID, "x and y_out must not alias");
+    SpmvArgs a = spmv_args(A);
+    a.x = x;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.y_in = y_in;
+    a.y_out = y_out;
+    a.red = A->red.r;
+    a.w0 = w;
+    a.w1 = nullptr;
+    a.result = dots;
+    a.op = FIN_STORE;
+    const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
+    return run_spmv(A, a, mode, dots ? 2 : 0, (cudaStream_t)stream);
+}
+
+int hec_axpby(int32_t n, double a, const double *x, double b, double *y, void *stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y)))
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (n == 0)
+        return HEC_OK;
+    VecArgs v{};
+    v.n = n;
+    v.a = a;
+    v.b = b;
+    v.x = x;
+    v.z = y;
+    return run_vec(V_AXPBY, v, (cudaStream_t)stream);
+}
+
+int hec_waxpby(int32_t n, double a, const double *x, double b, const double *y, double *z,
+               void *stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y || !z)))
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (n == 0)
+        return HEC_OK;
+    VecArgs v{};
+    v.n = n;
+    v.a = a;
+    v.b = b;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    return run_vec(V_WAXPBY, v, (cudaStream_t)stream);
+}
+
+int hec_dot(int32_t n, const double *x, const double *y, double *result, void *stream)
+{
+    if (n < 0 || !result || (n > 0 && (!x || !y)))
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
+        return HEC_OK;
+    }
+    VecArgs v{};
+    v.n = n;
+    v.x = x;
+    v.y = y;
+    v.result = result;
+    v.op = FIN_STORE;
+    HEC_TRY(global_reducer(s, v.red));
+    return run_vec(V_DOT, v, s);
+}
+
+int hec_nrm2(int32_t n, const double *x, double *result, void *stream)
+{
+    if (n < 0 || !result || (n > 0 && !x))
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
+        return HEC_OK;
+    }
+    VecArgs v{};
+    v.n = n;
+    v.x = x;
+    v.result = result;
+    v.op = FIN_STORE;
+    HEC_TRY(global_reducer(s, v.red));
+    v.op = FIN_STORE_SQRT;
+    return run_vec(V_NRM2SQ, v, s);
+}
+
+int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const double *w, double *h,
+                 void *stream)
+{
+    if (n < 1 || k < 1 || k > kMaxRestart + 1 || ldv < n || !V || !w || !h)
+        return fail(HEC_ERR_INVALID, "bad arguments (k must be in 1..%d)", kMaxRestart + 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    BasisArgs a{};
+    a.n = n;
+    a.k = k;
+    a.V = V;
+    a.ldv = ldv;
+    a.w = w;
+    a.result = h;
+    a.op = FIN_STORE;
+    HEC_TRY(global_reducer(s, a.red));
+    launch_multidot(a, grid_for(n, kThreads, 2), s);
+    return check_launch("multidot");
+}
+
+int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
+                hec_precond_t *out)
+{
+    (void)stream;
+    if (!A || !out)
+        return fail(HEC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const int n = A->hec.n;
+    if (k < 0 || overlap < 0 || nblocks < 1 || nblocks > n)
+        return fail(HEC_ERR_INVALID, "need k >= 0, overlap >= 0, 1 <= nblocks <= n");
+    std::string msg;
+    int rc = check_csr(n, A->csr.rp.data(), A->csr.ci.data(), (int)A->csr.ci.size(), true, msg);
+    if (rc != HEC_OK)
+        return fail(rc, "%s", msg.c_str());
+    std::unique_ptr<hec_precond_s> M(new hec_precond_s());
+    M->matrix_id = A->id;
+    M->n = n;
+    M->k = k;
+    M->nblocks = nblocks;
+    M->overlap = overlap;
+    M->host_only = A->host_only;
+    ras_blocks(A->csr, nblocks, overlap, M->blocks);
+    std::vector<int> rcs(nblocks, HEC_OK);
+    std::vector<std::string> msgs(nblocks);
+    parallel_for(nblocks, [&](int b) { rcs[b] = iluk_block(M->blocks[b], k, msgs[b]); });
+    for (int b = 0; b < nblocks; ++b)
+        if (rcs[b] != HEC_OK)
+            return fail(rcs[b], "block %d: %s", b, msgs[b].c_str());
+    *out = M.release();
+    return HEC_OK;
+}
+
+int level_schedule(hec_precond_t M, void *stream)
+{
+    if (!M)
+        return fail(HEC_ERR_INVALID, "null preconditioner");
+    if (M->scheduled)
+        return HEC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    parallel_for(M->nblocks, [&](int b) { levels_block(M->blocks[b]); });
+    std::string msg;
+    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, M->pack, msg);
+    if (rc != HEC_OK)
+        return fail(rc, "%s", msg.c_str());
+    if (!M->host_only) {
+        HEC_TRY(upload(M->d_pack, M->pack.pack, s));
+        HEC_TRY(upload(M->d_chunks, M->pack.chunks, s));
+        HEC_TRY(upload(M->d_blocks, M->pack.blocks, s));
+        HEC_TRY(M->d_ysc.alloc(std::max<int64_t>(M->pack.ysz, 1) * sizeof(double), s));
+        HEC_TRY(M->d_zsc.alloc(std::max<int64_t>(M->pack.zsz, 1) * sizeof(double), s));
+        HEC_TRY(M->d_err.alloc(sizeof(int), s));
+        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+        HEC_CK(cudaStreamSynchronize(s));
+        M->pack.pack.clear();
+        M->pack.pack.shrink_to_fit();
+    }
+    M->scheduled = true;
+    return HEC_OK;
+}
+
+int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
+{
+    if (!M || !info)
+        return fail(HEC_ERR_INVALID, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->nblocks = M->nblocks;
+    info->overlap = M->overlap;
+    info->k = M->k;
+    info->scheduled = M->scheduled ? 1 : 0;
+    for (const BlockFactor &B : M->blocks) {
+        info->rows_total += B.F.n;
+        info->factor_nnz += (int64_t)B.F.ci.size();
+        info->max_levels_L = std::max(info->max_levels_L, B.nlevL);
+        info->max_levels_U = std::max(info->max_levels_U, B.nlevU);
+    }
+    info->apply_bytes = M->scheduled ? M->pack.alg_bytes : 0;
+    info->device_bytes = M->device_bytes();
+    info->ring_slots = M->scheduled ? M->pack.ring_slots : 0;
+    for (const TrsvBlock &T : M->pack.blocks)
+        info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
+    return HEC_OK;
+}
+
+int hec_precond_get_block(hec_precond_t M, int32_t b, int32_t *nv, int32_t *own_lo,
+                          int32_t *own_hi, int32_t *rows)
+{
+    if (!M || b < 0 || b >= M->nblocks)
+        return fail(HEC_ERR_INVALID, "bad block");
+    const BlockFactor &B = M->blocks[b];
+    if (nv)
+        *nv = (int32_t)B.rows.size();
+    if (own_lo)
+        *own_lo = B.own_lo;
+    if (own_hi)
+        *own_hi = B.own_hi;
+    if (rows)
+        std::memcpy(rows, B.rows.data(), B.rows.size() * sizeof(int));
+    return HEC_OK;
+}
+
+int hec_precond_get_factor(hec_precond_t M, int32_t b, int32_t *nnz, int32_t *row_ptr,
+                           int32_t *col, double *val, int32_t *lev)
+{
+    if (!M || b < 0 || b >= M->nblocks || !nnz)
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    const BlockFactor &B = M->blocks[b];
+    *nnz = (int32_t)B.F.ci.size();
+    if (row_ptr)
+        std::memcpy(row_ptr, B.F.rp.data(), B.F.rp.size() * sizeof(int));
+    if (col)
+        std::memcpy(col, B.F.ci.data(), B.F.ci.size() * sizeof(int));
+    if (val)
+        std::memcpy(val, B.F.va.data(), B.F.va.size() * sizeof(double));
+    if (lev)
+        std::memcpy(lev, B.lev.data(), B.lev.size() * sizeof(int));
+    return HEC_OK;
+}
+
+int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *nlev,
+                           int32_t *level_ptr, int32_t *level_rows)
+{
+    if (!M || b < 0 || b >= M->nblocks || (which != HEC_FACTOR_L && which != HEC_FACTOR_U))
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (!M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    const BlockFactor &B = M->blocks[b];
+    const bool u = which == HEC_FACTOR_U;
+    if (nlev)
+        *nlev = u ? B.nlevU : B.nlevL;
+    const std::vector<int> &p = u ? B.lptrU : B.lptrL;
+    const std::vector<int> &r = u ? B.lrowsU : B.lrowsL;
+    if (level_ptr)
+        std::memcpy(level_ptr, p.data(), p.size() * sizeof(int));
+    if (level_rows)
+        std::memcpy(level_rows, r.data(), r.size() * sizeof(int));
+    return HEC_OK;
+}
+
+int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit, void *stream)
+{
+    if (!M || !r || !z || r == z)
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (M->host_only)
+        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+    if (!M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    TrsvArgs a = trsv_args(M, spin_limit ? spin_limit : kDefaultSpin);
+    a.r = r;
+    a.z = z;
+    return run_trsv(a, (cudaStream_t)stream);
+}
+
+int hec_precond_status(hec_precond_t M, void *stream)
+{
+    if (!M || M->host_only || !M->scheduled)
+        return fail(HEC_ERR_INVALID, "bad preconditioner");
+    cudaStream_t s = (cudaStream_t)stream;
+    int err = 0;
+    HEC_CK(cudaMemcpyAsync(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CK(cudaStreamSynchronize(s));
+    if (err) {
+        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+        HEC_CK(cudaStreamSynchronize(s));
+        return fail(err, "a bounded device wait ran out");
+    }
+    return HEC_OK;
+}
+
+void hec_precond_destroy(hec_precond_t M) { delete M; }
+
+int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, double tol,
+                 int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
+                 hec_solve_info_t *info)
+{
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    if (!A || !b || !x)
+        return fail(HEC_ERR_INVALID, "null argument");
+    if (A->host_only || (M && M->host_only))
+        return fail(HEC_ERR_INVALID, "host-only handle");
+    if (M && (M->matrix_id != A->id))
+        return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
+    if (M && !M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    hec_solve_opts_t o{};
+    if (opts)
+        o = *opts;
+    if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB)
+        return fail(HEC_ERR_INVALID, "unknown method");
+    if (!(tol >= 0.0) || maxit < 0)
+        return fail(HEC_ERR_INVALID, "tol >= 0 and maxit >= 0 required");
+    if (o.method == HEC_GMRES && (restart < 1 || restart > kMaxRestart))
+        return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
+    if (o.method == HEC_BICGSTAB)
+        restart = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver *S = nullptr;
+    HEC_TRY(make_solver(A, M, o.method, restart, s, S));
+    const int n = S->n;
+    const size_t vb = sizeof(double) * (size_t)n;
+    // state header
+    std::unique_ptr<SolverState> hp(new SolverState());
+    SolverState &h = *hp;
+    std::memset(&h, 0, offsetof(SolverState, H));
+    h.tol = tol;
+    h.maxit = maxit;
+    h.restart = restart;
+    h.method = o.method;
+    h.flags = o.flags;
+    h.h_while = S->h_while;
+    h.h_if = S->h_if;
+    HEC_CK(cudaMemcpyAsync(S->st, &h, offsetof(SolverState, H), cudaMemcpyHostToDevice, s));
+    int64_t h2d = 0, d2h = 0;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    HEC_CK(cudaMemcpyAsync(S->b, b, vb, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (!bdev)
+        h2d += vb;
+    if (o.flags & HEC_X0_ZERO) {
+        HEC_CK(cudaMemsetAsync(S->x, 0, vb, s));
+    } else {
+        HEC_CK(cudaMemcpyAsync(S->x, x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (!xdev)
+            h2d += vb;
+    }
+    HEC_CK(cudaGraphLaunch(S->exec, s));
+    HEC_CK(cudaMemcpyAsync(x, S->x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!xdev)
+        d2h += vb;
+    HEC_CK(cudaMemcpyAsync(&h, S->st, offsetof(SolverState, H), cudaMemcpyDeviceToHost, s));
+    HEC_CK(cudaStreamSynchronize(s));
+    int status = h.err ? h.err : h.status;
+    if (info) {
+        info->iters = h.iters;
+        info->restarts = h.restarts;
+        info->status = status;
+        info->rel_resid = h.rel_resid;
+        info->est_resid = h.est;
+        info->kernel_launches = (int64_t)h.launches;
+        info->h2d_bytes = h2d;
+        info->d2h_bytes = d2h;
+    }
+    if (h.err)
+        return fail(h.err, "a bounded device wait ran out during the solve");
+    return status;
+}
+
+} // extern "C"

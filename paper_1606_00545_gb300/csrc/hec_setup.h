@@ -1,0 +1,74 @@
+// hec_setup.h -- host-side setup of the library: HEC conversion, RAS
+// partition, ILU(k) factorisation, level schedule, and the level-major chunk
+// layout that the triangular-solve kernel streams.  Host C++ only.
+#pragma once
+
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace hec {
+
+struct HostCSR {
+    int n = 0;
+    std::vector<int> rp, ci;
+    std::vector<double> va;
+};
+
+// Returns HEC_OK, HEC_ERR_INVALID or HEC_ERR_UNSORTED_CSR (msg filled).
+int check_csr(int n, const int *rp, const int *ci, int nnz, bool need_diag, std::string &msg);
+
+// --------------------------------------------------------------- HEC (Section 2.1)
+struct HecHost {
+    int n = 0, K = 0, ld = 0;
+    std::vector<int> ell_col;      // K * ld, column-major
+    std::vector<double> ell_val;   // K * ld
+    std::vector<int> tail_rows;    // rows with more than K entries, ascending
+    std::vector<int> tail_ptr;     // tail_rows.size() + 1
+    std::vector<int> tail_col;
+    std::vector<double> tail_val;
+    std::vector<int> tile_tail;    // per SpMV tile: first tail row index (ntiles + 1)
+};
+int ell_width_auto(const HostCSR &A);
+void build_hec(const HostCSR &A, int K, int align, HecHost &H);
+
+// --------------------------------------------------------------- RAS + ILU(k)
+struct BlockFactor {
+    int own_lo = 0, own_hi = 0;  // owned global rows [own_lo, own_hi)
+    std::vector<int> rows;       // V_b, ascending global ids
+    HostCSR F;                   // A_b, then its ILU(k) factor (local indices)
+    std::vector<int> lev;        // fill level of every factor entry
+    std::vector<int> diag;       // position of the diagonal of every row in F
+    // Eq. 11 on the full factor
+    int nlevL = 0, nlevU = 0;
+    std::vector<int> levL, levU;            // level of each local row (1-based)
+    std::vector<int> lptrL, lrowsL, lptrU, lrowsU;
+};
+
+// Sequence partition + overlap growth + extraction of A[V_b, V_b].
+void ras_blocks(const HostCSR &A, int nblocks, int overlap, std::vector<BlockFactor> &out);
+// In place: B.F becomes the ILU(k) factor.  HEC_OK / HEC_ERR_ZERO_PIVOT / HEC_ERR_INVALID.
+int iluk_block(BlockFactor &B, int k, std::string &msg);
+// Level sets of L_b and U_b (Eq. 11).
+void levels_block(BlockFactor &B);
+
+// --------------------------------------------------------------- device layout
+struct TrsvPack {
+    std::vector<unsigned char> pack;
+    std::vector<uint2> chunks;
+    std::vector<TrsvBlock> blocks;
+    int64_t ysz = 0, zsz = 0;   // scratch lengths (doubles)
+    int ring_slots = 0;         // power of two (>= 32)
+    int64_t alg_bytes = 0;      // algorithmic bytes of one apply
+    int64_t rows_L = 0, rows_U = 0;
+};
+int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring,
+              TrsvPack &out, std::string &msg);
+
+// Run f(i) for i in [0, count) on the host's cores.
+void parallel_for(int count, const std::function<void(int)> &f);
+
+} // namespace hec

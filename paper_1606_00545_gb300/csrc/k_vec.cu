@@ -1,0 +1,312 @@
+// k_vec.cu -- vector operations (Section 2.3, Eqs. 3-6) and the fused vector
+// updates of the Krylov loops (Algorithm 4 and GMRES), each with its dot
+// products reduced in the same launch.
+#include "reduce.cuh"
+
+namespace hec {
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) k_vec(VecArgs a)
+{
+    count_launch(a.st);
+    SolverState *st = a.st;
+    constexpr int ND = (OP == V_DOT || OP == V_NRM2SQ || OP == V_BICG_S) ? 1
+                       : (OP == V_BICG_XR)                                 ? 2
+                                                                           : 0;
+    if (OP == V_BICG_S && st->skip)
+        return;
+    if (OP == V_ZERO_IF_ST && !st->zero_x)
+        return;
+    if ((a.guard == 1 && st->cycle_end) || (a.guard == 2 && st->done))
+        return;
+    const double *x = a.x;
+    double *z = a.z;
+    if (a.x_from_j)
+        x += (int64_t)st->j * a.ldv;
+    if (a.z_from_j)
+        z += (int64_t)st->j * a.ldv;
+    double acc[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
+        acc[d] = 0.0;
+
+    // per-launch scalars
+    double c0 = a.a, c1 = a.b;
+    int mode = 0;
+    if (OP == V_SCALE_ST)
+        c0 = st->scale;
+    if (OP == V_BICG_P) {
+        if (st->iters == 0) {
+            mode = 1; // first pass: p = r
+        } else {
+            c0 = (st->rho / st->rho_prev) * (st->alpha / st->omega); // beta
+            c1 = st->omega;
+        }
+    }
+    if (OP == V_BICG_S)
+        c0 = st->alpha;
+    if (OP == V_BICG_XR) {
+        c0 = st->alpha;
+        c1 = st->omega;
+        mode = st->s_conv ? 1 : (st->skip ? 2 : 0);
+    }
+
+    const int stride = gridDim.x * kThreads;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
+        if (OP == V_AXPBY) {
+            z[i] = c0 * x[i] + c1 * z[i];
+        } else if (OP == V_WAXPBY) {
+            z[i] = c0 * x[i] + c1 * a.y[i];
+        } else if (OP == V_DOT) {
+            acc[0] = fma(x[i], a.y[i], acc[0]);
+        } else if (OP == V_NRM2SQ) {
+            double t = x[i];
+            acc[0] = fma(t, t, acc[0]);
+        } else if (OP == V_COPY) {
+            z[i] = x[i];
+        } else if (OP == V_SCALE_ST) {
+            z[i] = c0 * x[i];
+        } else if (OP == V_BICG_P) {
+            // x = r, y = v, z = p
+            z[i] = mode ? x[i] : fma(c0, z[i] - c1 * a.y[i], x[i]);
+        } else if (OP == V_BICG_S) {
+            // x = r, y = v, z = s
+            double s = fma(-c0, a.y[i], x[i]);
+            z[i] = s;
+            acc[0] = fma(s, s, acc[0]);
+        } else if (OP == V_BICG_XR) {
+            // w = x (solution), u = p*, v = s*, q = t, x = s, y = r0, z = r
+            if (mode == 0) {
+                a.w[i] = fma(c1, a.v[i], fma(c0, a.u[i], a.w[i]));
+                double r = fma(-c1, a.q[i], x[i]);
+                z[i] = r;
+                acc[0] = fma(r, r, acc[0]);
+                acc[1] = fma(a.y[i], r, acc[1]);
+            } else if (mode == 1) {
+                a.w[i] = fma(c0, a.u[i], a.w[i]);
+            }
+        } else if (OP == V_AXPY_ST1) {
+            z[i] += x[i];
+        } else if (OP == V_ZERO_IF_ST) {
+            z[i] = 0.0;
+        }
+    }
+    if constexpr (ND > 0) {
+        double v[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+            v[d] = acc[d];
+        reduce_and_finalize<ND>(v, a.red, a.op, a.result, st);
+    }
+}
+
+int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s)
+{
+    switch (vop) {
+#define HEC_VEC_CASE(OPV)                                                                        \
+    case OPV:                                                                                    \
+        k_vec<OPV><<<grid, kThreads, 0, s>>>(a);                                                 \
+        return 0;
+        HEC_VEC_CASE(V_AXPBY)
+        HEC_VEC_CASE(V_WAXPBY)
+        HEC_VEC_CASE(V_DOT)
+        HEC_VEC_CASE(V_NRM2SQ)
+        HEC_VEC_CASE(V_COPY)
+        HEC_VEC_CASE(V_SCALE_ST)
+        HEC_VEC_CASE(V_BICG_P)
+        HEC_VEC_CASE(V_BICG_S)
+        HEC_VEC_CASE(V_BICG_XR)
+        HEC_VEC_CASE(V_AXPY_ST1)
+        HEC_VEC_CASE(V_ZERO_IF_ST)
+#undef HEC_VEC_CASE
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ GMRES basis kernels
+
+constexpr int kGroup = 8; // basis vectors per CTA in a projection
+
+// h[i] = (V_i, w), i < k.  Grid (row blocks, vector groups); every CTA keeps
+// kGroup running sums per thread and reduces them once at the end.
+__global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
+{
+    count_launch(a.st);
+    int k = a.k;
+    if (a.k_from_st == 1)
+        k = a.st->j + 1;
+    else if (a.k_from_st == 2)
+        k = a.st->jend;
+    const int g0 = blockIdx.y * kGroup;
+    double acc[kGroup];
+#pragma unroll
+    for (int q = 0; q < kGroup; ++q)
+        acc[q] = 0.0;
+    if (g0 < k) {
+        const int stride = gridDim.x * kThreads;
+        for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
+            const double wi = a.w[i];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q)
+                if (g0 + q < k)
+                    acc[q] = fma(a.V[(int64_t)(g0 + q) * a.ldv + i], wi, acc[q]);
+        }
+    }
+    // block reduction of the kGroup sums
+    __shared__ double sh[kGroup][kThreads / 32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kGroup; ++q) {
+        double t = warp_sum(acc[q]);
+        if (lane == 0)
+            sh[q][wid] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGroup) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w)
+            t += sh[threadIdx.x][w];
+        // partials layout: [vector][row block]
+        const int q = g0 + threadIdx.x;
+        if (q < k)
+            a.red.partials[(size_t)q * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned tk = atomicAdd(a.red.ticket, 1u);
+        s_last = (tk == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    for (int q = threadIdx.x; q < k; q += kThreads) {
+        double t = 0.0;
+        for (unsigned c = 0; c < gridDim.x; ++c)
+            t += __ldcg(&a.red.partials[(size_t)q * gridDim.x + c]);
+        if (a.op == FIN_GMRES_H1)
+            a.st->h1[q] = t;
+        else if (a.op == FIN_GMRES_H2)
+            a.st->h2[q] = t;
+        else
+            a.result[q] = t;
+    }
+    if (threadIdx.x == 0)
+        *a.red.ticket = 0u;
+}
+
+int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s)
+{
+    // a.k is the number of vectors, or an upper bound of it when k_from_st
+    dim3 g(grid, (a.k + kGroup - 1) / kGroup);
+    k_multidot<<<g, kThreads, 0, s>>>(a);
+    return 0;
+}
+
+// wout = w - sum_{i<k} coef[i] V_i, optionally with (wout, wout) reduced.
+template <bool NORM>
+__global__ void __launch_bounds__(kThreads) k_basis_update(BasisArgs a)
+{
+    count_launch(a.st);
+    int k = a.k;
+    if (a.k_from_st == 1)
+        k = a.st->j + 1;
+    else if (a.k_from_st == 2)
+        k = a.st->jend;
+    __shared__ double sc[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < k; q += kThreads)
+        sc[q] = a.coef[q];
+    __syncthreads();
+    double acc = 0.0;
+    const int stride = gridDim.x * kThreads;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
+        double t = a.w[i];
+        for (int q = 0; q < k; ++q)
+            t = fma(-sc[q], a.V[(int64_t)q * a.ldv + i], t);
+        a.wout[i] = t;
+        if (NORM)
+            acc = fma(t, t, acc);
+    }
+    if (NORM) {
+        double v[1] = {acc};
+        reduce_and_finalize<1>(v, a.red, a.op, a.result, a.st);
+    }
+}
+
+int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s)
+{
+    if (with_norm)
+        k_basis_update<true><<<grid, kThreads, 0, s>>>(a);
+    else
+        k_basis_update<false><<<grid, kThreads, 0, s>>>(a);
+    return 0;
+}
+
+// wout = sum_{i<k} coef[i] V_i
+__global__ void __launch_bounds__(kThreads) k_basis_combine(BasisArgs a)
+{
+    count_launch(a.st);
+    int k = a.k;
+    if (a.k_from_st == 1)
+        k = a.st->j + 1;
+    else if (a.k_from_st == 2)
+        k = a.st->jend;
+    __shared__ double sc[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < k; q += kThreads)
+        sc[q] = a.coef[q];
+    __syncthreads();
+    const int stride = gridDim.x * kThreads;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
+        double t = 0.0;
+        for (int q = 0; q < k; ++q)
+            t = fma(sc[q], a.V[(int64_t)q * a.ldv + i], t);
+        a.wout[i] = t;
+    }
+}
+
+int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s)
+{
+    k_basis_combine<<<grid, kThreads, 0, s>>>(a);
+    return 0;
+}
+
+// ------------------------------------------------------------------ small kernels
+
+// Back substitution R y = g of the Givens-reduced Hessenberg matrix (one thread).
+__global__ void k_gmres_lsq(SolverState *st)
+{
+    count_launch(st);
+    if (threadIdx.x != 0)
+        return;
+    const int je = st->jend, ld = kMaxRestart;
+    for (int i = je - 1; i >= 0; --i) {
+        double s = st->g[i];
+        for (int l = i + 1; l < je; ++l)
+            s -= st->H[i * ld + l] * st->y[l];
+        st->y[i] = s / st->H[i * ld + i];
+    }
+}
+
+int launch_gmres_lsq(SolverState *st, cudaStream_t s)
+{
+    k_gmres_lsq<<<1, 32, 0, s>>>(st);
+    return 0;
+}
+
+// Loop condition of the solve graph's while node.
+__global__ void k_loopcond(SolverState *st)
+{
+    count_launch(st);
+    if (threadIdx.x == 0)
+        set_cond(st->h_while, !st->done);
+}
+
+int launch_loopcond(SolverState *st, cudaStream_t s)
+{
+    k_loopcond<<<1, 32, 0, s>>>(st);
+    return 0;
+}
+
+} // namespace hec

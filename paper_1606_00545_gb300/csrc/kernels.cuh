@@ -1,0 +1,164 @@
+// kernels.cuh -- device-side data structures and launch wrappers shared by the
+// CUDA translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hec {
+
+constexpr int kThreads = 256;         // threads per CTA of the streaming kernels
+constexpr int kSpmvTile = 2 * kThreads; // rows per SpMV tile: 2 adjacent rows per thread
+constexpr int kMaxRestart = 128;      // largest GMRES(m) supported
+constexpr int kMaxDots = 2;           // fused reductions per launch
+
+// Reduction finalisers: what the last CTA of a reducing launch does with the
+// summed values (all of them run on one thread, after a fixed-order sum).
+enum FinOp : int {
+    FIN_STORE = 0,        // result[d] = sum_d
+    FIN_STORE_SQRT,       // result[0] = sqrt(sum_0)
+    FIN_NRM_B,            // ||b||: bnorm, b == 0 -> done + zero_x
+    FIN_BICG_INIT,        // r = b - A x0: rho = (r, r); converged test
+    FIN_BICG_ALPHA,       // v = A p*: alpha = rho / (r0, v)
+    FIN_BICG_S,           // s = r - alpha v: ||s|| test
+    FIN_BICG_OMEGA,       // t = A s*: omega = (t, s) / (t, t)
+    FIN_BICG_XR,          // x, r update: ||r||, rho_new, end-of-pass tests
+    FIN_TRUE_RESID,       // r = b - A x at exit: rel_resid
+    FIN_GMRES_CYCLE,      // r = b - A x at cycle start: beta, tests
+    FIN_GMRES_W0,         // w = A z: ||w|| before orthogonalisation
+    FIN_GMRES_H1,         // first projection h1 (k values)
+    FIN_GMRES_H2,         // second projection h2 (k values)
+    FIN_GMRES_STEP,       // ||w''||: Hessenberg column, Givens, cycle tests
+};
+
+// Device-resident solver state: scalars of Algorithm 4 / GMRES, loop flags,
+// and the conditional-node handles of the solve graph.
+struct __align__(16) SolverState {
+    // per-call inputs
+    double tol;
+    int maxit, restart, method, flags;
+    // scalars
+    double bnorm, rho, rho_prev, alpha, omega, scale, w0norm, est, rel_resid;
+    double dots[kMaxDots];
+    int iters, restarts, status, done;
+    int skip, s_conv, zero_x, j;
+    int jend, cycle_end, err, pad_;
+    unsigned long long launches;
+    cudaGraphConditionalHandle h_while, h_if;
+    // GMRES small dense part
+    double H[(kMaxRestart + 1) * kMaxRestart]; // H[i * kMaxRestart + j]
+    double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+    double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
+};
+
+// Reduction scratch of one launch stream: per-CTA partials and a ticket.
+struct RedScratch {
+    double *partials;   // >= grid * width doubles
+    unsigned *ticket;   // zero between launches
+    int capacity;       // doubles available in partials
+};
+
+// ------------------------------------------------------------------ SpMV
+struct SpmvArgs {
+    int n, ld, K, ntiles;
+    const int *ell_col;
+    const double *ell_val;
+    const int *tail_rows, *tail_ptr, *tail_col, *tile_tail;
+    const double *tail_val;
+    const double *x;
+    const double *y_in;
+    double *y_out;
+    const double *w0, *w1; // dot partners; nullptr = y_out itself
+    double alpha, beta;
+    RedScratch red;
+    double *result;        // FIN_STORE destination (device)
+    int op;
+    SolverState *st;       // nullable
+};
+// mode: 0 y = s, 1 y = alpha s, 2 y = alpha s + beta y_in
+int launch_spmv(const SpmvArgs &a, int mode, int ndot, bool has_tail, int grid,
+                cudaStream_t s);
+
+// ------------------------------------------------------------------ vector kernels
+enum VecOp : int {
+    V_AXPBY = 0,   // y = a x + b y
+    V_WAXPBY,      // z = a x + b y
+    V_DOT,         // (x, y)
+    V_NRM2SQ,      // (x, x)
+    V_COPY,        // z = x
+    V_SCALE_ST,    // z = st->scale * x           (GMRES basis normalisation)
+    V_BICG_P,      // p = r + beta (p - omega v)  (Algorithm 4)
+    V_BICG_S,      // s = r - alpha v, (s, s)
+    V_BICG_XR,     // x += alpha p* + omega s*, r = s - omega t, (r, r), (r0, r)
+    V_AXPY_ST1,    // y += x                       (GMRES x update)
+    V_ZERO_IF_ST,  // z = 0 if st->zero_x
+};
+struct VecArgs {
+    int n;
+    double a, b;
+    const double *x, *y;
+    double *z, *w;           // outputs (meaning per op)
+    const double *u, *v, *q; // extra inputs (meaning per op)
+    RedScratch red;
+    double *result;
+    int op;                  // FinOp
+    SolverState *st;
+    int x_from_j;            // x = x + st->j * ldv (GMRES basis column)
+    int z_from_j;
+    int64_t ldv;
+    int guard;               // 1: no-op if st->cycle_end, 2: no-op if st->done
+};
+int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s);
+
+// GMRES Arnoldi: projections and basis combinations (column-major basis V,
+// leading dimension ldv; k vectors = st->j + 1 when k_from_st).
+struct BasisArgs {
+    int n;
+    int k;                 // number of basis vectors (if !k_from_st)
+    int k_from_st;         // 1: k = st->j + 1; 2: k = st->jend
+    const double *V;
+    int64_t ldv;
+    const double *w;       // vector projected / updated
+    double *wout;          // updated vector
+    const double *coef;    // coefficients (device), e.g. st->h1
+    RedScratch red;
+    double *result;
+    int op;
+    SolverState *st;
+};
+int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s);
+// wout = w - sum_i coef[i] V_i  (with_norm: + fused (wout, wout) -> op)
+int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s);
+// wout = sum_i coef[i] V_i
+int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s);
+
+// ------------------------------------------------------------------ TRSV (RAS)
+struct TrsvBlock {
+    int chunk_begin, chunk_end; // chunk ids of this RAS block (L chunks then U chunks)
+    int ring_L, ring_U;         // 1: dependencies read from the shared-memory ring
+    int64_t yoff, zoff;         // offsets of this block in the y / z scratch
+};
+struct TrsvArgs {
+    int nblocks;
+    const TrsvBlock *blocks;
+    const uint2 *chunks;        // {offset in 16-byte units, bytes}
+    const unsigned char *pack;  // packed chunk data
+    const double *r;
+    double *z;
+    double *ysc, *zsc;          // scratch: y by L position, z by U position
+    int ring_mask;              // ring slots - 1 (power of two)
+    int stage_bytes, nstages;
+    long long spin_limit;
+    int *err;                   // device error word
+    SolverState *st;            // nullable: skip / basis column / launch count
+    int r_from_j;
+    int64_t ldv;
+};
+size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots);
+int launch_trsv(const TrsvArgs &a, cudaStream_t s);
+
+// ------------------------------------------------------------------ small solver kernels
+int launch_gmres_lsq(SolverState *st, cudaStream_t s);
+int launch_loopcond(SolverState *st, cudaStream_t s);
+
+} // namespace hec

@@ -1,0 +1,249 @@
+// reduce.cuh -- deterministic two-stage reductions fused into the streaming
+// kernels (Eqs. 5-6), and the scalar recurrences of the Krylov solvers that
+// the last CTA of a reducing launch evaluates.
+#pragma once
+
+#include "../../include/hecgpu.h"
+#include "kernels.cuh"
+
+namespace hec {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void count_launch(SolverState *st)
+{
+    if (st && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        atomicAdd(&st->launches, 1ull);
+}
+
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int on)
+{
+    cudaGraphSetConditional(h, on ? 1u : 0u);
+}
+
+// Scalar recurrences (one thread).  s[0..nd) are the reduced values.
+__device__ inline void finalize(int op, const double *s, int nd, double *result, SolverState *st)
+{
+    switch (op) {
+    case FIN_STORE:
+        for (int d = 0; d < nd; ++d)
+            result[d] = s[d];
+        break;
+    case FIN_STORE_SQRT:
+        result[0] = sqrt(s[0]);
+        break;
+    case FIN_NRM_B:
+        st->bnorm = sqrt(s[0]);
+        if (st->bnorm == 0.0) {
+            st->done = 1;
+            st->zero_x = 1;
+            st->status = HEC_OK;
+        }
+        break;
+    case FIN_BICG_INIT: {
+        // r_0 = b - A x_0 and the shadow residual r_0: rho_0 = (r_0, r_0)
+        double rr = s[0];
+        st->rho = rr;
+        if (st->done)
+            break;
+        st->est = sqrt(rr) / st->bnorm;
+        if (sqrt(rr) <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->status = HEC_OK;
+        } else if (st->maxit <= 0) {
+            st->done = 1;
+            st->status = HEC_MAXIT;
+        }
+        break;
+    }
+    case FIN_BICG_ALPHA: {
+        double r0v = s[0];
+        if (r0v == 0.0) {
+            st->skip = 1;
+            st->status = HEC_BREAKDOWN;
+        } else {
+            st->alpha = st->rho / r0v;
+        }
+        break;
+    }
+    case FIN_BICG_S: {
+        double sn = sqrt(s[0]);
+        if (sn <= st->tol * st->bnorm) {
+            st->s_conv = 1;
+            st->skip = 1;
+            st->est = sn / st->bnorm;
+        }
+        break;
+    }
+    case FIN_BICG_OMEGA: {
+        double ts = s[0], tt = s[1];
+        st->omega = (tt == 0.0) ? 0.0 : ts / tt;
+        break;
+    }
+    case FIN_BICG_XR: {
+        st->iters += 1;
+        if (st->s_conv) {
+            st->done = 1;
+            st->status = HEC_OK;
+        } else if (st->skip) { // (r0, v) = 0
+            st->done = 1;
+            st->status = HEC_BREAKDOWN;
+        } else {
+            double rn = sqrt(s[0]), rho_new = s[1];
+            st->est = rn / st->bnorm;
+            if (rn <= st->tol * st->bnorm) {
+                st->done = 1;
+                st->status = HEC_OK;
+            } else if (st->omega == 0.0 || rho_new == 0.0 || isnan(rn) || isnan(rho_new)) {
+                st->done = 1;
+                st->status = HEC_BREAKDOWN;
+            } else if (st->iters >= st->maxit) {
+                st->done = 1;
+                st->status = HEC_MAXIT;
+            }
+            st->rho_prev = st->rho;
+            st->rho = rho_new;
+        }
+        st->skip = 0;
+        st->s_conv = 0;
+        set_cond(st->h_while, !st->done);
+        break;
+    }
+    case FIN_TRUE_RESID:
+        st->rel_resid = (st->bnorm > 0.0) ? sqrt(s[0]) / st->bnorm : 0.0;
+        break;
+    case FIN_GMRES_CYCLE: {
+        double beta = sqrt(s[0]);
+        if (st->done)
+            break;
+        st->est = beta / st->bnorm;
+        if (beta <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->status = HEC_OK;
+        } else if (isnan(beta)) {
+            st->done = 1;
+            st->status = HEC_BREAKDOWN;
+        } else if (st->iters >= st->maxit) {
+            st->done = 1;
+            st->status = HEC_MAXIT;
+        } else {
+            st->restarts += 1;
+            st->j = 0;
+            st->cycle_end = 0;
+            for (int i = 0; i <= st->restart; ++i)
+                st->g[i] = 0.0;
+            st->g[0] = beta;
+            st->scale = 1.0 / beta;
+        }
+        break;
+    }
+    case FIN_GMRES_W0:
+        st->w0norm = sqrt(s[0]);
+        break;
+    case FIN_GMRES_STEP: {
+        const int j = st->j, m = st->restart;
+        const int ld = kMaxRestart;
+        double hn = sqrt(s[0]);
+        for (int i = 0; i <= j; ++i)
+            st->H[i * ld + j] = st->h1[i] + st->h2[i];
+        st->H[(j + 1) * ld + j] = hn;
+        for (int i = 0; i < j; ++i) {
+            double a = st->H[i * ld + j], c = st->H[(i + 1) * ld + j];
+            st->H[i * ld + j] = st->cs[i] * a + st->sn[i] * c;
+            st->H[(i + 1) * ld + j] = -st->sn[i] * a + st->cs[i] * c;
+        }
+        double a = st->H[j * ld + j], c = st->H[(j + 1) * ld + j];
+        double den = sqrt(a * a + c * c);
+        st->cs[j] = (den == 0.0) ? 1.0 : a / den;
+        st->sn[j] = (den == 0.0) ? 0.0 : c / den;
+        st->H[j * ld + j] = den;
+        st->H[(j + 1) * ld + j] = 0.0;
+        st->g[j + 1] = -st->sn[j] * st->g[j];
+        st->g[j] = st->cs[j] * st->g[j];
+        st->iters += 1;
+        double est = fabs(st->g[j + 1]);
+        st->est = est / st->bnorm;
+        int happy = (hn == 0.0) || (hn <= 1e-300 * st->w0norm);
+        int end = (est <= st->tol * st->bnorm) || happy || (j + 1 == m) ||
+                  (st->iters >= st->maxit) || isnan(est);
+        st->cycle_end = end;
+        if (end) {
+            st->jend = j + 1;
+        } else {
+            st->scale = 1.0 / hn;
+            st->j = j + 1;
+        }
+        set_cond(st->h_if, end);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Block reduction of ND per-thread values, per-CTA partials, and a
+// fixed-order sum plus finalize() by the CTA that arrives last.  All threads
+// of the CTA must call it.  The summation order depends only on the grid
+// size, never on timing, so results are deterministic.
+template <int ND>
+__device__ __forceinline__ void reduce_and_finalize(double (&v)[ND], const RedScratch &red, int op,
+                                                    double *result, SolverState *st)
+{
+    __shared__ double sh[ND][kThreads / 32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        double t = warp_sum(v[d]);
+        if (lane == 0)
+            sh[d][wid] = t;
+    }
+    __syncthreads();
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w)
+                t += sh[d][w];
+            red.partials[(size_t)bid * ND + d] = t;
+        }
+        __threadfence();
+        unsigned tk = atomicAdd(red.ticket, 1u);
+        s_last = (tk == nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        double t = 0.0;
+        for (unsigned c = threadIdx.x; c < nblk; c += kThreads)
+            t += __ldcg(&red.partials[(size_t)c * ND + d]);
+        t = warp_sum(t);
+        if (lane == 0)
+            sh[d][wid] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            s[d] = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w)
+                s[d] += sh[d][w];
+        }
+        *red.ticket = 0u;
+        finalize(op, s, ND, result, st);
+    }
+}
+
+} // namespace hec

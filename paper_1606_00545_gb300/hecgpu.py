@@ -1,0 +1,396 @@
+"""ctypes binding of the C ABI in ``include/hecgpu.h`` (same names, argument
+marshalling only -- every step of the computation runs in the CUDA library).
+
+Device vectors are ``torch.Tensor`` objects on a CUDA device (float64,
+contiguous); host vectors are numpy arrays.  ``stream`` defaults to torch's
+current stream.  Every failing call raises :class:`HecError`.  Importing this
+module loads ``_build/libhecgpu.so``; if the library has not been built the
+import fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhecgpu.so")
+
+OK = 0
+ERR_INVALID = -1
+ERR_OOM = -2
+ERR_ZERO_PIVOT = -3
+ERR_UNSORTED_CSR = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+MAXIT = 1
+BREAKDOWN = 2
+GMRES = 0
+BICGSTAB = 1
+HOST_ONLY = 1
+X0_ZERO = 1
+FACTOR_L = 0
+FACTOR_U = 1
+
+
+class HecError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s failed: status %d (%s): %s" % (where, status, _status_name(status), msg))
+        self.status = status
+
+
+def _status_name(s):
+    return {OK: "ok", ERR_INVALID: "invalid", ERR_OOM: "oom", ERR_ZERO_PIVOT: "zero pivot",
+            ERR_UNSORTED_CSR: "unsorted csr", ERR_CUDA: "cuda", ERR_TIMEOUT: "timeout",
+            MAXIT: "maxit", BREAKDOWN: "breakdown"}.get(s, "?")
+
+
+class CSR_t(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class Opts_t(C.Structure):
+    _fields_ = [("ell_width", C.c_int32), ("ell_ld_align", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class MatrixInfo_t(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("ell_width", C.c_int32),
+                ("ell_ld", C.c_int32), ("tail_rows", C.c_int32), ("tail_nnz", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class PrecondInfo_t(C.Structure):
+    _fields_ = [("nblocks", C.c_int32), ("overlap", C.c_int32), ("k", C.c_int32),
+                ("scheduled", C.c_int32), ("rows_total", C.c_int64), ("factor_nnz", C.c_int64),
+                ("max_levels_L", C.c_int32), ("max_levels_U", C.c_int32),
+                ("apply_bytes", C.c_int64), ("device_bytes", C.c_int64),
+                ("ring_slots", C.c_int32), ("global_passes", C.c_int32)]
+
+
+class SolveOpts_t(C.Structure):
+    _fields_ = [("method", C.c_int32), ("flags", C.c_int32), ("spin_limit", C.c_int64)]
+
+
+class SolveInfo_t(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32), ("rel_resid", C.c_double), ("est_resid", C.c_double),
+                ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64)]
+
+
+_vp = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+_dbl = C.c_double
+
+_SIGS = {
+    "hec_status_string": ([C.c_int], C.c_char_p),
+    "hec_last_error": ([], C.c_char_p),
+    "hec_set_allocator": ([_vp, _vp, _vp], C.c_int),
+    "hec_build": ([C.POINTER(CSR_t), C.POINTER(Opts_t), _vp, C.POINTER(_vp)], C.c_int),
+    "hec_matrix_info": ([_vp, C.POINTER(MatrixInfo_t)], C.c_int),
+    "hec_matrix_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "hec_matrix_destroy": ([_vp], None),
+    "hec_spmv": ([_vp, _dbl, _vp, _dbl, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "hec_axpby": ([_i32, _dbl, _vp, _dbl, _vp, _vp], C.c_int),
+    "hec_waxpby": ([_i32, _dbl, _vp, _dbl, _vp, _vp, _vp], C.c_int),
+    "hec_dot": ([_i32, _vp, _vp, _vp, _vp], C.c_int),
+    "hec_nrm2": ([_i32, _vp, _vp, _vp], C.c_int),
+    "hec_multidot": ([_i32, _i32, _vp, _i64, _vp, _vp, _vp], C.c_int),
+    "ilu_k_setup": ([_vp, _i32, _i32, _i32, _vp, C.POINTER(_vp)], C.c_int),
+    "level_schedule": ([_vp, _vp], C.c_int),
+    "hec_precond_info": ([_vp, C.POINTER(PrecondInfo_t)], C.c_int),
+    "hec_precond_get_block": ([_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), _vp],
+                              C.c_int),
+    "hec_precond_get_factor": ([_vp, _i32, C.POINTER(_i32), _vp, _vp, _vp, _vp], C.c_int),
+    "hec_precond_get_levels": ([_vp, _i32, _i32, C.POINTER(_i32), _vp, _vp], C.c_int),
+    "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
+    "hec_precond_status": ([_vp, _vp], C.c_int),
+    "hec_precond_destroy": ([_vp], None),
+    "krylov_solve": ([_vp, _vp, _vp, _vp, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
+                      C.POINTER(SolveInfo_t)], C.c_int),
+}
+
+_lock = threading.Lock()
+_lib = None
+_alloc_keep = []
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library and declare every ABI signature."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError("CUDA library %s is missing: run __graft_entry__.build()" % path)
+            lib = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc, where, ok=(OK,)):
+    if rc not in ok:
+        raise HecError(rc, where, _lib.hec_last_error().decode(errors="replace"))
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return C.c_void_p(t.ctypes.data)
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(t))
+
+
+def use_torch_allocator():
+    """Route every device allocation of the library through torch's caching allocator."""
+    import torch
+    lib = load_library()
+    AF = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+    FF = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # the library reports HEC_ERR_OOM
+            return None
+
+    def _free(p, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(p))
+
+    fa, ff = AF(_alloc), FF(_free)
+    _alloc_keep[:] = [fa, ff]
+    _check(lib.hec_set_allocator(C.cast(fa, C.c_void_p), C.cast(ff, C.c_void_p), None),
+           "hec_set_allocator")
+
+
+def use_cuda_allocator():
+    _check(load_library().hec_set_allocator(None, None, None), "hec_set_allocator")
+
+
+# ------------------------------------------------------------------ matrix
+class Matrix:
+    """An HEC matrix handle (Section 2.1)."""
+
+    def __init__(self, handle, n, nnz):
+        self._h = handle
+        self.n = n
+        self.nnz = nnz
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = MatrixInfo_t()
+        _check(_lib.hec_matrix_info(self._h, C.byref(inf)), "hec_matrix_info")
+        return {f: getattr(inf, f) for f, _ in MatrixInfo_t._fields_}
+
+    def export(self):
+        """Host copies of the ELL slab and CSR tail."""
+        inf = self.info()
+        K, ld, nt, tn = inf["ell_width"], inf["ell_ld"], inf["tail_rows"], inf["tail_nnz"]
+        ec = np.zeros(K * ld, np.int32)
+        ev = np.zeros(K * ld, np.float64)
+        tr = np.zeros(nt, np.int32)
+        tp = np.zeros(nt + 1, np.int32)
+        tc = np.zeros(tn, np.int32)
+        tv = np.zeros(tn, np.float64)
+        _check(_lib.hec_matrix_export(self._h, _ptr(ec), _ptr(ev), _ptr(tr), _ptr(tp), _ptr(tc),
+                                      _ptr(tv)), "hec_matrix_export")
+        return dict(K=K, ld=ld, ell_col=ec.reshape(K, ld), ell_val=ev.reshape(K, ld),
+                    tail_rows=tr, tail_ptr=tp, tail_col=tc, tail_val=tv)
+
+    def destroy(self):
+        if self._h and _lib is not None:
+            _lib.hec_matrix_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def hec_build(row_ptr, col, val, ell_width=0, ell_ld_align=0, host_only=False, stream=None):
+    """Section 2.1: CSR (numpy host arrays or torch device tensors) -> HEC matrix."""
+    lib = load_library()
+    on_dev = hasattr(row_ptr, "data_ptr")
+    if not on_dev:
+        row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float64)
+    n = int(row_ptr.shape[0] - 1)
+    nnz = int(col.shape[0])
+    A = CSR_t(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), 1 if on_dev else 0)
+    o = Opts_t(int(ell_width), int(ell_ld_align), HOST_ONLY if host_only else 0, 0)
+    h = C.c_void_p()
+    st = C.c_void_p(0) if host_only else _stream(stream)
+    _check(lib.hec_build(C.byref(A), C.byref(o), st, C.byref(h)), "hec_build")
+    return Matrix(h, n, nnz)
+
+
+def hec_spmv(A: Matrix, alpha, x, beta, y_in, y_out, w=None, dots=None, stream=None):
+    """Eq. 2: y_out = alpha A x + beta y_in, optional fused dots (see the header)."""
+    _check(load_library().hec_spmv(A.handle, float(alpha), _ptr(x), float(beta), _ptr(y_in),
+                                   _ptr(y_out), _ptr(w), _ptr(dots), _stream(stream)), "hec_spmv")
+
+
+def hec_axpby(a, x, b, y, stream=None):
+    _check(load_library().hec_axpby(int(y.numel()), float(a), _ptr(x), float(b), _ptr(y),
+                                    _stream(stream)), "hec_axpby")
+
+
+def hec_waxpby(a, x, b, y, z, stream=None):
+    _check(load_library().hec_waxpby(int(z.numel()), float(a), _ptr(x), float(b), _ptr(y),
+                                     _ptr(z), _stream(stream)), "hec_waxpby")
+
+
+def hec_dot(x, y, result, stream=None):
+    _check(load_library().hec_dot(int(x.numel()), _ptr(x), _ptr(y), _ptr(result),
+                                  _stream(stream)), "hec_dot")
+
+
+def hec_nrm2(x, result, stream=None):
+    _check(load_library().hec_nrm2(int(x.numel()), _ptr(x), _ptr(result), _stream(stream)),
+           "hec_nrm2")
+
+
+def hec_multidot(n, k, V, ldv, w, h, stream=None):
+    _check(load_library().hec_multidot(int(n), int(k), _ptr(V), int(ldv), _ptr(w), _ptr(h),
+                                       _stream(stream)), "hec_multidot")
+
+
+# ------------------------------------------------------------------ preconditioner
+class Precond:
+    """RAS blocks with ILU(k) factors (Sections 2.4-2.6)."""
+
+    def __init__(self, handle, A):
+        self._h = handle
+        self.A = A  # keeps the matrix alive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = PrecondInfo_t()
+        _check(_lib.hec_precond_info(self._h, C.byref(inf)), "hec_precond_info")
+        return {f: getattr(inf, f) for f, _ in PrecondInfo_t._fields_}
+
+    def block(self, b):
+        """(rows of V_b, own_lo, own_hi)."""
+        nv, lo, hi = _i32(), _i32(), _i32()
+        _check(_lib.hec_precond_get_block(self._h, b, C.byref(nv), C.byref(lo), C.byref(hi), None),
+               "hec_precond_get_block")
+        rows = np.zeros(nv.value, np.int32)
+        _check(_lib.hec_precond_get_block(self._h, b, None, None, None, _ptr(rows)),
+               "hec_precond_get_block")
+        return rows, lo.value, hi.value
+
+    def factor(self, b):
+        """Combined ILU(k) factor of block b: (row_ptr, col, val, lev), local indices."""
+        nnz = _i32()
+        _check(_lib.hec_precond_get_factor(self._h, b, C.byref(nnz), None, None, None, None),
+               "hec_precond_get_factor")
+        nv = self.block(b)[0].shape[0]
+        rp = np.zeros(nv + 1, np.int32)
+        ci = np.zeros(nnz.value, np.int32)
+        va = np.zeros(nnz.value, np.float64)
+        lev = np.zeros(nnz.value, np.int32)
+        _check(_lib.hec_precond_get_factor(self._h, b, C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(va),
+                                           _ptr(lev)), "hec_precond_get_factor")
+        return rp, ci, va, lev
+
+    def levels(self, b, which):
+        """Level sets of L_b (which=FACTOR_L) or U_b: (level_ptr, level_rows)."""
+        nlev = _i32()
+        _check(_lib.hec_precond_get_levels(self._h, b, which, C.byref(nlev), None, None),
+               "hec_precond_get_levels")
+        nv = self.block(b)[0].shape[0]
+        ptr = np.zeros(nlev.value + 1, np.int32)
+        rows = np.zeros(nv, np.int32)
+        _check(_lib.hec_precond_get_levels(self._h, b, which, C.byref(nlev), _ptr(ptr), _ptr(rows)),
+               "hec_precond_get_levels")
+        return ptr, rows
+
+    def destroy(self):
+        if self._h and _lib is not None:
+            _lib.hec_precond_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ilu_k_setup(A: Matrix, k: int, nblocks: int, overlap: int, stream=None) -> Precond:
+    h = C.c_void_p()
+    _check(load_library().ilu_k_setup(A.handle, int(k), int(nblocks), int(overlap), None,
+                                      C.byref(h)), "ilu_k_setup")
+    return Precond(h, A)
+
+
+def level_schedule(M: Precond, stream=None):
+    st = C.c_void_p(0) if M.A is not None and _is_host_only(M) else _stream(stream)
+    _check(load_library().level_schedule(M.handle, st), "level_schedule")
+
+
+def _is_host_only(M):
+    return M.A.info()["device_bytes"] == 0
+
+
+def hec_precond_apply(M: Precond, r, z, spin_limit: int = 0, stream=None):
+    _check(load_library().hec_precond_apply(M.handle, _ptr(r), _ptr(z), int(spin_limit),
+                                            _stream(stream)), "hec_precond_apply")
+
+
+def hec_precond_status(M: Precond, stream=None) -> int:
+    return load_library().hec_precond_status(M.handle, _stream(stream))
+
+
+# ------------------------------------------------------------------ Krylov
+def krylov_solve(A: Matrix, M, b, x, tol=1e-8, maxit=1000, restart=30, method=GMRES, flags=0,
+                 spin_limit=0, stream=None):
+    """Section 2.7.  Returns a dict of hec_solve_info_t; raises on errors
+    (HEC_MAXIT / HEC_BREAKDOWN are returned in info['status'])."""
+    o = SolveOpts_t(int(method), int(flags), int(spin_limit))
+    inf = SolveInfo_t()
+    rc = load_library().krylov_solve(A.handle, M.handle if M is not None else None, _ptr(b), _ptr(x),
+                                     float(tol), int(maxit), int(restart), C.byref(o),
+                                     _stream(stream), C.byref(inf))
+    _check(rc, "krylov_solve", ok=(OK, MAXIT, BREAKDOWN))
+    return {f: getattr(inf, f) for f, _ in SolveInfo_t._fields_ if f != "reserved"}

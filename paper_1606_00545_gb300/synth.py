@@ -270,6 +270,25 @@ def tridiagonal(n: int, seed: int) -> CSR:
     return _assemble(n, rows.astype(np.int64), cols.astype(np.int64), vals)
 
 
+def random_sparse_rows(n: int, per_row: int, seed: int, dominance: float = 1.5) -> CSR:
+    """Random nonsymmetric sparse matrix for large n: every row draws
+    ``per_row`` off-diagonal columns uniformly (duplicates merged), values
+    uniform on [-1, 1], diagonal ``dominance`` * off-diagonal abs row sum + 1."""
+    rng = np.random.default_rng(seed)
+    r = np.repeat(np.arange(n, dtype=np.int64), per_row)
+    c = rng.integers(0, n, size=r.shape[0])
+    keep = r != c
+    r, c = r[keep], c[keep]
+    key = np.unique(r * n + c)
+    r, c = key // n, key % n
+    v = rng.uniform(-1.0, 1.0, size=r.shape[0])
+    absrow = np.bincount(r, weights=np.abs(v), minlength=n)
+    rows = np.concatenate([r, np.arange(n)])
+    cols = np.concatenate([c, np.arange(n)])
+    vals = np.concatenate([v, dominance * absrow + 1.0])
+    return _assemble(n, rows, cols, vals)
+
+
 def random_sparse(n: int, density: float, seed: int, dominance: float = 1.5,
                   integer: bool = False) -> CSR:
     """Random nonsymmetric sparse matrix with full diagonal.
