@@ -218,6 +218,26 @@ int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_
 /* Synchronise the stream and return (and clear) the device error word of
  * the preconditioner: HEC_OK or HEC_ERR_TIMEOUT. */
 int hec_precond_status(hec_precond_t M, void *stream);
+/* The same z = M^{-1} r as hec_precond_apply, for callers that must not
+ * allocate device memory while they run: for example a time-stepping code
+ * whose device memory budget is fixed at start-up and shared with other
+ * processes, or a latency-bound loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  (The paper has no counterpart;
+ * it is a property of this library's interface.)  The call allocates
+ * nothing: the solve's intermediate vectors live in one static device array
+ * of 2^20 doubles (8 MiB) inside the library, which every device that loads
+ * the library holds until the process exits.  A preconditioner whose scratch
+ * (sum over blocks of the rows solved, plus the rows of blocks that read
+ * dependencies from global memory) exceeds 2^20 doubles is rejected with
+ * HEC_ERR_INVALID; hec_precond_apply has no such limit.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results, so serialise them.  Nothing in the
+ * array needs to start at zero.  Arguments, ownership and the bounded-wait
+ * status word are as for hec_precond_apply. */
+int hec_precond_apply_noalloc(hec_precond_t M, const double *r, double *z, int64_t spin_limit,
+                              void *stream);
 void hec_precond_destroy(hec_precond_t M);
 
 /* ---------------------------------------------------------------- Krylov */

@@ -1226,3 +1226,68 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
 }
 
 } // extern "C"
+
+// ====================================================================== apply without allocation
+// The triangular-solve kernel needs scratch for the intermediate y = L^{-1} r
+// (and, for blocks whose dependency window is too wide for shared memory, for
+// z by position).  hec_precond_apply uses the scratch that level_schedule
+// allocated in the handle; hec_precond_apply_noalloc uses this file-scope
+// device array instead, so the call itself never allocates.  The array is
+// part of the library image: every device that loads the library holds it
+// until the process exits.
+namespace {
+
+constexpr long long kNoallocScratchDoubles = 1ll << 20; // 8 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device.  In host code the array's name is only a host-side stand-in, so the
+// address must come from cudaGetSymbolAddress with the device current.
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    HEC_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(HEC_ERR_INVALID, "device %d beyond the %d devices supported", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        HEC_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return HEC_OK;
+}
+
+} // namespace
+
+extern "C" int hec_precond_apply_noalloc(hec_precond_t M, const double *r, double *z,
+                                         int64_t spin_limit, void *stream)
+{
+    if (!M || !r || !z || r == z)
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (M->host_only)
+        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+    if (!M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    const long long need = (long long)M->pack.ysz + (long long)M->pack.zsz;
+    if (need > kNoallocScratchDoubles)
+        return fail(HEC_ERR_INVALID,
+                    "preconditioner needs %lld scratch doubles; the static array of "
+                    "hec_precond_apply_noalloc holds %lld (use hec_precond_apply)",
+                    need, kNoallocScratchDoubles);
+    double *scratch = nullptr;
+    HEC_TRY(noalloc_scratch(&scratch));
+    // y and z scratch are written before they are read inside one launch, so
+    // nothing in the shared array has to start at zero.
+    TrsvArgs a = trsv_args(M, spin_limit ? spin_limit : kDefaultSpin);
+    a.r = r;
+    a.z = z;
+    a.ysc = scratch;
+    a.zsc = M->pack.zsz ? scratch + M->pack.ysz : nullptr;
+    return run_trsv(a, (cudaStream_t)stream);
+}

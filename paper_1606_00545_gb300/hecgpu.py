@@ -110,6 +110,7 @@ _SIGS = {
     "hec_precond_get_levels": ([_vp, _i32, _i32, C.POINTER(_i32), _vp, _vp], C.c_int),
     "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_status": ([_vp, _vp], C.c_int),
+    "hec_precond_apply_noalloc": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_destroy": ([_vp], None),
     "krylov_solve": ([_vp, _vp, _vp, _vp, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
                       C.POINTER(SolveInfo_t)], C.c_int),
@@ -376,6 +377,15 @@ def _is_host_only(M):
 def hec_precond_apply(M: Precond, r, z, spin_limit: int = 0, stream=None):
     _check(load_library().hec_precond_apply(M.handle, _ptr(r), _ptr(z), int(spin_limit),
                                             _stream(stream)), "hec_precond_apply")
+
+
+def hec_precond_apply_noalloc(M: Precond, r, z, spin_limit: int = 0, stream=None):
+    """z = M^{-1} r without any device allocation (for callers with a fixed
+    device-memory budget or that must avoid cudaMalloc's implicit
+    synchronisation); scratch is a static 8 MiB array in the library, shared
+    by all calls, so overlapping calls race."""
+    _check(load_library().hec_precond_apply_noalloc(M.handle, _ptr(r), _ptr(z), int(spin_limit),
+                                                    _stream(stream)), "hec_precond_apply_noalloc")
 
 
 def hec_precond_status(M: Precond, stream=None) -> int:
