@@ -201,7 +201,7 @@ struct hec_precond_s {
     std::vector<BlockFactor> blocks;
     TrsvPack pack;
     DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc, d_err;
-    int stage_bytes = 32768, nstages = 4;
+    int stage_bytes = 24576, nstages = 8;
     std::vector<std::unique_ptr<Solver>> solvers;
     int64_t device_bytes() const
     {
@@ -1024,6 +1024,7 @@ int level_schedule(hec_precond_t M, void *stream)
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
     if (!M->host_only) {
+        M->nstages = trsv_stages_for(M->stage_bytes, M->pack.ring_slots);
         HEC_TRY(upload(M->d_pack, M->pack.pack, s));
         HEC_TRY(upload(M->d_chunks, M->pack.chunks, s));
         HEC_TRY(upload(M->d_blocks, M->pack.blocks, s));

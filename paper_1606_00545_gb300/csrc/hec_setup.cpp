@@ -344,14 +344,37 @@ void levels_block(BlockFactor &B)
 
 namespace {
 
-inline int r2(int x) { return (x + 1) & ~1; }
-inline int r4(int x) { return (x + 3) & ~3; }
+constexpr int kWarpRows = 32;
+constexpr int kMaxWarps = kThreads / kWarpRows;
+// counts, one width and one segment offset per warp, section offsets
+constexpr int kChunkHeader = 16 + 4 * kMaxWarps + 4 * kMaxWarps + 16;
 
-size_t chunk_bytes(int nrows, int width, bool upass)
+inline int r32(int x) { return (x + kWarpRows - 1) & ~(kWarpRows - 1); }
+
+// Lane stride of warp w's segment: 32 for a full warp, the row count rounded
+// up to 4 for the last, partial one.
+inline int seg_stride(int w, int nrows)
 {
-    size_t b = 16 + (size_t)width * (8 * r2(nrows) + 4 * r4(nrows)) + 4 * (size_t)r4(nrows);
+    const int left = nrows - w * kWarpRows;
+    return left >= kWarpRows ? kWarpRows : (left + 3) & ~3;
+}
+
+// Chunk layout (offsets in bytes, every section 16-byte aligned):
+//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass)
+//   [16, 48)  width of every warp's segment (entries per row, uniform in the warp)
+//   [48, 80)  byte offset of every warp's segment
+//   [80, 96)  byte offsets of src, dst, dinv, and 0
+//   per warp w < nwarps: val[width_w][stride_w] (double), dep[width_w][stride_w] (int32)
+//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (double)
+// Row t of the chunk is handled by thread t (warp t / 32, lane t % 32).
+size_t chunk_bytes(const std::vector<int> &widths, int nrows, bool upass)
+{
+    size_t b = kChunkHeader;
+    for (size_t w = 0; w < widths.size(); ++w)
+        b += (size_t)widths[w] * seg_stride((int)w, nrows) * 12;
+    b += 4 * (size_t)r32(nrows);
     if (upass)
-        b += 4 * (size_t)r4(nrows) + 8 * (size_t)r2(nrows);
+        b += 12 * (size_t)r32(nrows);
     return (b + 15) & ~(size_t)15;
 }
 
@@ -383,7 +406,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
     struct BlockOut {
         std::vector<unsigned char> bytes;
         std::vector<uint2> chunks; // offsets relative to this block
-        int nL = 0, nU = 0, spanL = 0, spanU = 0;
+        int nL = 0, nU = 0, spanL = 0, spanU = 0, nchunksL = 0;
         int64_t alg = 0;
         std::string err;
     };
@@ -409,17 +432,30 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                     needL[F.ci[e]] = 1;
         }
         std::vector<int> posL(nv, -1), posU(nv, -1);
+        // off-diagonal entries of row i in the L (upass false) or U factor
+        auto row_len = [&](bool upass, int i) {
+            return upass ? F.rp[i + 1] - B.diag[i] - 1 : B.diag[i] - F.rp[i];
+        };
         auto order_pass = [&](bool upass, std::vector<int> &pos) {
             const std::vector<int> &ptr = upass ? B.lptrU : B.lptrL;
             const std::vector<int> &rows = upass ? B.lrowsU : B.lrowsL;
             const std::vector<char> &need = upass ? needU : needL;
             PassRows pr;
+            std::vector<int> lvl;
             for (size_t l = 0; l + 1 < ptr.size(); ++l) {
+                lvl.clear();
                 for (int q = ptr[l]; q < ptr[l + 1]; ++q)
-                    if (need[rows[q]]) {
-                        pos[rows[q]] = (int)pr.order.size();
-                        pr.order.push_back(rows[q]);
-                    }
+                    if (need[rows[q]])
+                        lvl.push_back(rows[q]);
+                // inside a level rows are independent: longest first, so each
+                // warp's segment pads little (stable: ties keep row order)
+                std::stable_sort(lvl.begin(), lvl.end(), [&](int x, int y) {
+                    return row_len(upass, x) > row_len(upass, y);
+                });
+                for (int i : lvl) {
+                    pos[i] = (int)pr.order.size();
+                    pr.order.push_back(i);
+                }
                 pr.level_end.push_back((int)pr.order.size());
             }
             return pr;
@@ -429,58 +465,92 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
         O.nL = (int)pl.order.size();
         O.nU = (int)pu.order.size();
         auto emit = [&](bool upass, const PassRows &pr, const std::vector<int> &pos, int &span) {
+            (void)pos;
             int start = 0;
             span = 0;
+            std::vector<int> widths;
             for (int end : pr.level_end) {
                 int q = start;
                 while (q < end) {
-                    // greedy chunk: rows [q, q2) of this level
-                    int q2 = q, width = 0;
+                    // greedy chunk: rows [q, q2) of this level, warp w takes rows
+                    // 32w .. 32w+31; rows are sorted longest first, so a warp's
+                    // width is the length of its first row
+                    int q2 = q;
+                    widths.clear();
                     while (q2 < end && q2 - q < kThreads) {
-                        const int i = pr.order[q2];
-                        const int len = upass ? F.rp[i + 1] - B.diag[i] - 1 : B.diag[i] - F.rp[i];
-                        const int w2 = std::max(width, len);
-                        if (chunk_bytes(q2 - q + 1, w2, upass) > (size_t)stage_bytes)
+                        const int j = q2 - q;
+                        if (j % kWarpRows == 0)
+                            widths.push_back(row_len(upass, pr.order[q2]));
+                        if (chunk_bytes(widths, j + 1, upass) > (size_t)stage_bytes) {
+                            if (j % kWarpRows == 0)
+                                widths.pop_back();
                             break;
-                        width = w2;
+                        }
                         ++q2;
                     }
                     if (q2 == q) {
                         O.err = "a factor row is too long for one shared-memory stage";
                         return;
                     }
-                    const int nr = q2 - q, n2 = r2(nr), n4 = r4(nr);
-                    const size_t bytes = chunk_bytes(nr, width, upass);
+                    const int nr = q2 - q, npad = r32(nr), nw = (int)widths.size();
+                    const size_t bytes = chunk_bytes(widths, nr, upass);
                     const size_t off = O.bytes.size();
                     O.bytes.resize(off + bytes, 0);
                     unsigned char *ch = O.bytes.data() + off;
-                    int hdr[4] = {nr, width, q, upass ? 1 : 0};
-                    std::memcpy(ch, hdr, 16);
-                    double *val = reinterpret_cast<double *>(ch + 16);
-                    int *dep = reinterpret_cast<int *>(val + (size_t)width * n2);
-                    int *src = dep + (size_t)width * n4;
-                    int *dst = src + n4;
-                    double *dinv = reinterpret_cast<double *>(dst + n4);
+                    int hdr[kChunkHeader / 4] = {nr, nw, q, upass ? 1 : 0};
+                    int segoff = kChunkHeader;
+                    for (int w = 0; w < nw; ++w) {
+                        hdr[4 + w] = widths[w];
+                        hdr[4 + kMaxWarps + w] = segoff;
+                        segoff += widths[w] * seg_stride(w, nr) * 12;
+                    }
+                    hdr[4 + 2 * kMaxWarps + 0] = segoff;                  // src
+                    hdr[4 + 2 * kMaxWarps + 1] = segoff + 4 * npad;       // dst
+                    hdr[4 + 2 * kMaxWarps + 2] = segoff + 8 * npad;       // dinv
+                    std::memcpy(ch, hdr, kChunkHeader);
+                    unsigned char *seg = ch + kChunkHeader;
+                    int *src = nullptr;
                     int mindep = q;
+                    for (int w = 0; w < nw; ++w) {
+                        const int wd = widths[w];
+                        const int ls = seg_stride(w, nr);
+                        double *val = reinterpret_cast<double *>(seg);
+                        int *dep = reinterpret_cast<int *>(val + (size_t)wd * ls);
+                        for (int lane = 0; lane < ls; ++lane) {
+                            const int t = w * kWarpRows + lane;
+                            if (t >= nr) {
+                                // rows past the chunk: never read, keep them valid
+                                for (int kk = 0; kk < wd; ++kk) {
+                                    dep[(size_t)kk * ls + lane] = q;
+                                    val[(size_t)kk * ls + lane] = 0.0;
+                                }
+                                continue;
+                            }
+                            const int i = pr.order[q + t];
+                            const int e0 = upass ? B.diag[i] + 1 : F.rp[i];
+                            const int len = row_len(upass, i);
+                            if (len == 0 && wd > 0) {
+                                // a row of level >= 2 always has a dependency
+                                O.err = "internal: dependency-free row in a dependent level";
+                                return;
+                            }
+                            for (int kk = 0; kk < wd; ++kk) {
+                                // padding repeats the first dependency with value 0
+                                const int e = kk < len ? e0 + kk : e0;
+                                const int d = (upass ? posU : posL)[F.ci[e]];
+                                dep[(size_t)kk * ls + lane] = d;
+                                val[(size_t)kk * ls + lane] = kk < len ? F.va[e] : 0.0;
+                                mindep = std::min(mindep, d);
+                            }
+                        }
+                        seg += (size_t)wd * ls * 12;
+                    }
+                    src = reinterpret_cast<int *>(seg);
+                    int *dst = src + npad;
+                    double *dinv = reinterpret_cast<double *>(dst + npad);
                     for (int t = 0; t < nr; ++t) {
                         const int i = pr.order[q + t];
-                        const int e0 = upass ? B.diag[i] + 1 : F.rp[i];
-                        const int e1 = upass ? F.rp[i + 1] : B.diag[i];
-                        const int len = e1 - e0;
-                        if (len == 0 && width > 0) {
-                            // a row of level >= 2 always has a dependency
-                            O.err = "internal: dependency-free row in a dependent level";
-                            return;
-                        }
-                        for (int kk = 0; kk < width; ++kk) {
-                            // padding repeats the first dependency with value 0
-                            const int e = kk < len ? e0 + kk : e0;
-                            const int d = (upass ? posU : posL)[F.ci[e]];
-                            dep[(size_t)kk * n4 + t] = d;
-                            val[(size_t)kk * n2 + t] = kk < len ? F.va[e] : 0.0;
-                            if (len > 0)
-                                mindep = std::min(mindep, d);
-                        }
+                        const int len = row_len(upass, i);
                         if (upass) {
                             src[t] = posL[i];
                             dst[t] = owned[i] ? B.rows[i] : -1;
@@ -502,6 +572,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
         emit(false, pl, posL, O.spanL);
         if (!O.err.empty())
             return;
+        O.nchunksL = (int)O.chunks.size();
         emit(true, pu, posU, O.spanU);
     });
     for (int b = 0; b < nb; ++b)
@@ -537,6 +608,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
         for (const uint2 &c : O.chunks)
             P.chunks.push_back(make_uint2((unsigned)(c.x + off / 16), c.y));
         T.chunk_end = (int)P.chunks.size();
+        T.chunk_mid = T.chunk_begin + O.nchunksL;
         std::memcpy(P.pack.data() + off, O.bytes.data(), O.bytes.size());
         off += O.bytes.size();
         T.ring_L = (O.spanL + 1 <= ring_need) ? 1 : 0;

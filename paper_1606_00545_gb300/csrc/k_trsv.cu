@@ -9,17 +9,23 @@
 // independent).  A chunk is one contiguous byte range in HBM holding, for its
 // rows, the factor entries column-major (value, dependency position), the
 // source index of the right-hand side, and for U the destination row and the
-// inverted diagonal.  Chunks stream into a ring of shared-memory stages with
-// cp.async.bulk (the TMA bulk-copy engine) completing on mbarriers, several
-// chunks ahead of the wavefront, so the factor bytes are in shared memory
-// when their level becomes ready.  Solved values of the last few levels live
-// in a shared-memory ring indexed by level-major position (the setup checks
-// that every dependency of a level lies within the ring's window); blocks
-// whose window does not fit read dependencies from the global scratch
-// instead.  Levels are separated by CTA barriers only -- no grid-wide
-// synchronisation.  Every wait is bounded: a wait that runs out sets the
-// device error word, the CTA waits (bounded) for its own copies in flight,
-// and returns.
+// inverted diagonal.  Rows of a level are sorted longest first and every warp
+// gets its own segment width, so little FP64 work is spent on padding.
+// Nothing on a level's critical path waits for HBM:
+//   - a producer warp streams chunks into a ring of shared-memory stages with
+//     cp.async.bulk (the TMA bulk-copy engine) completing on mbarriers, S
+//     chunks ahead of the solving warps;
+//   - the same warp gathers the right-hand sides of a chunk (L pass: from r;
+//     U pass: from the L results, once the L pass is complete) with 8-byte
+//     cp.async completing on a per-stage mbarrier;
+//   - solved values of the last few levels live in a shared-memory ring
+//     indexed by level-major position (the setup checks that every
+//     dependency of a chunk lies within the ring's window; passes whose
+//     window does not fit read dependencies from the global scratch).
+// Levels are separated by a barrier of the solving warps only -- no
+// grid-wide synchronisation.  Every wait is bounded: a wait that runs out
+// sets the device error word, the producer waits (bounded) for its copies in
+// flight, and the CTA returns.
 #include "reduce.cuh"
 
 namespace hec {
@@ -73,6 +79,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit)
 {
     for (long long it = 0; it < limit; ++it)
@@ -81,17 +100,197 @@ __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, lon
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Arrive on `bar` once every cp.async this thread issued before has landed;
+// the barrier's expected count already includes this arrival (.noinc).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Barrier of the consumer warps only (named barrier 1), OR-reducing a flag.
+__device__ __forceinline__ int consumer_sync_or(int flag)
+{
+    int any;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.s32 p, %1, 0;\n\t"
+                 "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
+                 "selp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(any)
+                 : "r"(flag), "n"(kThreads)
+                 : "memory");
+    return any;
+}
+
+// Shared memory of one CTA: S stages, S right-hand-side slots of kThreads
+// doubles, the ring, and 3 S + 1 mbarriers.
 size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots)
 {
-    return (size_t)stage_bytes * nstages + (size_t)ring_slots * sizeof(double) +
-           (size_t)nstages * sizeof(uint64_t);
+    return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * sizeof(double) +
+           (size_t)ring_slots * sizeof(double) + (size_t)(3 * nstages + 1) * sizeof(uint64_t);
+}
+
+int trsv_stages_for(int stage_bytes, int ring_slots)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    int S = 8;
+    while (S > 3 && trsv_smem_bytes(stage_bytes, S, ring_slots) > (size_t)optin)
+        --S;
+    return S;
 }
 
 // Drain bound for copies already issued when a wait ran out: copies complete
 // in microseconds, this only guarantees that the CTA never waits forever.
 constexpr long long kDrainPolls = 1ll << 24;
 
-__global__ void __launch_bounds__(kThreads, 1) k_trsv_ras(TrsvArgs a)
+// A chunk in shared memory (layout written by the setup's packer):
+//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass)
+//   [16, 48)  width of every warp's segment
+//   [48, 80)  byte offset of every warp's segment
+//   [80, 96)  byte offsets of src, dst, dinv
+//   per warp w < nwarps: val[width_w][stride_w] (double), dep[width_w][stride_w] (int32),
+//     stride_w = 32 for a full warp, the row count rounded up to 4 for the last one
+//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)], dinv[r32(nrows)] (double)
+constexpr int kWarpRows = 32;
+constexpr int kMaxWarps = kThreads / kWarpRows;
+
+__device__ __forceinline__ int seg_stride(int w, int nrows)
+{
+    const int left = nrows - w * kWarpRows;
+    return left >= kWarpRows ? kWarpRows : (left + 3) & ~3;
+}
+
+struct ChunkView {
+    int nrows, nwarps, base;
+    bool upass;
+    const int *src, *dst;
+    const double *dinv;
+};
+
+__device__ __forceinline__ ChunkView view_chunk(const unsigned char *ch)
+{
+    ChunkView v;
+    const int4 hdr = *reinterpret_cast<const int4 *>(ch);
+    const int4 off = *reinterpret_cast<const int4 *>(ch + 16 + 8 * kMaxWarps);
+    v.nrows = hdr.x;
+    v.nwarps = hdr.y;
+    v.base = hdr.z;
+    v.upass = (hdr.w & 1) != 0;
+    v.src = reinterpret_cast<const int *>(ch + off.x);
+    v.dst = reinterpret_cast<const int *>(ch + off.y);
+    v.dinv = reinterpret_cast<const double *>(ch + off.z);
+    return v;
+}
+
+// The segment of warp w: entry k of lane l at val[k * stride + l], dep[k * stride + l].
+struct Segment {
+    int width, stride;
+    const double *val;
+    const int *dep;
+};
+
+__device__ __forceinline__ Segment warp_segment(const unsigned char *ch, int nrows, int w)
+{
+    const int *hdr = reinterpret_cast<const int *>(ch);
+    Segment g;
+    g.width = hdr[4 + w];
+    g.stride = seg_stride(w, nrows);
+    g.val = reinterpret_cast<const double *>(ch + hdr[4 + kMaxWarps + w]);
+    g.dep = reinterpret_cast<const int *>(g.val + (size_t)g.width * g.stride);
+    return g;
+}
+
+// s - sum_k val[k] * y[dep[k]] for one row in ascending column order, width W
+// known at compile time: every shared-memory load of the row is issued before
+// the first multiply.  One accumulator: FP64 throughput, not the 64-cycle
+// latency of a dependent DFMA, bounds a level once several warps are busy,
+// and a second accumulator would cost one more FP64 add per row.
+template <int W, bool RING>
+__device__ __forceinline__ double row_solve(const Segment &g, int lane, const double *ring, int mask,
+                                            const double *gdep, double s)
+{
+    if constexpr (W == 0) {
+        return s;
+    } else {
+        double l[W], y[W];
+        int d[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            l[k] = g.val[k * g.stride + lane];
+            d[k] = g.dep[k * g.stride + lane];
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            y[k] = RING ? ring[d[k] & mask] : gdep[d[k]];
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            s = fma(-l[k], y[k], s);
+        return s;
+    }
+}
+
+template <bool RING>
+__device__ __forceinline__ double row_solve_any(const Segment &g, int lane, const double *ring,
+                                                int mask, const double *gdep, double s)
+{
+    switch (g.width) {
+    case 0: return s;
+    case 1: return row_solve<1, RING>(g, lane, ring, mask, gdep, s);
+    case 2: return row_solve<2, RING>(g, lane, ring, mask, gdep, s);
+    case 3: return row_solve<3, RING>(g, lane, ring, mask, gdep, s);
+    case 4: return row_solve<4, RING>(g, lane, ring, mask, gdep, s);
+    case 5: return row_solve<5, RING>(g, lane, ring, mask, gdep, s);
+    case 6: return row_solve<6, RING>(g, lane, ring, mask, gdep, s);
+    case 7: return row_solve<7, RING>(g, lane, ring, mask, gdep, s);
+    case 8: return row_solve<8, RING>(g, lane, ring, mask, gdep, s);
+    default: {
+        // wide rows: loads in blocks of 8 entries
+        int k = 0;
+        for (; k + 8 <= g.width; k += 8) {
+            double l[8], y[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                l[q] = g.val[(k + q) * g.stride + lane];
+                const int d = g.dep[(k + q) * g.stride + lane];
+                y[q] = RING ? ring[d & mask] : gdep[d];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                s = fma(-l[q], y[q], s);
+        }
+        for (; k < g.width; ++k) {
+            const int d = g.dep[k * g.stride + lane];
+            s = fma(-g.val[k * g.stride + lane], RING ? ring[d & mask] : gdep[d], s);
+        }
+        return s;
+    }
+    }
+}
+
+// Warp-specialised CTA: warps 0-7 solve rows (one row per thread per chunk),
+// warp 8 feeds them.  Per chunk c in stage s = c mod S:
+//   producer: wait empty[s] (chunk c - S released) -> arm full[s] with the
+//             chunk's byte count -> cp.async.bulk the chunk; then, G chunks
+//             behind, gather the right-hand side of chunk c - G into slot s'
+//             with 8-byte cp.async (a U chunk waits for ldone first: its
+//             right-hand side is the L pass's output); ready[s'] completes
+//             when the 32 lanes' gathers have landed (cp.async arrivals) and
+//             lane 0 -- which has seen the chunk's data land -- has arrived,
+//             so one barrier covers both;
+//   consumers: wait ready[s] -> solve -> consumer barrier ->
+//             one thread releases empty[s] (and ldone after the last L chunk).
+__global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     count_launch(a.st);
@@ -104,114 +303,185 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_ras(TrsvArgs a)
     const TrsvBlock blk = a.blocks[blockIdx.x];
     const int S = a.nstages;
     unsigned char *stages = smem;
-    double *ring = reinterpret_cast<double *>(smem + (size_t)S * a.stage_bytes);
+    double *rhs = reinterpret_cast<double *>(smem + (size_t)S * a.stage_bytes);
+    double *ring = rhs + (size_t)S * kThreads;
     const int mask = a.ring_mask;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ring + mask + 1);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + mask + 1);
+    uint64_t *empty = full + S;
+    uint64_t *ready = empty + S;
+    uint64_t *ldone = ready + S;
     const int nch = blk.chunk_end - blk.chunk_begin;
-    const bool stall_test = a.spin_limit < 0; // fault-injection: nothing is issued
+    const int nL = blk.chunk_mid - blk.chunk_begin; // chunks of the L pass
+    const bool stall_test = a.spin_limit < 0;       // fault injection: nothing is issued
     const long long limit = stall_test ? -a.spin_limit : a.spin_limit;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s)
-            mbar_init(&bar[s], 1);
-        fence_mbar_init();
-    }
-    for (int i = threadIdx.x; i <= mask; i += blockDim.x)
-        ring[i] = 0.0;
-    __syncthreads();
-
-    if (threadIdx.x == 0 && !stall_test) {
-        const int pro = nch < S ? nch : S;
-        for (int c = 0; c < pro; ++c) {
-            const uint2 d = a.chunks[blk.chunk_begin + c];
-            mbar_arrive_expect_tx(&bar[c], d.y);
-            bulk_g2s(stages + (size_t)c * a.stage_bytes, a.pack + (size_t)d.x * 16, d.y, &bar[c]);
-        }
-    }
-
+    const uint2 *chunks = a.chunks + blk.chunk_begin;
     const double *ysc = a.ysc + blk.yoff;
     double *ysc_w = a.ysc + blk.yoff;
     double *zsc = a.zsc ? a.zsc + blk.zoff : nullptr;
+    const int t = threadIdx.x;
 
-    int failed_at = -1;
+    if (t == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&ready[s], 33); // 32 gather arrivals + 1 data arrival
+        }
+        mbar_init(ldone, 1);
+        fence_mbar_init();
+    }
+    for (int i = t; i <= mask; i += blockDim.x)
+        ring[i] = 0.0;
+    __syncthreads();
+
+    if (t >= kThreads) {
+        // ------------------------------------------------------------ producer warp
+        if (stall_test)
+            return;
+        const int lane = t - kThreads;
+        const int G = S / 2; // right-hand-side gather lag behind the chunk stream
+        uint2 win = make_uint2(0, 0);
+        int wbase = -64;
+        int issued = 0, failed = 0;
+        bool ldone_seen = false;
+        for (int c = 0; c < nch + G && !failed; ++c) {
+            if (c < nch) {
+                const int s = c % S;
+                if (c >= wbase + 32) { // 32 descriptors per warp-wide load
+                    wbase = c;
+                    win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
+                }
+                const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
+                const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
+                // every wait decision is a warp vote: the lanes must stay converged
+                if (c >= S &&
+                    __any_sync(0xffffffffu,
+                               !bounded_wait(&empty[s], (uint32_t)((c / S) - 1) & 1u, limit))) {
+                    failed = 1;
+                    break;
+                }
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    bulk_g2s(stages + (size_t)s * a.stage_bytes, a.pack + (size_t)off16 * 16,
+                             bytes, &full[s]);
+                }
+                issued = c + 1;
+            }
+            const int g = c - G;
+            if (g >= 0 && g < nch) {
+                const int sg = g % S;
+                if (__any_sync(0xffffffffu, !bounded_wait(&full[sg], (uint32_t)(g / S) & 1u, limit))) {
+                    failed = 1;
+                    break;
+                }
+                const ChunkView v = view_chunk(stages + (size_t)sg * a.stage_bytes);
+                if (v.upass && !ldone_seen) {
+                    if (__any_sync(0xffffffffu, !bounded_wait(ldone, 0u, limit))) {
+                        failed = 1;
+                        break;
+                    }
+                    ldone_seen = true;
+                }
+                double *slot = rhs + (size_t)sg * kThreads;
+                for (int i = lane; i < v.nrows; i += 32)
+                    cp_async8(&slot[i], v.upass ? ysc + v.src[i] : r + v.src[i]);
+                cp_async_arrive_noinc(&ready[sg]); // when this lane's gathers land
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&ready[sg]); // the chunk's data has landed (seen above)
+            }
+        }
+        cp_async_wait_all();
+        if (failed) {
+            // the last S chunks issued may still be in flight
+            if (lane == 0) {
+                const int first = issued - S > 0 ? issued - S : 0;
+                for (int c = first; c < issued; ++c)
+                    bounded_wait(&full[c % S], (uint32_t)(c / S) & 1u, kDrainPolls);
+                atomicExch(a.err, HEC_ERR_TIMEOUT);
+                if (a.st)
+                    a.st->err = HEC_ERR_TIMEOUT;
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumer warps
+    int err = 0;
+    int s = 0;
+    uint32_t par = 0;
     for (int c = 0; c < nch; ++c) {
-        const int s = c % S;
-        const uint32_t par = (uint32_t)(c / S) & 1u;
-        int err = bounded_wait(&bar[s], par, limit) ? 0 : 1;
+        if (!bounded_wait(&ready[s], par, limit))
+            err = 1;
+        // results leave the critical path: global stores are issued after the
+        // stage is released, so the release does not wait for them
+        double out = 0.0;
+        double *gout = nullptr;
         if (!err) {
             const unsigned char *ch = stages + (size_t)s * a.stage_bytes;
-            const int4 hdr = *reinterpret_cast<const int4 *>(ch);
-            const int nrows = hdr.x, width = hdr.y, base = hdr.z;
-            const bool upass = (hdr.w & 1) != 0;
-            const int nr2 = (nrows + 1) & ~1, nr4 = (nrows + 3) & ~3;
-            const double *val = reinterpret_cast<const double *>(ch + 16);
-            const int *dep = reinterpret_cast<const int *>(val + (size_t)width * nr2);
-            const int *src = dep + (size_t)width * nr4;
-            const int *dst = src + nr4;
-            const double *dinv = reinterpret_cast<const double *>(dst + nr4);
-            const bool rm = upass ? blk.ring_U : blk.ring_L;
-            const double *gdep = upass ? zsc : ysc;
-            for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
-                double sacc = upass ? ysc[src[t]] : r[src[t]];
-                if (rm) {
-                    for (int k = 0; k < width; ++k)
-                        sacc = fma(-val[k * nr2 + t], ring[dep[k * nr4 + t] & mask], sacc);
-                } else {
-                    for (int k = 0; k < width; ++k)
-                        sacc = fma(-val[k * nr2 + t], gdep[dep[k * nr4 + t]], sacc);
-                }
-                const int pos = base + t;
-                if (upass) {
-                    sacc *= dinv[t];
+            const ChunkView v = view_chunk(ch);
+            if (t < v.nrows) {
+                const bool rm = v.upass ? blk.ring_U : blk.ring_L;
+                const double *gdep = v.upass ? zsc : ysc;
+                const Segment g = warp_segment(ch, v.nrows, t / kWarpRows);
+                const int lane = t % kWarpRows;
+                double sacc = rhs[(size_t)s * kThreads + t];
+                sacc = rm ? row_solve_any<true>(g, lane, ring, mask, gdep, sacc)
+                          : row_solve_any<false>(g, lane, ring, mask, gdep, sacc);
+                const int pos = v.base + t;
+                if (v.upass) {
+                    sacc *= v.dinv[t];
                     if (rm)
                         ring[pos & mask] = sacc;
                     else
-                        zsc[pos] = sacc;
-                    const int d = dst[t];
+                        zsc[pos] = sacc; // read by later levels of this pass
+                    const int d = v.dst[t];
                     if (d >= 0)
-                        a.z[d] = sacc;
+                        gout = a.z + d;
                 } else {
-                    if (rm)
+                    if (rm) {
                         ring[pos & mask] = sacc;
-                    ysc_w[pos] = sacc;
+                        gout = ysc_w + pos;
+                    } else {
+                        ysc_w[pos] = sacc; // read by later levels of this pass
+                    }
                 }
+                out = sacc;
             }
         }
-        if (__syncthreads_or(err)) {
-            failed_at = c;
-            break;
-        }
-        if (threadIdx.x == 0 && c + S < nch) {
-            fence_proxy_async_smem(); // generic reads of stage s before the async write
-            const uint2 d = a.chunks[blk.chunk_begin + c + S];
-            mbar_arrive_expect_tx(&bar[s], d.y);
-            bulk_g2s(stages + (size_t)s * a.stage_bytes, a.pack + (size_t)d.x * 16, d.y, &bar[s]);
-        }
-    }
-    if (failed_at >= 0) {
-        // copies issued for chunks failed_at .. failed_at + S - 1 may be in flight
-        if (threadIdx.x == 0) {
-            if (!stall_test) {
-                const int last = (failed_at + S < nch) ? failed_at + S : nch;
-                for (int c = failed_at; c < last; ++c)
-                    bounded_wait(&bar[c % S], (uint32_t)(c / S) & 1u, kDrainPolls);
+        if (consumer_sync_or(err)) {
+            if (t == 0) {
+                atomicExch(a.err, HEC_ERR_TIMEOUT);
+                if (a.st)
+                    a.st->err = HEC_ERR_TIMEOUT;
             }
-            atomicExch(a.err, HEC_ERR_TIMEOUT);
-            if (a.st)
-                a.st->err = HEC_ERR_TIMEOUT;
+            return; // the producer's own waits run out and drain its copies
         }
-        __syncthreads();
+        if (t == 0)
+            mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
+        if (gout)
+            *gout = out;
+        if (c == nL - 1) {
+            // every y of the L pass is written before the producer gathers
+            // the U pass's right-hand sides from them
+            consumer_sync_or(0);
+            if (t == 0)
+                mbar_arrive(ldone);
+        }
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
     }
 }
 
 int launch_trsv(const TrsvArgs &a, cudaStream_t s)
 {
     const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1);
-    cudaError_t e = cudaFuncSetAttribute(k_trsv_ras, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_trsv_ras, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return -1;
-    k_trsv_ras<<<a.nblocks, kThreads, smem, s>>>(a);
+    k_trsv_ras<<<a.nblocks, kThreads + 32, smem, s>>>(a);
     return 0;
 }
 

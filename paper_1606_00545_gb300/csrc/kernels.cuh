@@ -135,6 +135,7 @@ int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s);
 // ------------------------------------------------------------------ TRSV (RAS)
 struct TrsvBlock {
     int chunk_begin, chunk_end; // chunk ids of this RAS block (L chunks then U chunks)
+    int chunk_mid, pad_;        // first U chunk
     int ring_L, ring_U;         // 1: dependencies read from the shared-memory ring
     int64_t yoff, zoff;         // offsets of this block in the y / z scratch
 };
@@ -154,7 +155,10 @@ struct TrsvArgs {
     int r_from_j;
     int64_t ldv;
 };
+// Shared memory of one CTA: stages, ring, right-hand-side slots, barriers.
 size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots);
+// Largest stage count (2..8) that fits the device's shared memory per CTA.
+int trsv_stages_for(int stage_bytes, int ring_slots);
 int launch_trsv(const TrsvArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------------ small solver kernels
