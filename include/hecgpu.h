@@ -113,12 +113,19 @@ typedef struct {
 
 typedef struct {
     int32_t method;     /* HEC_GMRES or HEC_BICGSTAB                          */
-    int32_t flags;      /* HEC_X0_ZERO: ignore the content of x, start at 0   */
+    int32_t flags;      /* HEC_X0_ZERO: ignore the content of x, start at 0;
+                           HEC_SOLVE_EAGER: launch the solve's kernels
+                           directly on the stream and drive the loop from the
+                           host (one small read per iteration) instead of the
+                           device-side graph loop -- same kernels, same
+                           results; for profilers that cannot see the kernels
+                           of a graph with conditional nodes                */
     int64_t spin_limit; /* polls of a device wait before HEC_ERR_TIMEOUT;
                            0 = default (about a second)                      */
 } hec_solve_opts_t;
 
 #define HEC_X0_ZERO 1
+#define HEC_SOLVE_EAGER 2
 
 typedef struct {
     int32_t iters;          /* BiCGSTAB passes / GMRES Arnoldi steps          */

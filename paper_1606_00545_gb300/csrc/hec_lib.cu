@@ -369,7 +369,10 @@ int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
     return HEC_OK;
 }
 
-// --- launch sequences (used while capturing) --------------------------------
+// --- launch sequences ----------------------------------------------------------
+// The same sequences run inside the solve graph (captured once) or, for
+// profilers that cannot see the kernels of a graph with conditional nodes,
+// directly on a stream with one host check per iteration (HEC_SOLVE_EAGER).
 
 int seq_precond(const hec_precond_s *M, Solver &S, const double *in, double *out, int from_j,
                 cudaStream_t cs)
@@ -383,21 +386,21 @@ int seq_precond(const hec_precond_s *M, Solver &S, const double *in, double *out
     return run_trsv(a, cs);
 }
 
-int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+int seq_norm_b(Solver &S, cudaStream_t cs)
 {
-    const int n = S.n;
-    HEC_CK(cudaGraphCreate(&S.graph, 0));
-    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
-    std::vector<cudaGraphNode_t> tail;
-    // init: ||b||; r = b - A x0, rho = (r, r); r0 = r; loop condition
-    HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
     VecArgs va{};
-    va.n = n;
+    va.n = S.n;
     va.st = S.st;
     va.red = S.red.r;
     va.x = S.b;
     va.op = FIN_NRM_B;
-    HEC_TRY(run_vec(V_NRM2SQ, va, cs));
+    return run_vec(V_NRM2SQ, va, cs);
+}
+
+// Algorithm 4, first line: r0 = b - A x0, rho_0 = (r0, r0); shadow residual r0.
+int seq_bicg_init(hec_matrix_s *A, Solver &S, cudaStream_t cs)
+{
+    HEC_TRY(seq_norm_b(S, cs));
     SpmvArgs sa = spmv_args(A);
     sa.st = S.st;
     sa.red = S.red.r;
@@ -410,80 +413,74 @@ int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs
     sa.op = FIN_BICG_INIT;
     HEC_TRY(run_spmv(A, sa, 2, 1, cs));
     VecArgs cp{};
-    cp.n = n;
+    cp.n = S.n;
     cp.st = S.st;
     cp.x = S.r;
     cp.z = S.r0;
-    HEC_TRY(run_vec(V_COPY, cp, cs));
-    if (launch_loopcond(S.st, cs) != 0)
-        return fail(HEC_ERR_CUDA, "loopcond");
-    HEC_TRY(check_launch("loopcond"));
-    S.init_launches = 4;
-    HEC_TRY(end_capture(cs, tail));
-    cudaGraphNode_t wnode;
-    cudaGraph_t body;
-    HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
+    return run_vec(V_COPY, cp, cs);
+}
 
-    // body: one pass of Algorithm 4
-    HEC_TRY(begin_capture(cs, body, nullptr, 0));
-    {
-        VecArgs pa{};
-        pa.n = n;
-        pa.st = S.st;
-        pa.x = S.r;
-        pa.y = S.v;
-        pa.z = S.p;
-        HEC_TRY(run_vec(V_BICG_P, pa, cs)); // p = r + beta (p - omega v)
-        if (M)
-            HEC_TRY(seq_precond(M, S, S.p, S.ps, 0, cs)); // M p* = p
-        SpmvArgs v = spmv_args(A);
-        v.st = S.st;
-        v.red = S.red.r;
-        v.x = M ? S.ps : S.p;
-        v.y_out = S.v;
-        v.w0 = S.r0;
-        v.op = FIN_BICG_ALPHA;
-        HEC_TRY(run_spmv(A, v, 0, 1, cs)); // v = A p*, (r0, v) -> alpha
-        VecArgs sv{};
-        sv.n = n;
-        sv.st = S.st;
-        sv.red = S.red.r;
-        sv.x = S.r;
-        sv.y = S.v;
-        sv.z = S.s;
-        sv.op = FIN_BICG_S;
-        HEC_TRY(run_vec(V_BICG_S, sv, cs)); // s = r - alpha v, ||s||
-        if (M)
-            HEC_TRY(seq_precond(M, S, S.s, S.ss, 0, cs)); // M s* = s
-        SpmvArgs t = spmv_args(A);
-        t.st = S.st;
-        t.red = S.red.r;
-        t.x = M ? S.ss : S.s;
-        t.y_out = S.t;
-        t.w0 = S.s;
-        t.w1 = nullptr;
-        t.op = FIN_BICG_OMEGA;
-        HEC_TRY(run_spmv(A, t, 0, 2, cs)); // t = A s*, (t, s), (t, t) -> omega
-        VecArgs xr{};
-        xr.n = n;
-        xr.st = S.st;
-        xr.red = S.red.r;
-        xr.w = S.x;
-        xr.u = M ? S.ps : S.p;
-        xr.v = M ? S.ss : S.s;
-        xr.q = S.t;
-        xr.x = S.s;
-        xr.y = S.r0;
-        xr.z = S.r;
-        xr.op = FIN_BICG_XR;
-        HEC_TRY(run_vec(V_BICG_XR, xr, cs)); // x, r updates; tests; loop condition
-    }
-    HEC_TRY(end_capture(cs, tail));
+// One pass of the k loop of Algorithm 4.
+int seq_bicg_body(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    const int n = S.n;
+    VecArgs pa{};
+    pa.n = n;
+    pa.st = S.st;
+    pa.x = S.r;
+    pa.y = S.v;
+    pa.z = S.p;
+    HEC_TRY(run_vec(V_BICG_P, pa, cs)); // p = r + beta (p - omega v)
+    if (M)
+        HEC_TRY(seq_precond(M, S, S.p, S.ps, 0, cs)); // M p* = p
+    SpmvArgs v = spmv_args(A);
+    v.st = S.st;
+    v.red = S.red.r;
+    v.x = M ? S.ps : S.p;
+    v.y_out = S.v;
+    v.w0 = S.r0;
+    v.op = FIN_BICG_ALPHA;
+    HEC_TRY(run_spmv(A, v, 0, 1, cs)); // v = A p*, (r0, v) -> alpha
+    VecArgs sv{};
+    sv.n = n;
+    sv.st = S.st;
+    sv.red = S.red.r;
+    sv.x = S.r;
+    sv.y = S.v;
+    sv.z = S.s;
+    sv.op = FIN_BICG_S;
+    HEC_TRY(run_vec(V_BICG_S, sv, cs)); // s = r - alpha v, ||s||
+    if (M)
+        HEC_TRY(seq_precond(M, S, S.s, S.ss, 0, cs)); // M s* = s
+    SpmvArgs t = spmv_args(A);
+    t.st = S.st;
+    t.red = S.red.r;
+    t.x = M ? S.ss : S.s;
+    t.y_out = S.t;
+    t.w0 = S.s;
+    t.w1 = nullptr;
+    t.op = FIN_BICG_OMEGA;
+    HEC_TRY(run_spmv(A, t, 0, 2, cs)); // t = A s*, (t, s), (t, t) -> omega
+    VecArgs xr{};
+    xr.n = n;
+    xr.st = S.st;
+    xr.red = S.red.r;
+    xr.w = S.x;
+    xr.u = M ? S.ps : S.p;
+    xr.v = M ? S.ss : S.s;
+    xr.q = S.t;
+    xr.x = S.s;
+    xr.y = S.r0;
+    xr.z = S.r;
+    xr.op = FIN_BICG_XR;
+    return run_vec(V_BICG_XR, xr, cs); // x, r updates; tests; loop condition
+}
 
-    // exit: x = 0 if b = 0; true residual
-    HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
+// Exit: x = 0 if b = 0; the true residual ||b - A x|| / ||b||.
+int seq_exit(hec_matrix_s *A, Solver &S, cudaStream_t cs)
+{
     VecArgs zx{};
-    zx.n = n;
+    zx.n = S.n;
     zx.st = S.st;
     zx.z = S.x;
     HEC_TRY(run_vec(V_ZERO_IF_ST, zx, cs));
@@ -496,13 +493,10 @@ int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs
     fr.y_in = S.b;
     fr.y_out = S.r;
     fr.op = FIN_TRUE_RESID;
-    HEC_TRY(run_spmv(A, fr, 2, 1, cs));
-    HEC_TRY(end_capture(cs, tail));
-    HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
-    return HEC_OK;
+    return run_spmv(A, fr, 2, 1, cs);
 }
 
-// cycle start: r = b - A x, beta, v_1 = r / beta
+// GMRES cycle start: r = b - A x, beta = ||r||, v_1 = r / beta.
 int seq_gmres_cycle(hec_matrix_s *A, Solver &S, cudaStream_t cs)
 {
     SpmvArgs sa = spmv_args(A);
@@ -521,151 +515,198 @@ int seq_gmres_cycle(hec_matrix_s *A, Solver &S, cudaStream_t cs)
     sc.x = S.r;
     sc.z = S.V; // column 0
     sc.guard = 2;
-    HEC_TRY(run_vec(V_SCALE_ST, sc, cs));
+    return run_vec(V_SCALE_ST, sc, cs);
+}
+
+// One Arnoldi step: z = M^{-1} v_j, w = A z, two classical Gram-Schmidt
+// passes, h_{j+1,j} = ||w||, Givens update, v_{j+1} = w / h_{j+1,j}.
+int seq_gmres_step(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    const int n = S.n, m = S.restart;
+    if (M) {
+        HEC_TRY(seq_precond(M, S, S.V, S.z, 1, cs)); // z = M^{-1} v_j
+    } else {
+        VecArgs c{};
+        c.n = n;
+        c.st = S.st;
+        c.x = S.V;
+        c.x_from_j = 1;
+        c.ldv = S.ldv;
+        c.z = S.z;
+        HEC_TRY(run_vec(V_COPY, c, cs));
+    }
+    SpmvArgs w = spmv_args(A);
+    w.st = S.st;
+    w.red = S.red.r;
+    w.x = S.z;
+    w.y_out = S.w;
+    w.op = FIN_GMRES_W0;
+    HEC_TRY(run_spmv(A, w, 0, 1, cs)); // w = A z, ||w||
+    const int mdgrid = grid_for(n, kThreads, 2);
+    BasisArgs h{};
+    h.n = n;
+    h.k = m + 1;
+    h.k_from_st = 1;
+    h.V = S.V;
+    h.ldv = S.ldv;
+    h.w = S.w;
+    h.red = S.red.r;
+    h.st = S.st;
+    h.op = FIN_GMRES_H1;
+    launch_multidot(h, mdgrid, cs); // h1 = V^T w
+    HEC_TRY(check_launch("multidot"));
+    BasisArgs up = h;
+    up.coef = dev_field<double>(S.st, offsetof(SolverState, h1));
+    up.wout = S.w;
+    launch_basis_update(up, false, vec_grid(n), cs); // w -= V h1
+    HEC_TRY(check_launch("basis update"));
+    BasisArgs h2 = h;
+    h2.op = FIN_GMRES_H2;
+    launch_multidot(h2, mdgrid, cs); // h2 = V^T w
+    HEC_TRY(check_launch("multidot"));
+    BasisArgs up2 = h;
+    up2.coef = dev_field<double>(S.st, offsetof(SolverState, h2));
+    up2.wout = S.w;
+    up2.op = FIN_GMRES_STEP;
+    launch_basis_update(up2, true, vec_grid(n), cs); // w -= V h2, ||w||, Givens
+    HEC_TRY(check_launch("basis update"));
+    VecArgs sc{};
+    sc.n = n;
+    sc.st = S.st;
+    sc.x = S.w;
+    sc.z = S.V;
+    sc.z_from_j = 1; // j already advanced when the cycle goes on
+    sc.ldv = S.ldv;
+    sc.guard = 1;
+    return run_vec(V_SCALE_ST, sc, cs); // v_{j+1} = w / h_{j+1,j}
+}
+
+// Cycle end: y = R^{-1} g, x += M^{-1} V y, next cycle start.
+int seq_gmres_cycle_end(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    if (launch_gmres_lsq(S.st, cs) != 0)
+        return fail(HEC_ERR_CUDA, "lsq");
+    HEC_TRY(check_launch("lsq"));
+    BasisArgs cb{};
+    cb.n = S.n;
+    cb.k = S.restart;
+    cb.k_from_st = 2;
+    cb.V = S.V;
+    cb.ldv = S.ldv;
+    cb.coef = dev_field<double>(S.st, offsetof(SolverState, y));
+    cb.wout = S.u;
+    cb.st = S.st;
+    launch_basis_combine(cb, vec_grid(S.n), cs); // u = V y
+    HEC_TRY(check_launch("basis combine"));
+    if (M)
+        HEC_TRY(seq_precond(M, S, S.u, S.zu, 0, cs)); // zu = M^{-1} u
+    VecArgs ax{};
+    ax.n = S.n;
+    ax.st = S.st;
+    ax.x = M ? S.zu : S.u;
+    ax.z = S.x;
+    HEC_TRY(run_vec(V_AXPY_ST1, ax, cs)); // x += zu
+    return seq_gmres_cycle(A, S, cs);
+}
+
+int seq_loopcond(Solver &S, cudaStream_t cs)
+{
+    if (launch_loopcond(S.st, cs) != 0)
+        return fail(HEC_ERR_CUDA, "loopcond");
+    return check_launch("loopcond");
+}
+
+// --- solve graphs -------------------------------------------------------------
+
+int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    HEC_CK(cudaGraphCreate(&S.graph, 0));
+    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> tail;
+    HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
+    HEC_TRY(seq_bicg_init(A, S, cs));
+    HEC_TRY(seq_loopcond(S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
+    HEC_TRY(begin_capture(cs, body, nullptr, 0));
+    HEC_TRY(seq_bicg_body(A, M, S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
+    HEC_TRY(seq_exit(A, S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
     return HEC_OK;
 }
 
 int build_gmres(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
 {
-    const int n = S.n, m = S.restart;
     HEC_CK(cudaGraphCreate(&S.graph, 0));
     HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
     std::vector<cudaGraphNode_t> tail;
     HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
-    VecArgs va{};
-    va.n = n;
-    va.st = S.st;
-    va.red = S.red.r;
-    va.x = S.b;
-    va.op = FIN_NRM_B;
-    HEC_TRY(run_vec(V_NRM2SQ, va, cs));
+    HEC_TRY(seq_norm_b(S, cs));
     HEC_TRY(seq_gmres_cycle(A, S, cs));
-    if (launch_loopcond(S.st, cs) != 0)
-        return fail(HEC_ERR_CUDA, "loopcond");
-    HEC_TRY(check_launch("loopcond"));
+    HEC_TRY(seq_loopcond(S, cs));
     HEC_TRY(end_capture(cs, tail));
     cudaGraphNode_t wnode;
     cudaGraph_t body;
     HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
     HEC_CK(cudaGraphConditionalHandleCreate(&S.h_if, body, 0, cudaGraphCondAssignDefault));
-
-    // body: one Arnoldi step with CGS2
     HEC_TRY(begin_capture(cs, body, nullptr, 0));
-    {
-        if (M) {
-            HEC_TRY(seq_precond(M, S, S.V, S.z, 1, cs)); // z = M^{-1} v_j
-        } else {
-            VecArgs c{};
-            c.n = n;
-            c.st = S.st;
-            c.x = S.V;
-            c.x_from_j = 1;
-            c.ldv = S.ldv;
-            c.z = S.z;
-            HEC_TRY(run_vec(V_COPY, c, cs));
-        }
-        SpmvArgs w = spmv_args(A);
-        w.st = S.st;
-        w.red = S.red.r;
-        w.x = S.z;
-        w.y_out = S.w;
-        w.op = FIN_GMRES_W0;
-        HEC_TRY(run_spmv(A, w, 0, 1, cs)); // w = A z, ||w||
-        const int mdgrid = grid_for(n, kThreads, 2);
-        BasisArgs h{};
-        h.n = n;
-        h.k = m + 1;
-        h.k_from_st = 1;
-        h.V = S.V;
-        h.ldv = S.ldv;
-        h.w = S.w;
-        h.red = S.red.r;
-        h.st = S.st;
-        h.op = FIN_GMRES_H1;
-        launch_multidot(h, mdgrid, cs); // h1 = V^T w
-        HEC_TRY(check_launch("multidot"));
-        BasisArgs up = h;
-        up.coef = dev_field<double>(S.st, offsetof(SolverState, h1));
-        up.wout = S.w;
-        launch_basis_update(up, false, vec_grid(n), cs); // w -= V h1
-        HEC_TRY(check_launch("basis update"));
-        BasisArgs h2 = h;
-        h2.op = FIN_GMRES_H2;
-        launch_multidot(h2, mdgrid, cs); // h2 = V^T w
-        HEC_TRY(check_launch("multidot"));
-        BasisArgs up2 = h;
-        up2.coef = dev_field<double>(S.st, offsetof(SolverState, h2));
-        up2.wout = S.w;
-        up2.op = FIN_GMRES_STEP;
-        launch_basis_update(up2, true, vec_grid(n), cs); // w -= V h2, ||w||, Givens
-        HEC_TRY(check_launch("basis update"));
-        VecArgs sc{};
-        sc.n = n;
-        sc.st = S.st;
-        sc.x = S.w;
-        sc.z = S.V;
-        sc.z_from_j = 1; // j already advanced when the cycle goes on
-        sc.ldv = S.ldv;
-        sc.guard = 1;
-        HEC_TRY(run_vec(V_SCALE_ST, sc, cs)); // v_{j+1} = w / h_{j+1,j}
-    }
+    HEC_TRY(seq_gmres_step(A, M, S, cs));
     HEC_TRY(end_capture(cs, tail));
     cudaGraphNode_t ifnode;
     cudaGraph_t ifbody;
     HEC_TRY(add_conditional(body, tail, S.h_if, cudaGraphCondTypeIf, ifnode, ifbody));
-    // cycle end: y = R^{-1} g; x += M^{-1} V y; next cycle start
     HEC_TRY(begin_capture(cs, ifbody, nullptr, 0));
-    {
-        if (launch_gmres_lsq(S.st, cs) != 0)
-            return fail(HEC_ERR_CUDA, "lsq");
-        HEC_TRY(check_launch("lsq"));
-        BasisArgs cb{};
-        cb.n = n;
-        cb.k = m;
-        cb.k_from_st = 2;
-        cb.V = S.V;
-        cb.ldv = S.ldv;
-        cb.coef = dev_field<double>(S.st, offsetof(SolverState, y));
-        cb.wout = S.u;
-        cb.st = S.st;
-        launch_basis_combine(cb, vec_grid(n), cs); // u = V y
-        HEC_TRY(check_launch("basis combine"));
-        if (M)
-            HEC_TRY(seq_precond(M, S, S.u, S.zu, 0, cs)); // zu = M^{-1} u
-        VecArgs ax{};
-        ax.n = n;
-        ax.st = S.st;
-        ax.x = M ? S.zu : S.u;
-        ax.z = S.x;
-        HEC_TRY(run_vec(V_AXPY_ST1, ax, cs)); // x += zu
-        HEC_TRY(seq_gmres_cycle(A, S, cs));
-    }
+    HEC_TRY(seq_gmres_cycle_end(A, M, S, cs));
     HEC_TRY(end_capture(cs, tail));
     HEC_TRY(begin_capture(cs, body, &ifnode, 1));
-    if (launch_loopcond(S.st, cs) != 0)
-        return fail(HEC_ERR_CUDA, "loopcond");
-    HEC_TRY(check_launch("loopcond"));
+    HEC_TRY(seq_loopcond(S, cs));
     HEC_TRY(end_capture(cs, tail));
-
     HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
-    VecArgs zx{};
-    zx.n = n;
-    zx.st = S.st;
-    zx.z = S.x;
-    HEC_TRY(run_vec(V_ZERO_IF_ST, zx, cs));
-    SpmvArgs fr = spmv_args(A);
-    fr.st = S.st;
-    fr.red = S.red.r;
-    fr.x = S.x;
-    fr.alpha = -1.0;
-    fr.beta = 1.0;
-    fr.y_in = S.b;
-    fr.y_out = S.r;
-    fr.op = FIN_TRUE_RESID;
-    HEC_TRY(run_spmv(A, fr, 2, 1, cs));
+    HEC_TRY(seq_exit(A, S, cs));
     HEC_TRY(end_capture(cs, tail));
     HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
     return HEC_OK;
+}
+
+// The solve without graphs: the same launch sequences, the loop driven from
+// the host (one small device-to-host read per iteration).
+int run_eager(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t s)
+{
+    int flags[2] = {0, 0}; // done, cycle_end
+    auto read_flags = [&]() -> int {
+        HEC_CK(cudaMemcpyAsync(&flags[0], dev_field<int>(S.st, offsetof(SolverState, done)),
+                               sizeof(int), cudaMemcpyDeviceToHost, s));
+        HEC_CK(cudaMemcpyAsync(&flags[1], dev_field<int>(S.st, offsetof(SolverState, cycle_end)),
+                               sizeof(int), cudaMemcpyDeviceToHost, s));
+        HEC_CK(cudaStreamSynchronize(s));
+        return HEC_OK;
+    };
+    if (S.method == HEC_BICGSTAB) {
+        HEC_TRY(seq_bicg_init(A, S, s));
+        HEC_TRY(read_flags());
+        while (!flags[0]) {
+            HEC_TRY(seq_bicg_body(A, M, S, s));
+            HEC_TRY(read_flags());
+        }
+    } else {
+        HEC_TRY(seq_norm_b(S, s));
+        HEC_TRY(seq_gmres_cycle(A, S, s));
+        HEC_TRY(read_flags());
+        while (!flags[0]) {
+            HEC_TRY(seq_gmres_step(A, M, S, s));
+            HEC_TRY(read_flags());
+            if (flags[1]) {
+                HEC_TRY(seq_gmres_cycle_end(A, M, S, s));
+                HEC_TRY(read_flags());
+            }
+        }
+    }
+    return seq_exit(A, S, s);
 }
 
 int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cudaStream_t s,
@@ -1191,6 +1232,8 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
     h.flags = o.flags;
     h.h_while = S->h_while;
     h.h_if = S->h_if;
+    const bool eager = (o.flags & HEC_SOLVE_EAGER) != 0;
+    h.graph_mode = eager ? 0 : 1;
     HEC_CK(cudaMemcpyAsync(S->st, &h, offsetof(SolverState, H), cudaMemcpyHostToDevice, s));
     int64_t h2d = 0, d2h = 0;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
@@ -1204,7 +1247,10 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
         if (!xdev)
             h2d += vb;
     }
-    HEC_CK(cudaGraphLaunch(S->exec, s));
+    if (eager)
+        HEC_TRY(run_eager(A, M, *S, s));
+    else
+        HEC_CK(cudaGraphLaunch(S->exec, s));
     HEC_CK(cudaMemcpyAsync(x, S->x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!xdev)
         d2h += vb;

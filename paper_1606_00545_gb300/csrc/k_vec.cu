@@ -300,7 +300,7 @@ __global__ void k_loopcond(SolverState *st)
 {
     count_launch(st);
     if (threadIdx.x == 0)
-        set_cond(st->h_while, !st->done);
+        set_cond(st, st->h_while, !st->done);
 }
 
 int launch_loopcond(SolverState *st, cudaStream_t s)

@@ -42,7 +42,7 @@ struct __align__(16) SolverState {
     double dots[kMaxDots];
     int iters, restarts, status, done;
     int skip, s_conv, zero_x, j;
-    int jend, cycle_end, err, pad_;
+    int jend, cycle_end, err, graph_mode; // graph_mode: kernels run inside the solve graph
     unsigned long long launches;
     cudaGraphConditionalHandle h_while, h_if;
     // GMRES small dense part

@@ -22,9 +22,12 @@ __device__ __forceinline__ void count_launch(SolverState *st)
         atomicAdd(&st->launches, 1ull);
 }
 
-__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int on)
+// Set a conditional node's value -- only inside the solve graph; a solve
+// driven from the host reads the flags instead.
+__device__ __forceinline__ void set_cond(const SolverState *st, cudaGraphConditionalHandle h, int on)
 {
-    cudaGraphSetConditional(h, on ? 1u : 0u);
+    if (st->graph_mode)
+        cudaGraphSetConditional(h, on ? 1u : 0u);
 }
 
 // Scalar recurrences (one thread).  s[0..nd) are the reduced values.
@@ -112,7 +115,7 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         }
         st->skip = 0;
         st->s_conv = 0;
-        set_cond(st->h_while, !st->done);
+        set_cond(st, st->h_while, !st->done);
         break;
     }
     case FIN_TRUE_RESID:
@@ -179,7 +182,7 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
             st->scale = 1.0 / hn;
             st->j = j + 1;
         }
-        set_cond(st->h_if, end);
+        set_cond(st, st->h_if, end);
         break;
     }
     default:

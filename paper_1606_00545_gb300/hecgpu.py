@@ -31,6 +31,7 @@ GMRES = 0
 BICGSTAB = 1
 HOST_ONLY = 1
 X0_ZERO = 1
+SOLVE_EAGER = 2
 FACTOR_L = 0
 FACTOR_U = 1
 

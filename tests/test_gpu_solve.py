@@ -119,6 +119,22 @@ def test_host_buffers_match_device_path(H, orc):
         assert i1["h2d_bytes"] == 0 and i1["d2h_bytes"] == 0
 
 
+def test_eager_solve_matches_graph_solve(H):
+    """HEC_SOLVE_EAGER runs the same kernels from a host loop: identical results."""
+    A = synth.diffusion2d_5pt_lognormal(30, 2.0, 3)
+    b = synth.rhs_uniform(A.n, 6)
+    M, P = setup(H, A, 1, 3, 1)
+    for method in (H.BICGSTAB, H.GMRES):
+        xg = dev(np.zeros(A.n))
+        ig = H.krylov_solve(M, P, dev(b), xg, tol=1e-9, maxit=500, restart=8, method=method)
+        xe = dev(np.zeros(A.n))
+        ie = H.krylov_solve(M, P, dev(b), xe, tol=1e-9, maxit=500, restart=8, method=method,
+                            flags=H.SOLVE_EAGER)
+        assert np.array_equal(host(xg), host(xe))
+        assert ig["iters"] == ie["iters"] and ig["restarts"] == ie["restarts"]
+        assert ig["status"] == ie["status"] == H.OK
+
+
 def test_repeat_solves_are_identical(H):
     A = synth.poisson2d_5pt(30)
     b = synth.rhs_uniform(A.n, 4)
