@@ -61,7 +61,7 @@ def parse():
                     help="profiling: run the solve's kernels from a host loop instead of the "
                          "device-side graph loop (ncu cannot profile kernels of graphs with "
                          "conditional nodes); same kernels and results, slower")
-    ap.add_argument("--kernel", choices=["trsv", "spmv"], default=None,
+    ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
                          "--steps times (few launches before it, for ncu -k/-s/-c)")
     return ap.parse_args()
@@ -78,8 +78,12 @@ def run_kernel_only(args, local_rank):
     Ah = H.hec_build(A.row_ptr, A.col, A.val)
     P = H.ilu_k_setup(Ah, K_FILL, NBLOCKS, OVERLAP)
     H.level_schedule(P)
-    r = torch.tensor(b, device=dev)
+    fp32 = args.kernel.endswith("32")
+    r = torch.tensor(b, device=dev, dtype=torch.float32 if fp32 else torch.float64)
     z = torch.empty_like(r)
+    if fp32:  # the FP32 layouts are built on first use, outside the timed launches
+        H.hec_precond_apply_f32(P, r, z)
+        H.hec_spmv_f32(Ah, 1.0, r, 0.0, None, z)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for i in range(args.steps):
@@ -88,14 +92,20 @@ def run_kernel_only(args, local_rank):
             e0.record()
         if args.kernel == "trsv":
             H.hec_precond_apply(P, r, z)
+        elif args.kernel == "trsv32":
+            H.hec_precond_apply_f32(P, r, z)
+        elif args.kernel == "spmv32":
+            H.hec_spmv_f32(Ah, 1.0, r, 0.0, None, z)
         else:
             H.hec_spmv(Ah, 1.0, r, 0.0, None, z)
     e1.record()
     torch.cuda.synchronize()
-    if args.kernel == "trsv":
+    if args.kernel.startswith("trsv"):
         assert H.hec_precond_status(P) == H.OK
     ms = e0.elapsed_time(e1) / max(1, args.steps - 1) if args.steps > 1 else None
-    nbytes = P.info()["apply_bytes"] if args.kernel == "trsv" else A.nnz * 12 + A.n * 16
+    inf = P.info()
+    nbytes = {"trsv": inf["apply_bytes"], "trsv32": inf["apply_bytes_f32"],
+              "spmv": A.nnz * 12 + A.n * 16, "spmv32": A.nnz * 8 + A.n * 8}[args.kernel]
     print(json.dumps({"kernel": args.kernel, "launches": args.steps, "ms_per_launch": ms,
                       "alg_bytes": nbytes,
                       "gbs": nbytes / (ms * 1e-3) / 1e9 if ms else None}))
@@ -359,13 +369,32 @@ def run_ours(args, rank, world, local_rank):
     spmv_bytes = A.nnz * 12 + A.n * 16
     spmv_gbs = spmv_bytes / (ms_spmv * 1e-3 / reps) / 1e9
 
-    # GMRES(30) on the same system (Arnoldi/Givens rows of the path)
+    # GMRES(30) on the same system (Arnoldi/Givens rows of the path), FP64 and
+    # mixed precision (FP32 inner cycles, FP64 refinement)
     xg30 = torch.zeros_like(bd)
     H.krylov_solve(Ah, P, bd, xg30, tol=TOL, maxit=MAXIT, restart=30, method=H.GMRES,
                    flags=H.X0_ZERO)
     ms_g, ig = timed(lambda: H.krylov_solve(Ah, P, bd, xg30, tol=TOL, maxit=MAXIT, restart=30,
                                             method=H.GMRES, flags=H.X0_ZERO), 1)
     gm = ig[0]
+    xm30 = torch.zeros_like(bd)
+    mflags = H.X0_ZERO | H.MIXED_FP32
+    H.krylov_solve(Ah, P, bd, xm30, tol=TOL, maxit=MAXIT, restart=30, method=H.GMRES, flags=mflags)
+    ms_m, im = timed(lambda: H.krylov_solve(Ah, P, bd, xm30, tol=TOL, maxit=MAXIT, restart=30,
+                                            method=H.GMRES, flags=mflags), 1)
+    gmx = im[0]
+    mixed_err = float(torch.linalg.norm(xm30 - xg30) / torch.linalg.norm(xg30))
+    r32 = r.float()
+    z32 = torch.empty_like(r32)
+    for _ in range(3):
+        H.hec_precond_apply_f32(P, r32, z32)
+    ms_a32, _ = timed(lambda: H.hec_precond_apply_f32(P, r32, z32), reps)
+    assert H.hec_precond_status(P) == H.OK
+    y32 = torch.empty_like(r32)
+    for _ in range(3):
+        H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32)
+    ms_s32, _ = timed(lambda: H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32), reps)
+    pinf = P.info()
 
     if rank != 0:
         return
@@ -395,7 +424,18 @@ def run_ours(args, rank, world, local_rank):
         "spmv": {"achieved": spmv_gbs, "unit": "GB/s", "frac": spmv_gbs / peak,
                  "alg_bytes_per_launch": spmv_bytes, "launch_ms": ms_spmv / reps},
         "gmres30": {"iters": gm["iters"], "restarts": gm["restarts"],
-                    "iters_per_s": gm["iters"] / (ms_g * 1e-3), "rel_resid": gm["rel_resid"]},
+                    "iters_per_s": gm["iters"] / (ms_g * 1e-3), "rel_resid": gm["rel_resid"],
+                    "solve_ms": ms_g},
+        "gmres30_mixed": {"iters": gmx["iters"], "cycles": gmx["restarts"],
+                          "iters_per_s": gmx["iters"] / (ms_m * 1e-3),
+                          "rel_resid": gmx["rel_resid"], "solve_ms": ms_m,
+                          "speedup_vs_fp64_solve": ms_g / ms_m,
+                          "rel_error_vs_fp64_solution": mixed_err},
+        "fp32_kernels": {"trsv_ms": ms_a32 / reps,
+                         "trsv_gbs": pinf["apply_bytes_f32"] / (ms_a32 * 1e-3 / reps) / 1e9,
+                         "trsv_alg_bytes": pinf["apply_bytes_f32"],
+                         "spmv_ms": ms_s32 / reps,
+                         "spmv_gbs": (A.nnz * 8 + A.n * 8) / (ms_s32 * 1e-3 / reps) / 1e9},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -106,6 +106,7 @@ typedef struct {
     int32_t global_passes;   /* (block, factor) solves whose dependencies do
                                 not fit the window and are read from global
                                 memory instead                                */
+    int64_t apply_bytes_f32; /* the same for the FP32 layout (0 until built)   */
 } hec_precond_info_t;
 
 #define HEC_GMRES 0
@@ -126,6 +127,14 @@ typedef struct {
 
 #define HEC_X0_ZERO 1
 #define HEC_SOLVE_EAGER 2
+/* Mixed precision (GMRES only): every restart cycle is an inner solve in FP32
+ * -- FP32 SpMV, FP32 ILU(k) triangular solves, FP32 Krylov basis, FP32
+ * products and accumulation -- and FP64 is kept for the outer residual
+ * r = b - A x recomputed at every cycle start, the update of x, and the
+ * Hessenberg least-squares / Givens step: FP64 iterative refinement with
+ * FP32 GMRES cycles.  Convergence is judged on the FP64 residual.  A cycle
+ * also ends when its FP32 estimate has dropped by 1e-5. */
+#define HEC_MIXED_FP32 4
 
 typedef struct {
     int32_t iters;          /* BiCGSTAB passes / GMRES Arnoldi steps          */
@@ -172,6 +181,13 @@ void hec_matrix_destroy(hec_matrix_t A);
  * dots[1] = (y_out, y_out), each summed in a fixed order (deterministic). */
 int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const double *y_in,
              double *y_out, const double *w, double *dots, void *stream);
+
+/* The FP32 SpMV of the mixed-precision inner solves, Eq. 2 with FP32 values
+ * (the matrix's values rounded once to FP32, kept beside the FP64 ones after
+ * the first FP32 call), FP32 products and accumulation.  x, y_in, y_out:
+ * device arrays of n floats; no fused dots. */
+int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const float *y_in,
+                 float *y_out, void *stream);
 
 /* ---------------------------------------------------------------- vector ops */
 /* Eqs. 3-6 on device arrays of n doubles.  hec_dot / hec_nrm2 write their
@@ -245,6 +261,12 @@ int hec_precond_status(hec_precond_t M, void *stream);
  * status word are as for hec_precond_apply. */
 int hec_precond_apply_noalloc(hec_precond_t M, const double *r, double *z, int64_t spin_limit,
                               void *stream);
+/* The FP32 preconditioner of the mixed-precision inner solves: the same
+ * z = M^{-1} r with the ILU(k) factors rounded once to FP32 (a second device
+ * layout, built on first use) and FP32 arithmetic.  r, z: device arrays of n
+ * floats, r != z.  Status as for hec_precond_apply. */
+int hec_precond_apply_f32(hec_precond_t M, const float *r, float *z, int64_t spin_limit,
+                          void *stream);
 void hec_precond_destroy(hec_precond_t M);
 
 /* ---------------------------------------------------------------- Krylov */

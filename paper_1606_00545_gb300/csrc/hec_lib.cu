@@ -184,14 +184,32 @@ struct hec_matrix_s {
     HostCSR csr;
     HecHost hec;
     DevBuf ell_col, ell_val, tail_rows, tail_ptr, tail_col, tail_val, tile_tail;
+    DevBuf ell_val32, tail_val32; // FP32 copies of the values, made on first FP32 use
+    bool f32_ready = false;
     Reducer red;
     std::vector<std::unique_ptr<Solver>> solvers; // solves without a preconditioner
     int64_t device_bytes() const
     {
         return (int64_t)(ell_col.bytes + ell_val.bytes + tail_rows.bytes + tail_ptr.bytes +
-                         tail_col.bytes + tail_val.bytes + tile_tail.bytes + red.partials.bytes);
+                         tail_col.bytes + tail_val.bytes + tile_tail.bytes + red.partials.bytes +
+                         ell_val32.bytes + tail_val32.bytes);
     }
     ~hec_matrix_s();
+};
+
+// The device layout of the factors for one value type: the chunk stream the
+// triangular-solve kernel reads, and its scratch.
+struct TrsvLayout {
+    TrsvPack pack;
+    DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc;
+    int nstages = 8;
+    int vbytes = 8;
+    bool built = false;
+    int64_t device_bytes() const
+    {
+        return (int64_t)(d_pack.bytes + d_chunks.bytes + d_blocks.bytes + d_ysc.bytes +
+                         d_zsc.bytes);
+    }
 };
 
 struct hec_precond_s {
@@ -199,14 +217,13 @@ struct hec_precond_s {
     int n = 0, k = 0, nblocks = 0, overlap = 0;
     bool host_only = false, scheduled = false;
     std::vector<BlockFactor> blocks;
-    TrsvPack pack;
-    DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc, d_err;
-    int stage_bytes = 24576, nstages = 8;
+    TrsvLayout lay[2]; // [0] FP64 values (level_schedule), [1] FP32 (built on first use)
+    DevBuf d_err;
+    int stage_bytes = 24576;
     std::vector<std::unique_ptr<Solver>> solvers;
     int64_t device_bytes() const
     {
-        return (int64_t)(d_pack.bytes + d_chunks.bytes + d_blocks.bytes + d_ysc.bytes +
-                         d_zsc.bytes + d_err.bytes);
+        return lay[0].device_bytes() + lay[1].device_bytes() + (int64_t)d_err.bytes;
     }
     ~hec_precond_s();
 };
@@ -239,11 +256,30 @@ SpmvArgs spmv_args(const hec_matrix_s *A)
 
 int spmv_grid(const hec_matrix_s *A) { return grid_for((A->hec.n + kSpmvTile - 1) / kSpmvTile, 1, 8); }
 
-int run_spmv(const hec_matrix_s *A, SpmvArgs a, int mode, int ndot, cudaStream_t s)
+int run_spmv(const hec_matrix_s *A, SpmvArgs a, int mode, int ndot, cudaStream_t s,
+             bool fp32 = false)
 {
-    if (launch_spmv(a, mode, ndot, !A->hec.tail_rows.empty(), spmv_grid(A), s) != 0)
+    if (fp32) {
+        a.ell_val = A->ell_val32.p;
+        a.tail_val = A->tail_val32.p;
+    }
+    if (launch_spmv(a, mode, ndot, !A->hec.tail_rows.empty(), spmv_grid(A), s, fp32) != 0)
         return fail(HEC_ERR_INVALID, "no SpMV variant for mode %d ndot %d", mode, ndot);
     return check_launch("spmv");
+}
+
+// FP32 copies of the HEC values (slab and tail), for the FP32 inner solves.
+int ensure_f32(hec_matrix_s *A, cudaStream_t s)
+{
+    if (A->f32_ready)
+        return HEC_OK;
+    std::vector<float> ev(A->hec.ell_val.begin(), A->hec.ell_val.end());
+    std::vector<float> tv(A->hec.tail_val.begin(), A->hec.tail_val.end());
+    HEC_TRY(upload(A->ell_val32, ev, s));
+    HEC_TRY(upload(A->tail_val32, tv, s));
+    HEC_CK(cudaStreamSynchronize(s));
+    A->f32_ready = true;
+    return HEC_OK;
 }
 
 int vec_grid(int64_t n) { return grid_for(n, kThreads, 8); }
@@ -255,28 +291,56 @@ int run_vec(VecOp op, const VecArgs &a, cudaStream_t s)
     return check_launch("vector op");
 }
 
-TrsvArgs trsv_args(const hec_precond_s *M, long long spin)
+// Arguments of the triangular-solve kernel over layout L of M (L = M->lay[0]
+// for FP64 values, M->lay[1] for FP32).
+TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
 {
     TrsvArgs a{};
     a.nblocks = M->nblocks;
-    a.blocks = M->d_blocks.as<TrsvBlock>();
-    a.chunks = M->d_chunks.as<uint2>();
-    a.pack = M->d_pack.as<unsigned char>();
-    a.ysc = M->d_ysc.as<double>();
-    a.zsc = M->pack.zsz ? M->d_zsc.as<double>() : nullptr;
-    a.ring_mask = M->pack.ring_slots - 1;
+    a.blocks = L.d_blocks.as<TrsvBlock>();
+    a.chunks = L.d_chunks.as<uint2>();
+    a.pack = L.d_pack.as<unsigned char>();
+    a.ysc = L.d_ysc.p;
+    a.zsc = L.pack.zsz ? L.d_zsc.p : nullptr;
+    a.ring_mask = L.pack.ring_slots - 1;
     a.stage_bytes = M->stage_bytes;
-    a.nstages = M->nstages;
+    a.nstages = L.nstages;
     a.spin_limit = spin;
     a.err = M->d_err.as<int>();
     return a;
 }
 
-int run_trsv(const TrsvArgs &a, cudaStream_t s)
+int run_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false)
 {
-    if (launch_trsv(a, s) != 0)
+    if (launch_trsv(a, s, fp32) != 0)
         return fail(HEC_ERR_CUDA, "cannot configure the triangular-solve kernel");
     return check_launch("trsv");
+}
+
+// Pack, upload and size the scratch of the layout with vb-byte values.
+int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
+{
+    TrsvLayout &L = M->lay[idx];
+    if (L.built)
+        return HEC_OK;
+    L.vbytes = idx == 0 ? 8 : 4;
+    std::string msg;
+    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg);
+    if (rc != HEC_OK)
+        return fail(rc, "%s", msg.c_str());
+    if (!M->host_only) {
+        L.nstages = trsv_stages_for(M->stage_bytes, L.pack.ring_slots, L.vbytes);
+        HEC_TRY(upload(L.d_pack, L.pack.pack, s));
+        HEC_TRY(upload(L.d_chunks, L.pack.chunks, s));
+        HEC_TRY(upload(L.d_blocks, L.pack.blocks, s));
+        HEC_TRY(L.d_ysc.alloc(std::max<int64_t>(L.pack.ysz, 1) * L.vbytes, s));
+        HEC_TRY(L.d_zsc.alloc(std::max<int64_t>(L.pack.zsz, 1) * L.vbytes, s));
+        HEC_CK(cudaStreamSynchronize(s));
+        L.pack.pack.clear();
+        L.pack.pack.shrink_to_fit();
+    }
+    L.built = true;
+    return HEC_OK;
 }
 
 // Global reducer for the stand-alone vector calls (one per process).
@@ -300,14 +364,16 @@ int global_reducer(cudaStream_t s, RedScratch &out)
 struct Solver {
     uint64_t matrix_id = 0;
     int method = 0, restart = 0;
+    bool mixed = false; // GMRES with FP32 inner cycles and FP64 refinement
     int n = 0;
     int64_t ldv = 0;
-    DevBuf ws, st_buf;
+    DevBuf ws, ws32, st_buf;
     Reducer red;
     SolverState *st = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *r0 = nullptr, *p = nullptr, *ps = nullptr;
     double *v = nullptr, *s = nullptr, *ss = nullptr, *t = nullptr;
-    double *V = nullptr, *z = nullptr, *w = nullptr, *u = nullptr, *zu = nullptr;
+    // GMRES basis and step vectors: FP64, or FP32 when mixed
+    void *V = nullptr, *z = nullptr, *w = nullptr, *u = nullptr, *zu = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle h_while = 0, h_if = 0;
@@ -374,16 +440,18 @@ int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 // profilers that cannot see the kernels of a graph with conditional nodes,
 // directly on a stream with one host check per iteration (HEC_SOLVE_EAGER).
 
-int seq_precond(const hec_precond_s *M, Solver &S, const double *in, double *out, int from_j,
+// z = M^{-1} r inside a solve: FP64 layout, or the FP32 one for the inner
+// solves of the mixed-precision mode (in, out are then FP32 vectors).
+int seq_precond(const hec_precond_s *M, Solver &S, const void *in, void *out, int from_j,
                 cudaStream_t cs)
 {
-    TrsvArgs a = trsv_args(M, kDefaultSpin);
+    TrsvArgs a = trsv_args(M, M->lay[S.mixed ? 1 : 0], kDefaultSpin);
     a.r = in;
     a.z = out;
     a.st = S.st;
     a.r_from_j = from_j;
     a.ldv = S.ldv;
-    return run_trsv(a, cs);
+    return run_trsv(a, cs, S.mixed);
 }
 
 int seq_norm_b(Solver &S, cudaStream_t cs)
@@ -512,28 +580,35 @@ int seq_gmres_cycle(hec_matrix_s *A, Solver &S, cudaStream_t cs)
     VecArgs sc{};
     sc.n = S.n;
     sc.st = S.st;
-    sc.x = S.r;
-    sc.z = S.V; // column 0
+    sc.xv = S.r;
+    sc.zv = S.V; // column 0 (FP32 in the mixed mode: the inner solve's start vector)
     sc.guard = 2;
-    return run_vec(V_SCALE_ST, sc, cs);
+    if (launch_vec_typed(V_SCALE_ST, sc, false, S.mixed, vec_grid(S.n), cs) != 0)
+        return fail(HEC_ERR_INVALID, "bad typed vector op");
+    return check_launch("scale");
 }
 
 // One Arnoldi step: z = M^{-1} v_j, w = A z, two classical Gram-Schmidt
-// passes, h_{j+1,j} = ||w||, Givens update, v_{j+1} = w / h_{j+1,j}.
+// passes, h_{j+1,j} = ||w||, Givens update, v_{j+1} = w / h_{j+1,j}.  In the
+// mixed mode every vector of the step is FP32 (the Hessenberg column and the
+// Givens rotations stay FP64 in the solver state).
 int seq_gmres_step(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
 {
     const int n = S.n, m = S.restart;
+    const bool f = S.mixed;
     if (M) {
         HEC_TRY(seq_precond(M, S, S.V, S.z, 1, cs)); // z = M^{-1} v_j
     } else {
         VecArgs c{};
         c.n = n;
         c.st = S.st;
-        c.x = S.V;
+        c.xv = S.V;
         c.x_from_j = 1;
         c.ldv = S.ldv;
-        c.z = S.z;
-        HEC_TRY(run_vec(V_COPY, c, cs));
+        c.zv = S.z;
+        if (launch_vec_typed(V_COPY, c, f, f, vec_grid(n), cs) != 0)
+            return fail(HEC_ERR_INVALID, "bad typed vector op");
+        HEC_TRY(check_launch("copy"));
     }
     SpmvArgs w = spmv_args(A);
     w.st = S.st;
@@ -541,7 +616,7 @@ int seq_gmres_step(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs
     w.x = S.z;
     w.y_out = S.w;
     w.op = FIN_GMRES_W0;
-    HEC_TRY(run_spmv(A, w, 0, 1, cs)); // w = A z, ||w||
+    HEC_TRY(run_spmv(A, w, 0, 1, cs, f)); // w = A z, ||w||
     const int mdgrid = grid_for(n, kThreads, 2);
     BasisArgs h{};
     h.n = n;
@@ -553,37 +628,42 @@ int seq_gmres_step(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs
     h.red = S.red.r;
     h.st = S.st;
     h.op = FIN_GMRES_H1;
-    launch_multidot(h, mdgrid, cs); // h1 = V^T w
+    launch_multidot(h, mdgrid, cs, f); // h1 = V^T w
     HEC_TRY(check_launch("multidot"));
     BasisArgs up = h;
     up.coef = dev_field<double>(S.st, offsetof(SolverState, h1));
     up.wout = S.w;
-    launch_basis_update(up, false, vec_grid(n), cs); // w -= V h1
+    launch_basis_update(up, false, vec_grid(n), cs, f); // w -= V h1
     HEC_TRY(check_launch("basis update"));
     BasisArgs h2 = h;
     h2.op = FIN_GMRES_H2;
-    launch_multidot(h2, mdgrid, cs); // h2 = V^T w
+    launch_multidot(h2, mdgrid, cs, f); // h2 = V^T w
     HEC_TRY(check_launch("multidot"));
     BasisArgs up2 = h;
     up2.coef = dev_field<double>(S.st, offsetof(SolverState, h2));
     up2.wout = S.w;
     up2.op = FIN_GMRES_STEP;
-    launch_basis_update(up2, true, vec_grid(n), cs); // w -= V h2, ||w||, Givens
+    launch_basis_update(up2, true, vec_grid(n), cs, f); // w -= V h2, ||w||, Givens
     HEC_TRY(check_launch("basis update"));
     VecArgs sc{};
     sc.n = n;
     sc.st = S.st;
-    sc.x = S.w;
-    sc.z = S.V;
+    sc.xv = S.w;
+    sc.zv = S.V;
     sc.z_from_j = 1; // j already advanced when the cycle goes on
     sc.ldv = S.ldv;
     sc.guard = 1;
-    return run_vec(V_SCALE_ST, sc, cs); // v_{j+1} = w / h_{j+1,j}
+    if (launch_vec_typed(V_SCALE_ST, sc, f, f, vec_grid(n), cs) != 0) // v_{j+1} = w / h_{j+1,j}
+        return fail(HEC_ERR_INVALID, "bad typed vector op");
+    return check_launch("scale");
 }
 
-// Cycle end: y = R^{-1} g, x += M^{-1} V y, next cycle start.
+// Cycle end: y = R^{-1} g, x += M^{-1} V y, next cycle start.  In the mixed
+// mode the correction M^{-1} V y is FP32 and is added to the FP64 x; the
+// next cycle start recomputes the residual in FP64 (iterative refinement).
 int seq_gmres_cycle_end(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
 {
+    const bool f = S.mixed;
     if (launch_gmres_lsq(S.st, cs) != 0)
         return fail(HEC_ERR_CUDA, "lsq");
     HEC_TRY(check_launch("lsq"));
@@ -596,16 +676,18 @@ int seq_gmres_cycle_end(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream
     cb.coef = dev_field<double>(S.st, offsetof(SolverState, y));
     cb.wout = S.u;
     cb.st = S.st;
-    launch_basis_combine(cb, vec_grid(S.n), cs); // u = V y
+    launch_basis_combine(cb, vec_grid(S.n), cs, f); // u = V y
     HEC_TRY(check_launch("basis combine"));
     if (M)
         HEC_TRY(seq_precond(M, S, S.u, S.zu, 0, cs)); // zu = M^{-1} u
     VecArgs ax{};
     ax.n = S.n;
     ax.st = S.st;
-    ax.x = M ? S.zu : S.u;
-    ax.z = S.x;
-    HEC_TRY(run_vec(V_AXPY_ST1, ax, cs)); // x += zu
+    ax.xv = M ? S.zu : S.u;
+    ax.zv = S.x;
+    if (launch_vec_typed(V_AXPY_ST1, ax, f, false, vec_grid(S.n), cs) != 0) // x += zu
+        return fail(HEC_ERR_INVALID, "bad typed vector op");
+    HEC_TRY(check_launch("x update"));
     return seq_gmres_cycle(A, S, cs);
 }
 
@@ -709,12 +791,12 @@ int run_eager(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t s)
     return seq_exit(A, S, s);
 }
 
-int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cudaStream_t s,
-                Solver *&out)
+int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool mixed,
+                cudaStream_t s, Solver *&out)
 {
     auto &cache = M ? M->solvers : A->solvers;
     for (auto &p : cache)
-        if (p->matrix_id == A->id && p->method == method &&
+        if (p->matrix_id == A->id && p->method == method && p->mixed == mixed &&
             (method == HEC_BICGSTAB || p->restart == restart)) {
             out = p.get();
             return HEC_OK;
@@ -723,12 +805,18 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cuda
     S->matrix_id = A->id;
     S->method = method;
     S->restart = restart;
+    S->mixed = mixed;
     S->n = A->hec.n;
     S->ldv = ((int64_t)S->n + 31) / 32 * 32;
     const int64_t nv = S->ldv;
-    const int nvec = method == HEC_BICGSTAB ? 10 : (restart + 1) + 7;
+    const int nvec = method == HEC_BICGSTAB ? 10 : (mixed ? 3 : (restart + 1) + 7);
     HEC_TRY(S->ws.alloc((size_t)nvec * nv * sizeof(double), s));
     HEC_CK(cudaMemsetAsync(S->ws.p, 0, S->ws.bytes, s));
+    if (mixed) {
+        // FP32 basis and step vectors of the inner cycles
+        HEC_TRY(S->ws32.alloc((size_t)((restart + 1) + 4) * nv * sizeof(float), s));
+        HEC_CK(cudaMemsetAsync(S->ws32.p, 0, S->ws32.bytes, s));
+    }
     HEC_TRY(S->st_buf.alloc(sizeof(SolverState), s));
     HEC_CK(cudaMemsetAsync(S->st_buf.p, 0, sizeof(SolverState), s));
     HEC_TRY(S->red.init(s));
@@ -746,7 +834,7 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cuda
         S->s = vec(7);
         S->ss = vec(8);
         S->t = vec(9);
-    } else {
+    } else if (!mixed) {
         S->b = vec(0);
         S->x = vec(1);
         S->r = vec(2);
@@ -755,6 +843,17 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, cuda
         S->u = vec(5);
         S->zu = vec(6);
         S->V = vec(7);
+    } else {
+        S->b = vec(0);
+        S->x = vec(1);
+        S->r = vec(2);
+        float *b32 = S->ws32.as<float>();
+        auto vec32 = [&](int i) { return b32 + (int64_t)i * nv; };
+        S->z = vec32(0);
+        S->w = vec32(1);
+        S->u = vec32(2);
+        S->zu = vec32(3);
+        S->V = vec32(4);
     }
     HEC_CK(cudaStreamSynchronize(s));
     cudaStream_t cs;
@@ -931,6 +1030,29 @@ int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const d
     return run_spmv(A, a, mode, dots ? 2 : 0, (cudaStream_t)stream);
 }
 
+int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const float *y_in,
+                 float *y_out, void *stream)
+{
+    if (!A || !x || !y_out)
+        return fail(HEC_ERR_INVALID, "null argument");
+    if (A->host_only)
+        return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
+    if (beta != 0.0f && !y_in)
+        return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
+    if ((const void *)x == (const void *)y_out)
+        return fail(HEC_ERR_INVALID, "x and y_out must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    HEC_TRY(ensure_f32(A, s));
+    SpmvArgs a = spmv_args(A);
+    a.x = x;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.y_in = y_in;
+    a.y_out = y_out;
+    const int mode = (beta != 0.0f) ? 2 : (alpha != 1.0f ? 1 : 0);
+    return run_spmv(A, a, mode, 0, s, true);
+}
+
 int hec_axpby(int32_t n, double a, const double *x, double b, double *y, void *stream)
 {
     if (n < 0 || (n > 0 && (!x || !y)))
@@ -1060,22 +1182,11 @@ int level_schedule(hec_precond_t M, void *stream)
         return HEC_OK;
     cudaStream_t s = (cudaStream_t)stream;
     parallel_for(M->nblocks, [&](int b) { levels_block(M->blocks[b]); });
-    std::string msg;
-    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, M->pack, msg);
-    if (rc != HEC_OK)
-        return fail(rc, "%s", msg.c_str());
+    HEC_TRY(build_layout(M, 0, s));
     if (!M->host_only) {
-        M->nstages = trsv_stages_for(M->stage_bytes, M->pack.ring_slots);
-        HEC_TRY(upload(M->d_pack, M->pack.pack, s));
-        HEC_TRY(upload(M->d_chunks, M->pack.chunks, s));
-        HEC_TRY(upload(M->d_blocks, M->pack.blocks, s));
-        HEC_TRY(M->d_ysc.alloc(std::max<int64_t>(M->pack.ysz, 1) * sizeof(double), s));
-        HEC_TRY(M->d_zsc.alloc(std::max<int64_t>(M->pack.zsz, 1) * sizeof(double), s));
         HEC_TRY(M->d_err.alloc(sizeof(int), s));
         HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
         HEC_CK(cudaStreamSynchronize(s));
-        M->pack.pack.clear();
-        M->pack.pack.shrink_to_fit();
     }
     M->scheduled = true;
     return HEC_OK;
@@ -1096,10 +1207,11 @@ int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
         info->max_levels_L = std::max(info->max_levels_L, B.nlevL);
         info->max_levels_U = std::max(info->max_levels_U, B.nlevU);
     }
-    info->apply_bytes = M->scheduled ? M->pack.alg_bytes : 0;
+    info->apply_bytes = M->scheduled ? M->lay[0].pack.alg_bytes : 0;
     info->device_bytes = M->device_bytes();
-    info->ring_slots = M->scheduled ? M->pack.ring_slots : 0;
-    for (const TrsvBlock &T : M->pack.blocks)
+    info->ring_slots = M->scheduled ? M->lay[0].pack.ring_slots : 0;
+    info->apply_bytes_f32 = M->lay[1].built ? M->lay[1].pack.alg_bytes : 0;
+    for (const TrsvBlock &T : M->lay[0].pack.blocks)
         info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
     return HEC_OK;
 }
@@ -1167,10 +1279,27 @@ int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_
         return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
     if (!M->scheduled)
         return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    TrsvArgs a = trsv_args(M, spin_limit ? spin_limit : kDefaultSpin);
+    TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
     a.r = r;
     a.z = z;
     return run_trsv(a, (cudaStream_t)stream);
+}
+
+int hec_precond_apply_f32(hec_precond_t M, const float *r, float *z, int64_t spin_limit,
+                          void *stream)
+{
+    if (!M || !r || !z || (const void *)r == (const void *)z)
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (M->host_only)
+        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+    if (!M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    cudaStream_t s = (cudaStream_t)stream;
+    HEC_TRY(build_layout(M, 1, s));
+    TrsvArgs a = trsv_args(M, M->lay[1], spin_limit ? spin_limit : kDefaultSpin);
+    a.r = r;
+    a.z = z;
+    return run_trsv(a, s, true);
 }
 
 int hec_precond_status(hec_precond_t M, void *stream)
@@ -1216,9 +1345,17 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
         return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
     if (o.method == HEC_BICGSTAB)
         restart = 0;
+    const bool mixed = (o.flags & HEC_MIXED_FP32) != 0;
+    if (mixed && o.method != HEC_GMRES)
+        return fail(HEC_ERR_INVALID, "HEC_MIXED_FP32 needs method HEC_GMRES");
     cudaStream_t s = (cudaStream_t)stream;
+    if (mixed) {
+        HEC_TRY(ensure_f32(A, s));
+        if (M)
+            HEC_TRY(build_layout(M, 1, s));
+    }
     Solver *S = nullptr;
-    HEC_TRY(make_solver(A, M, o.method, restart, s, S));
+    HEC_TRY(make_solver(A, M, o.method, restart, mixed, s, S));
     const int n = S->n;
     const size_t vb = sizeof(double) * (size_t)n;
     // state header
@@ -1234,6 +1371,10 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
     h.h_if = S->h_if;
     const bool eager = (o.flags & HEC_SOLVE_EAGER) != 0;
     h.graph_mode = eager ? 0 : 1;
+    // an FP32 inner cycle also ends once it has reduced its FP32 residual by
+    // this factor: below it the FP32 arithmetic cannot be trusted, the FP64
+    // refinement (next cycle start) takes over
+    h.inner_rtol = mixed ? 1e-5 : 0.0;
     HEC_CK(cudaMemcpyAsync(S->st, &h, offsetof(SolverState, H), cudaMemcpyHostToDevice, s));
     int64_t h2d = 0, d2h = 0;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
@@ -1321,7 +1462,8 @@ extern "C" int hec_precond_apply_noalloc(hec_precond_t M, const double *r, doubl
         return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
     if (!M->scheduled)
         return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    const long long need = (long long)M->pack.ysz + (long long)M->pack.zsz;
+    const TrsvPack &P = M->lay[0].pack;
+    const long long need = (long long)P.ysz + (long long)P.zsz;
     if (need > kNoallocScratchDoubles)
         return fail(HEC_ERR_INVALID,
                     "preconditioner needs %lld scratch doubles; the static array of "
@@ -1331,10 +1473,10 @@ extern "C" int hec_precond_apply_noalloc(hec_precond_t M, const double *r, doubl
     HEC_TRY(noalloc_scratch(&scratch));
     // y and z scratch are written before they are read inside one launch, so
     // nothing in the shared array has to start at zero.
-    TrsvArgs a = trsv_args(M, spin_limit ? spin_limit : kDefaultSpin);
+    TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
     a.r = r;
     a.z = z;
     a.ysc = scratch;
-    a.zsc = M->pack.zsz ? scratch + M->pack.ysz : nullptr;
+    a.zsc = P.zsz ? scratch + P.ysz : nullptr;
     return run_trsv(a, (cudaStream_t)stream);
 }

@@ -150,7 +150,7 @@ void ras_blocks(const HostCSR &A, int nblocks, int overlap, std::vector<BlockFac
         B.own_hi = (int)((int64_t)(b + 1) * n / nblocks);
         std::vector<int> frontier, members;
         std::vector<char> in;
-        // grow by layers; membership kept in a hash-free sorted merge when small
+        // grow by breadth-first layers over the graph of A; membership is a byte map
         in.assign(n, 0);
         for (int i = B.own_lo; i < B.own_hi; ++i) {
             in[i] = 1;
@@ -364,18 +364,27 @@ inline int seg_stride(int w, int nrows)
 //   [16, 48)  width of every warp's segment (entries per row, uniform in the warp)
 //   [48, 80)  byte offset of every warp's segment
 //   [80, 96)  byte offsets of src, dst, dinv, and 0
-//   per warp w < nwarps: val[width_w][stride_w] (double), dep[width_w][stride_w] (int32)
-//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (double)
-// Row t of the chunk is handled by thread t (warp t / 32, lane t % 32).
-size_t chunk_bytes(const std::vector<int> &widths, int nrows, bool upass)
+//   per warp w < nwarps: val[width_w][stride_w] (value), dep[width_w][stride_w] (int32)
+//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (value)
+// Values are vb bytes: 8 (FP64 layout) or 4 (FP32 layout of the mixed-precision
+// mode).  Row t of the chunk is handled by thread t (warp t / 32, lane t % 32).
+size_t chunk_bytes(const std::vector<int> &widths, int nrows, bool upass, int vb)
 {
     size_t b = kChunkHeader;
     for (size_t w = 0; w < widths.size(); ++w)
-        b += (size_t)widths[w] * seg_stride((int)w, nrows) * 12;
+        b += (size_t)widths[w] * seg_stride((int)w, nrows) * (vb + 4);
     b += 4 * (size_t)r32(nrows);
     if (upass)
-        b += 12 * (size_t)r32(nrows);
+        b += (4 + vb) * (size_t)r32(nrows);
     return (b + 15) & ~(size_t)15;
+}
+
+inline void put_value(unsigned char *base, size_t i, double v, int vb)
+{
+    if (vb == 8)
+        reinterpret_cast<double *>(base)[i] = v;
+    else
+        reinterpret_cast<float *>(base)[i] = (float)v;
 }
 
 struct PassRows {
@@ -391,10 +400,14 @@ struct PassRows {
 // their L dependencies.  The other rows cannot influence the owned part of
 // the result and are left out of the device program (the result on the
 // owned rows is unchanged).
-int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int max_ring,
+int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int max_ring, int vb,
               TrsvPack &P, std::string &msg)
 {
     (void)n;
+    if (vb != 8 && vb != 4) {
+        msg = "value size must be 8 or 4 bytes";
+        return HEC_ERR_INVALID;
+    }
     const int nb = (int)Bs.size();
     P.pack.clear();
     P.chunks.clear();
@@ -481,7 +494,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                         const int j = q2 - q;
                         if (j % kWarpRows == 0)
                             widths.push_back(row_len(upass, pr.order[q2]));
-                        if (chunk_bytes(widths, j + 1, upass) > (size_t)stage_bytes) {
+                        if (chunk_bytes(widths, j + 1, upass, vb) > (size_t)stage_bytes) {
                             if (j % kWarpRows == 0)
                                 widths.pop_back();
                             break;
@@ -493,7 +506,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                         return;
                     }
                     const int nr = q2 - q, npad = r32(nr), nw = (int)widths.size();
-                    const size_t bytes = chunk_bytes(widths, nr, upass);
+                    const size_t bytes = chunk_bytes(widths, nr, upass, vb);
                     const size_t off = O.bytes.size();
                     O.bytes.resize(off + bytes, 0);
                     unsigned char *ch = O.bytes.data() + off;
@@ -502,7 +515,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                     for (int w = 0; w < nw; ++w) {
                         hdr[4 + w] = widths[w];
                         hdr[4 + kMaxWarps + w] = segoff;
-                        segoff += widths[w] * seg_stride(w, nr) * 12;
+                        segoff += widths[w] * seg_stride(w, nr) * (vb + 4);
                     }
                     hdr[4 + 2 * kMaxWarps + 0] = segoff;                  // src
                     hdr[4 + 2 * kMaxWarps + 1] = segoff + 4 * npad;       // dst
@@ -514,15 +527,15 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                     for (int w = 0; w < nw; ++w) {
                         const int wd = widths[w];
                         const int ls = seg_stride(w, nr);
-                        double *val = reinterpret_cast<double *>(seg);
-                        int *dep = reinterpret_cast<int *>(val + (size_t)wd * ls);
+                        unsigned char *val = seg;
+                        int *dep = reinterpret_cast<int *>(seg + (size_t)wd * ls * vb);
                         for (int lane = 0; lane < ls; ++lane) {
                             const int t = w * kWarpRows + lane;
                             if (t >= nr) {
                                 // rows past the chunk: never read, keep them valid
                                 for (int kk = 0; kk < wd; ++kk) {
                                     dep[(size_t)kk * ls + lane] = q;
-                                    val[(size_t)kk * ls + lane] = 0.0;
+                                    put_value(val, (size_t)kk * ls + lane, 0.0, vb);
                                 }
                                 continue;
                             }
@@ -539,27 +552,27 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                                 const int e = kk < len ? e0 + kk : e0;
                                 const int d = (upass ? posU : posL)[F.ci[e]];
                                 dep[(size_t)kk * ls + lane] = d;
-                                val[(size_t)kk * ls + lane] = kk < len ? F.va[e] : 0.0;
+                                put_value(val, (size_t)kk * ls + lane, kk < len ? F.va[e] : 0.0, vb);
                                 mindep = std::min(mindep, d);
                             }
                         }
-                        seg += (size_t)wd * ls * 12;
+                        seg += (size_t)wd * ls * (vb + 4);
                     }
                     src = reinterpret_cast<int *>(seg);
                     int *dst = src + npad;
-                    double *dinv = reinterpret_cast<double *>(dst + npad);
+                    unsigned char *dinv = reinterpret_cast<unsigned char *>(dst + npad);
                     for (int t = 0; t < nr; ++t) {
                         const int i = pr.order[q + t];
                         const int len = row_len(upass, i);
                         if (upass) {
                             src[t] = posL[i];
                             dst[t] = owned[i] ? B.rows[i] : -1;
-                            dinv[t] = 1.0 / F.va[B.diag[i]];
-                            O.alg += 12ll * len + 8 /*y*/ + 8 /*dinv*/ + 4 /*src*/ + 4 /*dst*/ +
-                                     (owned[i] ? 8 : 0);
+                            put_value(dinv, t, 1.0 / F.va[B.diag[i]], vb);
+                            O.alg += (4ll + vb) * len + vb /*y*/ + vb /*dinv*/ + 4 /*src*/ +
+                                     4 /*dst*/ + (owned[i] ? vb : 0);
                         } else {
                             src[t] = B.rows[i];
-                            O.alg += 12ll * len + 8 /*r*/ + 8 /*y*/ + 4 /*src*/;
+                            O.alg += (4ll + vb) * len + vb /*r*/ + vb /*y*/ + 4 /*src*/;
                         }
                     }
                     span = std::max(span, (q + nr) - mindep);

@@ -65,7 +65,8 @@ struct TrsvPack {
     int64_t alg_bytes = 0;      // algorithmic bytes of one apply
     int64_t rows_L = 0, rows_U = 0;
 };
-int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring,
+// vb: bytes per stored value, 8 (FP64 layout) or 4 (FP32 layout).
+int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,
               TrsvPack &out, std::string &msg);
 
 // Run f(i) for i in [0, count) on the host's cores.

@@ -12,20 +12,22 @@
 // inverted diagonal.  Rows of a level are sorted longest first and every warp
 // gets its own segment width, so little FP64 work is spent on padding.
 // Nothing on a level's critical path waits for HBM:
-//   - a producer warp streams chunks into a ring of shared-memory stages with
+//   - an issuer warp streams chunks into a ring of shared-memory stages with
 //     cp.async.bulk (the TMA bulk-copy engine) completing on mbarriers, S
 //     chunks ahead of the solving warps;
-//   - the same warp gathers the right-hand sides of a chunk (L pass: from r;
-//     U pass: from the L results, once the L pass is complete) with 8-byte
-//     cp.async completing on a per-stage mbarrier;
+//   - a gatherer warp, once a chunk has landed, gathers its right-hand sides
+//     (L pass: from r; U pass: from the L results, once the L pass is
+//     complete) with 4- or 8-byte cp.async completing on a per-stage
+//     mbarrier -- a separate warp, so that a stage the issuer waits to
+//     refill never holds back the gathers of chunks already in flight;
 //   - solved values of the last few levels live in a shared-memory ring
 //     indexed by level-major position (the setup checks that every
 //     dependency of a chunk lies within the ring's window; passes whose
 //     window does not fit read dependencies from the global scratch).
 // Levels are separated by a barrier of the solving warps only -- no
 // grid-wide synchronisation.  Every wait is bounded: a wait that runs out
-// sets the device error word, the producer waits (bounded) for its copies in
-// flight, and the CTA returns.
+// sets the device error word, one thread waits (bounded) for the copies still
+// in flight, and the CTA returns.
 #include "reduce.cuh"
 
 namespace hec {
@@ -79,19 +81,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N> __device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit)
 {
     for (long long it = 0; it < limit; ++it)
@@ -130,22 +119,30 @@ __device__ __forceinline__ int consumer_sync_or(int flag)
     return any;
 }
 
-// Shared memory of one CTA: S stages, S right-hand-side slots of kThreads
-// doubles, the ring, and 3 S + 1 mbarriers.
-size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots)
+// 4- or 8-byte asynchronous copy global -> shared (the right-hand-side gathers).
+template <int BYTES> __device__ __forceinline__ void cp_async_v(void *sdst, const void *gsrc)
 {
-    return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * sizeof(double) +
-           (size_t)ring_slots * sizeof(double) + (size_t)(3 * nstages + 1) * sizeof(uint64_t);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
+                 "n"(BYTES)
+                 : "memory");
 }
 
-int trsv_stages_for(int stage_bytes, int ring_slots)
+// Shared memory of one CTA: S stages, S right-hand-side slots of kThreads
+// values, the ring, and 3 S + 1 mbarriers.  vbytes: 8 (FP64) or 4 (FP32).
+size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
+{
+    return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * vbytes +
+           (size_t)ring_slots * vbytes + (size_t)(3 * nstages + 1) * sizeof(uint64_t);
+}
+
+int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 227 * 1024;
     int S = 8;
-    while (S > 3 && trsv_smem_bytes(stage_bytes, S, ring_slots) > (size_t)optin)
+    while (S > 3 && trsv_smem_bytes(stage_bytes, S, ring_slots, vbytes) > (size_t)optin)
         --S;
     return S;
 }
@@ -154,14 +151,15 @@ int trsv_stages_for(int stage_bytes, int ring_slots)
 // in microseconds, this only guarantees that the CTA never waits forever.
 constexpr long long kDrainPolls = 1ll << 24;
 
-// A chunk in shared memory (layout written by the setup's packer):
+// A chunk in shared memory (layout written by the setup's packer; T is the
+// value type, double or float):
 //   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass)
 //   [16, 48)  width of every warp's segment
 //   [48, 80)  byte offset of every warp's segment
 //   [80, 96)  byte offsets of src, dst, dinv
-//   per warp w < nwarps: val[width_w][stride_w] (double), dep[width_w][stride_w] (int32),
+//   per warp w < nwarps: val[width_w][stride_w] (T), dep[width_w][stride_w] (int32),
 //     stride_w = 32 for a full warp, the row count rounded up to 4 for the last one
-//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)], dinv[r32(nrows)] (double)
+//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (T)
 constexpr int kWarpRows = 32;
 constexpr int kMaxWarps = kThreads / kWarpRows;
 
@@ -171,16 +169,16 @@ __device__ __forceinline__ int seg_stride(int w, int nrows)
     return left >= kWarpRows ? kWarpRows : (left + 3) & ~3;
 }
 
-struct ChunkView {
+template <class T> struct ChunkView {
     int nrows, nwarps, base;
     bool upass;
     const int *src, *dst;
-    const double *dinv;
+    const T *dinv;
 };
 
-__device__ __forceinline__ ChunkView view_chunk(const unsigned char *ch)
+template <class T> __device__ __forceinline__ ChunkView<T> view_chunk(const unsigned char *ch)
 {
-    ChunkView v;
+    ChunkView<T> v;
     const int4 hdr = *reinterpret_cast<const int4 *>(ch);
     const int4 off = *reinterpret_cast<const int4 *>(ch + 16 + 8 * kMaxWarps);
     v.nrows = hdr.x;
@@ -189,41 +187,42 @@ __device__ __forceinline__ ChunkView view_chunk(const unsigned char *ch)
     v.upass = (hdr.w & 1) != 0;
     v.src = reinterpret_cast<const int *>(ch + off.x);
     v.dst = reinterpret_cast<const int *>(ch + off.y);
-    v.dinv = reinterpret_cast<const double *>(ch + off.z);
+    v.dinv = reinterpret_cast<const T *>(ch + off.z);
     return v;
 }
 
 // The segment of warp w: entry k of lane l at val[k * stride + l], dep[k * stride + l].
-struct Segment {
+template <class T> struct Segment {
     int width, stride;
-    const double *val;
+    const T *val;
     const int *dep;
 };
 
-__device__ __forceinline__ Segment warp_segment(const unsigned char *ch, int nrows, int w)
+template <class T>
+__device__ __forceinline__ Segment<T> warp_segment(const unsigned char *ch, int nrows, int w)
 {
     const int *hdr = reinterpret_cast<const int *>(ch);
-    Segment g;
+    Segment<T> g;
     g.width = hdr[4 + w];
     g.stride = seg_stride(w, nrows);
-    g.val = reinterpret_cast<const double *>(ch + hdr[4 + kMaxWarps + w]);
+    g.val = reinterpret_cast<const T *>(ch + hdr[4 + kMaxWarps + w]);
     g.dep = reinterpret_cast<const int *>(g.val + (size_t)g.width * g.stride);
     return g;
 }
 
 // s - sum_k val[k] * y[dep[k]] for one row in ascending column order, width W
 // known at compile time: every shared-memory load of the row is issued before
-// the first multiply.  One accumulator: FP64 throughput, not the 64-cycle
-// latency of a dependent DFMA, bounds a level once several warps are busy,
-// and a second accumulator would cost one more FP64 add per row.
-template <int W, bool RING>
-__device__ __forceinline__ double row_solve(const Segment &g, int lane, const double *ring, int mask,
-                                            const double *gdep, double s)
+// the first multiply.  One accumulator: in FP64 the pipe's throughput, not
+// the 64-cycle latency of a dependent DFMA, bounds a level once several warps
+// are busy, and a second accumulator would cost one more FP64 add per row.
+template <int W, bool RING, class T>
+__device__ __forceinline__ T row_solve(const Segment<T> &g, int lane, const T *ring, int mask,
+                                       const T *gdep, T s)
 {
     if constexpr (W == 0) {
         return s;
     } else {
-        double l[W], y[W];
+        T l[W], y[W];
         int d[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -240,9 +239,9 @@ __device__ __forceinline__ double row_solve(const Segment &g, int lane, const do
     }
 }
 
-template <bool RING>
-__device__ __forceinline__ double row_solve_any(const Segment &g, int lane, const double *ring,
-                                                int mask, const double *gdep, double s)
+template <bool RING, class T>
+__device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const T *ring, int mask,
+                                           const T *gdep, T s)
 {
     switch (g.width) {
     case 0: return s;
@@ -258,7 +257,7 @@ __device__ __forceinline__ double row_solve_any(const Segment &g, int lane, cons
         // wide rows: loads in blocks of 8 entries
         int k = 0;
         for (; k + 8 <= g.width; k += 8) {
-            double l[8], y[8];
+            T l[8], y[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 l[q] = g.val[(k + q) * g.stride + lane];
@@ -279,32 +278,35 @@ __device__ __forceinline__ double row_solve_any(const Segment &g, int lane, cons
 }
 
 // Warp-specialised CTA: warps 0-7 solve rows (one row per thread per chunk),
-// warp 8 feeds them.  Per chunk c in stage s = c mod S:
-//   producer: wait empty[s] (chunk c - S released) -> arm full[s] with the
-//             chunk's byte count -> cp.async.bulk the chunk; then, G chunks
-//             behind, gather the right-hand side of chunk c - G into slot s'
-//             with 8-byte cp.async (a U chunk waits for ldone first: its
-//             right-hand side is the L pass's output); ready[s'] completes
+// warps 8 and 9 feed them.  Per chunk c in stage s = c mod S:
+//   issuer (warp 8): wait empty[s] (chunk c - S released) -> arm full[s] with
+//             the chunk's byte count -> cp.async.bulk the chunk;
+//   gatherer (warp 9): wait full[s] -> gather the chunk's right-hand sides
+//             into slot s with cp.async (a U chunk waits for ldone first: its
+//             right-hand side is the L pass's output); ready[s] completes
 //             when the 32 lanes' gathers have landed (cp.async arrivals) and
 //             lane 0 -- which has seen the chunk's data land -- has arrived,
 //             so one barrier covers both;
 //   consumers: wait ready[s] -> solve -> consumer barrier ->
 //             one thread releases empty[s] (and ldone after the last L chunk).
-__global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
+// T = double: the FP64 path; T = float: the FP32 inner solves of the
+// mixed-precision mode (FP32 factors, products and accumulation).
+template <class T>
+__global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     count_launch(a.st);
     if (a.st && a.st->skip)
         return;
-    const double *r = a.r;
+    const T *r = reinterpret_cast<const T *>(a.r);
     if (a.r_from_j)
         r += (int64_t)a.st->j * a.ldv;
 
     const TrsvBlock blk = a.blocks[blockIdx.x];
     const int S = a.nstages;
     unsigned char *stages = smem;
-    double *rhs = reinterpret_cast<double *>(smem + (size_t)S * a.stage_bytes);
-    double *ring = rhs + (size_t)S * kThreads;
+    T *rhs = reinterpret_cast<T *>(smem + (size_t)S * a.stage_bytes);
+    T *ring = rhs + (size_t)S * kThreads;
     const int mask = a.ring_mask;
     uint64_t *full = reinterpret_cast<uint64_t *>(ring + mask + 1);
     uint64_t *empty = full + S;
@@ -315,9 +317,10 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
     const bool stall_test = a.spin_limit < 0;       // fault injection: nothing is issued
     const long long limit = stall_test ? -a.spin_limit : a.spin_limit;
     const uint2 *chunks = a.chunks + blk.chunk_begin;
-    const double *ysc = a.ysc + blk.yoff;
-    double *ysc_w = a.ysc + blk.yoff;
-    double *zsc = a.zsc ? a.zsc + blk.zoff : nullptr;
+    T *ysc_w = reinterpret_cast<T *>(a.ysc) + blk.yoff;
+    const T *ysc = ysc_w;
+    T *zsc = a.zsc ? reinterpret_cast<T *>(a.zsc) + blk.zoff : nullptr;
+    T *z = reinterpret_cast<T *>(a.z);
     const int t = threadIdx.x;
 
     if (t == 0) {
@@ -330,81 +333,73 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
         fence_mbar_init();
     }
     for (int i = t; i <= mask; i += blockDim.x)
-        ring[i] = 0.0;
+        ring[i] = T(0);
     __syncthreads();
 
-    if (t >= kThreads) {
-        // ------------------------------------------------------------ producer warp
-        if (stall_test)
-            return;
+    // shared state of the two feeding warps (written before the final barrier)
+    __shared__ int s_issued;
+    if (t == 0)
+        s_issued = 0;
+    __syncthreads();
+    int failed = 0;
+
+    if (t >= kThreads && t < kThreads + 32 && !stall_test) {
+        // ------------------------------------------------------------ issuer warp
+        // streams chunk c into stage c mod S once the consumers released it
         const int lane = t - kThreads;
-        const int G = S / 2; // right-hand-side gather lag behind the chunk stream
         uint2 win = make_uint2(0, 0);
         int wbase = -64;
-        int issued = 0, failed = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int s = c % S;
+            if (c >= wbase + 32) { // 32 descriptors per warp-wide load
+                wbase = c;
+                win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
+            }
+            const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
+            const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
+            // every wait decision is a warp vote: the lanes must stay converged
+            if (c >= S &&
+                __any_sync(0xffffffffu,
+                           !bounded_wait(&empty[s], (uint32_t)((c / S) - 1) & 1u, limit))) {
+                failed = 1;
+                break;
+            }
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&full[s], bytes);
+                bulk_g2s(stages + (size_t)s * a.stage_bytes, a.pack + (size_t)off16 * 16, bytes,
+                         &full[s]);
+                s_issued = c + 1;
+            }
+        }
+    } else if (t >= kThreads + 32 && !stall_test) {
+        // ------------------------------------------------------------ gatherer warp
+        // follows the chunks as they land: gathers each one's right-hand sides
+        const int lane = t - kThreads - 32;
         bool ldone_seen = false;
-        for (int c = 0; c < nch + G && !failed; ++c) {
-            if (c < nch) {
-                const int s = c % S;
-                if (c >= wbase + 32) { // 32 descriptors per warp-wide load
-                    wbase = c;
-                    win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
-                }
-                const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
-                const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
-                // every wait decision is a warp vote: the lanes must stay converged
-                if (c >= S &&
-                    __any_sync(0xffffffffu,
-                               !bounded_wait(&empty[s], (uint32_t)((c / S) - 1) & 1u, limit))) {
+        for (int g = 0; g < nch; ++g) {
+            const int sg = g % S;
+            if (__any_sync(0xffffffffu, !bounded_wait(&full[sg], (uint32_t)(g / S) & 1u, limit))) {
+                failed = 1;
+                break;
+            }
+            const ChunkView<T> v = view_chunk<T>(stages + (size_t)sg * a.stage_bytes);
+            if (v.upass && !ldone_seen) {
+                if (__any_sync(0xffffffffu, !bounded_wait(ldone, 0u, limit))) {
                     failed = 1;
                     break;
                 }
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(stages + (size_t)s * a.stage_bytes, a.pack + (size_t)off16 * 16,
-                             bytes, &full[s]);
-                }
-                issued = c + 1;
+                ldone_seen = true;
             }
-            const int g = c - G;
-            if (g >= 0 && g < nch) {
-                const int sg = g % S;
-                if (__any_sync(0xffffffffu, !bounded_wait(&full[sg], (uint32_t)(g / S) & 1u, limit))) {
-                    failed = 1;
-                    break;
-                }
-                const ChunkView v = view_chunk(stages + (size_t)sg * a.stage_bytes);
-                if (v.upass && !ldone_seen) {
-                    if (__any_sync(0xffffffffu, !bounded_wait(ldone, 0u, limit))) {
-                        failed = 1;
-                        break;
-                    }
-                    ldone_seen = true;
-                }
-                double *slot = rhs + (size_t)sg * kThreads;
-                for (int i = lane; i < v.nrows; i += 32)
-                    cp_async8(&slot[i], v.upass ? ysc + v.src[i] : r + v.src[i]);
-                cp_async_arrive_noinc(&ready[sg]); // when this lane's gathers land
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(&ready[sg]); // the chunk's data has landed (seen above)
-            }
+            T *slot = rhs + (size_t)sg * kThreads;
+            for (int i = lane; i < v.nrows; i += 32)
+                cp_async_v<sizeof(T)>(&slot[i], v.upass ? ysc + v.src[i] : r + v.src[i]);
+            cp_async_arrive_noinc(&ready[sg]); // when this lane's gathers land
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&ready[sg]); // the chunk's data has landed (seen above)
         }
         cp_async_wait_all();
-        if (failed) {
-            // the last S chunks issued may still be in flight
-            if (lane == 0) {
-                const int first = issued - S > 0 ? issued - S : 0;
-                for (int c = first; c < issued; ++c)
-                    bounded_wait(&full[c % S], (uint32_t)(c / S) & 1u, kDrainPolls);
-                atomicExch(a.err, HEC_ERR_TIMEOUT);
-                if (a.st)
-                    a.st->err = HEC_ERR_TIMEOUT;
-            }
-        }
-        return;
-    }
-
+    } else if (t < kThreads) {
     // ---------------------------------------------------------------- consumer warps
     int err = 0;
     int s = 0;
@@ -414,19 +409,19 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
             err = 1;
         // results leave the critical path: global stores are issued after the
         // stage is released, so the release does not wait for them
-        double out = 0.0;
-        double *gout = nullptr;
+        T out = T(0);
+        T *gout = nullptr;
         if (!err) {
             const unsigned char *ch = stages + (size_t)s * a.stage_bytes;
-            const ChunkView v = view_chunk(ch);
+            const ChunkView<T> v = view_chunk<T>(ch);
             if (t < v.nrows) {
                 const bool rm = v.upass ? blk.ring_U : blk.ring_L;
-                const double *gdep = v.upass ? zsc : ysc;
-                const Segment g = warp_segment(ch, v.nrows, t / kWarpRows);
+                const T *gdep = v.upass ? zsc : ysc;
+                const Segment<T> g = warp_segment<T>(ch, v.nrows, t / kWarpRows);
                 const int lane = t % kWarpRows;
-                double sacc = rhs[(size_t)s * kThreads + t];
-                sacc = rm ? row_solve_any<true>(g, lane, ring, mask, gdep, sacc)
-                          : row_solve_any<false>(g, lane, ring, mask, gdep, sacc);
+                T sacc = rhs[(size_t)s * kThreads + t];
+                sacc = rm ? row_solve_any<true, T>(g, lane, ring, mask, gdep, sacc)
+                          : row_solve_any<false, T>(g, lane, ring, mask, gdep, sacc);
                 const int pos = v.base + t;
                 if (v.upass) {
                     sacc *= v.dinv[t];
@@ -436,7 +431,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
                         zsc[pos] = sacc; // read by later levels of this pass
                     const int d = v.dst[t];
                     if (d >= 0)
-                        gout = a.z + d;
+                        gout = z + d;
                 } else {
                     if (rm) {
                         ring[pos & mask] = sacc;
@@ -449,19 +444,15 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
             }
         }
         if (consumer_sync_or(err)) {
-            if (t == 0) {
-                atomicExch(a.err, HEC_ERR_TIMEOUT);
-                if (a.st)
-                    a.st->err = HEC_ERR_TIMEOUT;
-            }
-            return; // the producer's own waits run out and drain its copies
+            failed = 1; // the feeding warps' own waits run out
+            break;
         }
         if (t == 0)
             mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
         if (gout)
             *gout = out;
         if (c == nL - 1) {
-            // every y of the L pass is written before the producer gathers
+            // every y of the L pass is written before the gatherer reads
             // the U pass's right-hand sides from them
             consumer_sync_or(0);
             if (t == 0)
@@ -472,17 +463,36 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_ras(TrsvArgs a)
             par ^= 1u;
         }
     }
+    }
+    // every role has left its loop: drain the copies still in flight, report
+    __syncthreads();
+    if (t == kThreads) {
+        const int issued = s_issued;
+        const int first = issued - S > 0 ? issued - S : 0;
+        for (int c = first; c < issued; ++c)
+            bounded_wait(&full[c % S], (uint32_t)(c / S) & 1u, kDrainPolls);
+    }
+    if (failed) {
+        atomicExch(a.err, HEC_ERR_TIMEOUT);
+        if (a.st)
+            a.st->err = HEC_ERR_TIMEOUT;
+    }
 }
 
-int launch_trsv(const TrsvArgs &a, cudaStream_t s)
+template <class T> static int launch_t(const TrsvArgs &a, cudaStream_t s)
 {
-    const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_trsv_ras, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1, sizeof(T));
+    cudaError_t e = cudaFuncSetAttribute(k_trsv_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess)
         return -1;
-    k_trsv_ras<<<a.nblocks, kThreads + 32, smem, s>>>(a);
+    k_trsv_ras<T><<<a.nblocks, kThreads + 64, smem, s>>>(a);
     return 0;
+}
+
+int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32)
+{
+    return fp32 ? launch_t<float>(a, s) : launch_t<double>(a, s);
 }
 
 } // namespace hec

@@ -123,13 +123,64 @@ int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s)
     return -1;
 }
 
+// ------------------------------------------------------------------ typed vector kernels
+
+// V_COPY, V_SCALE_ST, V_AXPY_ST1 with element types TX (x) and TZ (z).
+template <int OP, class TX, class TZ> __global__ void __launch_bounds__(kThreads) k_vec_typed(VecArgs a)
+{
+    count_launch(a.st);
+    SolverState *st = a.st;
+    if ((a.guard == 1 && st->cycle_end) || (a.guard == 2 && st->done))
+        return;
+    const TX *x = reinterpret_cast<const TX *>(a.xv);
+    TZ *z = reinterpret_cast<TZ *>(a.zv);
+    if (a.x_from_j)
+        x += (int64_t)st->j * a.ldv;
+    if (a.z_from_j)
+        z += (int64_t)st->j * a.ldv;
+    const double sc = (OP == V_SCALE_ST) ? st->scale : 1.0;
+    const int stride = gridDim.x * kThreads;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
+        if (OP == V_COPY)
+            z[i] = TZ(x[i]);
+        else if (OP == V_SCALE_ST)
+            z[i] = TZ(sc * double(x[i]));
+        else if (OP == V_AXPY_ST1)
+            z[i] = z[i] + TZ(x[i]);
+    }
+}
+
+template <int OP> static int launch_typed_op(const VecArgs &a, bool x32, bool z32, int grid, cudaStream_t s)
+{
+    if (x32 && z32)
+        k_vec_typed<OP, float, float><<<grid, kThreads, 0, s>>>(a);
+    else if (x32)
+        k_vec_typed<OP, float, double><<<grid, kThreads, 0, s>>>(a);
+    else if (z32)
+        k_vec_typed<OP, double, float><<<grid, kThreads, 0, s>>>(a);
+    else
+        k_vec_typed<OP, double, double><<<grid, kThreads, 0, s>>>(a);
+    return 0;
+}
+
+int launch_vec_typed(VecOp vop, const VecArgs &a, bool x32, bool z32, int grid, cudaStream_t s)
+{
+    switch (vop) {
+    case V_COPY: return launch_typed_op<V_COPY>(a, x32, z32, grid, s);
+    case V_SCALE_ST: return launch_typed_op<V_SCALE_ST>(a, x32, z32, grid, s);
+    case V_AXPY_ST1: return launch_typed_op<V_AXPY_ST1>(a, x32, z32, grid, s);
+    default: return -1;
+    }
+}
+
 // ------------------------------------------------------------------ GMRES basis kernels
 
 constexpr int kGroup = 8; // basis vectors per CTA in a projection
 
 // h[i] = (V_i, w), i < k.  Grid (row blocks, vector groups); every CTA keeps
-// kGroup running sums per thread and reduces them once at the end.
-__global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
+// kGroup running sums per thread (in T) and reduces them once at the end (in
+// FP64, fixed order).
+template <class T> __global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
 {
     count_launch(a.st);
     int k = a.k;
@@ -137,19 +188,21 @@ __global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
         k = a.st->j + 1;
     else if (a.k_from_st == 2)
         k = a.st->jend;
+    const T *V = reinterpret_cast<const T *>(a.V);
+    const T *w = reinterpret_cast<const T *>(a.w);
     const int g0 = blockIdx.y * kGroup;
-    double acc[kGroup];
+    T acc[kGroup];
 #pragma unroll
     for (int q = 0; q < kGroup; ++q)
-        acc[q] = 0.0;
+        acc[q] = T(0);
     if (g0 < k) {
         const int stride = gridDim.x * kThreads;
         for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
-            const double wi = a.w[i];
+            const T wi = w[i];
 #pragma unroll
             for (int q = 0; q < kGroup; ++q)
                 if (g0 + q < k)
-                    acc[q] = fma(a.V[(int64_t)(g0 + q) * a.ldv + i], wi, acc[q]);
+                    acc[q] = fma(V[(int64_t)(g0 + q) * a.ldv + i], wi, acc[q]);
         }
     }
     // block reduction of the kGroup sums
@@ -158,15 +211,15 @@ __global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kGroup; ++q) {
-        double t = warp_sum(acc[q]);
+        double t = warp_sum(double(acc[q]));
         if (lane == 0)
             sh[q][wid] = t;
     }
     __syncthreads();
     if (threadIdx.x < kGroup) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w)
-            t += sh[threadIdx.x][w];
+        for (int ww = 0; ww < kThreads / 32; ++ww)
+            t += sh[threadIdx.x][ww];
         // partials layout: [vector][row block]
         const int q = g0 + threadIdx.x;
         if (q < k)
@@ -197,17 +250,19 @@ __global__ void __launch_bounds__(kThreads) k_multidot(BasisArgs a)
         *a.red.ticket = 0u;
 }
 
-int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s)
+int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s, bool fp32)
 {
     // a.k is the number of vectors, or an upper bound of it when k_from_st
     dim3 g(grid, (a.k + kGroup - 1) / kGroup);
-    k_multidot<<<g, kThreads, 0, s>>>(a);
+    if (fp32)
+        k_multidot<float><<<g, kThreads, 0, s>>>(a);
+    else
+        k_multidot<double><<<g, kThreads, 0, s>>>(a);
     return 0;
 }
 
 // wout = w - sum_{i<k} coef[i] V_i, optionally with (wout, wout) reduced.
-template <bool NORM>
-__global__ void __launch_bounds__(kThreads) k_basis_update(BasisArgs a)
+template <bool NORM, class T> __global__ void __launch_bounds__(kThreads) k_basis_update(BasisArgs a)
 {
     count_launch(a.st);
     int k = a.k;
@@ -215,37 +270,47 @@ __global__ void __launch_bounds__(kThreads) k_basis_update(BasisArgs a)
         k = a.st->j + 1;
     else if (a.k_from_st == 2)
         k = a.st->jend;
-    __shared__ double sc[kMaxRestart + 1];
+    const T *V = reinterpret_cast<const T *>(a.V);
+    const T *w = reinterpret_cast<const T *>(a.w);
+    T *wout = reinterpret_cast<T *>(a.wout);
+    __shared__ T sc[kMaxRestart + 1];
     for (int q = threadIdx.x; q < k; q += kThreads)
-        sc[q] = a.coef[q];
+        sc[q] = T(a.coef[q]);
     __syncthreads();
-    double acc = 0.0;
+    T acc = T(0);
     const int stride = gridDim.x * kThreads;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
-        double t = a.w[i];
+        T t = w[i];
         for (int q = 0; q < k; ++q)
-            t = fma(-sc[q], a.V[(int64_t)q * a.ldv + i], t);
-        a.wout[i] = t;
+            t = fma(-sc[q], V[(int64_t)q * a.ldv + i], t);
+        wout[i] = t;
         if (NORM)
             acc = fma(t, t, acc);
     }
     if (NORM) {
-        double v[1] = {acc};
+        double v[1] = {double(acc)};
         reduce_and_finalize<1>(v, a.red, a.op, a.result, a.st);
     }
 }
 
-int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s)
+int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s, bool fp32)
 {
-    if (with_norm)
-        k_basis_update<true><<<grid, kThreads, 0, s>>>(a);
-    else
-        k_basis_update<false><<<grid, kThreads, 0, s>>>(a);
+    if (with_norm) {
+        if (fp32)
+            k_basis_update<true, float><<<grid, kThreads, 0, s>>>(a);
+        else
+            k_basis_update<true, double><<<grid, kThreads, 0, s>>>(a);
+    } else {
+        if (fp32)
+            k_basis_update<false, float><<<grid, kThreads, 0, s>>>(a);
+        else
+            k_basis_update<false, double><<<grid, kThreads, 0, s>>>(a);
+    }
     return 0;
 }
 
 // wout = sum_{i<k} coef[i] V_i
-__global__ void __launch_bounds__(kThreads) k_basis_combine(BasisArgs a)
+template <class T> __global__ void __launch_bounds__(kThreads) k_basis_combine(BasisArgs a)
 {
     count_launch(a.st);
     int k = a.k;
@@ -253,22 +318,27 @@ __global__ void __launch_bounds__(kThreads) k_basis_combine(BasisArgs a)
         k = a.st->j + 1;
     else if (a.k_from_st == 2)
         k = a.st->jend;
-    __shared__ double sc[kMaxRestart + 1];
+    const T *V = reinterpret_cast<const T *>(a.V);
+    T *wout = reinterpret_cast<T *>(a.wout);
+    __shared__ T sc[kMaxRestart + 1];
     for (int q = threadIdx.x; q < k; q += kThreads)
-        sc[q] = a.coef[q];
+        sc[q] = T(a.coef[q]);
     __syncthreads();
     const int stride = gridDim.x * kThreads;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += stride) {
-        double t = 0.0;
+        T t = T(0);
         for (int q = 0; q < k; ++q)
-            t = fma(sc[q], a.V[(int64_t)q * a.ldv + i], t);
-        a.wout[i] = t;
+            t = fma(sc[q], V[(int64_t)q * a.ldv + i], t);
+        wout[i] = t;
     }
 }
 
-int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s)
+int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s, bool fp32)
 {
-    k_basis_combine<<<grid, kThreads, 0, s>>>(a);
+    if (fp32)
+        k_basis_combine<float><<<grid, kThreads, 0, s>>>(a);
+    else
+        k_basis_combine<double><<<grid, kThreads, 0, s>>>(a);
     return 0;
 }
 

@@ -39,6 +39,7 @@ struct __align__(16) SolverState {
     int maxit, restart, method, flags;
     // scalars
     double bnorm, rho, rho_prev, alpha, omega, scale, w0norm, est, rel_resid;
+    double inner_rtol, beta_cycle; // mixed precision: inner cycle tolerance, cycle start ||r||
     double dots[kMaxDots];
     int iters, restarts, status, done;
     int skip, s_conv, zero_x, j;
@@ -59,16 +60,18 @@ struct RedScratch {
 };
 
 // ------------------------------------------------------------------ SpMV
+// Values and vectors are FP64, or FP32 when launched with fp32 = true (the
+// inner solves of the mixed-precision mode); indices are always int32.
 struct SpmvArgs {
     int n, ld, K, ntiles;
     const int *ell_col;
-    const double *ell_val;
+    const void *ell_val;
     const int *tail_rows, *tail_ptr, *tail_col, *tile_tail;
-    const double *tail_val;
-    const double *x;
-    const double *y_in;
-    double *y_out;
-    const double *w0, *w1; // dot partners; nullptr = y_out itself
+    const void *tail_val;
+    const void *x;
+    const void *y_in;
+    void *y_out;
+    const void *w0, *w1;   // dot partners; nullptr = y_out itself
     double alpha, beta;
     RedScratch red;
     double *result;        // FIN_STORE destination (device)
@@ -77,7 +80,7 @@ struct SpmvArgs {
 };
 // mode: 0 y = s, 1 y = alpha s, 2 y = alpha s + beta y_in
 int launch_spmv(const SpmvArgs &a, int mode, int ndot, bool has_tail, int grid,
-                cudaStream_t s);
+                cudaStream_t s, bool fp32 = false);
 
 // ------------------------------------------------------------------ vector kernels
 enum VecOp : int {
@@ -107,30 +110,39 @@ struct VecArgs {
     int z_from_j;
     int64_t ldv;
     int guard;               // 1: no-op if st->cycle_end, 2: no-op if st->done
+    const void *xv;          // typed operands of launch_vec_typed
+    void *zv;
 };
 int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s);
+// V_COPY, V_SCALE_ST and V_AXPY_ST1 on a.xv / a.zv with element types chosen
+// by x32 / z32 (FP32 if set, else FP64): the FP32 basis of the mixed-precision
+// mode, the FP64 -> FP32 start vector and the FP32 -> FP64 correction.
+int launch_vec_typed(VecOp vop, const VecArgs &a, bool x32, bool z32, int grid, cudaStream_t s);
 
 // GMRES Arnoldi: projections and basis combinations (column-major basis V,
 // leading dimension ldv; k vectors = st->j + 1 when k_from_st).
+// V, w, wout: FP64, or FP32 when launched with fp32 = true (coefficients and
+// reduced values stay FP64).
 struct BasisArgs {
     int n;
     int k;                 // number of basis vectors (if !k_from_st)
     int k_from_st;         // 1: k = st->j + 1; 2: k = st->jend
-    const double *V;
+    const void *V;
     int64_t ldv;
-    const double *w;       // vector projected / updated
-    double *wout;          // updated vector
+    const void *w;         // vector projected / updated
+    void *wout;            // updated vector
     const double *coef;    // coefficients (device), e.g. st->h1
     RedScratch red;
     double *result;
     int op;
     SolverState *st;
 };
-int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s);
+int launch_multidot(const BasisArgs &a, int grid, cudaStream_t s, bool fp32 = false);
 // wout = w - sum_i coef[i] V_i  (with_norm: + fused (wout, wout) -> op)
-int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s);
+int launch_basis_update(const BasisArgs &a, bool with_norm, int grid, cudaStream_t s,
+                        bool fp32 = false);
 // wout = sum_i coef[i] V_i
-int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s);
+int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s, bool fp32 = false);
 
 // ------------------------------------------------------------------ TRSV (RAS)
 struct TrsvBlock {
@@ -144,9 +156,9 @@ struct TrsvArgs {
     const TrsvBlock *blocks;
     const uint2 *chunks;        // {offset in 16-byte units, bytes}
     const unsigned char *pack;  // packed chunk data
-    const double *r;
-    double *z;
-    double *ysc, *zsc;          // scratch: y by L position, z by U position
+    const void *r;              // FP64, or FP32 for the FP32 layout
+    void *z;
+    void *ysc, *zsc;            // scratch: y by L position, z by U position
     int ring_mask;              // ring slots - 1 (power of two)
     int stage_bytes, nstages;
     long long spin_limit;
@@ -155,11 +167,12 @@ struct TrsvArgs {
     int r_from_j;
     int64_t ldv;
 };
-// Shared memory of one CTA: stages, ring, right-hand-side slots, barriers.
-size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots);
-// Largest stage count (2..8) that fits the device's shared memory per CTA.
-int trsv_stages_for(int stage_bytes, int ring_slots);
-int launch_trsv(const TrsvArgs &a, cudaStream_t s);
+// Shared memory of one CTA: stages, ring, right-hand-side slots, barriers
+// (vbytes: 8 for FP64 values, 4 for FP32).
+size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes);
+// Largest stage count (3..8) that fits the device's shared memory per CTA.
+int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes);
+int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false);
 
 // ------------------------------------------------------------------ small solver kernels
 int launch_gmres_lsq(SolverState *st, cudaStream_t s);

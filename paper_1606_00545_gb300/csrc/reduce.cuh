@@ -139,6 +139,7 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
             st->restarts += 1;
             st->j = 0;
             st->cycle_end = 0;
+            st->beta_cycle = beta;
             for (int i = 0; i <= st->restart; ++i)
                 st->g[i] = 0.0;
             st->g[0] = beta;
@@ -174,7 +175,8 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         st->est = est / st->bnorm;
         int happy = (hn == 0.0) || (hn <= 1e-300 * st->w0norm);
         int end = (est <= st->tol * st->bnorm) || happy || (j + 1 == m) ||
-                  (st->iters >= st->maxit) || isnan(est);
+                  (st->iters >= st->maxit) || isnan(est) ||
+                  (est <= st->inner_rtol * st->beta_cycle);
         st->cycle_end = end;
         if (end) {
             st->jend = j + 1;

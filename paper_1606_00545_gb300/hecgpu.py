@@ -32,6 +32,7 @@ BICGSTAB = 1
 HOST_ONLY = 1
 X0_ZERO = 1
 SOLVE_EAGER = 2
+MIXED_FP32 = 4
 FACTOR_L = 0
 FACTOR_U = 1
 
@@ -69,7 +70,8 @@ class PrecondInfo_t(C.Structure):
                 ("scheduled", C.c_int32), ("rows_total", C.c_int64), ("factor_nnz", C.c_int64),
                 ("max_levels_L", C.c_int32), ("max_levels_U", C.c_int32),
                 ("apply_bytes", C.c_int64), ("device_bytes", C.c_int64),
-                ("ring_slots", C.c_int32), ("global_passes", C.c_int32)]
+                ("ring_slots", C.c_int32), ("global_passes", C.c_int32),
+                ("apply_bytes_f32", C.c_int64)]
 
 
 class SolveOpts_t(C.Structure):
@@ -97,6 +99,7 @@ _SIGS = {
     "hec_matrix_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "hec_matrix_destroy": ([_vp], None),
     "hec_spmv": ([_vp, _dbl, _vp, _dbl, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "hec_spmv_f32": ([_vp, C.c_float, _vp, C.c_float, _vp, _vp, _vp], C.c_int),
     "hec_axpby": ([_i32, _dbl, _vp, _dbl, _vp, _vp], C.c_int),
     "hec_waxpby": ([_i32, _dbl, _vp, _dbl, _vp, _vp, _vp], C.c_int),
     "hec_dot": ([_i32, _vp, _vp, _vp, _vp], C.c_int),
@@ -112,6 +115,7 @@ _SIGS = {
     "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_status": ([_vp, _vp], C.c_int),
     "hec_precond_apply_noalloc": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
+    "hec_precond_apply_f32": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_destroy": ([_vp], None),
     "krylov_solve": ([_vp, _vp, _vp, _vp, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
                       C.POINTER(SolveInfo_t)], C.c_int),
@@ -269,6 +273,12 @@ def hec_spmv(A: Matrix, alpha, x, beta, y_in, y_out, w=None, dots=None, stream=N
                                    _ptr(y_out), _ptr(w), _ptr(dots), _stream(stream)), "hec_spmv")
 
 
+def hec_spmv_f32(A: Matrix, alpha, x, beta, y_in, y_out, stream=None):
+    """FP32 SpMV of the mixed-precision inner solves (float32 tensors)."""
+    _check(load_library().hec_spmv_f32(A.handle, float(alpha), _ptr(x), float(beta), _ptr(y_in),
+                                       _ptr(y_out), _stream(stream)), "hec_spmv_f32")
+
+
 def hec_axpby(a, x, b, y, stream=None):
     _check(load_library().hec_axpby(int(y.numel()), float(a), _ptr(x), float(b), _ptr(y),
                                     _stream(stream)), "hec_axpby")
@@ -387,6 +397,12 @@ def hec_precond_apply_noalloc(M: Precond, r, z, spin_limit: int = 0, stream=None
     by all calls, so overlapping calls race."""
     _check(load_library().hec_precond_apply_noalloc(M.handle, _ptr(r), _ptr(z), int(spin_limit),
                                                     _stream(stream)), "hec_precond_apply_noalloc")
+
+
+def hec_precond_apply_f32(M: Precond, r, z, spin_limit: int = 0, stream=None):
+    """FP32 preconditioner apply of the mixed-precision inner solves (float32 tensors)."""
+    _check(load_library().hec_precond_apply_f32(M.handle, _ptr(r), _ptr(z), int(spin_limit),
+                                                _stream(stream)), "hec_precond_apply_f32")
 
 
 def hec_precond_status(M: Precond, stream=None) -> int:

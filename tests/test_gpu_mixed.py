@@ -1,0 +1,156 @@
+"""Mixed precision: FP32 inner GMRES cycles (FP32 SpMV, FP32 ILU(k) solves, FP32
+Krylov basis) inside FP64 iterative refinement, checked against the FP64 oracle.
+
+Tolerances:
+  * FP32 SpMV, per row i with k_i stored entries: |y - y_ref| <= (k_i + 2) u
+    sum_j |a_ij x_j| (u = 2^-24): the first-order bound of a k-term dot product
+    whose inputs are rounded to FP32 once and whose products and sums are FP32.
+  * FP32 preconditioner apply: stated per case (error relative to max|z|),
+    asserted below 1e-3 -- the triangular solves amplify the FP32 rounding by
+    the conditioning of the factors, which the test matrices keep moderate.
+  * Mixed solves: the FP64 residual reaches tol (1e-8) and the solution agrees
+    with the oracle's FP64 solution to 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_00545_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu
+    hecgpu.load_library()
+    torch.cuda.set_device(0)
+    return hecgpu
+
+
+def dev(a, dtype=None):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float64, device="cuda:0")
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("case", ["poisson2d", "irregular27", "random_tail"])
+def test_spmv_f32_within_fp32_bound(H, orc, case):
+    import torch
+    A, K = {"poisson2d": (synth.poisson2d_5pt(64), 0),
+            "irregular27": (synth.stencil27_irregular(12, 4, 5), 0),
+            "random_tail": (synth.random_sparse(1200, 0.02, seed=2), 3)}[case]
+    x = synth.rhs_uniform(A.n, 5)
+    M = H.hec_build(A.row_ptr, A.col, A.val, ell_width=K)
+    y = torch.empty(A.n, dtype=torch.float32, device="cuda:0")
+    H.hec_spmv_f32(M, 1.0, dev(x, torch.float32), 0.0, None, y)
+    got = host(y)
+    ref = orc.spmv(A, x)
+    scale = orc.spmv(synth.CSR(A.row_ptr, A.col, np.abs(A.val)), np.abs(x))
+    bound = (A.row_lengths() + 2) * U32 * scale * 1.01 + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+@pytest.mark.parametrize("case", ["c1_poisson64_ilu0", "diffusion3d_ilu1_ras8", "irregular_ras4"])
+def test_precond_f32_vs_fp64_oracle(H, orc, case):
+    import torch
+    A, k, nb, ov = {"c1_poisson64_ilu0": (synth.poisson2d_5pt(64), 0, 1, 0),
+                    "diffusion3d_ilu1_ras8": (synth.diffusion3d_7pt_lognormal(16, 2.0, 2), 1, 8, 1),
+                    "irregular_ras4": (synth.stencil27_irregular(10, 4, 5), 0, 4, 1)}[case]
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P)
+    r = synth.rhs_uniform(A.n, 1)
+    z = torch.full((A.n,), float("nan"), dtype=torch.float32, device="cuda:0")
+    H.hec_precond_apply_f32(P, dev(r, torch.float32), z)
+    assert H.hec_precond_status(P) == H.OK
+    got = host(z)
+    ref = orc.RAS(A, k, nb, ov).apply(r)
+    assert np.all(np.isfinite(got))
+    err = np.max(np.abs(got - ref)) / np.abs(ref).max()
+    print("fp32 preconditioner, %s: max error / max|z| = %.2e" % (case, err))
+    assert err <= 1e-3
+
+
+def test_mixed_gmres_c1(H, orc):
+    """64x64 Poisson, ILU(0), mixed GMRES(30): FP64 residual 1e-8."""
+    A = synth.poisson2d_5pt(64)
+    b = synth.rhs_uniform(A.n, 1)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    H.level_schedule(P)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=2000, restart=30, method=H.GMRES,
+                          flags=H.MIXED_FP32)
+    xg = host(x)
+    assert info["status"] == H.OK and info["rel_resid"] <= 1e-8, info
+    assert np.linalg.norm(b - orc.spmv(A, xg)) / np.linalg.norm(b) <= 1e-8
+    xd = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) <= 1e-6
+
+
+@pytest.mark.parametrize("k,nb,ov,m", [(1, 8, 1, 30), (0, 1, 0, 50)])
+def test_mixed_matches_fp64_oracle_solution(H, orc, k, nb, ov, m):
+    A = synth.diffusion3d_7pt_lognormal(20, 2.0, 2)
+    b = synth.rhs_uniform(A.n, 3)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=5000, restart=m, method=H.GMRES,
+                          flags=H.MIXED_FP32)
+    xr, ir = orc.gmres(A, b, M=orc.RAS(A, k, nb, ov), tol=1e-8, maxit=5000, restart=m)
+    xg = host(x)
+    assert info["status"] == H.OK and info["rel_resid"] <= 1e-8, info
+    err = np.linalg.norm(xg - xr) / np.linalg.norm(xr)
+    print("mixed GMRES(%d): %d steps (oracle FP64: %d), error vs oracle %.2e"
+          % (m, info["iters"], ir.iters, err))
+    assert err <= 1e-6
+
+
+def test_mixed_unpreconditioned(H, orc):
+    A = synth.poisson2d_5pt(16)
+    b = synth.rhs_uniform(A.n, 2)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, None, dev(b), x, tol=1e-9, maxit=4000, restart=40, method=H.GMRES,
+                          flags=H.MIXED_FP32)
+    assert info["status"] == H.OK
+    assert np.linalg.norm(b - orc.spmv(A, host(x))) / np.linalg.norm(b) <= 1e-9
+
+
+def test_mixed_rejects_bicgstab(H):
+    A = synth.poisson2d_5pt(8)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    with pytest.raises(H.HecError):
+        H.krylov_solve(M, None, dev(np.ones(A.n)), dev(np.zeros(A.n)), method=H.BICGSTAB,
+                       flags=H.MIXED_FP32)
+
+
+def test_c3_irregular_96_mixed_gmres50(H, orc):
+    """96^3 27-point + 2% irregular rows (30-120 extra entries, N(0, 0.01)),
+    diagonal 1.1 x off-diagonal row sum; ILU(0) on 64 RAS blocks; FP32 inner
+    GMRES(50) with FP64 refinement to 1e-8.  Manufactured solution x*."""
+    A = synth.stencil27_irregular(96, 4, 5)
+    xs = synth.rhs_uniform(A.n, 6)
+    b = orc.spmv(A, xs)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    inf = M.info()
+    assert inf["tail_rows"] > 0  # the HEC tail is exercised
+    P = H.ilu_k_setup(M, 0, 64, 1)
+    H.level_schedule(P)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=5000, restart=50, method=H.GMRES,
+                          flags=H.MIXED_FP32)
+    xg = host(x)
+    assert info["status"] == H.OK and info["rel_resid"] <= 1e-8, info
+    assert np.linalg.norm(b - orc.spmv(A, xg)) / np.linalg.norm(b) <= 1e-8
+    assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) <= 1e-6
