@@ -198,7 +198,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("k_trsv.cu", "hec_setup.cpp"):  # the kernel and the layout it streams
+    for f in ("k_trsv.cu", "ptx.cuh", "hec_setup.cpp"):  # the kernel and the layout it streams
         with open(os.path.join(ROOT, "paper_1606_00545_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

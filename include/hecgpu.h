@@ -284,6 +284,107 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
                  int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
                  hec_solve_info_t *info);
 
+/* ---------------------------------------------------------------- batches */
+/* Many independent systems A_s x_s = b_s (s = 0 .. nsys-1), each with nrhs
+ * right-hand sides, solved by ONE persistent kernel launch: every system is
+ * solved start to finish by one CTA, the costliest systems first, with the
+ * same operations as the single-system path -- HEC SpMV (Eq. 2, Algorithm
+ * 1), ILU(k) factors (Eqs. 9-10, Algorithm 2) applied by level-scheduled
+ * triangular solves (Eq. 11, Algorithm 3), restarted GMRES(m) (Section 2.7)
+ * -- and up to 4 right-hand sides of a system advanced in lockstep, so the
+ * matrix and factor entries are read once for all of them.  The paper solves
+ * one system at a time; batching is this library's extension.
+ *
+ * A system's arithmetic depends only on the system, nrhs and the batch
+ * configuration (threads per CTA), never on the other systems: a system gives
+ * bit-identical results alone and in any batch solved with the same
+ * configuration. */
+typedef struct hec_batch_s *hec_batch_t;
+
+/* The systems as one concatenated CSR (host memory, copied).  System s owns
+ * global rows [sys_ptr[s], sys_ptr[s+1]); its column indices are local to it
+ * (0 .. n_s - 1), strictly ascending in every row, diagonal stored. */
+typedef struct {
+    int32_t nsys;            /* >= 1                                          */
+    int32_t reserved;
+    const int64_t *sys_ptr;  /* nsys + 1 entries, sys_ptr[0] = 0              */
+    const int64_t *row_ptr;  /* sys_ptr[nsys] + 1 entries into col / val      */
+    const int32_t *col;
+    const double *val;
+} hec_batch_csr_t;
+
+/* Launch configuration of the batched kernel.  Zero fields take defaults. */
+typedef struct {
+    int32_t threads;      /* CTA size, a multiple of 32 in [128, 512]; 0 = 256   */
+    int32_t ctas_per_sm;  /* resident CTAs per SM; 0 = as many as fit (<= 4)    */
+    int32_t ell_width;    /* 0: per system, the largest K that a third of its
+                             rows reach; > 0: this K for every system.  Rows
+                             longer than K are stored whole in the CSR tail   */
+    int32_t nstages;      /* bulk-copy stages of the triangular solves; 0 = 8   */
+} hec_batch_config_t;
+
+typedef struct {
+    int32_t nsys;
+    int32_t ilu_k;           /* -1 before ilu_k_setup_batched                  */
+    int64_t rows, nnz;       /* totals over the systems                         */
+    int64_t factor_nnz;      /* sum of nnz(L_s) + nnz(U_s)                      */
+    int32_t max_n;           /* largest system                                  */
+    int32_t ring_slots;      /* shared-memory window of solved values (positions) */
+    int64_t device_bytes;    /* matrices, factors and the last solve's workspace */
+    hec_batch_config_t config;
+} hec_batch_info_t;
+
+/* Outcome of one system (the worst of its right-hand sides). */
+typedef struct {
+    int32_t iters;      /* Arnoldi steps, summed over groups of 4 right-hand sides */
+    int32_t cycles;     /* restart cycles                                         */
+    int32_t status;     /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN                        */
+    int32_t reserved;
+    double rel_resid;   /* largest true ||b - A x|| / ||b|| over its right-hand sides */
+} hec_batch_sys_info_t;
+
+/* Builds the batch: copies and checks every system (HEC_ERR_UNSORTED_CSR,
+ * HEC_ERR_INVALID as for hec_build).  cfg may be NULL.  Device memory is laid
+ * out on first use. */
+int hec_build_batched(const hec_batch_csr_t *A, const hec_batch_config_t *cfg, void *stream,
+                      hec_batch_t *out);
+/* ILU(k) of every system (Eqs. 9-10, Algorithm 2) and the level sets of its
+ * factors (Eq. 11); the unknowns of a system are then stored in the level
+ * order of L.  Returns HEC_OK, HEC_ERR_ZERO_PIVOT (system index in
+ * hec_last_error) or HEC_ERR_INVALID. */
+int ilu_k_setup_batched(hec_batch_t B, int32_t k);
+int hec_batch_info(hec_batch_t B, hec_batch_info_t *info);
+/* Replaces the launch configuration (the ELL width rebuilds the layout). */
+int hec_batch_set_config(hec_batch_t B, const hec_batch_config_t *cfg);
+/* Autotuner: times the solve of a sample of the systems (about two per SM,
+ * spread over the size range, one restart cycle each) under candidate
+ * configurations -- CTA size, CTAs per SM, bulk-copy stages and ELL width --
+ * keeps the fastest in B and returns it in *chosen (may be NULL).  nrhs,
+ * restart and opts (HEC_MIXED_FP32) as the solves it tunes for. */
+int hec_batch_autotune(hec_batch_t B, int32_t nrhs, int32_t restart,
+                       const hec_solve_opts_t *opts, void *stream, hec_batch_config_t *chosen);
+/* Solves every system.  b, x: device or host arrays of sys_ptr[nsys] x nrhs
+ * doubles, row-major (value of right-hand side r of global row i at
+ * i * nrhs + r); x holds x0 unless HEC_X0_ZERO.  tol, maxit (Arnoldi steps
+ * per group of <= 4 right-hand sides), restart (<= 64) as for krylov_solve.
+ * Without HEC_MIXED_FP32 the inner cycles run in FP64; with it, in FP32
+ * inside FP64 refinement (cycles end when their estimate has dropped by
+ * 1e-5).  A right-hand side with b = 0 returns x = 0.  One kernel launch;
+ * the call synchronises the stream.  Returns HEC_OK when every system
+ * converged, else the first non-OK system status, or an error.  info (sums
+ * over systems, rel_resid the largest) and sys_info (nsys entries, host) may
+ * be NULL. */
+int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs, double tol,
+                         int32_t maxit, int32_t restart, const hec_solve_opts_t *opts,
+                         void *stream, hec_solve_info_t *info, hec_batch_sys_info_t *sys_info);
+/* The batched kernel's single operations, for tests: x = A b per system
+ * (op 0: FP64 values; op 1: FP32 values and arithmetic) and x = M^{-1} b
+ * (op 2: FP32 factors and arithmetic; op 3: FP64).  b, x: device arrays laid
+ * out as in krylov_solve_batched. */
+int hec_batch_apply(hec_batch_t B, int32_t op, const double *b, double *x, int32_t nrhs,
+                    void *stream);
+void hec_batch_destroy(hec_batch_t B);
+
 #ifdef __cplusplus
 }
 #endif

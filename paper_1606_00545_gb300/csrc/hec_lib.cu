@@ -17,13 +17,18 @@
 #include "../../include/hecgpu.h"
 #include "hec_setup.h"
 #include "kernels.cuh"
+#include "runtime.h"
 
 using namespace hec;
 
-// ====================================================================== errors
-namespace {
+// ====================================================================== runtime
+namespace hec {
 
+namespace {
 thread_local std::string g_last_error;
+std::mutex g_alloc_mu;
+AllocFns g_alloc;
+} // namespace
 
 int fail(int code, const char *fmt, ...)
 {
@@ -36,21 +41,6 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
-#define HEC_CK(call)                                                                              \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(HEC_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
-                        __LINE__);                                                                \
-    } while (0)
-
-#define HEC_TRY(expr)                                                                             \
-    do {                                                                                          \
-        int r_ = (expr);                                                                          \
-        if (r_ != HEC_OK)                                                                         \
-            return r_;                                                                            \
-    } while (0)
-
 int check_launch(const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -59,70 +49,16 @@ int check_launch(const char *what)
     return HEC_OK;
 }
 
-// ====================================================================== allocator
-struct AllocFns {
-    void *(*alloc)(size_t, void *, void *) = nullptr;
-    void (*free_)(void *, void *, void *) = nullptr;
-    void *ctx = nullptr;
-};
-std::mutex g_alloc_mu;
-AllocFns g_alloc;
-
-// One device allocation, returned through the allocator that made it.
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    AllocFns fns;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() { release(); }
-    void release()
-    {
-        if (!p)
-            return;
-        if (fns.free_)
-            fns.free_(p, nullptr, fns.ctx);
-        else
-            cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    int alloc(size_t nbytes, cudaStream_t s)
-    {
-        release();
-        if (nbytes == 0)
-            nbytes = 16;
-        {
-            std::lock_guard<std::mutex> lk(g_alloc_mu);
-            fns = g_alloc;
-        }
-        if (fns.alloc) {
-            p = fns.alloc(nbytes, (void *)s, fns.ctx);
-            if (!p)
-                return fail(HEC_ERR_OOM, "allocator returned NULL for %zu bytes", nbytes);
-        } else {
-            cudaError_t e = cudaMalloc(&p, nbytes);
-            if (e != cudaSuccess) {
-                p = nullptr;
-                cudaGetLastError();
-                return fail(e == cudaErrorMemoryAllocation ? HEC_ERR_OOM : HEC_ERR_CUDA,
-                            "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
-            }
-        }
-        bytes = nbytes;
-        return HEC_OK;
-    }
-    template <class T> T *as() const { return static_cast<T *>(p); }
-};
-
-template <class T>
-int upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s)
+AllocFns current_allocator()
 {
-    HEC_TRY(d.alloc(h.size() * sizeof(T), s));
-    if (!h.empty())
-        HEC_CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    return HEC_OK;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+
+void set_allocator(const AllocFns &f)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = f;
 }
 
 int device_sms()
@@ -137,12 +73,30 @@ int device_sms()
     return sms;
 }
 
-inline int grid_for(int64_t items, int per_cta, int ctas_per_sm)
+int device_smem_optin()
 {
-    int64_t need = (items + per_cta - 1) / per_cta;
-    int64_t cap = (int64_t)device_sms() * ctas_per_sm;
-    return (int)std::max<int64_t>(1, std::min(need, cap));
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    return optin;
 }
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+const char *last_error_text() { return g_last_error.c_str(); }
+
+} // namespace hec
+
+namespace {
 
 // Reduction scratch: partials sized for every reducing launch of the library.
 struct Reducer {
@@ -162,16 +116,6 @@ struct Reducer {
 };
 
 std::atomic<uint64_t> g_next_id(1);
-
-bool is_device_ptr(const void *p)
-{
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 } // namespace
 
@@ -903,17 +847,18 @@ const char *hec_status_string(int status)
     }
 }
 
-const char *hec_last_error(void) { return g_last_error.c_str(); }
+const char *hec_last_error(void) { return hec::last_error_text(); }
 
 int hec_set_allocator(void *(*alloc_fn)(size_t, void *, void *), void (*free_fn)(void *, void *, void *),
                       void *ctx)
 {
     if ((alloc_fn == nullptr) != (free_fn == nullptr))
         return fail(HEC_ERR_INVALID, "allocator needs both functions or neither");
-    std::lock_guard<std::mutex> lk(g_alloc_mu);
-    g_alloc.alloc = alloc_fn;
-    g_alloc.free_ = free_fn;
-    g_alloc.ctx = ctx;
+    AllocFns f;
+    f.alloc = alloc_fn;
+    f.free_ = free_fn;
+    f.ctx = ctx;
+    set_allocator(f);
     return HEC_OK;
 }
 

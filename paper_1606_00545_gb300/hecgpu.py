@@ -85,6 +85,28 @@ class SolveInfo_t(C.Structure):
                 ("d2h_bytes", C.c_int64)]
 
 
+class BatchCSR_t(C.Structure):
+    _fields_ = [("nsys", C.c_int32), ("reserved", C.c_int32), ("sys_ptr", C.c_void_p),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class BatchConfig_t(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("ell_width", C.c_int32),
+                ("nstages", C.c_int32)]
+
+
+class BatchInfo_t(C.Structure):
+    _fields_ = [("nsys", C.c_int32), ("ilu_k", C.c_int32), ("rows", C.c_int64),
+                ("nnz", C.c_int64), ("factor_nnz", C.c_int64), ("max_n", C.c_int32),
+                ("ring_slots", C.c_int32), ("device_bytes", C.c_int64),
+                ("config", BatchConfig_t)]
+
+
+class BatchSysInfo_t(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32), ("rel_resid", C.c_double)]
+
+
 _vp = C.c_void_p
 _i32 = C.c_int32
 _i64 = C.c_int64
@@ -119,6 +141,17 @@ _SIGS = {
     "hec_precond_destroy": ([_vp], None),
     "krylov_solve": ([_vp, _vp, _vp, _vp, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
                       C.POINTER(SolveInfo_t)], C.c_int),
+    "hec_build_batched": ([C.POINTER(BatchCSR_t), C.POINTER(BatchConfig_t), _vp, C.POINTER(_vp)],
+                          C.c_int),
+    "ilu_k_setup_batched": ([_vp, _i32], C.c_int),
+    "hec_batch_info": ([_vp, C.POINTER(BatchInfo_t)], C.c_int),
+    "hec_batch_set_config": ([_vp, C.POINTER(BatchConfig_t)], C.c_int),
+    "hec_batch_autotune": ([_vp, _i32, _i32, C.POINTER(SolveOpts_t), _vp, C.POINTER(BatchConfig_t)],
+                           C.c_int),
+    "krylov_solve_batched": ([_vp, _vp, _vp, _i32, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
+                              C.POINTER(SolveInfo_t), _vp], C.c_int),
+    "hec_batch_apply": ([_vp, _i32, _vp, _vp, _i32, _vp], C.c_int),
+    "hec_batch_destroy": ([_vp], None),
 }
 
 _lock = threading.Lock()
@@ -421,3 +454,113 @@ def krylov_solve(A: Matrix, M, b, x, tol=1e-8, maxit=1000, restart=30, method=GM
                                      _stream(stream), C.byref(inf))
     _check(rc, "krylov_solve", ok=(OK, MAXIT, BREAKDOWN))
     return {f: getattr(inf, f) for f, _ in SolveInfo_t._fields_ if f != "reserved"}
+
+
+# ------------------------------------------------------------------ batches
+BATCH_SPMV64 = 0
+BATCH_SPMV32 = 1
+BATCH_PRECOND32 = 2
+BATCH_PRECOND64 = 3
+
+
+def _cfg_dict(c):
+    return {f: getattr(c, f) for f, _ in BatchConfig_t._fields_}
+
+
+class Batch:
+    """A batch of independent systems solved by one persistent launch."""
+
+    def __init__(self, handle, sys_ptr):
+        self._h = handle
+        self.sys_ptr = sys_ptr
+        self.nsys = len(sys_ptr) - 1
+        self.rows = int(sys_ptr[-1])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = BatchInfo_t()
+        _check(_lib.hec_batch_info(self._h, C.byref(inf)), "hec_batch_info")
+        d = {f: getattr(inf, f) for f, _ in BatchInfo_t._fields_ if f != "config"}
+        d["config"] = _cfg_dict(inf.config)
+        return d
+
+    def set_config(self, threads=0, ctas_per_sm=0, ell_width=0, nstages=0):
+        c = BatchConfig_t(int(threads), int(ctas_per_sm), int(ell_width), int(nstages))
+        _check(_lib.hec_batch_set_config(self._h, C.byref(c)), "hec_batch_set_config")
+
+    def destroy(self):
+        if self._h and _lib is not None:
+            _lib.hec_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def hec_build_batched(systems, threads=0, ctas_per_sm=0, ell_width=0, nstages=0, stream=None):
+    """systems: a list of CSR matrices (objects with row_ptr, col, val) or a
+    tuple (sys_ptr, row_ptr, col, val) of the concatenated form."""
+    lib = load_library()
+    if isinstance(systems, tuple):
+        sp, rp, ci, va = systems
+        sp = np.ascontiguousarray(sp, np.int64)
+        rp = np.ascontiguousarray(rp, np.int64)
+        ci = np.ascontiguousarray(ci, np.int32)
+        va = np.ascontiguousarray(va, np.float64)
+    else:
+        ns = [int(len(A.row_ptr) - 1) for A in systems]
+        sp = np.zeros(len(systems) + 1, np.int64)
+        sp[1:] = np.cumsum(ns)
+        nnz = [int(A.row_ptr[-1]) for A in systems]
+        off = np.concatenate([[0], np.cumsum(nnz)]).astype(np.int64)
+        rp = np.concatenate([np.asarray(A.row_ptr[:-1], np.int64) + off[i]
+                             for i, A in enumerate(systems)] + [[off[-1]]]).astype(np.int64)
+        ci = np.ascontiguousarray(np.concatenate([np.asarray(A.col) for A in systems]), np.int32)
+        va = np.ascontiguousarray(np.concatenate([np.asarray(A.val) for A in systems]), np.float64)
+    csr = BatchCSR_t(len(sp) - 1, 0, sp.ctypes.data, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+    c = BatchConfig_t(int(threads), int(ctas_per_sm), int(ell_width), int(nstages))
+    h = C.c_void_p()
+    _check(lib.hec_build_batched(C.byref(csr), C.byref(c), _stream(stream), C.byref(h)),
+           "hec_build_batched")
+    return Batch(h, sp)
+
+
+def ilu_k_setup_batched(B: Batch, k: int):
+    _check(load_library().ilu_k_setup_batched(B.handle, int(k)), "ilu_k_setup_batched")
+
+
+def hec_batch_autotune(B: Batch, nrhs=1, restart=30, flags=0, stream=None):
+    o = SolveOpts_t(GMRES, int(flags), 0)
+    c = BatchConfig_t()
+    _check(load_library().hec_batch_autotune(B.handle, int(nrhs), int(restart), C.byref(o),
+                                             _stream(stream), C.byref(c)), "hec_batch_autotune")
+    return _cfg_dict(c)
+
+
+def krylov_solve_batched(B: Batch, b, x, nrhs=1, tol=1e-8, maxit=1000, restart=30, flags=0,
+                         spin_limit=0, stream=None, per_system=False):
+    """Returns the summary dict (and, with per_system, a list of per-system dicts)."""
+    o = SolveOpts_t(GMRES, int(flags), int(spin_limit))
+    inf = SolveInfo_t()
+    si = (BatchSysInfo_t * B.nsys)() if per_system else None
+    rc = load_library().krylov_solve_batched(B.handle, _ptr(b), _ptr(x), int(nrhs), float(tol),
+                                             int(maxit), int(restart), C.byref(o),
+                                             _stream(stream), C.byref(inf),
+                                             C.cast(si, C.c_void_p) if si is not None else None)
+    _check(rc, "krylov_solve_batched", ok=(OK, MAXIT, BREAKDOWN))
+    summary = {f: getattr(inf, f) for f, _ in SolveInfo_t._fields_ if f != "reserved"}
+    if not per_system:
+        return summary
+    return summary, [{f: getattr(v, f) for f, _ in BatchSysInfo_t._fields_ if f != "reserved"}
+                     for v in si]
+
+
+def hec_batch_apply(B: Batch, op, b, x, nrhs=1, stream=None):
+    _check(load_library().hec_batch_apply(B.handle, int(op), _ptr(b), _ptr(x), int(nrhs),
+                                          _stream(stream)), "hec_batch_apply")

@@ -1,0 +1,244 @@
+"""Batched solver (one persistent launch, one CTA per system) against the FP64
+oracle, system by system.
+
+Tolerances:
+  * FP64 SpMV: |y - y_ref| <= 1e-12 sum_j |a_ij x_j| per entry (summation
+    order differs from the oracle's).
+  * FP32 SpMV: (k_i + 2) u sum_j |a_ij x_j|, u = 2^-24, k_i stored entries.
+  * FP64 preconditioner apply: 1e-10 relative to max|z| (same factors, level
+    order instead of row order, FMA contraction).
+  * FP32 preconditioner apply: 1e-3 relative to max|z|, the value reported.
+  * Solves: true FP64 residual <= tol and solution within 1e-6 of the
+    oracle's FP64 GMRES solution (or of the manufactured solution).
+"""
+import numpy as np
+import pytest
+
+from paper_1606_00545_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu
+    hecgpu.load_library()
+    torch.cuda.set_device(0)
+    return hecgpu
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a, np.float64), device="cuda:0")
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def mixed_systems():
+    """Uneven sizes, both stencil families, tail rows (random rows longer than
+    the ELL width), a 1-row system."""
+    return [synth.diffusion2d_5pt_lognormal(12, 2.0, 7),
+            synth.poisson2d_5pt(9),
+            synth.random_sparse(300, 0.03, seed=3),
+            synth.diffusion3d_7pt_lognormal(6, 2.0, 8),
+            synth.tridiagonal(50, 4),
+            synth.CSR(np.array([0, 1]), np.array([0]), np.array([2.5])),
+            synth.diffusion2d_5pt_lognormal(20, 2.0, 9, Ny=7)]
+
+
+def stack(vs, nrhs):
+    return np.concatenate(vs, axis=0).reshape(-1, nrhs)
+
+
+def split(x, systems):
+    out, o = [], 0
+    for A in systems:
+        out.append(x[o:o + A.n])
+        o += A.n
+    return out
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 5])
+def test_batch_spmv_fp64_and_fp32(H, orc, nrhs):
+    sy = mixed_systems()
+    B = H.hec_build_batched(sy)
+    rng = np.random.default_rng(nrhs)
+    xs = [rng.uniform(-1, 1, (A.n, nrhs)) for A in sy]
+    xb = dev(stack(xs, nrhs))
+    y = dev(np.zeros((B.rows, nrhs)))
+    H.hec_batch_apply(B, H.BATCH_SPMV64, xb, y, nrhs)
+    y64 = split(host(y), sy)
+    y.zero_()
+    H.hec_batch_apply(B, H.BATCH_SPMV32, xb, y, nrhs)
+    y32 = split(host(y), sy)
+    for A, x, g64, g32 in zip(sy, xs, y64, y32):
+        absA = synth.CSR(A.row_ptr, A.col, np.abs(A.val))
+        for r in range(nrhs):
+            ref = orc.spmv(A, x[:, r])
+            scale = orc.spmv(absA, np.abs(x[:, r]))
+            assert np.all(np.abs(g64[:, r] - ref) <= 1e-12 * scale + 1e-300)
+            x32 = x[:, r].astype(np.float32).astype(np.float64)
+            bound = (A.row_lengths() + 2) * U32 * orc.spmv(absA, np.abs(x32)) * 1.01
+            assert np.all(np.abs(g32[:, r] - orc.spmv(A, x32)) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_batch_precond_vs_oracle(H, orc, k):
+    sy = mixed_systems()
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, k)
+    nrhs = 4
+    rng = np.random.default_rng(10 + k)
+    rs = [rng.uniform(-1, 1, (A.n, nrhs)) for A in sy]
+    rb = dev(stack(rs, nrhs))
+    z = dev(np.full((B.rows, nrhs), np.nan))
+    H.hec_batch_apply(B, H.BATCH_PRECOND64, rb, z, nrhs)
+    z64 = split(host(z), sy)
+    H.hec_batch_apply(B, H.BATCH_PRECOND32, rb, z, nrhs)
+    z32 = split(host(z), sy)
+    worst32 = 0.0
+    for A, r, g64, g32 in zip(sy, rs, z64, z32):
+        M = orc.RAS(A, k, 1, 0)
+        for j in range(nrhs):
+            ref = M.apply(r[:, j])
+            sc = np.abs(ref).max()
+            assert np.max(np.abs(g64[:, j] - ref)) <= 1e-10 * sc
+            e32 = np.max(np.abs(g32[:, j] - ref)) / sc
+            worst32 = max(worst32, e32)
+            assert e32 <= 1e-3
+    print("batched FP32 ILU(%d) apply: worst error / max|z| = %.2e" % (k, worst32))
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_batch_solve_vs_oracle(H, orc, mixed, nrhs):
+    sy = mixed_systems()
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, 0)
+    rng = np.random.default_rng(20 + nrhs)
+    bs = [rng.uniform(-1, 1, (A.n, nrhs)) for A in sy]
+    x = dev(np.zeros((B.rows, nrhs)))
+    info, per = H.krylov_solve_batched(B, dev(stack(bs, nrhs)), x, nrhs=nrhs, tol=1e-8, maxit=3000,
+                                       restart=30, flags=H.MIXED_FP32 if mixed else 0,
+                                       per_system=True)
+    assert info["status"] == H.OK, (info, per)
+    assert info["kernel_launches"] == 1
+    xs = split(host(x), sy)
+    for A, b, xg, p in zip(sy, bs, xs, per):
+        assert p["status"] == H.OK and p["rel_resid"] <= 1e-8
+        for j in range(nrhs):
+            rr = np.linalg.norm(b[:, j] - orc.spmv(A, xg[:, j])) / np.linalg.norm(b[:, j])
+            assert rr <= 1e-8
+            xr, _ = orc.gmres(A, b[:, j], M=orc.RAS(A, 0, 1, 0), tol=1e-12, maxit=5000,
+                              restart=30)
+            assert np.linalg.norm(xg[:, j] - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_batch_result_identical_alone_and_in_batch(H):
+    """Per-system arithmetic is independent of the other systems."""
+    sy = mixed_systems()
+    target = 3
+    nrhs = 2
+    rng = np.random.default_rng(5)
+    bs = [rng.uniform(-1, 1, (A.n, nrhs)) for A in sy]
+    res = []
+    for group in (sy, [sy[target]]):
+        B = H.hec_build_batched(group, threads=256)
+        H.ilu_k_setup_batched(B, 1)
+        bb = bs if len(group) > 1 else [bs[target]]
+        x = dev(np.zeros((B.rows, nrhs)))
+        H.krylov_solve_batched(B, dev(stack(bb, nrhs)), x, nrhs=nrhs, tol=1e-9, maxit=2000,
+                               restart=20, flags=H.MIXED_FP32)
+        xs = split(host(x), group)
+        res.append(xs[target] if len(group) > 1 else xs[0])
+    assert np.array_equal(res[0], res[1])
+
+
+def test_batch_nrhs_columns_match_single_rhs(H, orc):
+    """Four right-hand sides in lockstep give the same solutions (to the
+    tolerance) as four separate single-rhs solves."""
+    sy = [synth.diffusion2d_5pt_lognormal(24, 2.0, 11), synth.poisson3d_7pt(8)]
+    nrhs = 4
+    rng = np.random.default_rng(3)
+    bs = [rng.uniform(-1, 1, (A.n, nrhs)) for A in sy]
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, 0)
+    x4 = dev(np.zeros((B.rows, nrhs)))
+    H.krylov_solve_batched(B, dev(stack(bs, nrhs)), x4, nrhs=nrhs, tol=1e-10, maxit=3000)
+    x4 = split(host(x4), sy)
+    for j in range(nrhs):
+        x1 = dev(np.zeros((B.rows, 1)))
+        H.krylov_solve_batched(B, dev(stack([b[:, j:j + 1] for b in bs], 1)), x1, nrhs=1,
+                               tol=1e-10, maxit=3000)
+        for a, b_ in zip(x4, split(host(x1), sy)):
+            assert np.linalg.norm(a[:, j] - b_[:, 0]) <= 1e-7 * np.linalg.norm(b_[:, 0])
+
+
+def test_batch_edge_cases(H):
+    sy = [synth.poisson2d_5pt(6), synth.poisson2d_5pt(5)]
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, 0)
+    # a zero right-hand side returns x = 0 even from a nonzero x0
+    b = np.ones((B.rows, 2))
+    b[:, 1] = 0.0
+    x = dev(np.full((B.rows, 2), 3.0))
+    info = H.krylov_solve_batched(B, dev(b), x, nrhs=2, tol=1e-10, maxit=500)
+    xh = host(x)
+    assert info["status"] == H.OK
+    assert np.all(xh[:, 1] == 0.0)
+    # maxit reached
+    x = dev(np.zeros((B.rows, 1)))
+    info, per = H.krylov_solve_batched(B, dev(np.ones((B.rows, 1))), x, nrhs=1, tol=1e-14,
+                                       maxit=2, restart=2, per_system=True)
+    assert info["status"] == H.MAXIT and all(p["status"] == H.MAXIT for p in per)
+    assert all(p["iters"] == 2 for p in per)
+    # host buffers are staged and counted
+    xh = np.zeros((B.rows, 1))
+    info = H.krylov_solve_batched(B, np.ones((B.rows, 1)), xh, nrhs=1, tol=1e-10, maxit=500,
+                                  flags=H.X0_ZERO)
+    assert info["status"] == H.OK
+    assert info["h2d_bytes"] == B.rows * 8 and info["d2h_bytes"] == B.rows * 8
+    # invalid arguments
+    with pytest.raises(H.HecError):
+        H.krylov_solve_batched(B, dev(b), x, nrhs=1, restart=65)
+    with pytest.raises(H.HecError):
+        B.set_config(threads=100)
+
+
+def test_batch_unpreconditioned(H, orc):
+    sy = [synth.poisson2d_5pt(10), synth.tridiagonal(40, 2)]
+    B = H.hec_build_batched(sy)
+    rng = np.random.default_rng(1)
+    bs = [rng.uniform(-1, 1, (A.n, 1)) for A in sy]
+    x = dev(np.zeros((B.rows, 1)))
+    info = H.krylov_solve_batched(B, dev(stack(bs, 1)), x, nrhs=1, tol=1e-10, maxit=2000,
+                                  restart=40)
+    assert info["status"] == H.OK
+    for A, b, xg in zip(sy, bs, split(host(x), sy)):
+        assert np.linalg.norm(b[:, 0] - orc.spmv(A, xg[:, 0])) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_batch_autotune_then_solve(H, orc):
+    sy = [synth.diffusion2d_5pt_lognormal(s, 2.0, 30 + s) for s in (16, 24, 33, 40, 57)]
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, 0)
+    cfg = H.hec_batch_autotune(B, nrhs=4, restart=30, flags=H.MIXED_FP32)
+    assert cfg["threads"] in (128, 256, 512) and cfg["ctas_per_sm"] >= 1
+    assert B.info()["config"] == cfg
+    rng = np.random.default_rng(2)
+    bs = [rng.uniform(-1, 1, (A.n, 4)) for A in sy]
+    x = dev(np.zeros((B.rows, 4)))
+    info = H.krylov_solve_batched(B, dev(stack(bs, 4)), x, nrhs=4, tol=1e-8, maxit=3000,
+                                  flags=H.MIXED_FP32)
+    assert info["status"] == H.OK
+    for A, b, xg in zip(sy, bs, split(host(x), sy)):
+        for j in range(4):
+            assert np.linalg.norm(b[:, j] - orc.spmv(A, xg[:, j])) <= 1e-8 * np.linalg.norm(b[:, j])
