@@ -48,6 +48,12 @@ MAXIT = 20000
 WORKLOAD = "diffusion3d_7pt_128^3_lognormal_sigma2_ilu1_ras64_ov1_bicgstab_tol1e-8_fp64"
 METRIC = "BiCGSTAB iterations/s (ILU(1)+RAS 64 blocks overlap 1, 128^3 7-pt log-normal diffusion, FP64, to 1e-8)"
 CPU_SAMPLE_ITERS = 24
+# C3: irregular-row 27-point system, FP32 inner GMRES(50) with FP64 refinement
+C3_N, C3_STRUCT_SEED, C3_VALUE_SEED, C3_RHS_SEED = 96, 4, 5, 6
+C3_RESTART, C3_NBLOCKS = 50, 64
+# C4: batch of 4096 2D systems, sides uniform on [16, 128], 4 right-hand sides
+C4_NSYS, C4_SMIN, C4_SMAX, C4_SEED, C4_NRHS, C4_RESTART = 4096, 16, 128, 7, 4, 30
+C4_SAMPLE = 32  # systems solved one per launch for the per-launch comparison
 
 
 def parse():
@@ -61,6 +67,8 @@ def parse():
                     help="profiling: run the solve's kernels from a host loop instead of the "
                          "device-side graph loop (ncu cannot profile kernels of graphs with "
                          "conditional nodes); same kernels and results, slower")
+    ap.add_argument("--skip", default="",
+                    help="comma-separated sections to leave out of the JSON line: c3, c4")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
                          "--steps times (few launches before it, for ncu -k/-s/-c)")
@@ -269,6 +277,144 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ C3 and C4 sections
+def c3_section(H, torch, dev, timed):
+    """96^3 27-point + 2% irregular rows: ILU(0) on 64 RAS blocks, GMRES(50),
+    FP64 against mixed (FP32 inner cycles, FP64 refinement), manufactured
+    solution."""
+    A = synth.stencil27_irregular(C3_N, C3_STRUCT_SEED, C3_VALUE_SEED)
+    xs = synth.rhs_uniform(A.n, C3_RHS_SEED)
+    Ah = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(Ah, 0, C3_NBLOCKS, 1)
+    H.level_schedule(P)
+    xsd = torch.tensor(xs, device=dev)
+    bd = torch.empty_like(xsd)
+    H.hec_spmv(Ah, 1.0, xsd, 0.0, None, bd)  # b = A x*
+    out = {"workload": "stencil27_irregular_96^3_ilu0_ras64_ov1_gmres50_tol1e-8",
+           "n": A.n, "nnz": A.nnz, "tail_rows": Ah.info()["tail_rows"]}
+    for name, flags in (("fp64", 0), ("mixed", H.MIXED_FP32)):
+        x = torch.zeros_like(bd)
+        run = lambda: H.krylov_solve(Ah, P, bd, x, tol=TOL, maxit=MAXIT, restart=C3_RESTART,
+                                     method=H.GMRES, flags=H.X0_ZERO | flags)
+        run()
+        ms, infos = timed(run, 2)
+        inf = infos[-1]
+        out[name] = {"solve_ms": ms / 2, "iters": inf["iters"], "cycles": inf["restarts"],
+                     "iters_per_s": inf["iters"] / (ms / 2 * 1e-3), "rel_resid": inf["rel_resid"],
+                     "rel_error_vs_manufactured": float(torch.linalg.norm(x - xsd) /
+                                                        torch.linalg.norm(xsd))}
+    out["mixed_speedup"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
+    return out
+
+
+def c4_bytes(Bs, per, nrhs, m_restart):
+    """Algorithmic bytes of one batched mixed solve from the per-system step
+    and cycle counts (stored nonzeros only, every vector counted once per
+    pass, cycles of equal length, second Gram-Schmidt passes not counted)."""
+    V, I, D = 4, 4, 8  # FP32 value, index, FP64
+    total = 0.0
+    rp, sp = Bs.row_ptr, Bs.sys_ptr
+    rows_of = np.repeat(np.arange(Bs.rows), np.diff(rp))
+    local_row = rows_of - np.repeat(sp[:-1], np.diff(sp))[rows_of]
+    lower = Bs.col < local_row
+    upper = Bs.col > local_row
+    sys_of_row = np.repeat(np.arange(Bs.nsys), np.diff(sp))
+    nl = np.bincount(sys_of_row[rows_of[lower]], minlength=Bs.nsys)
+    nu = np.bincount(sys_of_row[rows_of[upper]], minlength=Bs.nsys)
+    nnz = np.diff(rp[sp])
+    for s in range(Bs.nsys):
+        n = float(sp[s + 1] - sp[s])
+        vec = n * nrhs * V
+        trsv = nl[s] * (V + I) + nu[s] * (V + I) + n * (I + I + V) + 4 * vec
+        spmv = nnz[s] * (V + I) + 2 * vec
+        steps, cycles = per[s]["iters"], max(1, per[s]["cycles"])
+        jlen = steps / cycles
+        arn = cycles * sum((j + 2) * vec + (j + 3) * vec for j in range(int(round(jlen))))
+        cyc = cycles * (nnz[s] * (D + I) + n * nrhs * (2 * D) + vec     # residual, v_0
+                        + (jlen + 1) * vec + trsv + n * nrhs * (3 * D) + vec)  # u, M^-1 u, x += z
+        grp = n * nrhs * D * 5  # b, x in; b, x staged; x out
+        total += steps * (trsv + spmv) + arn + cyc + grp
+    return total
+
+
+def c4_section(H, torch, dev, timed, peak):
+    """4096 independent 2D log-normal diffusion systems, 4 right-hand sides
+    each, ILU(0); one persistent launch, mixed precision, autotuned; against
+    the FP64 batched form and FP64 one-system-per-launch solves."""
+    Bs = synth.batch_diffusion2d(C4_NSYS, C4_SMIN, C4_SMAX, SIGMA, C4_SEED)
+    nrhs = C4_NRHS
+    b = synth.rhs_uniform(Bs.rows * nrhs, C4_SEED + 1).reshape(-1, nrhs)
+    t0 = time.perf_counter()
+    Bh = H.hec_build_batched((Bs.sys_ptr, Bs.row_ptr, Bs.col, Bs.val))
+    H.ilu_k_setup_batched(Bh, 0)
+    setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cfg = H.hec_batch_autotune(Bh, nrhs=nrhs, restart=C4_RESTART, flags=H.MIXED_FP32)
+    tune_s = time.perf_counter() - t0
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+    out = {"workload": "batch_4096x_diffusion2d_5pt_side16-128_lognormal_sigma2_ilu0_"
+                       "gmres30_4rhs_tol1e-8",
+           "nsys": Bs.nsys, "rows": Bs.rows, "nnz": int(Bs.row_ptr[-1]), "nrhs": nrhs,
+           "setup_s": round(setup_s, 2), "autotune_s": round(tune_s, 2), "config": cfg}
+
+    def batched(flags):
+        return H.krylov_solve_batched(Bh, bd, x, nrhs=nrhs, tol=TOL, maxit=MAXIT,
+                                      restart=C4_RESTART, flags=H.X0_ZERO | flags,
+                                      per_system=True)
+
+    for name, flags in (("mixed", H.MIXED_FP32), ("fp64", 0)):
+        if name == "fp64":  # tuned for its own inner type
+            cfg64 = H.hec_batch_autotune(Bh, nrhs=nrhs, restart=C4_RESTART, flags=0)
+        batched(flags)
+        ms, res = timed(lambda: batched(flags), 2)
+        inf, per = res[-1]
+        ms /= 2
+        ok = sum(p["status"] == H.OK for p in per)
+        d = {"solve_ms": ms, "solves_per_s": Bs.nsys * nrhs / (ms * 1e-3),
+             "systems_per_s": Bs.nsys / (ms * 1e-3), "steps": inf["iters"],
+             "steps_per_s": inf["iters"] / (ms * 1e-3), "max_rel_resid": inf["rel_resid"],
+             "converged_systems": ok, "kernel_launches": inf["kernel_launches"]}
+        if name == "mixed":
+            nbytes = c4_bytes(Bs, per, nrhs, C4_RESTART)
+            d["roofline"] = {"bound": "hbm", "kernel": "k_batch<float,4> (whole batched solve)",
+                             "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+                             "alg_bytes": nbytes}
+        if name == "fp64":
+            d["config"] = cfg64
+        out[name] = d
+    # FP64, one system per launch sequence (the single-system graph path), on
+    # systems evenly spaced in size; the batch time is the sample mean x nsys
+    order = np.argsort(Bs.sides, kind="stable")
+    pick = order[np.linspace(0, Bs.nsys - 1, C4_SAMPLE).astype(int)]
+    tot_ms, tot_it = 0.0, 0
+    for s in pick:
+        A = Bs.system(int(s))
+        Ah = H.hec_build(A.row_ptr, A.col, A.val)
+        P = H.ilu_k_setup(Ah, 0, 1, 0)
+        H.level_schedule(P)
+        r0 = int(Bs.sys_ptr[s])
+        xs1 = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        cols = [bd[r0:r0 + A.n, j].contiguous() for j in range(nrhs)]
+        H.krylov_solve(Ah, P, cols[0], xs1, tol=TOL, maxit=MAXIT, restart=C4_RESTART,
+                       method=H.GMRES, flags=H.X0_ZERO)
+        ms, infs = timed(lambda: [H.krylov_solve(Ah, P, c, xs1, tol=TOL, maxit=MAXIT,
+                                                 restart=C4_RESTART, method=H.GMRES,
+                                                 flags=H.X0_ZERO) for c in cols], 1)
+        tot_ms += ms
+        tot_it += sum(i["iters"] for i in infs[0])
+    est_ms = tot_ms / len(pick) * Bs.nsys
+    out["fp64_per_launch"] = {"sample_systems": len(pick), "sample_ms": tot_ms,
+                              "est_batch_ms": est_ms,
+                              "solves_per_s": Bs.nsys * nrhs / (est_ms * 1e-3),
+                              "sample_steps": tot_it}
+    out["mixed_batched_speedup_vs_fp64_per_launch"] = est_ms / out["mixed"]["solve_ms"]
+    out["mixed_batched_speedup_vs_fp64_batched"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
+    Bh.destroy()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -395,6 +541,9 @@ def run_ours(args, rank, world, local_rank):
         H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32)
     ms_s32, _ = timed(lambda: H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32), reps)
     pinf = P.info()
+    skip = set(filter(None, args.skip.split(",")))
+    c3 = c3_section(H, torch, dev, timed) if "c3" not in skip else None
+    c4 = c4_section(H, torch, dev, timed, peak) if "c4" not in skip else None
 
     if rank != 0:
         return
@@ -436,6 +585,8 @@ def run_ours(args, rank, world, local_rank):
                          "trsv_alg_bytes": pinf["apply_bytes_f32"],
                          "spmv_ms": ms_s32 / reps,
                          "spmv_gbs": (A.nnz * 8 + A.n * 8) / (ms_s32 * 1e-3 / reps) / 1e9},
+        "c3_irregular_mixed": c3,
+        "c4_batched": c4,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -315,7 +315,7 @@ typedef struct {
 
 /* Launch configuration of the batched kernel.  Zero fields take defaults. */
 typedef struct {
-    int32_t threads;      /* CTA size, a multiple of 32 in [128, 512]; 0 = 256   */
+    int32_t threads;      /* CTA size: 128, 256 or 512; 0 = 256                 */
     int32_t ctas_per_sm;  /* resident CTAs per SM; 0 = as many as fit (<= 4)    */
     int32_t ell_width;    /* 0: per system, the largest K that a third of its
                              rows reach; > 0: this K for every system.  Rows
@@ -356,7 +356,7 @@ int ilu_k_setup_batched(hec_batch_t B, int32_t k);
 int hec_batch_info(hec_batch_t B, hec_batch_info_t *info);
 /* Replaces the launch configuration (the ELL width rebuilds the layout). */
 int hec_batch_set_config(hec_batch_t B, const hec_batch_config_t *cfg);
-/* Autotuner: times the solve of a sample of the systems (about two per SM,
+/* Autotuner: times the solve of a sample of the systems (about eight per SM,
  * spread over the size range, one restart cycle each) under candidate
  * configurations -- CTA size, CTAs per SM, bulk-copy stages and ELL width --
  * keeps the fastest in B and returns it in *chosen (may be NULL).  nrhs,
@@ -366,7 +366,7 @@ int hec_batch_autotune(hec_batch_t B, int32_t nrhs, int32_t restart,
 /* Solves every system.  b, x: device or host arrays of sys_ptr[nsys] x nrhs
  * doubles, row-major (value of right-hand side r of global row i at
  * i * nrhs + r); x holds x0 unless HEC_X0_ZERO.  tol, maxit (Arnoldi steps
- * per group of <= 4 right-hand sides), restart (<= 64) as for krylov_solve.
+ * per group of <= 4 right-hand sides), restart (<= 31) as for krylov_solve.
  * Without HEC_MIXED_FP32 the inner cycles run in FP64; with it, in FP32
  * inside FP64 refinement (cycles end when their estimate has dropped by
  * 1e-5).  A right-hand side with b = 0 returns x = 0.  One kernel launch;

@@ -13,8 +13,9 @@ namespace hec {
 
 // Rows per triangular-solve chunk: a chunk is consecutive rows of one level.
 constexpr int kBatchChunkRows = 128;
-// Longest GMRES cycle the batched kernel accepts.
-constexpr int kBatchMaxRestart = 64;
+// Longest GMRES cycle the batched kernel accepts: the basis passes keep one
+// partial dot product per basis vector in registers (31 vectors + ||w||^2).
+constexpr int kBatchMaxRestart = 31;
 // Largest CTA the batched kernel is compiled for.
 constexpr int kBatchMaxThreads = 512;
 
@@ -88,38 +89,43 @@ struct BatchArgs {
     double *x;
     unsigned char *ws;     // per-CTA workspace, ws_stride bytes each
     long long ws_stride;
-    long long E;           // elements of one vector slot (positions x NR, rounded to 4)
+    long long E;           // elements of one vector (positions x NR, rounded to the CTA size)
     long long offZ, offY, offX, offB, offR;  // byte offsets in a CTA's workspace
     int ring_mask, nstages, stage_bytes, ent_bytes;
+    int sstages, sbytes;   // basis-tile stages: count and bytes (m + 1 slots of a tile)
     long long spin_limit;
     int *queue;
     int *err;
     BatchResult *res;
 };
 
-// Dynamic shared memory of one CTA.
+// Dynamic shared memory of one CTA.  The triangular-solve stages and the
+// basis-tile stages are used at different times and share one region.
 struct BatchSmem {
-    int stage, ring, bar, red, out, coef, dbl, misc, total;
+    int stage, ring, bar, bar2, red, out, coef, dbl, misc, total;
 };
 
 // Doubles of per-right-hand-side state: h, h2, cs, sn, g, y, sig, scalars.
 __host__ __device__ inline int batch_rhs_doubles(int m) { return 7 * m + 22; }
 
-__host__ __device__ inline BatchSmem batch_smem(int nstages, int stage_bytes, int ring_slots,
-                                                int NR, int tsz, int m)
+__host__ __device__ inline BatchSmem batch_smem(int nstages, int stage_bytes, int sstages,
+                                                int sbytes, int ring_slots, int NR, int tsz, int m,
+                                                int threads)
 {
     auto al = [](int p, int a) { return (p + a - 1) / a * a; };
     BatchSmem o;
     o.stage = 0;
-    int p = nstages * stage_bytes;
+    int p = nstages * stage_bytes > sstages * sbytes ? nstages * stage_bytes : sstages * sbytes;
     o.ring = al(p, 16);
     p = o.ring + (ring_slots + 1) * NR * tsz;
     o.bar = al(p, 16);
     p = o.bar + nstages * 8;
+    o.bar2 = al(p, 16);
+    p = o.bar2 + sstages * 8;
     o.red = al(p, 16);
-    p = o.red + 32 * 32 * 8;
+    p = o.red + (threads / 32) * 32 * 4 * 8;
     o.out = al(p, 16);
-    p = o.out + 32 * 8;
+    p = o.out + 32 * 4 * 8;
     o.coef = al(p, 16);
     p = o.coef + (m + 1) * 4 * tsz;
     o.dbl = al(p, 16);

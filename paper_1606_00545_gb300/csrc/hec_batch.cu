@@ -98,8 +98,8 @@ int64_t r16(int64_t x) { return (x + 15) & ~(int64_t)15; }
 
 int check_config(const hec_batch_config_t &c)
 {
-    if (c.threads != 0 && (c.threads % 32 != 0 || c.threads < 128 || c.threads > kBatchMaxThreads))
-        return fail(HEC_ERR_INVALID, "threads must be a multiple of 32 in [128, %d]", kBatchMaxThreads);
+    if (c.threads != 0 && c.threads != 128 && c.threads != 256 && c.threads != 512)
+        return fail(HEC_ERR_INVALID, "threads must be 128, 256 or 512");
     if (c.ctas_per_sm < 0 || c.ell_width < 0 || c.nstages < 0 || c.nstages > 16)
         return fail(HEC_ERR_INVALID, "bad batch configuration");
     return HEC_OK;
@@ -407,6 +407,7 @@ int build_factors(hec_batch_s *B, int vb, cudaStream_t st)
 struct Launch {
     bool fp32 = true;
     int NR = 1, threads = 256, ctas = 1, grid = 1, nstages = 8, stage_bytes = 0, smem = 0;
+    int sstages = 2, sbytes = 0;
 };
 
 int resolve_launch(hec_batch_s *B, bool fp32, int nrhs, int m, Launch &L)
@@ -419,11 +420,26 @@ int resolve_launch(hec_batch_s *B, bool fp32, int nrhs, int m, Launch &L)
     const FacArena &F = B->fac[fp32 ? 0 : 1];
     L.stage_bytes = (int)r16(F.ent_bytes + batch_rhs_area(L.NR, tsz));
     const int optin = device_smem_optin();
+    // A configuration that does not fit the shared memory gives up, in this
+    // order: triangular-solve stages (down to 2), the second basis-tile stage,
+    // half the CTA size (down to 128).
     for (;;) {
-        L.smem = batch_smem(L.nstages, L.stage_bytes, B->ring_slots, L.NR, tsz, m).total;
-        if (L.smem <= optin || L.nstages <= 2)
+        // basis tiles: m + 1 slots of one CTA-size tile; a third stage when it
+        // fits in the triangular-solve stages' share of the region
+        L.sbytes = (m + 1) * L.threads * tsz;
+        L.sstages = 3 * L.sbytes <= L.nstages * L.stage_bytes ? 3 : 2;
+        auto total = [&]() {
+            return batch_smem(L.nstages, L.stage_bytes, L.sstages, L.sbytes, B->ring_slots, L.NR,
+                              tsz, m, L.threads).total;
+        };
+        while (total() > optin && L.nstages > 2)
+            --L.nstages;
+        if (total() > optin)
+            L.sstages = 1;
+        L.smem = total();
+        if (L.smem <= optin || L.threads <= 128)
             break;
-        --L.nstages;
+        L.threads /= 2;
     }
     if (L.smem > optin)
         return fail(HEC_ERR_INVALID,
@@ -451,7 +467,7 @@ int run_batch(hec_batch_s *B, int op, bool fp32, const double *b, double *x, int
     Launch L;
     HEC_TRY(resolve_launch(B, fp32, nrhs, m, L));
     const int tsz = fp32 ? 4 : 8;
-    const int64_t E = ((int64_t)B->max_n * L.NR + 3) & ~(int64_t)3;
+    const int64_t E = ((int64_t)B->max_n * L.NR + L.threads - 1) / L.threads * L.threads;
     auto al = [](int64_t v) { return (v + 255) & ~(int64_t)255; };
     const int64_t offZ = al((int64_t)(m + 1) * E * tsz);
     const int64_t offY = offZ + al(E * tsz);
@@ -507,6 +523,8 @@ int run_batch(hec_batch_s *B, int op, bool fp32, const double *b, double *x, int
     a.nstages = L.nstages;
     a.stage_bytes = L.stage_bytes;
     a.ent_bytes = (int)r16(F.ent_bytes);
+    a.sstages = L.sstages;
+    a.sbytes = L.sbytes;
     a.spin_limit = spin;
     a.queue = B->queue.as<int>();
     a.err = B->err.as<int>();
@@ -691,12 +709,15 @@ int hec_batch_autotune(hec_batch_t B, int32_t nrhs, int32_t restart, const hec_s
         return fail(HEC_ERR_INVALID, "invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp32 = opts && (opts->flags & HEC_MIXED_FP32);
-    // sample: about two systems per SM, evenly spaced over the size ranking
+    // sample: about eight systems per SM, evenly spaced over the size ranking,
+    // so that every CTA of a trial works through several systems as in the
+    // full batch (a trial of one system per CTA would time the largest
+    // system's latency, not the throughput)
     std::vector<int> bysize(B->nsys);
     std::iota(bysize.begin(), bysize.end(), 0);
     std::stable_sort(bysize.begin(), bysize.end(),
                      [&](int x, int y) { return B->sys[x].A.n > B->sys[y].A.n; });
-    const int want = std::min(B->nsys, 2 * device_sms());
+    const int want = std::min(B->nsys, 8 * device_sms());
     std::vector<int> idx;
     for (int i = 0; i < want; ++i)
         idx.push_back(bysize[(int64_t)i * B->nsys / want]);

@@ -10,9 +10,11 @@
 //   cycle:  r = b - A x in FP64, beta = ||r||;  v_0 = r / beta in T
 //           Arnoldi in T: z = M^{-1} v_j (level-scheduled L and U passes,
 //           Eq. 11, Algorithm 3), w = A z (HEC: ELL slab + CSR tail, Eq. 2,
-//           Algorithm 1), classical Gram-Schmidt with a second pass when
-//           ||w|| drops below ||w_0|| / sqrt(2) (the Daniel-Gragg-Kaufman-
-//           Stewart test), Givens rotations and least squares in FP64;
+//           Algorithm 1), classical Gram-Schmidt with a second projection
+//           when the first leaves ||w'|| < ||w|| / sqrt(2) (the Daniel-
+//           Gragg-Kaufman-Stewart test; the first update and the second
+//           projection's dot products share one read of the basis), Givens
+//           rotations and least squares in FP64;
 //           the cycle ends when |g_{j+1}| <= max(inner_rtol beta, tol ||b||)
 //           x += M^{-1} (V y) with the update added in FP64.
 // The basis is kept unnormalised: v_i = sig_i * V_i, and sig_i is applied
@@ -24,6 +26,12 @@
 // the right-hand sides of a triangular-solve chunk are one contiguous slice
 // that the bulk-copy engine fetches with the chunk's factor entries, S chunks
 // ahead; solved values live in a shared-memory ring indexed by position.
+// The Krylov basis is stored tile-interleaved (tile = CTA-size elements of
+// every slot, contiguous), so the Gram-Schmidt passes stream whole tiles of
+// all slots into shared memory with one bulk copy each, several tiles ahead:
+// the bytes in flight per SM do not depend on registers.  One thread issues
+// every bulk copy: lane 0 of the last warp, which holds no row of a chunk of
+// up to (CTA size - 32) rows, so issuing stays off the solving threads' path.
 // Every wait is bounded; a wait that runs out sets the error word, drains the
 // copies in flight and ends the CTA.
 #include "../../include/hecgpu.h"
@@ -137,12 +145,38 @@ template <class V> __device__ __forceinline__ V warp_allsum(V x)
     return x;
 }
 
+// A ring of bulk-copy stages.  Every thread keeps the consumer state (next
+// stage, parity of each stage's next completion, copies consumed); the
+// issuing thread also keeps its own stage cursor and issue count.
+struct Pipe {
+    int S = 1, cst = 0, ist = 0, issued = 0, consumed = 0;
+    uint32_t cpar = 0;
+    __device__ void start_pass()
+    {
+        issued = 0;
+        consumed = 0;
+    }
+    __device__ int next_issue()
+    {
+        const int s = ist;
+        ist = ist + 1 == S ? 0 : ist + 1;
+        ++issued;
+        return s;
+    }
+    __device__ void advance()
+    {
+        cpar ^= 1u << cst;
+        cst = cst + 1 == S ? 0 : cst + 1;
+        ++consumed;
+    }
+};
+
 template <class T, int NR> struct Batch {
     const BatchArgs &a;
-    int tid, nt, lane, warp, nw;
+    int tid, nt, lane, warp, nw, tshift, issuer;
     unsigned char *stages;
     T *ring;
-    uint64_t *full;
+    uint64_t *full, *full2;
     void *red;
     void *out;
     T *coef;
@@ -150,9 +184,10 @@ template <class T, int NR> struct Batch {
     int *misc;
     T *V, *z, *yU;
     double *xp, *bp, *R;
+    Pipe tp, sp;
     BatchSys s;
-    long long E, nE;
-    long long kc = 0, ki = 0;
+    long long nE, Ep;
+    int ntiles;
 
     __device__ Batch(const BatchArgs &args, unsigned char *smem) : a(args)
     {
@@ -161,10 +196,14 @@ template <class T, int NR> struct Batch {
         lane = tid & 31;
         warp = tid >> 5;
         nw = nt >> 5;
-        const BatchSmem L = batch_smem(a.nstages, a.stage_bytes, a.ring_mask + 1, NR, (int)sizeof(T), a.m);
+        tshift = 31 - __clz(nt);
+        issuer = nt - 32;  // lane 0 of the last warp: rows of a chunk go to the first threads
+        const BatchSmem L = batch_smem(a.nstages, a.stage_bytes, a.sstages, a.sbytes,
+                                       a.ring_mask + 1, NR, (int)sizeof(T), a.m, nt);
         stages = smem + L.stage;
         ring = reinterpret_cast<T *>(smem + L.ring);
         full = reinterpret_cast<uint64_t *>(smem + L.bar);
+        full2 = reinterpret_cast<uint64_t *>(smem + L.bar2);
         red = smem + L.red;
         out = smem + L.out;
         coef = reinterpret_cast<T *>(smem + L.coef);
@@ -177,9 +216,16 @@ template <class T, int NR> struct Batch {
         xp = reinterpret_cast<double *>(w + a.offX);
         bp = reinterpret_cast<double *>(w + a.offB);
         R = reinterpret_cast<double *>(w + a.offR);
+        tp.S = a.nstages;
+        sp.S = a.sstages;
     }
 
-    __device__ T *slot(int i) const { return V + (size_t)i * a.E; }
+    // The basis is tile-interleaved: tile t (nt elements) of slots 0..m is
+    // one contiguous block, so one bulk copy brings every slot of a tile.
+    __device__ T *vel(int slot, long long e) const
+    {
+        return V + ((((size_t)(e >> tshift)) * (a.m + 1) + slot) << tshift) + (e & (nt - 1));
+    }
 
     struct RhsView {
         double *h, *h2, *cs, *sn, *g, *y, *sig, *sc;
@@ -206,9 +252,9 @@ template <class T, int NR> struct Batch {
     {
         W *rd = reinterpret_cast<W *>(red);
         W *o = reinterpret_cast<W *>(out);
-        const W s = warp_transpose_sum<N, W>(v, lane);
+        const W s_ = warp_transpose_sum<N, W>(v, lane);
         if (lane < N)
-            rd[warp * N + lane] = s;
+            rd[warp * N + lane] = s_;
         __syncthreads();
         if (tid < N) {
             W t = 0;
@@ -219,15 +265,62 @@ template <class T, int NR> struct Batch {
         __syncthreads();
     }
 
+    // Sums v[i] (i < 32) over the threads of each right-hand side (a thread's
+    // elements all belong to right-hand side tid % NR) into out[i * NR + q].
+    // Halving over the lane bits above log2(NR) leaves lane l with NR values,
+    // indices c + (l & ~(NR - 1)), summed over the lanes of its right-hand
+    // side; the warps' values are then added in a fixed order.
+    __device__ void reduce32(T (&v)[32])
+    {
+        T *rd = reinterpret_cast<T *>(red);
+        T *o = reinterpret_cast<T *>(out);
+#pragma unroll
+        for (int off = 16; off >= NR; off >>= 1) {
+            const bool up = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < off; ++i) {
+                const T send = up ? v[i] : v[i + off];
+                const T keep = up ? v[i + off] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            rd[(warp * 32 + lane) * NR + c] = v[c];
+        __syncthreads();
+        for (int k = tid; k < 32 * NR; k += nt) {
+            const int i = k / NR, q = k % NR;
+            const int l = (i & ~(NR - 1)) | q, c = i & (NR - 1);
+            T t = T(0);
+            for (int w = 0; w < nw; ++w)
+                t += rd[(w * 32 + l) * NR + c];
+            o[k] = t;
+        }
+        __syncthreads();
+    }
+
     // ------------------------------------------------------------- HEC SpMV
-    // y = bvec - A x in FP64 (bvec may be null: y = -A x); per-rhs partial
-    // sums of y^2 in part.  Rows of the slab are one per thread; rows of the
-    // tail one per warp with a shuffle reduction.
+    // y = bvec - A x in FP64 (bvec may be null: y = -A x); y is written to
+    // basis slot `slot` (ys == null) or to the plain array ys; per-rhs partial
+    // sums of y^2 in part.  Rows of the slab one per thread, rows of the tail
+    // one per warp with a shuffle reduction.
     template <class TO>
-    __device__ void resid64(const double *bvec, const double *x, TO *y, double (&part)[NR])
+    __device__ void resid64(const double *bvec, const double *x, int slot, TO *ys, double (&part)[NR])
     {
         const int *col = a.ell_col + s.ell;
         const double *val = a.ell_val64 + s.ell;
+        auto put = [&](int p, const double (&acc)[NR]) {
+            TO o[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                o[r] = (TO)acc[r];
+                part[r] += acc[r] * acc[r];
+            }
+            if (ys)
+                stn<TO, NR>(ys + (size_t)p * NR, o);
+            else
+                stn<TO, NR>(reinterpret_cast<TO *>(vel(slot, (long long)p * NR)), o);
+        };
         for (int p = tid; p < s.n; p += nt) {
             const int c0 = col[p];
             if (c0 < 0)
@@ -248,13 +341,7 @@ template <class T, int NR> struct Batch {
                 for (int r = 0; r < NR; ++r)
                     acc[r] -= v * xv[r];
             }
-            TO o[NR];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                o[r] = (TO)acc[r];
-                part[r] += acc[r] * acc[r];
-            }
-            stn<TO, NR>(y + (size_t)p * NR, o);
+            put(p, acc);
         }
         const int *trow = a.tail_rows + s.tail;
         const long long *tptr = a.tail_ptr + s.tptr;
@@ -276,19 +363,15 @@ template <class T, int NR> struct Batch {
                 double bv[NR];
                 if (bvec)
                     ldn<double, NR>(bvec + (size_t)p * NR, bv);
-                TO o[NR];
-                for (int r = 0; r < NR; ++r) {
-                    const double y_ = (bvec ? bv[r] : 0.0) - acc[r];
-                    o[r] = (TO)y_;
-                    part[r] += y_ * y_;
-                }
-                stn<TO, NR>(y + (size_t)p * NR, o);
+                for (int r = 0; r < NR; ++r)
+                    acc[r] = (bvec ? bv[r] : 0.0) - acc[r];
+                put(p, acc);
             }
         }
     }
 
-    // y = A x in the inner type; per-rhs partial sums of y^2 in part.
-    __device__ void spmv_in(const T *x, T *y, T (&part)[NR])
+    // Basis slot `slot` = A x in the inner type (x: a plain array).
+    __device__ void spmv_in(const T *x, int slot)
     {
         const int *col = a.ell_col + s.ell;
         const T *val = static_cast<const T *>(a.ell_val) + s.ell;
@@ -309,10 +392,7 @@ template <class T, int NR> struct Batch {
                 for (int r = 0; r < NR; ++r)
                     acc[r] += v * xv[r];
             }
-            stn<T, NR>(y + (size_t)p * NR, acc);
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-                part[r] += acc[r] * acc[r];
+            stn<T, NR>(vel(slot, (long long)p * NR), acc);
         }
         const int *trow = a.tail_rows + s.tail;
         const long long *tptr = a.tail_ptr + s.tptr;
@@ -331,38 +411,54 @@ template <class T, int NR> struct Batch {
             }
             for (int r = 0; r < NR; ++r)
                 acc[r] = warp_allsum(acc[r]);
-            if (lane == 0) {
-                stn<T, NR>(y + (size_t)p * NR, acc);
-                for (int r = 0; r < NR; ++r)
-                    part[r] += acc[r] * acc[r];
-            }
+            if (lane == 0)
+                stn<T, NR>(vel(slot, (long long)p * NR), acc);
         }
     }
 
-    // ------------------------------------------------- triangular passes
-    __device__ void issue(const BChunk &ch, const T *rhs_base)
+    // ------------------------------------------------- bulk-copy pipes
+    // The issuing thread, after a wait ran out: wait (bounded) for every copy
+    // still in flight so that none lands after the CTA has left.
+    __device__ void drain(const Pipe &P, uint64_t *bars)
     {
-        const int st = (int)(ki % a.nstages);
-        ++ki;
-        unsigned char *dst = stages + (size_t)st * a.stage_bytes;
-        const long long rb = NR * (long long)sizeof(T);
-        const long long lo = ((long long)ch.first * rb) & ~15ll;
-        const long long hi = ((long long)(ch.first + ch.nrows) * rb + 15) & ~15ll;
-        mbar_arrive_expect_tx(&full[st], (uint32_t)(ch.bytes + (hi - lo)));
-        bulk_g2s(dst, a.fac + (size_t)ch.off16 * 16, (uint32_t)ch.bytes, &full[st]);
-        bulk_g2s(dst + a.ent_bytes, reinterpret_cast<const unsigned char *>(rhs_base) + lo,
-                 (uint32_t)(hi - lo), &full[st]);
+        if (tid != issuer)
+            return;
+        int st = P.cst;
+        for (int k = P.consumed; k < P.issued; ++k) {
+            bounded_wait(&bars[st], (P.cpar >> st) & 1u, kBatchDrainPolls);
+            st = st + 1 == P.S ? 0 : st + 1;
+        }
+        atomicExch(a.err, HEC_ERR_TIMEOUT);
     }
 
-    // Thread 0, after a wait ran out: wait (bounded) for every copy still in
-    // flight so that no bulk copy lands after the CTA has left.
-    __device__ void drain()
+    // Right-hand side of a triangular pass: a basis slot or a plain array.
+    struct Src {
+        const T *base;
+        int slot;  // >= 0: basis slot; < 0: base
+    };
+
+    __device__ void issue_chunk(const BChunk &ch, const Src &src)
     {
-        if (tid != 0)
-            return;
-        for (long long q = kc; q < ki; ++q)
-            bounded_wait(&full[q % a.nstages], (uint32_t)((q / a.nstages) & 1), kBatchDrainPolls);
-        atomicExch(a.err, HEC_ERR_TIMEOUT);
+        const int st = tp.next_issue();
+        unsigned char *dst = stages + (size_t)st * a.stage_bytes;
+        constexpr long long epb = 16 / sizeof(T);  // elements per 16 bytes
+        const long long e0 = (long long)ch.first * NR, e1 = (long long)(ch.first + ch.nrows) * NR;
+        const long long lo = e0 & ~(epb - 1), hi = (e1 + epb - 1) & ~(epb - 1);
+        mbar_arrive_expect_tx(&full[st], (uint32_t)(ch.bytes + (hi - lo) * sizeof(T)));
+        bulk_g2s(dst, a.fac + (size_t)ch.off16 * 16, (uint32_t)ch.bytes, &full[st]);
+        unsigned char *rd = dst + a.ent_bytes;
+        if (src.slot < 0) {
+            bulk_g2s(rd, src.base + lo, (uint32_t)((hi - lo) * sizeof(T)), &full[st]);
+        } else {
+            // a slice of a basis slot: one copy per tile it touches
+            for (long long p = lo; p < hi;) {
+                const long long tend = ((p >> tshift) + 1) << tshift;
+                const long long q = tend < hi ? tend : hi;
+                bulk_g2s(rd + (p - lo) * sizeof(T), vel(src.slot, p), (uint32_t)((q - p) * sizeof(T)),
+                         &full[st]);
+                p = q;
+            }
+        }
     }
 
     // One pass over chunks [c0, c0 + nch): rows of the chunk solve
@@ -372,35 +468,34 @@ template <class T, int NR> struct Batch {
     // and to outv at the chunk's destination positions.  Returns false after
     // a wait ran out (the CTA must then end).
     template <bool UP>
-    __device__ bool tri_pass(int c0, int nch, const T *rhs_base, const T (&scale)[NR], T *outv,
+    __device__ bool tri_pass(int c0, int nch, const Src &src, const T (&scale)[NR], T *outv,
                              bool fence_out)
     {
-        const int S = a.nstages;
-        const int pre = nch < S ? nch : S;
+        const int S = tp.S;
+        tp.start_pass();
         BChunk nxt{};
-        if (tid == 0) {
+        if (tid == issuer) {
+            const int pre = nch < S ? nch : S;
             for (int i = 0; i < pre; ++i)
-                issue(a.chunks[c0 + i], rhs_base);
+                issue_chunk(a.chunks[c0 + i], src);
             if (pre < nch)
                 nxt = a.chunks[c0 + pre];
         }
-        const long long rb = NR * (long long)sizeof(T);
+        constexpr long long epb = 16 / sizeof(T);
         for (int i = 0; i < nch; ++i) {
-            const int st = (int)(kc % S);
-            const uint32_t par = (uint32_t)((kc / S) & 1);
-            const bool ok = bounded_wait(&full[st], par, a.spin_limit);
+            const int st = tp.cst;
+            const bool ok = bounded_wait(&full[st], (tp.cpar >> st) & 1u, a.spin_limit);
             if (ok) {
-                ++kc;
-                const unsigned char *sp = stages + (size_t)st * a.stage_bytes;
-                const int4 hdr = *reinterpret_cast<const int4 *>(sp);
+                const unsigned char *spp = stages + (size_t)st * a.stage_bytes;
+                const int4 hdr = *reinterpret_cast<const int4 *>(spp);
                 const int nrows = hdr.x, width = hdr.y, first = hdr.z;
                 const int stride = (nrows + 3) & ~3;
-                const int *dst = reinterpret_cast<const int *>(sp + 16);
+                const int *dst = reinterpret_cast<const int *>(spp + 16);
                 const int *dep = dst + stride;
                 const T *val = reinterpret_cast<const T *>(dep + (size_t)width * stride);
                 const T *dinv = val + (size_t)width * stride;
-                const T *rhs = reinterpret_cast<const T *>(sp + a.ent_bytes +
-                                                           (((long long)first * rb) & 15));
+                const T *rhs = reinterpret_cast<const T *>(spp + a.ent_bytes) +
+                               (((long long)first * NR) & (epb - 1));
                 for (int r_ = tid; r_ < nrows; r_ += nt) {
                     T acc[NR];
                     ldn<T, NR>(rhs + (size_t)r_ * NR, acc);
@@ -431,11 +526,12 @@ template <class T, int NR> struct Batch {
             if (fence_out && i == nch - 1)
                 fence_proxy_async_global();
             if (__syncthreads_or(!ok)) {
-                drain();
+                drain(tp, full);
                 return false;
             }
-            if (tid == 0 && i + S < nch) {
-                issue(nxt, rhs_base);
+            tp.advance();
+            if (tid == issuer && i + S < nch) {
+                issue_chunk(nxt, src);
                 if (i + S + 1 < nch)
                     nxt = a.chunks[c0 + i + S + 1];
             }
@@ -444,59 +540,52 @@ template <class T, int NR> struct Batch {
     }
 
     // z = M^{-1} (scale * src): L pass into yU, U pass into z.
-    __device__ bool precond(const T *src, const T (&scale)[NR])
+    __device__ bool precond(const Src &src, const T (&scale)[NR])
     {
-        if (s.nchL == 0) {
-            // no factor: z = scale * src
+        if (s.nchL == 0) {  // no factor: z = scale * src
             for (long long e = tid; e < nE; e += nt)
-                z[e] = src[e] * scale[e % NR];
+                z[e] = (src.slot < 0 ? src.base[e] : *vel(src.slot, e)) * scale[e % NR];
             __syncthreads();
             return true;
         }
         if (!tri_pass<false>(s.chL, s.nchL, src, scale, yU, true))
             return false;
-        return tri_pass<true>(s.chU, s.nchU, yU, scale, z, false);
+        return tri_pass<true>(s.chU, s.nchU, Src{yU, -1}, scale, z, false);
     }
 
-    // ------------------------------------------------- Krylov basis passes
-    // h[r][i] (or h2) = sig[r][i] * (V_i . w) for i in [0, j].
-    __device__ void dots(int j, const T *w, bool second)
+    // Streams basis tiles 0 .. ntiles-1 (slots [0, nv) of each) through the
+    // stage ring; body(stage, tile) runs on every thread, thread tid owning
+    // element tid of the tile.
+    __device__ void issue_tile(int t, uint32_t bytes)
     {
-        constexpr int G = sizeof(T) == 4 ? 8 : 4;
-        for (int g0 = 0; g0 <= j; g0 += G) {
-            const int ng = (j + 1 - g0) < G ? (j + 1 - g0) : G;
-            T acc[G * 4];
-#pragma unroll
-            for (int i = 0; i < G * 4; ++i)
-                acc[i] = T(0);
-            for (long long q = tid; q < a.E / 4; q += nt) {
-                T wv[4];
-                Vec4<T>::ld(w + 4 * q, wv);
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    if (i < ng) {
-                        T v[4];
-                        Vec4<T>::ld(slot(g0 + i) + 4 * q, v);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            acc[i * 4 + u] += v[u] * wv[u];
-                    }
-                }
+        const int st = sp.next_issue();
+        mbar_arrive_expect_tx(&full2[st], bytes);
+        bulk_g2s(stages + (size_t)st * a.sbytes, V + ((size_t)t * (a.m + 1) << tshift), bytes,
+                 &full2[st]);
+    }
+
+    template <class F> __device__ bool stream(int nv, F &&body)
+    {
+        const uint32_t bytes = (uint32_t)((size_t)nv * sizeof(T)) << tshift;
+        const int S = sp.S;
+        sp.start_pass();
+        if (tid == issuer)
+            for (int t = 0; t < S && t < ntiles; ++t)
+                issue_tile(t, bytes);
+        for (int t = 0; t < ntiles; ++t) {
+            const int st = sp.cst;
+            const bool ok = bounded_wait(&full2[st], (sp.cpar >> st) & 1u, a.spin_limit);
+            if (ok)
+                body(reinterpret_cast<const T *>(stages + (size_t)st * a.sbytes), t);
+            if (__syncthreads_or(!ok)) {
+                drain(sp, full2);
+                return false;
             }
-            block_sum<G * 4, T>(acc);
-            if (tid < ng * NR) {
-                const int i = tid / NR, r = tid % NR;
-                const T *o = reinterpret_cast<const T *>(out);
-                T sum = T(0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u % NR == r)
-                        sum += o[i * 4 + u];
-                RhsView v = rv(r);
-                (second ? v.h2 : v.h)[g0 + i] = v.sig[g0 + i] * (double)sum;
-            }
+            sp.advance();
+            if (tid == issuer && t + S < ntiles)
+                issue_tile(t + S, bytes);
         }
-        __syncthreads();
+        return true;
     }
 
     // coef[i][u] = c_r[i] * sig_r[i], r = u % NR, from c = h, h2 or y.
@@ -511,32 +600,113 @@ template <class T, int NR> struct Batch {
         __syncthreads();
     }
 
-    // w -= sum_{i < cnt} coef[i] V_i; partial ||w||^2 per lane-of-4 in w2.
-    __device__ void update(int cnt, T *w, T (&w2)[4])
+    // h (or h2)[r][i] = sig[r][i] * sum, and the extra value 31 into sc[x]
+    // (||w||^2 before or after the projection), from reduce32's out.
+    __device__ void take_dots(int j, bool second, int scx)
     {
-        for (long long q = tid; q < a.E / 4; q += nt) {
-            T wv[4];
-            Vec4<T>::ld(w + 4 * q, wv);
-#pragma unroll 4
-            for (int i = 0; i < cnt; ++i) {
-                T v[4];
-                Vec4<T>::ld(slot(i) + 4 * q, v);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    wv[u] -= coef[i * 4 + u] * v[u];
-            }
-            Vec4<T>::st(w + 4 * q, wv);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                w2[u] += wv[u] * wv[u];
+        const T *o = reinterpret_cast<const T *>(out);
+        for (int k = tid; k < (j + 1) * NR; k += nt) {
+            const int i = k / NR, r = k % NR;
+            RhsView v = rv(r);
+            (second ? v.h2 : v.h)[i] = v.sig[i] * (double)o[i * NR + r];
         }
+        if (tid < NR)
+            rv(tid).sc[scx] = (double)o[31 * NR + tid];
+        __syncthreads();
+    }
+
+    // One Arnoldi step's orthogonalisation of w = basis slot j + 1 against
+    // slots 0..j: classical Gram-Schmidt, projected twice unless the first
+    // projection kept ||w'|| >= ||w|| / sqrt(2) for every right-hand side.
+    //   pass 1: h = V^T w, ||w||^2
+    //   pass 2: w' = w - V h; h2 = V^T w', ||w'||^2       (one read of V)
+    //   pass 3: w'' = w' - V h2, ||w''||^2; h += h2       (when needed)
+    __device__ bool orthogonalise(int j)
+    {
+        const int u4 = tid & 3;
+        const int wi = (j + 1) << tshift;
+        {
+            T acc[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                acc[i] = T(0);
+            if (!stream(j + 2, [&](const T *st, int) {
+                    const T w = st[wi + tid];
+#pragma unroll
+                    for (int i = 0; i < 31; ++i)
+                        if (i <= j)
+                            acc[i] += st[(i << tshift) + tid] * w;
+                    acc[31] += w * w;
+                }))
+                return false;
+            reduce32(acc);
+            take_dots(j, false, SC_WW);
+        }
+        set_coef(j + 1, 0);
+        {
+            T acc[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                acc[i] = T(0);
+            if (!stream(j + 2, [&](const T *st, int t) {
+                    T w = st[wi + tid];
+#pragma unroll
+                    for (int i = 0; i < 31; ++i)
+                        if (i <= j)
+                            w -= coef[i * 4 + u4] * st[(i << tshift) + tid];
+#pragma unroll
+                    for (int i = 0; i < 31; ++i)
+                        if (i <= j)
+                            acc[i] += st[(i << tshift) + tid] * w;
+                    acc[31] += w * w;
+                    V[(((size_t)t * (a.m + 1) + j + 1) << tshift) + tid] = w;
+                }))
+                return false;
+            fence_proxy_async_global();
+            reduce32(acc);
+            take_dots(j, true, SC_W2);
+        }
+        bool reorth = false;
+        for (int r = 0; r < NR; ++r) {
+            RhsView v = rv(r);
+            reorth |= v.sc[SC_ACTIVE] != 0.0 && v.sc[SC_W2] < 0.5 * v.sc[SC_WW];
+        }
+        if (reorth) {
+            set_coef(j + 1, 1);
+            T w2[4] = {T(0), T(0), T(0), T(0)};
+            if (!stream(j + 2, [&](const T *st, int t) {
+                    T w = st[wi + tid];
+#pragma unroll
+                    for (int i = 0; i < 31; ++i)
+                        if (i <= j)
+                            w -= coef[i * 4 + u4] * st[(i << tshift) + tid];
+                    w2[u4] += w * w;
+                    V[(((size_t)t * (a.m + 1) + j + 1) << tshift) + tid] = w;
+                }))
+                return false;
+            fence_proxy_async_global();
+            block_sum<4, T>(w2);
+            if (tid < NR) {
+                const T *o = reinterpret_cast<const T *>(out);
+                RhsView v = rv(tid);
+                double t = 0.0;
+                for (int u = 0; u < 4; ++u)
+                    if (u % NR == tid)
+                        t += (double)o[u];
+                v.sc[SC_W2] = t;
+                for (int i = 0; i <= j; ++i)
+                    v.h[i] += v.h2[i];
+            }
+            __syncthreads();
+        }
+        return true;
     }
 
     // --------------------------------------------------------- one system
     __device__ void load_group(int g0)
     {
         const int *rop = a.row_of_pos + s.perm;
-        for (long long e = tid; e < a.E; e += nt) {
+        for (long long e = tid; e < Ep; e += nt) {
             const long long p = e / NR;
             const int rr = g0 * NR + (int)(e % NR);
             double bv = 0.0, xv = 0.0;
@@ -549,21 +719,21 @@ template <class T, int NR> struct Batch {
             bp[e] = bv;
             xp[e] = xv;
         }
-        // padding of every basis slot stays zero for the flat passes
-        const long long pad = a.E - nE;
+        // padding of every basis slot stays zero for the tile passes
+        const long long pad = Ep - nE;
         for (long long t = tid; t < (long long)(a.m + 1) * pad; t += nt)
-            slot((int)(t / pad))[nE + t % pad] = T(0);
+            *vel((int)(t / pad), nE + t % pad) = T(0);
         __syncthreads();
     }
 
-    template <class S_> __device__ void store_group(int g0, const S_ *src, double sign)
+    template <class G> __device__ void store_group(int g0, G &&get)
     {
         const int *rop = a.row_of_pos + s.perm;
         for (long long e = tid; e < nE; e += nt) {
             const long long p = e / NR;
             const int rr = g0 * NR + (int)(e % NR);
             if (rr < a.nrhs)
-                a.x[(s.row0 + rop[p]) * a.nrhs + rr] = sign * (double)src[e];
+                a.x[(s.row0 + rop[p]) * a.nrhs + rr] = get(e);
         }
     }
 
@@ -575,7 +745,7 @@ template <class T, int NR> struct Batch {
         // ||b|| per right-hand side
         {
             double bb[4] = {0.0, 0.0, 0.0, 0.0};
-            for (long long e = tid; e < a.E; e += nt)
+            for (long long e = tid; e < Ep; e += nt)
                 bb[e & 3] += bp[e] * bp[e];
             block_sum<4, double>(bb);
             if (tid < NR) {
@@ -588,7 +758,7 @@ template <class T, int NR> struct Batch {
             }
             __syncthreads();
             // b = 0: the solution is 0
-            for (long long e = tid; e < a.E; e += nt)
+            for (long long e = tid; e < Ep; e += nt)
                 if (rv((int)(e % NR)).sc[SC_BNORM] == 0.0)
                     xp[e] = 0.0;
             __syncthreads();
@@ -602,7 +772,7 @@ template <class T, int NR> struct Batch {
                 double part[NR];
                 for (int r = 0; r < NR; ++r)
                     part[r] = 0.0;
-                resid64<T>(bp, xp, slot(0), part);
+                resid64<T>(bp, xp, 0, nullptr, part);
                 fence_proxy_async_global();
                 double pv[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int r = 0; r < NR; ++r)
@@ -647,63 +817,13 @@ template <class T, int NR> struct Batch {
                 T scale[NR];
                 for (int r = 0; r < NR; ++r)
                     scale[r] = (T)rv(r).sig[j];
-                if (!precond(slot(j), scale))
+                if (!precond(Src{nullptr, j}, scale))
                     return false;
-                T *w = slot(j + 1);
-                T ww[NR];
-                for (int r = 0; r < NR; ++r)
-                    ww[r] = T(0);
-                spmv_in(z, w, ww);
-                __syncthreads();
-                dots(j, w, false);
-                set_coef(j + 1, 0);
-                T w2[4] = {T(0), T(0), T(0), T(0)};
-                update(j + 1, w, w2);
+                spmv_in(z, j + 1);
                 fence_proxy_async_global();
-                {
-                    T pl[8];
-                    for (int u = 0; u < 4; ++u)
-                        pl[u] = w2[u];
-                    for (int u = 0; u < 4; ++u)
-                        pl[4 + u] = u < NR ? ww[u] : T(0);
-                    block_sum<8, T>(pl);
-                }
-                if (tid < NR) {
-                    const T *o = reinterpret_cast<const T *>(out);
-                    RhsView v = rv(tid);
-                    double t = 0.0;
-                    for (int u = 0; u < 4; ++u)
-                        if (u % NR == tid)
-                            t += (double)o[u];
-                    v.sc[SC_W2] = t;
-                    v.sc[SC_WW] = (double)o[4 + tid];
-                }
                 __syncthreads();
-                bool reorth = false;
-                for (int r = 0; r < NR; ++r) {
-                    RhsView v = rv(r);
-                    reorth |= v.sc[SC_ACTIVE] != 0.0 && v.sc[SC_W2] < 0.5 * v.sc[SC_WW];
-                }
-                if (reorth) {
-                    dots(j, w, true);
-                    set_coef(j + 1, 1);
-                    T w2b[4] = {T(0), T(0), T(0), T(0)};
-                    update(j + 1, w, w2b);
-                    fence_proxy_async_global();
-                    block_sum<4, T>(w2b);
-                    if (tid < NR) {
-                        const T *o = reinterpret_cast<const T *>(out);
-                        RhsView v = rv(tid);
-                        double t = 0.0;
-                        for (int u = 0; u < 4; ++u)
-                            if (u % NR == tid)
-                                t += (double)o[u];
-                        v.sc[SC_W2] = t;
-                        for (int i = 0; i <= j; ++i)
-                            v.h[i] += v.h2[i];
-                    }
-                    __syncthreads();
-                }
+                if (!orthogonalise(j))
+                    return false;
                 // ---- Givens rotations and least-squares residual, FP64
                 if (tid < NR) {
                     RhsView v = rv(tid);
@@ -770,28 +890,25 @@ template <class T, int NR> struct Batch {
                 }
             }
             __syncthreads();
-            // ---- u = sum y_i v_i (T), z = M^{-1} u, x += z in FP64
+            // ---- u = sum y_i v_i (T) into slot j, z = M^{-1} u, x += z in FP64
             set_coef(j, 2);
             {
-                T *u = slot(j);
-                for (long long q = tid; q < a.E / 4; q += nt) {
-                    T acc[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 4
-                    for (int i = 0; i < j; ++i) {
-                        T v[4];
-                        Vec4<T>::ld(slot(i) + 4 * q, v);
+                const int u4 = tid & 3, jj = j;
+                if (!stream(jj, [&](const T *st, int t) {
+                        T u = T(0);
 #pragma unroll
-                        for (int w_ = 0; w_ < 4; ++w_)
-                            acc[w_] += coef[i * 4 + w_] * v[w_];
-                    }
-                    Vec4<T>::st(u + 4 * q, acc);
-                }
+                        for (int i = 0; i < 31; ++i)
+                            if (i < jj)
+                                u += coef[i * 4 + u4] * st[(i << tshift) + tid];
+                        V[(((size_t)t * (a.m + 1) + jj) << tshift) + tid] = u;
+                    }))
+                    return false;
                 fence_proxy_async_global();
                 __syncthreads();
                 T one[NR];
                 for (int r = 0; r < NR; ++r)
                     one[r] = T(1);
-                if (!precond(u, one))
+                if (!precond(Src{nullptr, jj}, one))
                     return false;
                 for (long long e = tid; e < nE; e += nt)
                     xp[e] += (double)z[e];
@@ -803,7 +920,7 @@ template <class T, int NR> struct Batch {
         if (status != HEC_OK && res.status == HEC_OK)
             res.status = status;
         res.rel_resid = worst > res.rel_resid ? worst : res.rel_resid;
-        store_group(g0, xp, 1.0);
+        store_group(g0, [&](long long e) { return xp[e]; });
         __syncthreads();
         return true;
     }
@@ -816,27 +933,27 @@ template <class T, int NR> struct Batch {
             double part[NR];
             for (int r = 0; r < NR; ++r)
                 part[r] = 0.0;
-            resid64<double>(nullptr, bp, xp, part);
+            resid64<double>(nullptr, bp, 0, xp, part);
             __syncthreads();
-            store_group(g0, xp, -1.0);
+            store_group(g0, [&](long long e) { return -xp[e]; });
+        } else if (a.op == BOP_SPMV_IN) {
+            for (long long e = tid; e < Ep; e += nt)
+                z[e] = (T)bp[e];
+            __syncthreads();
+            spmv_in(z, 1);
+            __syncthreads();
+            store_group(g0, [&](long long e) { return (double)*vel(1, e); });
         } else {
-            for (long long e = tid; e < a.E; e += nt)
-                slot(0)[e] = (T)bp[e];
+            for (long long e = tid; e < Ep; e += nt)
+                *vel(0, e) = (T)bp[e];
             fence_proxy_async_global();
             __syncthreads();
-            if (a.op == BOP_SPMV_IN) {
-                T part[NR];
-                spmv_in(slot(0), slot(1), part);
-                __syncthreads();
-                store_group(g0, slot(1), 1.0);
-            } else {
-                T one[NR];
-                for (int r = 0; r < NR; ++r)
-                    one[r] = T(1);
-                if (!precond(slot(0), one))
-                    return false;
-                store_group(g0, z, 1.0);
-            }
+            T one[NR];
+            for (int r = 0; r < NR; ++r)
+                one[r] = T(1);
+            if (!precond(Src{nullptr, 0}, one))
+                return false;
+            store_group(g0, [&](long long e) { return (double)z[e]; });
         }
         __syncthreads();
         return true;
@@ -847,6 +964,8 @@ template <class T, int NR> struct Batch {
         if (tid == 0) {
             for (int i = 0; i < a.nstages; ++i)
                 mbar_init(&full[i], 1);
+            for (int i = 0; i < a.sstages; ++i)
+                mbar_init(&full2[i], 1);
             fence_mbar_init();
         }
         // the ring's zero slot (padding dependencies)
@@ -870,6 +989,8 @@ template <class T, int NR> struct Batch {
                 return;
             s = a.sys[sidx];
             nE = (long long)s.n * NR;
+            Ep = ((nE + nt - 1) >> tshift) << tshift;
+            ntiles = (int)(Ep >> tshift);
             BatchResult res{0, 0, HEC_OK, 0, 0.0};
             for (int g = 0; g < groups; ++g) {
                 const bool ok = a.op == BOP_SOLVE ? solve_group(g, res) : op_group(g);

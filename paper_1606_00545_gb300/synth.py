@@ -23,6 +23,10 @@ The workloads stand in for the paper's test matrices (Section 3: the
   N(0, variance)), with the diagonal set to a multiple of the off-diagonal
   absolute row sum (strictly diagonally dominant).
 * ``rhs_uniform(n, seed)`` -- right-hand side uniform on [-1, 1].
+* ``batch_diffusion2d(nsys, smin, smax, sigma, seed)`` -- a batch of
+  independent 2D log-normal diffusion systems with square sides drawn
+  uniformly from [smin, smax], concatenated (system offsets, int64 row
+  pointers, local column indices).
 
 All matrices come back as ``(row_ptr int32[n+1], col int32[nnz], val
 float64[nnz])`` with strictly ascending column indices in every row and the
@@ -42,6 +46,8 @@ __all__ = [
     "rhs_uniform",
     "tridiagonal",
     "random_sparse",
+    "batch_diffusion2d",
+    "Batch",
 ]
 
 
@@ -312,3 +318,58 @@ def random_sparse(n: int, density: float, seed: int, dominance: float = 1.5,
     cols = np.concatenate([c, np.arange(n)])
     vals = np.concatenate([v, d])
     return _assemble(n, rows.astype(np.int64), cols.astype(np.int64), vals.astype(np.float64))
+
+
+class Batch:
+    """Independent systems concatenated: system s owns rows
+    ``sys_ptr[s]:sys_ptr[s+1]``; ``row_ptr`` (int64) indexes ``col`` (local
+    column indices, int32) and ``val``."""
+
+    __slots__ = ("sys_ptr", "row_ptr", "col", "val", "sides")
+
+    def __init__(self, sys_ptr, row_ptr, col, val, sides=None):
+        self.sys_ptr = np.ascontiguousarray(sys_ptr, dtype=np.int64)
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+        self.sides = sides
+
+    @property
+    def nsys(self) -> int:
+        return int(self.sys_ptr.shape[0] - 1)
+
+    @property
+    def rows(self) -> int:
+        return int(self.sys_ptr[-1])
+
+    def system(self, s: int) -> CSR:
+        r0, r1 = int(self.sys_ptr[s]), int(self.sys_ptr[s + 1])
+        e0 = int(self.row_ptr[r0])
+        return CSR(self.row_ptr[r0:r1 + 1] - e0, self.col[e0:self.row_ptr[r1]],
+                   self.val[e0:self.row_ptr[r1]])
+
+
+def batch_diffusion2d(nsys: int, smin: int, smax: int, sigma: float, seed: int) -> Batch:
+    """``nsys`` systems ``diffusion2d_5pt_lognormal(s_i, sigma, c_i)``.
+
+    From ``default_rng(seed)``: the sides s_i = integers(smin, smax + 1, nsys)
+    (uniform on [smin, smax]), then the coefficient seeds
+    c_i = integers(0, 2**31 - 1, nsys).
+    """
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(smin, smax + 1, nsys)
+    cseeds = rng.integers(0, 2 ** 31 - 1, nsys)
+    mats = [diffusion2d_5pt_lognormal(int(n), sigma, int(c)) for n, c in zip(sides, cseeds)]
+    ns = np.array([A.n for A in mats], dtype=np.int64)
+    nnz = np.array([A.nnz for A in mats], dtype=np.int64)
+    sys_ptr = np.zeros(nsys + 1, dtype=np.int64)
+    sys_ptr[1:] = np.cumsum(ns)
+    eoff = np.zeros(nsys + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum(nnz)
+    row_ptr = np.empty(int(sys_ptr[-1]) + 1, dtype=np.int64)
+    for i, A in enumerate(mats):
+        row_ptr[sys_ptr[i]:sys_ptr[i + 1]] = A.row_ptr[:-1].astype(np.int64) + eoff[i]
+    row_ptr[-1] = eoff[-1]
+    col = np.concatenate([A.col for A in mats])
+    val = np.concatenate([A.val for A in mats])
+    return Batch(sys_ptr, row_ptr, col, val, sides)
