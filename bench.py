@@ -54,6 +54,8 @@ C3_RESTART, C3_NBLOCKS = 50, 64
 # C4: batch of 4096 2D systems, sides uniform on [16, 128], 4 right-hand sides
 C4_NSYS, C4_SMIN, C4_SMAX, C4_SEED, C4_NRHS, C4_RESTART = 4096, 16, 128, 7, 4, 30
 C4_SAMPLE = 32  # systems solved one per launch for the per-launch comparison
+# C5: served solves -- Poisson arrivals, sizes log-uniform 1e3..1e6, 5/7/27-point
+C5_LAMBDA, C5_SEED, C5_POOL, C5_REQUESTS, C5_COLD, C5_LANES = 2000.0, 8, 24, 96, 24, 8
 
 
 def parse():
@@ -68,7 +70,7 @@ def parse():
                          "device-side graph loop (ncu cannot profile kernels of graphs with "
                          "conditional nodes); same kernels and results, slower")
     ap.add_argument("--skip", default="",
-                    help="comma-separated sections to leave out of the JSON line: c3, c4")
+                    help="comma-separated sections to leave out of the JSON line: c3, c4, c5")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
                          "--steps times (few launches before it, for ncu -k/-s/-c)")
@@ -415,6 +417,90 @@ def c4_section(H, torch, dev, timed, peak):
     return out
 
 
+def c5_section(H):
+    """Served solves: an open-loop Poisson request stream against the solve
+    server (lanes of CUDA streams, admission by device memory).  Requests
+    draw their system from a pool of C5_POOL matrices of the request mix
+    (keyed: set up once, resident), each with its own right-hand side; a
+    cold run sets up every request.  Latency = completion - submission on
+    the server clock."""
+    specs = synth.serving_requests(C5_POOL, C5_SEED)
+    t0 = time.perf_counter()
+    pool = [synth.serving_matrix(r, SIGMA) for r in specs]
+    rhs = [synth.rhs_uniform(A.n, C5_SEED * 1000 + i) for i, A in enumerate(pool)]
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(C5_SEED + 1)
+
+    def stream(rate, nreq):
+        """A request stream: Poisson arrival offsets and pool picks."""
+        return np.cumsum(rng.exponential(1.0 / rate, nreq)), rng.integers(0, len(pool), nreq)
+
+    def register(S):
+        t = time.perf_counter()
+        for i, A in enumerate(pool):
+            S.submit(A, rhs[i], ilu_k=specs[i]["k"], key=i + 1, tag=10 ** 6 + i)
+        got = []
+        while len(got) < len(pool):
+            got += S.poll(wait_ms=100)
+        assert all(r["status"] == H.OK for r in got), got
+        return time.perf_counter() - t
+
+    def open_loop(S, rate, req, keyed):
+        arr, picks = req
+        nreq = len(arr)
+        res = []
+        w0 = time.perf_counter()
+        for i in range(nreq):
+            while True:
+                left = arr[i] - (time.perf_counter() - w0)
+                if left <= 0:
+                    break
+                time.sleep(min(left, 0.002))
+            p = int(picks[i])
+            S.submit(None if keyed else pool[p], rhs[p], ilu_k=specs[p]["k"],
+                     key=p + 1 if keyed else 0, tag=i)
+            res += S.poll(max_results=1024)
+        while len(res) < nreq:
+            res += S.poll(max_results=1024, wait_ms=100)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        return {"offered_per_s": rate, "requests": nreq, "solves_per_s": nreq / span,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "mean_wait_ms": 1e3 * float(np.mean([r["t_start"] - r["t_submit"] for r in res])),
+                "ok": int(sum(r["status"] == H.OK for r in res)),
+                "status_counts": {str(k): int(v) for k, v in zip(*np.unique(
+                    [r["status"] for r in res], return_counts=True))},
+                "fp64_finish": int(sum(r["fp64_finish"] for r in res)),
+                "max_rel_resid": float(max(r["rel_resid"] for r in res)),
+                "mean_unknowns": float(np.mean([pool[int(picks[r["tag"]])].n for r in res]))}
+
+    out = {"workload": "serve_pool24_loguniform_1e3-1e6_5-7-27pt_lognormal_sigma2_ilu0-1_"
+                       "gmres30_tol1e-8_poisson_arrivals",
+           "pool_unknowns": [A.n for A in pool], "generate_s": round(gen_s, 1),
+           "lanes": C5_LANES, "note": "keyed runs: each pool system set up once and kept "
+                                     "resident, requests carry right-hand sides; cold run: "
+                                     "every request carries its matrix and is set up"}
+    req_lambda = stream(C5_LAMBDA, C5_REQUESTS)
+    with H.Server(lanes=C5_LANES, flags=H.MIXED_FP32, keep_solutions=False) as S:
+        out["register_s"] = round(register(S), 2)
+        out["mixed_lambda"] = open_loop(S, C5_LAMBDA, req_lambda, True)
+        out["mixed_quarter_lambda"] = open_loop(S, C5_LAMBDA / 4, stream(C5_LAMBDA / 4, C5_REQUESTS),
+                                                True)
+        cap = out["mixed_lambda"]["solves_per_s"]
+        out["mixed_half_capacity"] = open_loop(S, 0.5 * cap, stream(0.5 * cap, 40), True)
+    # the plain form on the same request stream: FP64, one system at a time,
+    # every solve through the single-system launch sequence
+    with H.Server(lanes=1, flags=0, small_rows=1, keep_solutions=False) as S:
+        register(S)
+        out["fp64_one_at_a_time"] = open_loop(S, C5_LAMBDA, req_lambda, True)
+    out["mixed_served_speedup_vs_fp64_one_at_a_time"] = (
+        out["mixed_lambda"]["solves_per_s"] / out["fp64_one_at_a_time"]["solves_per_s"])
+    with H.Server(lanes=C5_LANES, flags=H.MIXED_FP32, keep_solutions=False) as S:
+        out["mixed_cold_setup"] = open_loop(S, 20.0, stream(20.0, C5_COLD), False)
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -544,6 +630,7 @@ def run_ours(args, rank, world, local_rank):
     skip = set(filter(None, args.skip.split(",")))
     c3 = c3_section(H, torch, dev, timed) if "c3" not in skip else None
     c4 = c4_section(H, torch, dev, timed, peak) if "c4" not in skip else None
+    c5 = c5_section(H) if "c5" not in skip else None
 
     if rank != 0:
         return
@@ -587,6 +674,7 @@ def run_ours(args, rank, world, local_rank):
                          "spmv_gbs": (A.nnz * 8 + A.n * 8) / (ms_s32 * 1e-3 / reps) / 1e9},
         "c3_irregular_mixed": c3,
         "c4_batched": c4,
+        "c5_serving": c5,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -28,7 +28,9 @@
  *     stream).  All device work is ordered on it; calls that return host data
  *     (queries, krylov_solve's info) synchronise it.
  *   - Handles own their device memory.  It comes from the allocator set with
- *     hec_set_allocator (default: cudaMalloc / cudaFree).  Vectors passed in
+ *     hec_set_allocator (default: the stream-ordered cudaMallocAsync /
+ *     cudaFreeAsync on the stream a handle was created with, so destroy a
+ *     handle before that stream).  Vectors passed in
  *     (x, y, r, z, b) are owned by the caller and only borrowed for the call.
  *   - Values are FP64.  There is no CPU fallback: a call that needs the
  *     device fails with HEC_ERR_CUDA when no CUDA device is present.
@@ -140,7 +142,13 @@ typedef struct {
     int32_t iters;          /* BiCGSTAB passes / GMRES Arnoldi steps          */
     int32_t restarts;       /* GMRES cycles started                           */
     int32_t status;         /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN or an error   */
-    int32_t reserved;
+    int32_t fp64_finish;    /* HEC_MIXED_FP32: the FP32 cycles stopped refining
+                               (two cycles in a row left a true FP64 residual
+                               above 10x the cycle's own final estimate and
+                               above half the cycle's starting residual) and
+                               the solve was finished in FP64 from the current
+                               x (iters, restarts count both phases); batched
+                               solves: the number of systems finished so    */
     double rel_resid;       /* true ||b - A x|| / ||b|| recomputed at the end */
     double est_resid;       /* GMRES: last Givens estimate / ||b||; BiCGSTAB:
                                last recursive residual / ||b||                */
@@ -369,7 +377,10 @@ int hec_batch_autotune(hec_batch_t B, int32_t nrhs, int32_t restart,
  * per group of <= 4 right-hand sides), restart (<= 31) as for krylov_solve.
  * Without HEC_MIXED_FP32 the inner cycles run in FP64; with it, in FP32
  * inside FP64 refinement (cycles end when their estimate has dropped by
- * 1e-5).  A right-hand side with b = 0 returns x = 0.  One kernel launch;
+ * 1e-5); a system whose FP32 cycles stop refining (see fp64_finish) is
+ * finished in FP64 from its current x by a second launch
+ * restricted to such systems (info->fp64_finish counts them).  A right-hand
+ * side with b = 0 returns x = 0.  One kernel launch (two with FP64 finishes);
  * the call synchronises the stream.  Returns HEC_OK when every system
  * converged, else the first non-OK system status, or an error.  info (sums
  * over systems, rel_resid the largest) and sys_info (nsys entries, host) may
@@ -384,6 +395,83 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
 int hec_batch_apply(hec_batch_t B, int32_t op, const double *b, double *x, int32_t nrhs,
                     void *stream);
 void hec_batch_destroy(hec_batch_t B);
+
+/* ---------------------------------------------------------------- serving */
+/* A solve server: requests (a matrix, a right-hand side, the ILU level) are
+ * queued, admitted in arrival order when their device memory fits the
+ * budget, set up (HEC layout, ILU(k), level schedule) and solved with
+ * restarted GMRES(m) to tol -- the paper's per-system method -- by `lanes`
+ * host threads, each with its own CUDA stream, so that the solves of
+ * different requests overlap on the device and a lane takes the next request
+ * as soon as its last one is done (continuous batching).  A request's matrix,
+ * factors and Krylov basis stay resident on the device while it runs; with a
+ * nonzero key they stay resident afterwards too (least recently used evicted
+ * first when the budget needs room), and later requests with the same key
+ * reuse them without setup (a key serves one request at a time: a request
+ * whose key is in use waits, and later requests may start before it).  Systems of at most small_rows unknowns run on
+ * the batched kernel as one-CTA launches, larger ones on the single-system
+ * path with RAS blocks of about block_rows rows.  A request's result depends
+ * only on the request: it is bit-identical alone and in any mix.  The paper
+ * has no serving layer; this is the library's extension. */
+typedef struct hec_server_s *hec_server_t;
+
+typedef struct {
+    int64_t device_budget;  /* bytes for resident requests; 0 = half the free memory */
+    int32_t lanes;          /* concurrent solves; 0 = 8                                */
+    int32_t restart;        /* GMRES(m), <= 31; 0 = 30                                 */
+    int32_t maxit;          /* Arnoldi steps per solve; 0 = 20000                      */
+    int32_t flags;          /* HEC_MIXED_FP32: FP32 inner cycles, FP64 refinement     */
+    double tol;             /* relative residual; 0 = 1e-8                             */
+    int32_t small_rows;     /* 0 = 32768                                               */
+    int32_t block_rows;     /* 0 = 16384                                               */
+    int32_t keep_solutions; /* 1: keep x for hec_server_solution; 0: discard           */
+    int32_t reserved;
+} hec_server_opts_t;
+
+typedef struct {
+    hec_csr_t A;      /* host arrays, copied at submit; with a key, A.row_ptr may
+                         be NULL (A.n still set): solve with the system resident
+                         under that key (HEC_ERR_INVALID in the result if none)     */
+    const double *b;  /* host, A.n values, copied                                   */
+    int32_t ilu_k;    /* >= 0                                                       */
+    int32_t reserved;
+    uint64_t key;     /* 0: nothing kept; else requests with equal keys must carry
+                         the same matrix and level and reuse its set-up form         */
+    uint64_t tag;     /* returned with the result                                   */
+} hec_request_t;
+
+typedef struct {
+    uint64_t ticket, tag;
+    int32_t status;     /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN or an error code           */
+    int32_t iters;      /* Arnoldi steps                                               */
+    double rel_resid;   /* true FP64 ||b - A x|| / ||b||                               */
+    double t_submit;    /* seconds on the server clock (hec_server_clock)              */
+    double t_start;     /* admitted to a lane                                          */
+    double t_setup;     /* set-up done (= t_start when reused)                         */
+    double t_done;
+    int32_t lane;
+    int32_t reused;     /* 1: the matrix and factors were resident already             */
+    int32_t fp64_finish;/* 1: the mixed-precision solve was finished in FP64           */
+    int32_t reserved;
+    int64_t device_bytes;
+} hec_result_t;
+
+int hec_server_create(const hec_server_opts_t *opts, hec_server_t *out);
+/* Queues a request; *ticket identifies it.  Never blocks on the device. */
+int hec_server_submit(hec_server_t S, const hec_request_t *req, uint64_t *ticket);
+/* Moves up to max finished results into out (completion order), waiting up
+ * to wait_ms for the first; *count = number returned. */
+int hec_server_poll(hec_server_t S, hec_result_t *out, int32_t max, int32_t *count,
+                    int32_t wait_ms);
+/* Copies the solution of a finished request (keep_solutions = 1) and drops it. */
+int hec_server_solution(hec_server_t S, uint64_t ticket, double *x, int32_t n);
+/* Seconds since the server started (the clock of hec_result_t). */
+double hec_server_clock(hec_server_t S);
+/* Requests queued, running, finished-but-not-polled; bytes reserved. */
+int hec_server_stats(hec_server_t S, int32_t *queued, int32_t *running, int32_t *finished,
+                     int64_t *reserved_bytes);
+/* Waits for every submitted request to finish, then frees everything. */
+void hec_server_destroy(hec_server_t S);
 
 #ifdef __cplusplus
 }

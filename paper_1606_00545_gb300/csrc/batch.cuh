@@ -97,6 +97,7 @@ struct BatchArgs {
     int *queue;
     int *err;
     BatchResult *res;
+    const unsigned char *only;  // nullable: solve only the systems marked 1
 };
 
 // Dynamic shared memory of one CTA.  The triangular-solve stages and the
@@ -106,7 +107,11 @@ struct BatchSmem {
 };
 
 // Doubles of per-right-hand-side state: h, h2, cs, sn, g, y, sig, scalars.
-__host__ __device__ inline int batch_rhs_doubles(int m) { return 7 * m + 22; }
+__host__ __device__ inline int batch_rhs_doubles(int m) { return 7 * m + 24; }
+
+// Per-system status of a mixed-precision solve whose FP32 cycles stopped
+// reducing the FP64 residual; the host finishes such systems in FP64.
+constexpr int kBatchStagnated = 100;
 
 __host__ __device__ inline BatchSmem batch_smem(int nstages, int stage_bytes, int sstages,
                                                 int sbytes, int ring_slots, int NR, int tsz, int m,

@@ -458,7 +458,7 @@ int resolve_launch(hec_batch_s *B, bool fp32, int nrhs, int m, Launch &L)
 // Runs the batched kernel once; b and x are device arrays.  ms: device time.
 int run_batch(hec_batch_s *B, int op, bool fp32, const double *b, double *x, int nrhs, double tol,
               int maxit, int m, double inner_rtol, bool x0_zero, long long spin, cudaStream_t st,
-              float *ms)
+              float *ms, const unsigned char *only = nullptr)
 {
     HEC_TRY(build_layout(B, st));
     const bool need_fac = B->ilu_k >= 0;
@@ -529,6 +529,7 @@ int run_batch(hec_batch_s *B, int op, bool fp32, const double *b, double *x, int
     a.queue = B->queue.as<int>();
     a.err = B->err.as<int>();
     a.res = B->res.as<BatchResult>();
+    a.only = only;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) {
         HEC_CK(cudaEventCreate(&e0));
@@ -822,16 +823,46 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
     }
     HEC_TRY(run_batch(B, BOP_SOLVE, fp32, db, dx, nrhs, tol, maxit, restart, fp32 ? 1e-5 : 0.0,
                       (o.flags & HEC_X0_ZERO) != 0, spin, st, nullptr));
-    if (!xdev) {
-        HEC_CK(cudaMemcpyAsync(x, dx, nb, cudaMemcpyDeviceToHost, st));
-        d2h += (int64_t)nb;
-    }
     std::vector<BatchResult> res(B->nsys);
     HEC_CK(cudaMemcpyAsync(res.data(), B->res.p, sizeof(BatchResult) * res.size(),
                            cudaMemcpyDeviceToHost, st));
     HEC_CK(cudaStreamSynchronize(st));
+    // systems whose FP32 cycles stopped refining: finish them in FP64, from
+    // their current x, in one more launch restricted to them
+    std::vector<unsigned char> only(B->nsys, 0);
+    int nstag = 0;
+    for (int s = 0; s < B->nsys; ++s)
+        if (res[s].status == kBatchStagnated) {
+            only[s] = 1;
+            ++nstag;
+        }
+    int launches = 1;
+    if (nstag > 0) {
+        DevBuf donly;
+        HEC_TRY(upload(donly, only, st));
+        HEC_TRY(run_batch(B, BOP_SOLVE, false, db, dx, nrhs, tol, maxit, restart, 0.0, false, spin,
+                          st, nullptr, donly.as<unsigned char>()));
+        std::vector<BatchResult> r64(B->nsys);
+        HEC_CK(cudaMemcpyAsync(r64.data(), B->res.p, sizeof(BatchResult) * r64.size(),
+                               cudaMemcpyDeviceToHost, st));
+        HEC_CK(cudaStreamSynchronize(st));
+        for (int s = 0; s < B->nsys; ++s)
+            if (only[s]) {
+                res[s].iters += r64[s].iters;
+                res[s].cycles += r64[s].cycles;
+                res[s].status = r64[s].status;
+                res[s].rel_resid = r64[s].rel_resid;
+            }
+        launches = 2;
+    }
+    if (!xdev) {
+        HEC_CK(cudaMemcpyAsync(x, dx, nb, cudaMemcpyDeviceToHost, st));
+        d2h += (int64_t)nb;
+    }
+    HEC_CK(cudaStreamSynchronize(st));
     int status = HEC_OK;
     hec_solve_info_t I{};
+    I.fp64_finish = nstag;
     for (int s = 0; s < B->nsys; ++s) {
         const BatchResult &r = res[s];
         I.iters += r.iters;
@@ -848,7 +879,7 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
         }
     }
     I.status = status;
-    I.kernel_launches = 1;
+    I.kernel_launches = launches;
     I.h2d_bytes = h2d;
     I.d2h_bytes = d2h;
     if (info)

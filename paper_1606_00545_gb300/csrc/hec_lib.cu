@@ -82,6 +82,20 @@ int device_smem_optin()
     return optin;
 }
 
+void keep_pool_memory()
+{
+    static std::once_flag once;
+    std::call_once(once, []() {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+}
+
 bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes at;
@@ -1355,6 +1369,25 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
     }
     if (h.err)
         return fail(h.err, "a bounded device wait ran out during the solve");
+    if (mixed && h.stagnated && !h.err) {
+        // the FP32 cycles stopped refining: finish in FP64 from the current x
+        hec_solve_opts_t o64 = o;
+        o64.flags &= ~(HEC_MIXED_FP32 | HEC_X0_ZERO);
+        hec_solve_info_t i64{};
+        status = krylov_solve(A, M, b, x, tol, std::max(0, maxit - h.iters), restart, &o64, stream,
+                              &i64);
+        if (info) {
+            info->iters += i64.iters;
+            info->restarts += i64.restarts;
+            info->status = i64.status;
+            info->rel_resid = i64.rel_resid;
+            info->est_resid = i64.est_resid;
+            info->kernel_launches += i64.kernel_launches;
+            info->h2d_bytes += i64.h2d_bytes;
+            info->d2h_bytes += i64.d2h_bytes;
+            info->fp64_finish = 1;
+        }
+    }
     return status;
 }
 

@@ -34,6 +34,9 @@
 // up to (CTA size - 32) rows, so issuing stays off the solving threads' path.
 // Every wait is bounded; a wait that runs out sets the error word, drains the
 // copies in flight and ends the CTA.
+#include <mutex>
+#include <set>
+
 #include "../../include/hecgpu.h"
 #include "batch.cuh"
 #include "ptx.cuh"
@@ -44,7 +47,9 @@ namespace {
 constexpr long long kBatchDrainPolls = 1ll << 24;
 
 // Scalars of a right-hand side's state.
-enum { SC_BETA = 0, SC_BNORM, SC_BCYCLE, SC_EST, SC_WW, SC_W2, SC_ACTIVE, SC_BROKE };
+enum { SC_BETA = 0, SC_BNORM, SC_BCYCLE, SC_EST, SC_WW, SC_W2, SC_ACTIVE, SC_BROKE,
+       SC_RUN = 8 /* cycles in a row whose true residual exceeded 10x the estimate */,
+       SC_STAG = 9 };
 // Shared integers.
 enum { MI_SYS = 0, MI_STOP };
 
@@ -784,6 +789,18 @@ template <class T, int NR> struct Batch {
                 const double beta = sqrt(reinterpret_cast<const double *>(out)[tid]);
                 const double bn = v.sc[SC_BNORM];
                 const bool act = bn > 0.0 && !(beta <= a.tol * bn);
+                // the previous FP32 cycle promised a residual of SC_EST: a
+                // true FP64 residual far above it with less than a halving
+                // over the cycle, two cycles in a row, means the FP32
+                // arithmetic limits the refinement
+                if (cycles == 0)
+                    v.sc[SC_RUN] = 0.0;
+                else if (v.sc[SC_ACTIVE] != 0.0)
+                    v.sc[SC_RUN] = (v.sc[SC_EST] > 0.0 && beta > 10.0 * v.sc[SC_EST] &&
+                                    beta > 0.5 * v.sc[SC_BCYCLE])
+                                       ? v.sc[SC_RUN] + 1.0
+                                       : 0.0;
+                v.sc[SC_STAG] = (sizeof(T) == 4 && act && v.sc[SC_RUN] >= 2.0) ? 1.0 : 0.0;
                 v.sc[SC_BETA] = beta;
                 v.sc[SC_ACTIVE] = act ? 1.0 : 0.0;
                 v.sc[SC_BCYCLE] = beta;
@@ -792,11 +809,12 @@ template <class T, int NR> struct Batch {
                 v.g[0] = act ? beta : 0.0;
             }
             __syncthreads();
-            bool any = false, bad = false;
+            bool any = false, bad = false, stag = false;
             worst = 0.0;
             for (int r = 0; r < NR; ++r) {
                 RhsView v = rv(r);
                 any |= v.sc[SC_ACTIVE] != 0.0;
+                stag |= v.sc[SC_STAG] != 0.0;
                 bad |= !isfinite(v.sc[SC_BETA]);
                 const double rel = v.sc[SC_BNORM] > 0.0 ? v.sc[SC_BETA] / v.sc[SC_BNORM] : 0.0;
                 worst = rel > worst ? rel : worst;
@@ -807,6 +825,10 @@ template <class T, int NR> struct Batch {
             }
             if (!any)
                 break;
+            if (stag) {
+                status = kBatchStagnated;
+                break;
+            }
             if (steps >= a.maxit) {
                 status = HEC_MAXIT;
                 break;
@@ -987,6 +1009,10 @@ template <class T, int NR> struct Batch {
             const int sidx = misc[MI_SYS];
             if (sidx < 0)
                 return;
+            if (a.only && !a.only[sidx]) {
+                __syncthreads();  // every thread has read misc before it is rewritten
+                continue;
+            }
             s = a.sys[sidx];
             nE = (long long)s.n * NR;
             Ep = ((nE + nt - 1) >> tshift) << tshift;
@@ -1014,11 +1040,36 @@ __global__ void __launch_bounds__(kBatchMaxThreads) k_batch(const __grid_constan
 
 template <class T, int NR> const void *kernel_ptr() { return (const void *)k_batch<T, NR>; }
 
-const void *select(bool fp32, int NR)
+const void *select_kernel(bool fp32, int NR)
 {
     if (fp32)
         return NR == 1 ? kernel_ptr<float, 1>() : NR == 2 ? kernel_ptr<float, 2>() : kernel_ptr<float, 4>();
     return NR == 1 ? kernel_ptr<double, 1>() : NR == 2 ? kernel_ptr<double, 2>() : kernel_ptr<double, 4>();
+}
+
+// The dynamic shared memory limit is an attribute of the kernel, shared by
+// every thread of the process: it is raised once, to the device's opt-in
+// maximum, never lowered per launch (concurrent launches of different sizes
+// from several host threads would otherwise race on it).
+cudaError_t prepare(const void *k)
+{
+    static std::mutex mu;
+    static std::set<const void *> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(k))
+        return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, k);
+    if (e == cudaSuccess)  // the opt-in limit covers static and dynamic shared memory
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        done.insert(k);
+    return e;
 }
 
 } // namespace
@@ -1026,8 +1077,8 @@ const void *select(bool fp32, int NR)
 int launch_batch(const BatchArgs &a, bool fp32, int NR, int threads, int grid, int smem,
                  cudaStream_t s)
 {
-    const void *k = select(fp32, NR);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void *k = select_kernel(fp32, NR);
+    cudaError_t e = prepare(k);
     if (e != cudaSuccess)
         return (int)e;
     void *args[] = {(void *)&a};
@@ -1036,8 +1087,8 @@ int launch_batch(const BatchArgs &a, bool fp32, int NR, int threads, int grid, i
 
 int batch_occupancy(bool fp32, int NR, int threads, int smem)
 {
-    const void *k = select(fp32, NR);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    const void *k = select_kernel(fp32, NR);
+    if (prepare(k) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

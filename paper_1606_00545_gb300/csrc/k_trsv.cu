@@ -28,6 +28,8 @@
 // grid-wide synchronisation.  Every wait is bounded: a wait that runs out
 // sets the device error word, one thread waits (bounded) for the copies still
 // in flight, and the CTA returns.
+#include <mutex>
+
 #include "ptx.cuh"
 #include "reduce.cuh"
 
@@ -399,12 +401,31 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
     }
 }
 
+// The dynamic shared memory limit is a process-wide attribute of the kernel:
+// raised once to the device's opt-in maximum, so that launches of different
+// sizes from several host threads never race on it.
+template <class T> static cudaError_t prepare_trsv()
+{
+    static std::once_flag once;
+    static cudaError_t e = cudaSuccess;
+    std::call_once(once, []() {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaFuncAttributes fa{};
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncGetAttributes(&fa, k_trsv_ras<T>);
+        if (e == cudaSuccess)  // the opt-in limit covers static and dynamic shared memory
+            e = cudaFuncSetAttribute(k_trsv_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+    });
+    return e;
+}
+
 template <class T> static int launch_t(const TrsvArgs &a, cudaStream_t s)
 {
     const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1, sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(k_trsv_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess)
+    if (prepare_trsv<T>() != cudaSuccess)
         return -1;
     k_trsv_ras<T><<<a.nblocks, kThreads + 64, smem, s>>>(a);
     return 0;

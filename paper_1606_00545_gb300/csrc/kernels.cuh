@@ -40,6 +40,8 @@ struct __align__(16) SolverState {
     // scalars
     double bnorm, rho, rho_prev, alpha, omega, scale, w0norm, est, rel_resid;
     double inner_rtol, beta_cycle; // mixed precision: inner cycle tolerance, cycle start ||r||
+    int stag_run, stagnated;       // mixed precision: cycles in a row whose true FP64
+                                   // residual exceeded 10x the FP32 cycle's estimate
     double dots[kMaxDots];
     int iters, restarts, status, done;
     int skip, s_conv, zero_x, j;

@@ -125,6 +125,15 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         double beta = sqrt(s[0]);
         if (st->done)
             break;
+        // mixed precision: the previous FP32 cycle promised a residual of
+        // est * ||b||; a true FP64 residual far above it, with less than a
+        // halving over the cycle, means the FP32 arithmetic, not the Krylov
+        // space, limits the refinement
+        const double promised = st->est * st->bnorm;
+        if (st->inner_rtol > 0.0 && st->restarts > 0)
+            st->stag_run = (promised > 0.0 && beta > 10.0 * promised && beta > 0.5 * st->beta_cycle)
+                               ? st->stag_run + 1
+                               : 0;
         st->est = beta / st->bnorm;
         if (beta <= st->tol * st->bnorm) {
             st->done = 1;
@@ -134,6 +143,11 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
             st->status = HEC_BREAKDOWN;
         } else if (st->iters >= st->maxit) {
             st->done = 1;
+            st->status = HEC_MAXIT;
+        } else if (st->stag_run >= 2) {
+            // two cycles in a row: the host continues in FP64
+            st->done = 1;
+            st->stagnated = 1;
             st->status = HEC_MAXIT;
         } else {
             st->restarts += 1;

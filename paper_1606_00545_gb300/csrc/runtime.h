@@ -46,10 +46,19 @@ struct AllocFns {
 AllocFns current_allocator();
 void set_allocator(const AllocFns &f);
 
-// One device allocation, returned through the allocator that made it.
+// Keeps freed memory of the device's default stream-ordered pool cached
+// instead of returning it at every synchronisation.
+void keep_pool_memory();
+
+// One device allocation, returned through the allocator that made it.  The
+// default allocator is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// stream of the allocation), so a handle's allocations and frees never
+// synchronise the device while other streams run; a handle must therefore be
+// destroyed before the stream it was created on.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t st = nullptr;
     AllocFns fns;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
@@ -60,9 +69,9 @@ struct DevBuf {
         if (!p)
             return;
         if (fns.free_)
-            fns.free_(p, nullptr, fns.ctx);
+            fns.free_(p, (void *)st, fns.ctx);
         else
-            cudaFree(p);
+            cudaFreeAsync(p, st);
         p = nullptr;
         bytes = 0;
     }
@@ -72,17 +81,19 @@ struct DevBuf {
         if (nbytes == 0)
             nbytes = 16;
         fns = current_allocator();
+        st = s;
         if (fns.alloc) {
             p = fns.alloc(nbytes, (void *)s, fns.ctx);
             if (!p)
                 return fail(HEC_ERR_OOM, "allocator returned NULL for %zu bytes", nbytes);
         } else {
-            cudaError_t e = cudaMalloc(&p, nbytes);
+            keep_pool_memory();
+            cudaError_t e = cudaMallocAsync(&p, nbytes, s);
             if (e != cudaSuccess) {
                 p = nullptr;
                 cudaGetLastError();
                 return fail(e == cudaErrorMemoryAllocation ? HEC_ERR_OOM : HEC_ERR_CUDA,
-                            "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
+                            "cudaMallocAsync(%zu): %s", nbytes, cudaGetErrorString(e));
             }
         }
         bytes = nbytes;

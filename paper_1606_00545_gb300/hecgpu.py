@@ -80,7 +80,7 @@ class SolveOpts_t(C.Structure):
 
 class SolveInfo_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
-                ("reserved", C.c_int32), ("rel_resid", C.c_double), ("est_resid", C.c_double),
+                ("fp64_finish", C.c_int32), ("rel_resid", C.c_double), ("est_resid", C.c_double),
                 ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64)]
 
@@ -105,6 +105,26 @@ class BatchInfo_t(C.Structure):
 class BatchSysInfo_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("status", C.c_int32),
                 ("reserved", C.c_int32), ("rel_resid", C.c_double)]
+
+
+class ServerOpts_t(C.Structure):
+    _fields_ = [("device_budget", C.c_int64), ("lanes", C.c_int32), ("restart", C.c_int32),
+                ("maxit", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double),
+                ("small_rows", C.c_int32), ("block_rows", C.c_int32),
+                ("keep_solutions", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Request_t(C.Structure):
+    _fields_ = [("A", CSR_t), ("b", C.c_void_p), ("ilu_k", C.c_int32), ("reserved", C.c_int32),
+                ("key", C.c_uint64), ("tag", C.c_uint64)]
+
+
+class Result_t(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32),
+                ("iters", C.c_int32), ("rel_resid", C.c_double), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_setup", C.c_double), ("t_done", C.c_double),
+                ("lane", C.c_int32), ("reused", C.c_int32), ("fp64_finish", C.c_int32),
+                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 _vp = C.c_void_p
@@ -152,6 +172,14 @@ _SIGS = {
                               C.POINTER(SolveInfo_t), _vp], C.c_int),
     "hec_batch_apply": ([_vp, _i32, _vp, _vp, _i32, _vp], C.c_int),
     "hec_batch_destroy": ([_vp], None),
+    "hec_server_create": ([C.POINTER(ServerOpts_t), C.POINTER(_vp)], C.c_int),
+    "hec_server_submit": ([_vp, C.POINTER(Request_t), C.POINTER(C.c_uint64)], C.c_int),
+    "hec_server_poll": ([_vp, _vp, _i32, C.POINTER(_i32), _i32], C.c_int),
+    "hec_server_solution": ([_vp, C.c_uint64, _vp, _i32], C.c_int),
+    "hec_server_clock": ([_vp], C.c_double),
+    "hec_server_stats": ([_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32),
+                          C.POINTER(_i64)], C.c_int),
+    "hec_server_destroy": ([_vp], None),
 }
 
 _lock = threading.Lock()
@@ -564,3 +592,72 @@ def krylov_solve_batched(B: Batch, b, x, nrhs=1, tol=1e-8, maxit=1000, restart=3
 def hec_batch_apply(B: Batch, op, b, x, nrhs=1, stream=None):
     _check(load_library().hec_batch_apply(B.handle, int(op), _ptr(b), _ptr(x), int(nrhs),
                                           _stream(stream)), "hec_batch_apply")
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """The solve server (continuous batching over lanes of CUDA streams)."""
+
+    def __init__(self, device_budget=0, lanes=0, restart=0, maxit=0, flags=0, tol=0.0,
+                 small_rows=0, block_rows=0, keep_solutions=True):
+        lib = load_library()
+        o = ServerOpts_t(int(device_budget), int(lanes), int(restart), int(maxit), int(flags),
+                         float(tol), int(small_rows), int(block_rows), int(bool(keep_solutions)), 0)
+        h = C.c_void_p()
+        _check(lib.hec_server_create(C.byref(o), C.byref(h)), "hec_server_create")
+        self._h = h
+
+    def submit(self, A, b, ilu_k=0, key=0, tag=0):
+        """A: a CSR matrix, or None to solve with the system resident under key."""
+        bb = np.ascontiguousarray(b, np.float64)
+        if A is None:
+            csr = CSR_t(len(bb), 0, None, None, None, 0)
+        else:
+            rp = np.ascontiguousarray(A.row_ptr, np.int32)
+            ci = np.ascontiguousarray(A.col, np.int32)
+            va = np.ascontiguousarray(A.val, np.float64)
+            csr = CSR_t(len(rp) - 1, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)
+        req = Request_t(csr, bb.ctypes.data, int(ilu_k), 0, int(key), int(tag))
+        t = C.c_uint64()
+        _check(_lib.hec_server_submit(self._h, C.byref(req), C.byref(t)), "hec_server_submit")
+        return t.value
+
+    def poll(self, max_results=256, wait_ms=0):
+        buf = (Result_t * max_results)()
+        cnt = C.c_int32()
+        _check(_lib.hec_server_poll(self._h, C.cast(buf, C.c_void_p), int(max_results),
+                                    C.byref(cnt), int(wait_ms)), "hec_server_poll")
+        return [{f: getattr(buf[i], f) for f, _ in Result_t._fields_} for i in range(cnt.value)]
+
+    def solution(self, ticket, n):
+        x = np.empty(n, np.float64)
+        _check(_lib.hec_server_solution(self._h, int(ticket), x.ctypes.data, int(n)),
+               "hec_server_solution")
+        return x
+
+    def clock(self):
+        return _lib.hec_server_clock(self._h)
+
+    def stats(self):
+        q, r, f = C.c_int32(), C.c_int32(), C.c_int32()
+        b = C.c_int64()
+        _check(_lib.hec_server_stats(self._h, C.byref(q), C.byref(r), C.byref(f), C.byref(b)),
+               "hec_server_stats")
+        return {"queued": q.value, "running": r.value, "finished": f.value, "reserved": b.value}
+
+    def close(self):
+        if self._h and _lib is not None:
+            _lib.hec_server_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -23,6 +23,12 @@ The workloads stand in for the paper's test matrices (Section 3: the
   N(0, variance)), with the diagonal set to a multiple of the off-diagonal
   absolute row sum (strictly diagonally dominant).
 * ``rhs_uniform(n, seed)`` -- right-hand side uniform on [-1, 1].
+* ``stencil27_lognormal(N, sigma, seed)`` -- symmetric 27-point coupling on
+  N^3 with one log-normal coefficient per neighbour pair (and per missing
+  neighbour at the boundary, added to the diagonal only): an M-matrix,
+  symmetric positive definite.
+* ``serving_requests(count, seed)`` -- the request mix of the serving
+  workload (sizes log-uniform, stencil and ILU level drawn per request).
 * ``batch_diffusion2d(nsys, smin, smax, sigma, seed)`` -- a batch of
   independent 2D log-normal diffusion systems with square sides drawn
   uniformly from [smin, smax], concatenated (system offsets, int64 row
@@ -48,6 +54,9 @@ __all__ = [
     "random_sparse",
     "batch_diffusion2d",
     "Batch",
+    "stencil27_lognormal",
+    "serving_requests",
+    "serving_matrix",
 ]
 
 
@@ -373,3 +382,82 @@ def batch_diffusion2d(nsys: int, smin: int, smax: int, sigma: float, seed: int) 
     col = np.concatenate([A.col for A in mats])
     val = np.concatenate([A.val for A in mats])
     return Batch(sys_ptr, row_ptr, col, val, sides)
+
+
+_OFF27 = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+          if (dz, dy, dx) > (0, 0, 0)]  # the 13 "forward" neighbour offsets
+
+
+def stencil27_lognormal(N: int, sigma: float, seed: int) -> CSR:
+    """27-point coupling on N^3 (x fastest), log-normal(0, sigma) coefficients.
+
+    From ``default_rng(seed)``: G of shape (13, N, N, N) -- G[o, cell] couples
+    cell and cell + offset_o (offsets in the order of ``_OFF27``) -- then H of
+    the same shape, the coupling of cell with a missing neighbour at
+    cell - offset_o.  Off-diagonal A_ij = -kappa_ij; A_ii = sum of the
+    kappa of all 26 neighbour slots of cell i (a slot outside the grid keeps
+    its coefficient on the diagonal, like a Dirichlet neighbour).  Both draws
+    are exp(sigma * standard normal)."""
+    rng = np.random.default_rng(seed)
+    G = np.exp(sigma * rng.standard_normal((13, N, N, N)))
+    Hh = np.exp(sigma * rng.standard_normal((13, N, N, N)))
+    n = N ** 3
+    idx = np.arange(n, dtype=np.int64).reshape(N, N, N)  # (z, y, x)
+    diag = np.zeros((N, N, N))
+    rows_l, cols_l, vals_l = [], [], []
+    for o, (dx, dy, dz) in enumerate(_OFF27):
+        # forward neighbour: cell + (dx, dy, dz)
+        zs = slice(max(0, -dz), N - max(0, dz))
+        ys = slice(max(0, -dy), N - max(0, dy))
+        xs = slice(max(0, -dx), N - max(0, dx))
+        zt = slice(max(0, dz), N - max(0, -dz))
+        yt = slice(max(0, dy), N - max(0, -dy))
+        xt = slice(max(0, dx), N - max(0, -dx))
+        k = G[o][zs, ys, xs]
+        a = idx[zs, ys, xs].ravel()
+        b = idx[zt, yt, xt].ravel()
+        rows_l += [a, b]
+        cols_l += [b, a]
+        vals_l += [-k.ravel(), -k.ravel()]
+        diag[zs, ys, xs] += k
+        diag[zt, yt, xt] += k
+        # forward slot leaving the grid: G keeps its value on the diagonal
+        m = np.ones((N, N, N), dtype=bool)
+        m[zs, ys, xs] = False
+        diag[m] += G[o][m]
+        # backward slot leaving the grid: H
+        m = np.ones((N, N, N), dtype=bool)
+        m[zt, yt, xt] = False
+        diag[m] += Hh[o][m]
+    rows_l.append(idx.ravel())
+    cols_l.append(idx.ravel())
+    vals_l.append(diag.ravel())
+    return _assemble(n, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(vals_l))
+
+
+def serving_requests(count: int, seed: int, nmin: float = 1e3, nmax: float = 1e6):
+    """The request mix: from ``default_rng(seed)``, per request in order --
+    log10(n) uniform on [log10 nmin, log10 nmax]; stencil uniform over
+    (5, 7, 27); ILU level 0 or 1 with probability 1/2; a coefficient seed
+    (integers below 2^31 - 1).  The grid side is round(n^(1/d)) (at least 2).
+    Returns dicts {stencil, side, n, k, seed}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = 10.0 ** rng.uniform(np.log10(nmin), np.log10(nmax))
+        st = int(rng.choice([5, 7, 27]))
+        k = int(rng.integers(0, 2))
+        cs = int(rng.integers(0, 2 ** 31 - 1))
+        d = 2 if st == 5 else 3
+        side = max(2, int(round(n ** (1.0 / d))))
+        out.append({"stencil": st, "side": side, "n": side ** d, "k": k, "seed": cs})
+    return out
+
+
+def serving_matrix(req, sigma: float = 2.0) -> CSR:
+    """The matrix of one request of ``serving_requests``."""
+    if req["stencil"] == 5:
+        return diffusion2d_5pt_lognormal(req["side"], sigma, req["seed"])
+    if req["stencil"] == 7:
+        return diffusion3d_7pt_lognormal(req["side"], sigma, req["seed"])
+    return stencil27_lognormal(req["side"], sigma, req["seed"])

@@ -278,3 +278,16 @@ def test_c4_full_size_mixed(H, orc):
                 xd = np.linalg.solve(D, bj)
                 err = np.linalg.norm(xj - xd) / np.linalg.norm(xd)
                 assert err <= 2 * np.linalg.cond(D) * 1e-8, (s, err)
+
+
+def test_batch_stagnated_systems_finish_in_fp64(H):
+    """tol below the attainable accuracy: every system's FP32 cycles stagnate,
+    a second launch restricted to them continues in FP64 from their x."""
+    sy = [synth.diffusion2d_5pt_lognormal(40, 2.0, 5), synth.poisson2d_5pt(12)]
+    B = H.hec_build_batched(sy)
+    H.ilu_k_setup_batched(B, 0)
+    x = dev(np.zeros((B.rows, 1)))
+    info, per = H.krylov_solve_batched(B, dev(np.ones((B.rows, 1))), x, nrhs=1, tol=1e-17,
+                                       maxit=600, flags=H.MIXED_FP32, per_system=True)
+    assert info["fp64_finish"] == 2 and info["kernel_launches"] == 2
+    assert all(p["status"] == H.MAXIT and p["rel_resid"] < 1e-11 for p in per), per

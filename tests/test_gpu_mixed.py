@@ -154,3 +154,36 @@ def test_c3_irregular_96_mixed_gmres50(H, orc):
     assert info["status"] == H.OK and info["rel_resid"] <= 1e-8, info
     assert np.linalg.norm(b - orc.spmv(A, xg)) / np.linalg.norm(b) <= 1e-8
     assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) <= 1e-6
+
+
+def test_mixed_ill_conditioned_converges(H, orc):
+    """An ill-conditioned 859^2 2D log-normal (sigma = 2) system with ILU(1)
+    on RAS blocks (about 4,000 GMRES(30) steps): the mixed solve reaches the
+    FP64 residual 1e-8, by FP32 refinement alone or with an FP64 finish."""
+    req = synth.serving_requests(24, 8)[16]
+    A = synth.serving_matrix(req)
+    b = synth.rhs_uniform(A.n, 16)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, req["k"], 46, 1)
+    H.level_schedule(P)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=20000, restart=30, method=H.GMRES,
+                          flags=H.MIXED_FP32 | H.X0_ZERO)
+    print("ill-conditioned mixed solve:", info)
+    assert info["status"] == H.OK, info
+    assert np.linalg.norm(b - orc.spmv(A, host(x))) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_mixed_unreachable_tol_switches_to_fp64(H):
+    """A tolerance below what the arithmetic reaches: the mixed solve
+    stagnates, switches to FP64 and ends at maxit."""
+    A = synth.diffusion2d_5pt_lognormal(48, 2.0, 3)
+    b = synth.rhs_uniform(A.n, 4)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    H.level_schedule(P)
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-17, maxit=1500, restart=30, method=H.GMRES,
+                          flags=H.MIXED_FP32 | H.X0_ZERO)
+    assert info["fp64_finish"] == 1 and info["status"] == H.MAXIT and info["iters"] == 1500
+    assert info["rel_resid"] < 1e-11

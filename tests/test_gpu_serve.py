@@ -1,0 +1,136 @@
+"""The solve server: continuous batching over lanes, admission by device
+memory, keyed residency, results independent of the mix.
+
+Tolerance: every solve reaches the true FP64 relative residual 1e-8 (checked
+with the oracle's SpMV); the same request gives a bit-identical solution
+alone and in a mix (each request's arithmetic is fixed by the request)."""
+import numpy as np
+import pytest
+
+from paper_1606_00545_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu
+    hecgpu.load_library()
+    torch.cuda.set_device(0)
+    return hecgpu
+
+
+def mix():
+    """Requests on both paths (one-CTA batched for <= 32768 unknowns, the
+    single-system RAS path above), all three stencils, ILU(0) and ILU(1)."""
+    reqs = []
+    for i, (st, side, k) in enumerate([(5, 20, 0), (7, 12, 1), (27, 9, 0), (5, 90, 1),
+                                       (7, 40, 0), (27, 33, 1), (5, 200, 0), (7, 16, 0),
+                                       (27, 14, 1), (5, 64, 0)]):
+        A = synth.serving_matrix({"stencil": st, "side": side, "k": k, "seed": 100 + i})
+        reqs.append((A, synth.rhs_uniform(A.n, 200 + i), k))
+    return reqs
+
+
+def run_all(H, reqs, lanes, budget=0, keys=None, flags=None):
+    flags = H.MIXED_FP32 if flags is None else flags
+    out = {}
+    with H.Server(lanes=lanes, device_budget=budget, flags=flags) as S:
+        tickets = []
+        for i, (A, b, k) in enumerate(reqs):
+            tickets.append(S.submit(A, b, ilu_k=k, key=(keys[i] if keys else 0), tag=i))
+        got = []
+        while len(got) < len(reqs):
+            got += S.poll(wait_ms=200)
+        for r in got:
+            out[r["tag"]] = (r, S.solution(r["ticket"], reqs[r["tag"]][0].n))
+    return out
+
+
+def test_serve_mix_converges(H, orc):
+    reqs = mix()
+    res = run_all(H, reqs, lanes=6)
+    assert sorted(res) == list(range(len(reqs)))
+    for i, (A, b, k) in enumerate(reqs):
+        r, x = res[i]
+        assert r["status"] == H.OK, r
+        assert np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b) <= 1e-8
+        assert r["t_submit"] <= r["t_start"] <= r["t_setup"] <= r["t_done"]
+    # the lanes overlapped: some request started before another one finished
+    iv = sorted((res[i][0]["t_start"], res[i][0]["t_done"]) for i in res)
+    assert any(iv[j + 1][0] < iv[j][1] for j in range(len(iv) - 1))
+
+
+def test_serve_result_identical_alone_and_in_mix(H):
+    reqs = mix()
+    together = run_all(H, reqs, lanes=8)
+    for i in (0, 3, 5, 6):
+        alone = run_all(H, [reqs[i]], lanes=1)
+        assert np.array_equal(alone[0][1], together[i][1]), i
+        assert alone[0][0]["iters"] == together[i][0]["iters"]
+
+
+def test_serve_admission_by_device_memory(H, orc):
+    """A budget below two requests' footprint: requests still all complete,
+    one at a time."""
+    reqs = [r for r in mix() if r[0].n > 5000][:4]
+    res = run_all(H, reqs, lanes=4, budget=1)
+    iv = sorted((res[i][0]["t_start"], res[i][0]["t_done"]) for i in res)
+    assert all(iv[j + 1][0] >= iv[j][1] for j in range(len(iv) - 1))
+    for i, (A, b, k) in enumerate(reqs):
+        assert res[i][0]["status"] == H.OK
+        assert np.linalg.norm(b - orc.spmv(A, res[i][1])) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_serve_keyed_reuse(H, orc):
+    A = synth.serving_matrix({"stencil": 7, "side": 36, "k": 1, "seed": 5})
+    bs = [synth.rhs_uniform(A.n, s) for s in (1, 2, 3)]
+    with H.Server(lanes=2, flags=H.MIXED_FP32) as S:
+        t = [S.submit(A, b, ilu_k=1, key=77, tag=i) for i, b in enumerate(bs)]
+        got = []
+        while len(got) < 3:
+            got += S.poll(wait_ms=200)
+        got.sort(key=lambda r: r["tag"])
+        assert [r["reused"] for r in got] == [0, 1, 1]
+        # one key serves one request at a time
+        assert got[1]["t_start"] >= got[0]["t_done"] and got[2]["t_start"] >= got[1]["t_done"]
+        for r, b in zip(got, bs):
+            x = S.solution(r["ticket"], A.n)
+            assert r["status"] == H.OK
+            assert np.linalg.norm(b - orc.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
+        assert S.stats()["reserved"] > 0  # the keyed system stays resident
+        # a keyed request without its matrix uses the resident system
+        t = S.submit(None, bs[0], ilu_k=1, key=77, tag=5)
+        r = []
+        while not r:
+            r = S.poll(wait_ms=200)
+        assert r[0]["status"] == H.OK and r[0]["reused"] == 1
+        S.solution(t, A.n)
+        S.submit(None, np.ones(5), ilu_k=0, key=78, tag=6)  # nothing resident under 78
+        r = []
+        while not r:
+            r = S.poll(wait_ms=200)
+        assert r[0]["status"] == H.ERR_INVALID
+        # the same key with another matrix is refused per request
+        B = synth.serving_matrix({"stencil": 5, "side": 10, "k": 1, "seed": 6})
+        S.submit(B, np.ones(B.n), ilu_k=1, key=77, tag=9)
+        r = []
+        while not r:
+            r = S.poll(wait_ms=200)
+        assert r[0]["status"] == H.ERR_INVALID
+
+
+def test_serve_fp64_and_invalid(H, orc):
+    reqs = mix()[:3]
+    res = run_all(H, reqs, lanes=2, flags=0)
+    for i, (A, b, k) in enumerate(reqs):
+        assert res[i][0]["status"] == H.OK
+        assert np.linalg.norm(b - orc.spmv(A, res[i][1])) <= 1e-8 * np.linalg.norm(b)
+    with pytest.raises(H.HecError):
+        H.Server(restart=40)
+    with H.Server(lanes=1) as S:
+        with pytest.raises(H.HecError):
+            S.solution(12345, 10)

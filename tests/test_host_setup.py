@@ -25,7 +25,7 @@ def H():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "hecgpu.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^(?:int|void|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^(?:int|void|double|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
