@@ -101,7 +101,10 @@ def _load():
             lib.orc_ras_block_factor.restype = C.POINTER(_CSR)
             lib.orc_ras_free.argtypes = [C.c_void_p]
             lib.orc_ras_free.restype = None
-            for name in ("orc_bicgstab",):
+            lib.orc_jacobi_setup.argtypes = [C.c_int, _ip, _ip, _dp, C.c_double,
+                                             C.POINTER(C.c_int)]
+            lib.orc_jacobi_setup.restype = C.c_void_p
+            for name in ("orc_bicgstab", "orc_cg"):
                 f = getattr(lib, name)
                 f.argtypes = [C.c_int, _ip, _ip, _dp, C.c_void_p, _dp, _dp, C.c_double, C.c_int,
                               C.POINTER(_Info)]
@@ -282,6 +285,21 @@ class RAS:
         return rows, lo.value, hi.value, F
 
 
+class Jacobi(RAS):
+    """Damped Jacobi z = omega D^{-1} r (a smoother the paper builds from
+    SpMV and vector operations), usable wherever a RAS object is."""
+
+    def __init__(self, A, omega: float = 1.0):
+        rp, ci, va = _arrs(A)
+        st = C.c_int(0)
+        self._h = _load().orc_jacobi_setup(A.n, rp, ci, va, float(omega), C.byref(st))
+        if not self._h:
+            raise OracleError(st.value)
+        self.n = A.n
+        self.nblocks = 0
+        self.omega = omega
+
+
 # ---------------------------------------------------------------- Krylov
 class Info:
     def __init__(self, ci: _Info):
@@ -304,6 +322,16 @@ def bicgstab(A, b, M=None, x0=None, tol=1e-8, maxit=1000):
     _load().orc_bicgstab(A.n, rp, ci, va, M.handle if M is not None else None,
                          np.ascontiguousarray(b, np.float64), x, float(tol), int(maxit),
                          C.byref(info))
+    return x, Info(info)
+
+
+def cg(A, b, M=None, x0=None, tol=1e-8, maxit=1000):
+    """Preconditioned conjugate gradients.  M: RAS, Jacobi or None."""
+    rp, ci, va = _arrs(A)
+    x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    info = _Info()
+    _load().orc_cg(A.n, rp, ci, va, M.handle if M is not None else None,
+                   np.ascontiguousarray(b, np.float64), x, float(tol), int(maxit), C.byref(info))
     return x, Info(info)
 
 

@@ -317,6 +317,7 @@ int orc_usolve(int n, const int *rp, const int *ci, const double *va,
 
 struct orc_ras {
     int n, nblocks;
+    double *dinv;         /* damped Jacobi: omega / a_ii (then nblocks = 0) */
     int *own_lo, *own_hi; /* owned range W_b = [own_lo, own_hi) */
     int *nv;              /* |V_b| */
     int **rows;           /* V_b, ascending global ids */
@@ -342,7 +343,41 @@ void orc_ras_free(orc_ras *M)
     free(M->wr);
     free(M->wy);
     free(M->wz);
+    free(M->dinv);
     free(M);
+}
+
+/*
+ * Damped Jacobi (Section 2.8 names it among the smoothers built from the
+ * SpMV and vector operations): one relaxation step x <- x + omega D^{-1}
+ * (b - A x) from x = 0, used as the preconditioner z = omega D^{-1} r, D the
+ * diagonal of A.  The factor omega / a_ii is formed once per row.  A zero
+ * or missing diagonal entry gives ORC_ERR_ZERO_PIVOT.
+ */
+orc_ras *orc_jacobi_setup(int n, const int *rp, const int *ci, const double *va, double omega,
+                          int *status)
+{
+    *status = ORC_OK;
+    if (n <= 0 || !(omega > 0.0)) {
+        *status = ORC_ERR_INVALID;
+        return NULL;
+    }
+    orc_ras *M = (orc_ras *)calloc(1, sizeof(orc_ras));
+    M->n = n;
+    M->dinv = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] == i)
+                d = va[e];
+        if (d == 0.0) {
+            *status = ORC_ERR_ZERO_PIVOT;
+            orc_ras_free(M);
+            return NULL;
+        }
+        M->dinv[i] = omega / d;
+    }
+    return M;
 }
 
 /*
@@ -457,6 +492,11 @@ orc_ras *orc_ras_setup(int n, const int *rp, const int *ci, const double *va, in
  * (Eq. 7-8 on the block), and write back only the rows the block owns. */
 void orc_ras_apply(const orc_ras *M, const double *r, double *z)
 {
+    if (M->dinv) { /* damped Jacobi */
+        for (int i = 0; i < M->n; ++i)
+            z[i] = M->dinv[i] * r[i];
+        return;
+    }
     for (int b = 0; b < M->nblocks; ++b) {
         const orc_csr *F = &M->fac[b];
         int nv = M->nv[b];
@@ -600,6 +640,84 @@ finish:
         info->rel_resid = orc_nrm2(n, r) / bnorm;
     }
     free(r); free(r0); free(p); free(ps); free(v); free(s); free(ss); free(t);
+    return status;
+}
+
+/*
+ * Preconditioned conjugate gradients.  The paper lists CG among the Krylov
+ * solvers it implements (Section 2.7) and refers to Saad's book and the
+ * Templates for the method; this is their textbook preconditioned form:
+ *   r_0 = b - A x_0, z_0 = M^{-1} r_0, p_0 = z_0;
+ *   for j = 0, 1, ...: alpha_j = (r_j, z_j) / (A p_j, p_j);
+ *     x_{j+1} = x_j + alpha_j p_j;  r_{j+1} = r_j - alpha_j A p_j;
+ *     stop when ||r_{j+1}|| <= tol ||b||;
+ *     z_{j+1} = M^{-1} r_{j+1};  beta_j = (r_{j+1}, z_{j+1}) / (r_j, z_j);
+ *     p_{j+1} = z_{j+1} + beta_j p_j.
+ * Readings: one pass of the loop is one iteration; (A p, p) = 0 or
+ * (r, z) = 0 before convergence is a breakdown (A or M not positive
+ * definite); b = 0 returns x = 0; the true residual is recomputed at exit.
+ */
+int orc_cg(int n, const int *rp, const int *ci, const double *va, const orc_ras *M,
+           const double *b, double *x, double tol, int maxit, orc_info *info)
+{
+    memset(info, 0, sizeof(*info));
+    size_t sz = sizeof(double) * (size_t)n;
+    double *r = (double *)malloc(sz), *z = (double *)malloc(sz), *p = (double *)malloc(sz);
+    double *q = (double *)malloc(sz);
+    double bnorm = orc_nrm2(n, b);
+    int status = ORC_MAXIT;
+    int j = 0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sz);
+        status = ORC_OK;
+        goto finish;
+    }
+    true_resid(n, rp, ci, va, b, x, r); /* r_0 = b - A x_0 */
+    if (orc_nrm2(n, r) <= tol * bnorm) {
+        status = ORC_OK;
+        goto finish;
+    }
+    precond(M, n, r, z); /* z_0 = M^{-1} r_0 */
+    memcpy(p, z, sz);    /* p_0 = z_0 */
+    double rz = orc_dot(n, r, z);
+    if (rz == 0.0) {
+        status = ORC_BREAKDOWN;
+        goto finish;
+    }
+    while (j < maxit) {
+        orc_spmv(n, rp, ci, va, 1.0, p, 0.0, q); /* q = A p_j */
+        double pq = orc_dot(n, p, q);
+        if (pq == 0.0) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = rz / pq;
+        orc_axpby(n, alpha, p, 1.0, x);  /* x_{j+1} = x_j + alpha p_j */
+        orc_axpby(n, -alpha, q, 1.0, r); /* r_{j+1} = r_j - alpha A p_j */
+        ++j;
+        if (orc_nrm2(n, r) <= tol * bnorm) {
+            status = ORC_OK;
+            break;
+        }
+        precond(M, n, r, z); /* z_{j+1} = M^{-1} r_{j+1} */
+        double rz_new = orc_dot(n, r, z);
+        if (rz_new == 0.0) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double beta = rz_new / rz;
+        for (int i = 0; i < n; ++i) /* p_{j+1} = z_{j+1} + beta p_j */
+            p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+    }
+finish:
+    info->iters = j;
+    info->status = status;
+    if (bnorm > 0.0) {
+        true_resid(n, rp, ci, va, b, x, r);
+        info->rel_resid = orc_nrm2(n, r) / bnorm;
+    }
+    free(r); free(z); free(p); free(q);
     return status;
 }
 

@@ -20,6 +20,7 @@
  *   orc_lsolve_unit, orc_usolve                        pinned
  *   orc_ras_*                                          pinned
  *   orc_bicgstab, orc_gmres                            pinned
+ *   orc_jacobi_setup, orc_cg                           pinned
  */
 #ifndef HEC_ORACLE_H
 #define HEC_ORACLE_H
@@ -101,6 +102,17 @@ typedef struct {
     double rel_resid;   /* true ||b - A x|| / ||b|| recomputed at exit */
     double est_resid;   /* GMRES: last Givens estimate |g_{j+1}| / ||b|| */
 } orc_info;
+
+/* Damped Jacobi preconditioner z = omega D^{-1} r (an orc_ras handle with
+ * no blocks: orc_ras_apply and the solvers take it like a RAS one).  status:
+ * ORC_OK, ORC_ERR_INVALID (n <= 0 or omega <= 0) or ORC_ERR_ZERO_PIVOT. */
+orc_ras *orc_jacobi_setup(int n, const int *rp, const int *ci, const double *va, double omega,
+                          int *status);
+
+/* Preconditioned conjugate gradients (Saad / Templates); M == NULL means no
+ * preconditioner.  x holds x0 on entry and the solution on exit. */
+int orc_cg(int n, const int *rp, const int *ci, const double *va, const orc_ras *M,
+           const double *b, double *x, double tol, int maxit, orc_info *info);
 
 /* Algorithm 4: right-preconditioned BiCGSTAB.  M == NULL means no
  * preconditioner.  x holds x0 on entry and the solution on exit. */

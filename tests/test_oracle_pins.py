@@ -488,3 +488,115 @@ def test_gmres_maxit(orc):
     b = synth.rhs_uniform(A.n, 1)
     x, info = orc.gmres(A, b, tol=1e-14, maxit=7, restart=3)
     assert info.status == orc.MAXIT and info.iters == 7
+
+
+# --------------------------------------------------------------------------- damped Jacobi, CG
+def dense_csr(D):
+    """A dense matrix as CSR with every entry stored (zeros included on the diagonal)."""
+    n = D.shape[0]
+    rows, cols = np.nonzero((D != 0) | np.eye(n, dtype=bool))
+    return synth.CSR(np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]), cols,
+                     D[rows, cols])
+
+
+def test_jacobi_on_a_diagonal_matrix_is_the_scaled_exact_solve(orc):
+    rng = np.random.default_rng(5)
+    d = rng.uniform(0.5, 3.0, 40) * rng.choice([-1.0, 1.0], 40)
+    A = dense_csr(np.diag(d))
+    r = rng.standard_normal(40)
+    for omega in (1.0, 0.6):
+        z = orc.Jacobi(A, omega).apply(r)
+        np.testing.assert_allclose(z, omega * np.linalg.solve(np.diag(d), r), rtol=1e-15)
+    # with omega = 1 the preconditioner is exact: one iteration of each solver
+    b = rng.standard_normal(40)
+    for solve in (orc.bicgstab, orc.cg):
+        x, info = solve(dense_csr(np.diag(np.abs(d))), b, M=orc.Jacobi(dense_csr(np.diag(np.abs(d)))),
+                        tol=1e-13)
+        assert info.status == orc.OK and info.iters == 1
+
+
+def test_damped_jacobi_iteration_contracts_at_the_closed_form_rate(orc):
+    # x <- x + M (b - A x) with M = omega D^{-1} on tridiag(-1, 2, -1): the error
+    # contracts by the spectral radius max_k |1 - omega (1 - cos(k pi / (n+1)))|
+    n, omega = 20, 2.0 / 3.0
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    A = dense_csr(T)
+    M = orc.Jacobi(A, omega)
+    xs = np.linspace(-1, 1, n) ** 2 + 0.3
+    b = T @ xs
+    x = np.zeros(n)
+    errs = []
+    for _ in range(700):
+        x = x + M.apply(b - T @ x)
+        errs.append(np.linalg.norm(x - xs))
+    rate = errs[-1] / errs[-2]
+    k = np.arange(1, n + 1)
+    rho = np.max(np.abs(1 - omega * (1 - np.cos(k * np.pi / (n + 1)))))
+    assert abs(rate - rho) <= 1e-6
+
+
+def test_jacobi_zero_diagonal_and_bad_omega(orc):
+    D = np.diag([1.0, 0.0, 2.0])
+    D[1, 0] = 1.0
+    with pytest.raises(orc.OracleError) as e:
+        orc.Jacobi(dense_csr(D))
+    assert e.value.status == orc.ERR_ZERO_PIVOT
+    with pytest.raises(orc.OracleError):
+        orc.Jacobi(dense_csr(np.eye(3)), 0.0)
+
+
+def test_cg_iterates_minimise_the_energy_norm_over_the_krylov_space(orc):
+    # x_k = argmin over K_k(A, b) of ||x - x*||_A, computed by a dense projection
+    A = synth.diffusion2d_5pt_lognormal(6, 0.5, seed=3)
+    T = A.to_dense()
+    b = synth.rhs_uniform(A.n, 4)
+    K = np.empty((A.n, 0))
+    v = b.copy()
+    for k in range(1, 7):
+        K = np.column_stack([K, v])
+        v = T @ v
+        Q, _ = np.linalg.qr(K)
+        xk = Q @ np.linalg.solve(Q.T @ T @ Q, Q.T @ b)
+        x, info = orc.cg(A, b, tol=0.0, maxit=k)
+        assert info.iters == k and info.status == orc.MAXIT
+        assert np.linalg.norm(x - xk) <= 1e-9 * np.linalg.norm(xk)
+
+
+def test_cg_converges_in_as_many_steps_as_distinct_eigenvalues(orc):
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    lam = np.repeat([1.0, 4.0, 9.0], 10)
+    A = dense_csr(Q @ np.diag(lam) @ Q.T)
+    b = rng.standard_normal(30)
+    x, info = orc.cg(A, b, tol=1e-10, maxit=10)
+    assert info.status == orc.OK and info.iters == 3
+
+
+def test_cg_exact_preconditioner_and_finite_termination(orc):
+    A = synth.poisson2d_5pt(6)
+    b = synth.rhs_uniform(A.n, 1)
+    x, info = orc.cg(A, b, tol=1e-10, maxit=A.n)
+    assert info.status == orc.OK and info.iters <= A.n and info.rel_resid <= 1e-10
+    x, info = orc.cg(A, b, M=orc.RAS(A, 100, 1, 0), tol=1e-12)
+    assert info.iters == 1 and info.rel_resid <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["none", "ilu0", "jacobi"])
+def test_cg_manufactured_solution(orc, prec):
+    A = synth.diffusion2d_5pt_lognormal(20, 1.0, seed=6)
+    xs = synth.rhs_uniform(A.n, 3)
+    b = orc.spmv(A, xs)
+    M = {"none": None, "ilu0": orc.RAS(A, 0, 1, 0), "jacobi": orc.Jacobi(A, 0.8)}[prec]
+    x, info = orc.cg(A, b, M=M, tol=1e-11, maxit=2000)
+    assert info.status == orc.OK and info.rel_resid <= 1e-11
+    xd = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-7
+
+
+def test_cg_breakdown_and_zero_rhs(orc):
+    A = dense_csr(np.diag([1.0, -1.0]))
+    x, info = orc.cg(A, np.array([1.0, 1.0]), tol=1e-12, maxit=5)
+    assert info.status == orc.BREAKDOWN
+    B = synth.poisson2d_5pt(4)
+    x, info = orc.cg(B, np.zeros(B.n), x0=np.ones(B.n))
+    assert info.status == orc.OK and np.all(x == 0) and info.iters == 0
