@@ -113,9 +113,17 @@ typedef struct {
 
 #define HEC_GMRES 0
 #define HEC_BICGSTAB 1
+/* Preconditioned conjugate gradients (Section 2.7 lists CG among the Krylov
+ * methods and refers to Saad's book for it): r_0 = b - A x_0, z = M^{-1} r,
+ * p = z; per pass alpha = (r, z) / (A p, p), x += alpha p, r -= alpha A p,
+ * stop when ||r|| <= tol ||b||, z = M^{-1} r, beta = (r_new, z_new) /
+ * (r, z), p = z + beta p.  For symmetric positive definite A and M (ILU(k)
+ * with one block of a symmetric matrix, damped Jacobi, none); (A p, p) = 0
+ * or (r, z) = 0 before convergence ends with HEC_BREAKDOWN.  FP64 only. */
+#define HEC_CG 2
 
 typedef struct {
-    int32_t method;     /* HEC_GMRES or HEC_BICGSTAB                          */
+    int32_t method;     /* HEC_GMRES, HEC_BICGSTAB or HEC_CG                  */
     int32_t flags;      /* HEC_X0_ZERO: ignore the content of x, start at 0;
                            HEC_SOLVE_EAGER: launch the solve's kernels
                            directly on the stream and drive the loop from the
@@ -139,7 +147,7 @@ typedef struct {
 #define HEC_MIXED_FP32 4
 
 typedef struct {
-    int32_t iters;          /* BiCGSTAB passes / GMRES Arnoldi steps          */
+    int32_t iters;          /* BiCGSTAB, CG passes / GMRES Arnoldi steps      */
     int32_t restarts;       /* GMRES cycles started                           */
     int32_t status;         /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN or an error   */
     int32_t fp64_finish;    /* HEC_MIXED_FP32: the FP32 cycles stopped refining
@@ -217,6 +225,17 @@ int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const doubl
  * A[V_b, V_b] by ILU(k).  Factors are computed on the host and kept there
  * until level_schedule uploads them.  Returns HEC_ERR_ZERO_PIVOT if a pivot
  * is zero, HEC_ERR_INVALID if a diagonal entry is missing. */
+/* Damped Jacobi (Section 2.8 builds it, as a smoother, from the SpMV and
+ * vector operations): the preconditioner z = omega D^{-1} r, D the diagonal
+ * of A, usable wherever an ILU(k)/RAS handle is (apply calls, krylov_solve
+ * with any method, the mixed-precision mode).  omega / a_ii is formed once
+ * on the host in FP64 and kept on the device (an FP32 copy is made on the
+ * first FP32 use).  The handle needs no level_schedule (calling it is a
+ * no-op); hec_precond_info reports k = -1, nblocks = 0 and 24 n algorithmic
+ * bytes per apply; the block/factor/level queries return HEC_ERR_INVALID.
+ * Returns HEC_ERR_INVALID for omega <= 0 or not finite, HEC_ERR_ZERO_PIVOT
+ * for a zero or missing diagonal entry. */
+int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *out);
 int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
                 hec_precond_t *out);
 /* Section 2.6 (Eq. 11, Algorithm 3): level of every row of every L_b and
@@ -279,10 +298,10 @@ void hec_precond_destroy(hec_precond_t M);
 
 /* ---------------------------------------------------------------- Krylov */
 /* Section 2.7: solve A x = b with the right-preconditioned BiCGSTAB of
- * Algorithm 4 or restarted GMRES(restart), M == NULL meaning no
- * preconditioner.  Convergence: ||r|| <= tol ||b|| (BiCGSTAB: the recursive
- * residual of Algorithm 4; GMRES: the true residual checked at every cycle
- * end).  b and x are device or host arrays of n doubles (host arrays are
+ * Algorithm 4, restarted GMRES(restart) or preconditioned CG (opts->method),
+ * M == NULL meaning no preconditioner; M is an ILU(k)/RAS or a damped-Jacobi
+ * handle.  Convergence: ||r|| <= tol ||b|| (BiCGSTAB, CG: the recursive
+ * residual; GMRES: the true residual checked at every cycle end).  b and x are device or host arrays of n doubles (host arrays are
  * staged through device memory; the byte counts are reported in info);
  * x holds x0 on entry unless HEC_X0_ZERO, and the solution on exit.  The
  * whole iteration runs on the device as one CUDA graph with a device-side

@@ -172,6 +172,9 @@ struct TrsvLayout {
 
 struct hec_precond_s {
     uint64_t matrix_id = 0;
+    int kind = 0; // 0: RAS with ILU(k) blocks, 1: damped Jacobi
+    double omega = 1.0;
+    DevBuf dinv, dinv32; // damped Jacobi: omega / a_ii (FP64; FP32 copy on first mixed use)
     int n = 0, k = 0, nblocks = 0, overlap = 0;
     bool host_only = false, scheduled = false;
     std::vector<BlockFactor> blocks;
@@ -181,7 +184,8 @@ struct hec_precond_s {
     std::vector<std::unique_ptr<Solver>> solvers;
     int64_t device_bytes() const
     {
-        return lay[0].device_bytes() + lay[1].device_bytes() + (int64_t)d_err.bytes;
+        return lay[0].device_bytes() + lay[1].device_bytes() + (int64_t)d_err.bytes +
+               (int64_t)dinv.bytes + (int64_t)dinv32.bytes;
     }
     ~hec_precond_s();
 };
@@ -189,6 +193,7 @@ struct hec_precond_s {
 namespace {
 
 constexpr long long kDefaultSpin = 1ll << 24;
+constexpr int kJacobi = 1; // hec_precond_s::kind of a damped-Jacobi handle
 constexpr int kMaxRing = 8192; // shared-memory ring slots (doubles)
 
 // ---------------------------------------------------------------- launch helpers
@@ -301,6 +306,37 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
     return HEC_OK;
 }
 
+// The FP32 form of a preconditioner for the mixed-precision inner solves:
+// the FP32 factor layout, or the FP32 copy of a Jacobi diagonal.
+int ensure_precond_f32(hec_precond_s *M, cudaStream_t s)
+{
+    if (M->kind != kJacobi)
+        return build_layout(M, 1, s);
+    if (M->dinv32.p)
+        return HEC_OK;
+    std::vector<double> d(M->n);
+    HEC_CK(cudaMemcpyAsync(d.data(), M->dinv.p, sizeof(double) * d.size(), cudaMemcpyDeviceToHost,
+                           s));
+    HEC_CK(cudaStreamSynchronize(s));
+    std::vector<float> f(d.begin(), d.end());
+    HEC_TRY(upload(M->dinv32, f, s));
+    HEC_CK(cudaStreamSynchronize(s));
+    return HEC_OK;
+}
+
+// z = omega D^{-1} r on the caller's stream (FP64 or FP32 operands).
+int run_jacobi(const hec_precond_s *M, const void *r, void *z, bool fp32, cudaStream_t s)
+{
+    VecArgs va{};
+    va.n = M->n;
+    va.xv = r;
+    va.zv = z;
+    va.dv = fp32 ? M->dinv32.p : M->dinv.p;
+    if (launch_vec_typed(V_JACOBI, va, fp32, fp32, vec_grid(M->n), s) != 0)
+        return fail(HEC_ERR_INVALID, "bad typed vector op");
+    return check_launch("jacobi");
+}
+
 // Global reducer for the stand-alone vector calls (one per process).
 std::mutex g_red_mu;
 std::unique_ptr<Reducer> g_red;
@@ -330,6 +366,7 @@ struct Solver {
     SolverState *st = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *r0 = nullptr, *p = nullptr, *ps = nullptr;
     double *v = nullptr, *s = nullptr, *ss = nullptr, *t = nullptr;
+    double *q = nullptr; // CG: A p
     // GMRES basis and step vectors: FP64, or FP32 when mixed
     void *V = nullptr, *z = nullptr, *w = nullptr, *u = nullptr, *zu = nullptr;
     cudaGraph_t graph = nullptr;
@@ -403,6 +440,19 @@ int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 int seq_precond(const hec_precond_s *M, Solver &S, const void *in, void *out, int from_j,
                 cudaStream_t cs)
 {
+    if (M->kind == kJacobi) {
+        VecArgs va{};
+        va.n = S.n;
+        va.st = S.st;
+        va.xv = in;
+        va.x_from_j = from_j;
+        va.ldv = S.ldv;
+        va.zv = out;
+        va.dv = S.mixed ? M->dinv32.p : M->dinv.p;
+        if (launch_vec_typed(V_JACOBI, va, S.mixed, S.mixed, vec_grid(S.n), cs) != 0)
+            return fail(HEC_ERR_INVALID, "bad typed vector op");
+        return check_launch("jacobi");
+    }
     TrsvArgs a = trsv_args(M, M->lay[S.mixed ? 1 : 0], kDefaultSpin);
     a.r = in;
     a.z = out;
@@ -500,6 +550,72 @@ int seq_bicg_body(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
     xr.z = S.r;
     xr.op = FIN_BICG_XR;
     return run_vec(V_BICG_XR, xr, cs); // x, r updates; tests; loop condition
+}
+
+// Preconditioned CG, start: ||b||, r = b - A x0 (||r|| test), z = M^{-1} r,
+// rho = (r, z), p = z.
+int seq_cg_rz_p(hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    double *z = S.r;
+    if (M) {
+        HEC_TRY(seq_precond(M, S, S.r, S.s, 0, cs)); // z = M^{-1} r
+        z = S.s;
+    }
+    VecArgs d{};
+    d.n = S.n;
+    d.st = S.st;
+    d.red = S.red.r;
+    d.x = S.r;
+    d.y = z;
+    d.op = FIN_CG_RHO;
+    HEC_TRY(run_vec(V_DOT, d, cs)); // (r, z): beta, rho, loop condition
+    VecArgs pp{};
+    pp.n = S.n;
+    pp.st = S.st;
+    pp.x = z;
+    pp.z = S.p;
+    return run_vec(V_CG_P, pp, cs); // p = z + beta p
+}
+
+int seq_cg_init(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    HEC_TRY(seq_norm_b(S, cs));
+    SpmvArgs sa = spmv_args(A);
+    sa.st = S.st;
+    sa.red = S.red.r;
+    sa.x = S.x;
+    sa.alpha = -1.0;
+    sa.beta = 1.0;
+    sa.y_in = S.b;
+    sa.y_out = S.r;
+    sa.op = FIN_CG_INIT;
+    HEC_TRY(run_spmv(A, sa, 2, 1, cs)); // r = b - A x0, ||r||
+    return seq_cg_rz_p(M, S, cs);
+}
+
+// One pass: q = A p with (p, q) -> alpha; x += alpha p, r -= alpha q with
+// ||r|| -> tests; z = M^{-1} r; (r, z) -> beta; p = z + beta p.
+int seq_cg_body(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    SpmvArgs q = spmv_args(A);
+    q.st = S.st;
+    q.red = S.red.r;
+    q.x = S.p;
+    q.y_out = S.q;
+    q.w0 = S.p;
+    q.op = FIN_CG_ALPHA;
+    HEC_TRY(run_spmv(A, q, 0, 1, cs)); // q = A p, (p, q)
+    VecArgs xr{};
+    xr.n = S.n;
+    xr.st = S.st;
+    xr.red = S.red.r;
+    xr.w = S.x;
+    xr.u = S.p;
+    xr.q = S.q;
+    xr.z = S.r;
+    xr.op = FIN_CG_R;
+    HEC_TRY(run_vec(V_CG_XR, xr, cs)); // x, r updates, ||r||
+    return seq_cg_rz_p(M, S, cs);
 }
 
 // Exit: x = 0 if b = 0; the true residual ||b - A x|| / ||b||.
@@ -680,6 +796,28 @@ int build_bicgstab(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs
     return HEC_OK;
 }
 
+int build_cg(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
+{
+    HEC_CK(cudaGraphCreate(&S.graph, 0));
+    HEC_CK(cudaGraphConditionalHandleCreate(&S.h_while, S.graph, 1, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> tail;
+    HEC_TRY(begin_capture(cs, S.graph, nullptr, 0));
+    HEC_TRY(seq_cg_init(A, M, S, cs));
+    HEC_TRY(seq_loopcond(S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    HEC_TRY(add_conditional(S.graph, tail, S.h_while, cudaGraphCondTypeWhile, wnode, body));
+    HEC_TRY(begin_capture(cs, body, nullptr, 0));
+    HEC_TRY(seq_cg_body(A, M, S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_TRY(begin_capture(cs, S.graph, &wnode, 1));
+    HEC_TRY(seq_exit(A, S, cs));
+    HEC_TRY(end_capture(cs, tail));
+    HEC_CK(cudaGraphInstantiate(&S.exec, S.graph, 0));
+    return HEC_OK;
+}
+
 int build_gmres(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
 {
     HEC_CK(cudaGraphCreate(&S.graph, 0));
@@ -733,6 +871,13 @@ int run_eager(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t s)
             HEC_TRY(seq_bicg_body(A, M, S, s));
             HEC_TRY(read_flags());
         }
+    } else if (S.method == HEC_CG) {
+        HEC_TRY(seq_cg_init(A, M, S, s));
+        HEC_TRY(read_flags());
+        while (!flags[0]) {
+            HEC_TRY(seq_cg_body(A, M, S, s));
+            HEC_TRY(read_flags());
+        }
     } else {
         HEC_TRY(seq_norm_b(S, s));
         HEC_TRY(seq_gmres_cycle(A, S, s));
@@ -755,7 +900,7 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool
     auto &cache = M ? M->solvers : A->solvers;
     for (auto &p : cache)
         if (p->matrix_id == A->id && p->method == method && p->mixed == mixed &&
-            (method == HEC_BICGSTAB || p->restart == restart)) {
+            (method != HEC_GMRES || p->restart == restart)) {
             out = p.get();
             return HEC_OK;
         }
@@ -767,7 +912,9 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool
     S->n = A->hec.n;
     S->ldv = ((int64_t)S->n + 31) / 32 * 32;
     const int64_t nv = S->ldv;
-    const int nvec = method == HEC_BICGSTAB ? 10 : (mixed ? 3 : (restart + 1) + 7);
+    const int nvec = method == HEC_BICGSTAB ? 10
+                     : method == HEC_CG  ? 6
+                                         : (mixed ? 3 : (restart + 1) + 7);
     HEC_TRY(S->ws.alloc((size_t)nvec * nv * sizeof(double), s));
     HEC_CK(cudaMemsetAsync(S->ws.p, 0, S->ws.bytes, s));
     if (mixed) {
@@ -792,6 +939,13 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool
         S->s = vec(7);
         S->ss = vec(8);
         S->t = vec(9);
+    } else if (method == HEC_CG) {
+        S->b = vec(0);
+        S->x = vec(1);
+        S->r = vec(2);
+        S->s = vec(3); // z = M^{-1} r
+        S->p = vec(4);
+        S->q = vec(5);
     } else if (!mixed) {
         S->b = vec(0);
         S->x = vec(1);
@@ -816,7 +970,9 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool
     HEC_CK(cudaStreamSynchronize(s));
     cudaStream_t cs;
     HEC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = method == HEC_BICGSTAB ? build_bicgstab(A, M, *S, cs) : build_gmres(A, M, *S, cs);
+    int rc = method == HEC_BICGSTAB ? build_bicgstab(A, M, *S, cs)
+             : method == HEC_CG     ? build_cg(A, M, *S, cs)
+                                    : build_gmres(A, M, *S, cs);
     cudaStreamDestroy(cs);
     if (rc != HEC_OK)
         return rc;
@@ -1133,12 +1289,49 @@ int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, voi
     return HEC_OK;
 }
 
+int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *out)
+{
+    if (!A || !out)
+        return fail(HEC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (!(omega > 0.0) || !std::isfinite(omega))
+        return fail(HEC_ERR_INVALID, "omega must be a finite positive number");
+    const int n = A->hec.n;
+    const HostCSR &C = A->csr;
+    std::vector<double> d(n);
+    for (int i = 0; i < n; ++i) {
+        double a = 0.0;
+        for (int e = C.rp[i]; e < C.rp[i + 1]; ++e)
+            if (C.ci[e] == i)
+                a = C.va[e];
+        if (a == 0.0)
+            return fail(HEC_ERR_ZERO_PIVOT, "row %d has a zero or missing diagonal entry", i);
+        d[i] = omega / a;
+    }
+    std::unique_ptr<hec_precond_s> M(new hec_precond_s());
+    M->matrix_id = A->id;
+    M->kind = kJacobi;
+    M->omega = omega;
+    M->n = n;
+    M->host_only = A->host_only;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!M->host_only) {
+        HEC_TRY(upload(M->dinv, d, s));
+        HEC_TRY(M->d_err.alloc(sizeof(int), s));
+        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+        HEC_CK(cudaStreamSynchronize(s));
+    }
+    M->scheduled = true;
+    *out = M.release();
+    return HEC_OK;
+}
+
 int level_schedule(hec_precond_t M, void *stream)
 {
     if (!M)
         return fail(HEC_ERR_INVALID, "null preconditioner");
     if (M->scheduled)
-        return HEC_OK;
+        return HEC_OK; // also every damped-Jacobi handle: nothing to schedule
     cudaStream_t s = (cudaStream_t)stream;
     parallel_for(M->nblocks, [&](int b) { levels_block(M->blocks[b]); });
     HEC_TRY(build_layout(M, 0, s));
@@ -1158,7 +1351,7 @@ int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
     std::memset(info, 0, sizeof(*info));
     info->nblocks = M->nblocks;
     info->overlap = M->overlap;
-    info->k = M->k;
+    info->k = M->kind == kJacobi ? -1 : M->k;
     info->scheduled = M->scheduled ? 1 : 0;
     for (const BlockFactor &B : M->blocks) {
         info->rows_total += B.F.n;
@@ -1166,7 +1359,9 @@ int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
         info->max_levels_L = std::max(info->max_levels_L, B.nlevL);
         info->max_levels_U = std::max(info->max_levels_U, B.nlevU);
     }
-    info->apply_bytes = M->scheduled ? M->lay[0].pack.alg_bytes : 0;
+    info->apply_bytes = M->kind == kJacobi ? (int64_t)M->n * 24 // r, d read; z written
+                        : M->scheduled          ? M->lay[0].pack.alg_bytes
+                                                : 0;
     info->device_bytes = M->device_bytes();
     info->ring_slots = M->scheduled ? M->lay[0].pack.ring_slots : 0;
     info->apply_bytes_f32 = M->lay[1].built ? M->lay[1].pack.alg_bytes : 0;
@@ -1238,6 +1433,8 @@ int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_
         return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
     if (!M->scheduled)
         return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    if (M->kind == kJacobi)
+        return run_jacobi(M, r, z, false, (cudaStream_t)stream);
     TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
     a.r = r;
     a.z = z;
@@ -1254,7 +1451,9 @@ int hec_precond_apply_f32(hec_precond_t M, const float *r, float *z, int64_t spi
     if (!M->scheduled)
         return fail(HEC_ERR_INVALID, "level_schedule has not run");
     cudaStream_t s = (cudaStream_t)stream;
-    HEC_TRY(build_layout(M, 1, s));
+    HEC_TRY(ensure_precond_f32(M, s));
+    if (M->kind == kJacobi)
+        return run_jacobi(M, r, z, true, s);
     TrsvArgs a = trsv_args(M, M->lay[1], spin_limit ? spin_limit : kDefaultSpin);
     a.r = r;
     a.z = z;
@@ -1296,13 +1495,13 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
     hec_solve_opts_t o{};
     if (opts)
         o = *opts;
-    if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB)
+    if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB && o.method != HEC_CG)
         return fail(HEC_ERR_INVALID, "unknown method");
     if (!(tol >= 0.0) || maxit < 0)
         return fail(HEC_ERR_INVALID, "tol >= 0 and maxit >= 0 required");
     if (o.method == HEC_GMRES && (restart < 1 || restart > kMaxRestart))
         return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
-    if (o.method == HEC_BICGSTAB)
+    if (o.method != HEC_GMRES)
         restart = 0;
     const bool mixed = (o.flags & HEC_MIXED_FP32) != 0;
     if (mixed && o.method != HEC_GMRES)
@@ -1311,7 +1510,7 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
     if (mixed) {
         HEC_TRY(ensure_f32(A, s));
         if (M)
-            HEC_TRY(build_layout(M, 1, s));
+            HEC_TRY(ensure_precond_f32(M, s));
     }
     Solver *S = nullptr;
     HEC_TRY(make_solver(A, M, o.method, restart, mixed, s, S));
@@ -1440,6 +1639,8 @@ extern "C" int hec_precond_apply_noalloc(hec_precond_t M, const double *r, doubl
         return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
     if (!M->scheduled)
         return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    if (M->kind == kJacobi) // no scratch at all
+        return run_jacobi(M, r, z, false, (cudaStream_t)stream);
     const TrsvPack &P = M->lay[0].pack;
     const long long need = (long long)P.ysz + (long long)P.zsz;
     if (need > kNoallocScratchDoubles)

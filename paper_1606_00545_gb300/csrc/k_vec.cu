@@ -10,10 +10,12 @@ __global__ void __launch_bounds__(kThreads) k_vec(VecArgs a)
 {
     count_launch(a.st);
     SolverState *st = a.st;
-    constexpr int ND = (OP == V_DOT || OP == V_NRM2SQ || OP == V_BICG_S) ? 1
-                       : (OP == V_BICG_XR)                                 ? 2
-                                                                           : 0;
+    constexpr int ND = (OP == V_DOT || OP == V_NRM2SQ || OP == V_BICG_S || OP == V_CG_XR) ? 1
+                       : (OP == V_BICG_XR)                                                  ? 2
+                                                                                            : 0;
     if (OP == V_BICG_S && st->skip)
+        return;
+    if (OP == V_CG_P && st->done)
         return;
     if (OP == V_ZERO_IF_ST && !st->zero_x)
         return;
@@ -45,6 +47,14 @@ __global__ void __launch_bounds__(kThreads) k_vec(VecArgs a)
     }
     if (OP == V_BICG_S)
         c0 = st->alpha;
+    if (OP == V_CG_XR) {
+        c0 = st->alpha;
+        mode = st->skip; // breakdown in alpha: no update (the sum still runs)
+    }
+    if (OP == V_CG_P) {
+        mode = st->iters == 0; // first pass: p = z
+        c0 = st->cg_beta;
+    }
     if (OP == V_BICG_XR) {
         c0 = st->alpha;
         c1 = st->omega;
@@ -85,6 +95,17 @@ __global__ void __launch_bounds__(kThreads) k_vec(VecArgs a)
             } else if (mode == 1) {
                 a.w[i] = fma(c0, a.u[i], a.w[i]);
             }
+        } else if (OP == V_CG_XR) {
+            // w = x (solution), u = p, q = A p, z = r
+            if (!mode) {
+                a.w[i] = fma(c0, a.u[i], a.w[i]);
+                const double r = fma(-c0, a.q[i], z[i]);
+                z[i] = r;
+                acc[0] = fma(r, r, acc[0]);
+            }
+        } else if (OP == V_CG_P) {
+            // x = z (preconditioned residual), z = p
+            z[i] = mode ? x[i] : fma(c0, z[i], x[i]);
         } else if (OP == V_AXPY_ST1) {
             z[i] += x[i];
         } else if (OP == V_ZERO_IF_ST) {
@@ -118,6 +139,8 @@ int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s)
         HEC_VEC_CASE(V_BICG_XR)
         HEC_VEC_CASE(V_AXPY_ST1)
         HEC_VEC_CASE(V_ZERO_IF_ST)
+        HEC_VEC_CASE(V_CG_XR)
+        HEC_VEC_CASE(V_CG_P)
 #undef HEC_VEC_CASE
     }
     return -1;
@@ -125,13 +148,16 @@ int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s)
 
 // ------------------------------------------------------------------ typed vector kernels
 
-// V_COPY, V_SCALE_ST, V_AXPY_ST1 with element types TX (x) and TZ (z).
+// V_COPY, V_SCALE_ST, V_AXPY_ST1, V_JACOBI with element types TX (x) and TZ (z).
 template <int OP, class TX, class TZ> __global__ void __launch_bounds__(kThreads) k_vec_typed(VecArgs a)
 {
     count_launch(a.st);
     SolverState *st = a.st;
     if ((a.guard == 1 && st->cycle_end) || (a.guard == 2 && st->done))
         return;
+    if (OP == V_JACOBI && st && st->skip) // as the triangular solves: a skipped apply
+        return;
+    const TZ *d = reinterpret_cast<const TZ *>(a.dv);
     const TX *x = reinterpret_cast<const TX *>(a.xv);
     TZ *z = reinterpret_cast<TZ *>(a.zv);
     if (a.x_from_j)
@@ -147,6 +173,8 @@ template <int OP, class TX, class TZ> __global__ void __launch_bounds__(kThreads
             z[i] = TZ(sc * double(x[i]));
         else if (OP == V_AXPY_ST1)
             z[i] = z[i] + TZ(x[i]);
+        else if (OP == V_JACOBI)
+            z[i] = d[i] * TZ(x[i]);
     }
 }
 
@@ -169,6 +197,7 @@ int launch_vec_typed(VecOp vop, const VecArgs &a, bool x32, bool z32, int grid, 
     case V_COPY: return launch_typed_op<V_COPY>(a, x32, z32, grid, s);
     case V_SCALE_ST: return launch_typed_op<V_SCALE_ST>(a, x32, z32, grid, s);
     case V_AXPY_ST1: return launch_typed_op<V_AXPY_ST1>(a, x32, z32, grid, s);
+    case V_JACOBI: return launch_typed_op<V_JACOBI>(a, x32, z32, grid, s);
     default: return -1;
     }
 }

@@ -29,6 +29,10 @@ enum FinOp : int {
     FIN_GMRES_H1,         // first projection h1 (k values)
     FIN_GMRES_H2,         // second projection h2 (k values)
     FIN_GMRES_STEP,       // ||w''||: Hessenberg column, Givens, cycle tests
+    FIN_CG_INIT,          // r = b - A x0: ||r|| test
+    FIN_CG_RHO,           // (r, z): rho, beta = rho_new / rho; loop condition
+    FIN_CG_ALPHA,         // q = A p: alpha = rho / (p, q)
+    FIN_CG_R,             // x, r update: ||r|| test, iteration count
 };
 
 // Device-resident solver state: scalars of Algorithm 4 / GMRES, loop flags,
@@ -40,6 +44,7 @@ struct __align__(16) SolverState {
     // scalars
     double bnorm, rho, rho_prev, alpha, omega, scale, w0norm, est, rel_resid;
     double inner_rtol, beta_cycle; // mixed precision: inner cycle tolerance, cycle start ||r||
+    double cg_beta;                // CG: (r_{j+1}, z_{j+1}) / (r_j, z_j)
     int stag_run, stagnated;       // mixed precision: cycles in a row whose true FP64
                                    // residual exceeded 10x the FP32 cycle's estimate
     double dots[kMaxDots];
@@ -97,6 +102,9 @@ enum VecOp : int {
     V_BICG_XR,     // x += alpha p* + omega s*, r = s - omega t, (r, r), (r0, r)
     V_AXPY_ST1,    // y += x                       (GMRES x update)
     V_ZERO_IF_ST,  // z = 0 if st->zero_x
+    V_CG_XR,       // x += alpha p, r -= alpha q, (r, r)          (CG)
+    V_CG_P,        // p = z + beta p (first pass: p = z)           (CG)
+    V_JACOBI,      // z = d .* x (typed: damped Jacobi, d = omega / a_ii)
 };
 struct VecArgs {
     int n;
@@ -114,9 +122,10 @@ struct VecArgs {
     int guard;               // 1: no-op if st->cycle_end, 2: no-op if st->done
     const void *xv;          // typed operands of launch_vec_typed
     void *zv;
+    const void *dv;          // V_JACOBI: the scaled inverse diagonal (z's type)
 };
 int launch_vec(VecOp vop, const VecArgs &a, int grid, cudaStream_t s);
-// V_COPY, V_SCALE_ST and V_AXPY_ST1 on a.xv / a.zv with element types chosen
+// V_COPY, V_SCALE_ST, V_AXPY_ST1 and V_JACOBI on a.xv / a.zv with element types chosen
 // by x32 / z32 (FP32 if set, else FP64): the FP32 basis of the mixed-precision
 // mode, the FP64 -> FP32 start vector and the FP32 -> FP64 correction.
 int launch_vec_typed(VecOp vop, const VecArgs &a, bool x32, bool z32, int grid, cudaStream_t s);

@@ -201,6 +201,68 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         set_cond(st, st->h_if, end);
         break;
     }
+    case FIN_CG_INIT: {
+        // r_0 = b - A x_0
+        if (st->done)
+            break;
+        const double rn = sqrt(s[0]);
+        st->est = rn / st->bnorm;
+        if (rn <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->status = HEC_OK;
+        } else if (st->maxit <= 0) {
+            st->done = 1;
+            st->status = HEC_MAXIT;
+        }
+        break;
+    }
+    case FIN_CG_RHO: {
+        // (r_{j+1}, z_{j+1}): beta_j and the next rho; the loop goes on
+        // unless the residual test, the budget or a breakdown ended it
+        if (!st->done) {
+            const double rz = s[0];
+            if (rz == 0.0 || isnan(rz)) {
+                st->done = 1;
+                st->status = HEC_BREAKDOWN;
+            } else {
+                st->cg_beta = (st->iters > 0) ? rz / st->rho : 0.0;
+                st->rho = rz;
+            }
+        }
+        st->skip = 0; // the last pass skipped its preconditioner apply; the exit runs
+        set_cond(st, st->h_while, !st->done);
+        break;
+    }
+    case FIN_CG_ALPHA: {
+        const double pq = s[0];
+        if (pq == 0.0 || isnan(pq)) {
+            st->skip = 1; // no update of x, r; the pass ends the loop
+            st->done = 1;
+            st->status = HEC_BREAKDOWN;
+        } else {
+            st->alpha = st->rho / pq;
+        }
+        break;
+    }
+    case FIN_CG_R: {
+        if (st->skip)
+            break;
+        st->iters += 1;
+        const double rn = sqrt(s[0]);
+        st->est = rn / st->bnorm;
+        if (rn <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->status = HEC_OK;
+        } else if (isnan(rn)) {
+            st->done = 1;
+            st->status = HEC_BREAKDOWN;
+        } else if (st->iters >= st->maxit) {
+            st->done = 1;
+            st->status = HEC_MAXIT;
+        }
+        st->skip = st->done; // no preconditioner apply after the last pass
+        break;
+    }
     default:
         break;
     }

@@ -29,6 +29,7 @@ MAXIT = 1
 BREAKDOWN = 2
 GMRES = 0
 BICGSTAB = 1
+CG = 2
 HOST_ONLY = 1
 X0_ZERO = 1
 SOLVE_EAGER = 2
@@ -148,6 +149,7 @@ _SIGS = {
     "hec_nrm2": ([_i32, _vp, _vp, _vp], C.c_int),
     "hec_multidot": ([_i32, _i32, _vp, _i64, _vp, _vp, _vp], C.c_int),
     "ilu_k_setup": ([_vp, _i32, _i32, _i32, _vp, C.POINTER(_vp)], C.c_int),
+    "hec_jacobi_setup": ([_vp, C.c_double, _vp, C.POINTER(_vp)], C.c_int),
     "level_schedule": ([_vp, _vp], C.c_int),
     "hec_precond_info": ([_vp, C.POINTER(PrecondInfo_t)], C.c_int),
     "hec_precond_get_block": ([_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), _vp],
@@ -428,6 +430,14 @@ class Precond:
             self.destroy()
         except Exception:
             pass
+
+
+def jacobi_setup(A: Matrix, omega: float = 1.0, stream=None) -> Precond:
+    """Damped Jacobi z = omega D^{-1} r as a preconditioner handle."""
+    h = C.c_void_p()
+    _check(load_library().hec_jacobi_setup(A.handle, float(omega), _stream(stream), C.byref(h)),
+           "hec_jacobi_setup")
+    return Precond(h, A)
 
 
 def ilu_k_setup(A: Matrix, k: int, nblocks: int, overlap: int, stream=None) -> Precond:
