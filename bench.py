@@ -71,6 +71,10 @@ def parse():
                          "conditional nodes); same kernels and results, slower")
     ap.add_argument("--skip", default="",
                     help="comma-separated sections to leave out of the JSON line: c3, c4, c5")
+    ap.add_argument("--table4", action="store_true",
+                    help="instead of the benchmark line: the paper's Table 4 / Table 5 sweep "
+                         "(ILU(k), RAS blocks, overlap; BiCGSTAB and GMRES(30)) and CG with "
+                         "damped Jacobi on the 150^3 3D Poisson matrix, on one GPU")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
                          "--steps times (few launches before it, for ncu -k/-s/-c)")
@@ -626,6 +630,15 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(3):
         H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32)
     ms_s32, _ = timed(lambda: H.hec_spmv_f32(Ah, 1.0, r32, 0.0, None, y32), reps)
+    # preconditioned CG (the matrix is symmetric positive definite) with the
+    # damped-Jacobi preconditioner on the same system
+    J = H.jacobi_setup(Ah, 1.0)
+    xcg = torch.zeros_like(bd)
+    cg_solve = lambda: H.krylov_solve(Ah, J, bd, xcg, tol=TOL, maxit=MAXIT, method=H.CG,
+                                      flags=H.X0_ZERO)
+    cg_solve()
+    ms_cg, icg = timed(cg_solve, 1)
+    cgi = icg[0]
     pinf = P.info()
     skip = set(filter(None, args.skip.split(",")))
     c3 = c3_section(H, torch, dev, timed) if "c3" not in skip else None
@@ -667,6 +680,9 @@ def run_ours(args, rank, world, local_rank):
                           "rel_resid": gmx["rel_resid"], "solve_ms": ms_m,
                           "speedup_vs_fp64_solve": ms_g / ms_m,
                           "rel_error_vs_fp64_solution": mixed_err},
+        "cg_jacobi": {"iters": cgi["iters"], "status": cgi["status"],
+                      "iters_per_s": cgi["iters"] / (ms_cg * 1e-3), "rel_resid": cgi["rel_resid"],
+                      "solve_ms": ms_cg},
         "fp32_kernels": {"trsv_ms": ms_a32 / reps,
                          "trsv_gbs": pinf["apply_bytes_f32"] / (ms_a32 * 1e-3 / reps) / 1e9,
                          "trsv_alg_bytes": pinf["apply_bytes_f32"],
@@ -680,6 +696,117 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ Table 4 / 5 sweep
+# The paper's Krylov experiment: 3D_Poisson, 150^3 (n = 3,375,000, nnz =
+# 23,490,000), BiCGSTAB with ILU(k) on RAS blocks (Table 4: k = 0..3, inner RAS
+# 8 / 128 / 1024 per GPU, outer RAS = GPUs; Table 5: overlap 0 / 1).  One GPU
+# has only the inner level, so outer x inner blocks stand for a row.  The
+# paper gives neither its right-hand side nor its tolerance: uniform[-1, 1]
+# (seed 10) and 1e-8 here.
+T4_N, T4_RHS_SEED = 150, 10
+T4_PAPER = {  # (outer, inner, k): (iterations, GPU seconds) of Table 4
+    (1, 8, 0): (45, 1.82), (1, 8, 1): (30, 1.56), (1, 8, 2): (42, 3.95), (1, 8, 3): (33, 3.42),
+    (4, 8, 0): (44, 0.62), (4, 8, 1): (34, 0.81), (4, 8, 2): (39, 2.05), (4, 8, 3): (38, 2.47),
+    (4, 128, 0): (48, 0.62), (4, 128, 1): (40, 0.66), (4, 128, 2): (51, 1.50),
+    (4, 128, 3): (45, 1.56),
+    (4, 1024, 0): (55, 0.67), (4, 1024, 1): (47, 0.72), (4, 1024, 2): (58, 1.39),
+    (4, 1024, 3): (46, 1.27)}
+T5_PAPER = {0: (44, 0.61), 1: (38, 0.63)}  # overlap (outer = inner): iterations, GPU s
+
+
+def run_table4(args, local_rank):
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu as H
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    H.load_library()
+    A = synth.poisson3d_7pt(T4_N)
+    b = synth.rhs_uniform(A.n, T4_RHS_SEED)
+    Ah = H.hec_build(A.row_ptr, A.col, A.val)
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+    peak, _ = measured_peaks()
+
+    def timed_solve(P, method, restart=30, tol=TOL):
+        def go():
+            return H.krylov_solve(Ah, P, bd, x, tol=tol, maxit=MAXIT, restart=restart,
+                                  method=method, flags=H.X0_ZERO)
+        go()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inf = go()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"iters": inf["iters"], "status": inf["status"], "rel_resid": inf["rel_resid"],
+                "solve_ms": round(ms, 2), "ms_per_iter": round(ms / max(1, inf["iters"]), 3)}
+
+    def apply_time(P):
+        r = torch.tensor(synth.rhs_uniform(A.n, 7), device=dev)
+        z = torch.empty_like(r)
+        for _ in range(3):
+            H.hec_precond_apply(P, r, z)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            H.hec_precond_apply(P, r, z)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        nbytes = P.info()["apply_bytes"]
+        return {"apply_ms": round(ms, 3), "apply_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                "apply_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+
+    rows = []
+
+    def one(outer, inner, k, ov, methods):
+        t0 = time.perf_counter()
+        P = H.ilu_k_setup(Ah, k, outer * inner, ov)
+        H.level_schedule(P)
+        torch.cuda.synchronize()
+        row = {"outer": outer, "inner": inner, "blocks": outer * inner, "overlap": ov, "k": k,
+               "setup_s": round(time.perf_counter() - t0, 2),
+               "factor_nnz_per_row": round(P.info()["factor_nnz"] / A.n, 1)}
+        row.update(apply_time(P))
+        for name, method in methods:
+            row[name] = timed_solve(P, method)
+        if outer == 1:
+            # the paper states no tolerance: iterations to looser ones, for comparison
+            row["bicgstab_iters_at_tol"] = {
+                t: timed_solve(P, H.BICGSTAB, tol=float(t))["iters"] for t in ("1e-4", "1e-6")}
+        paper = T4_PAPER.get((outer, inner, k))
+        if paper and ov == 0:
+            row["paper_table4"] = {"iters": paper[0], "gpu_s": paper[1]}
+        rows.append(row)
+        P.destroy()
+        print(json.dumps(row), file=sys.stderr, flush=True)
+
+    both = (("bicgstab", H.BICGSTAB), ("gmres30", H.GMRES))
+    for k in range(4):
+        one(1, 8, k, 0, both)
+    for inner in (8, 128, 1024):
+        for k in range(4):
+            one(4, inner, k, 0, (("bicgstab", H.BICGSTAB),))
+    table5 = []
+    for ov in (0, 1):
+        one(4, 8, 0, ov, (("bicgstab", H.BICGSTAB),))
+        r = dict(rows[-1])
+        r["paper_table5"] = {"iters": T5_PAPER[ov][0], "gpu_s": T5_PAPER[ov][1]}
+        table5.append(r)
+    J = H.jacobi_setup(Ah, 1.0)
+    cg = {"preconditioner": "damped Jacobi, omega = 1", **timed_solve(J, H.CG)}
+    cg_none = {"preconditioner": "none", **timed_solve(None, H.CG)}
+    print(json.dumps({"workload": "poisson3d_7pt_150^3_rhs_uniform_seed10_tol1e-8",
+                      "n": A.n, "nnz": A.nnz, "table4": rows[:-2], "table5": table5,
+                      "cg": [cg, cg_none]}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -690,6 +817,9 @@ def main():
         return
     if args.kernel:
         run_kernel_only(args, local_rank)
+        return
+    if args.table4:
+        run_table4(args, local_rank)
         return
     if world > 1:
         import torch
