@@ -75,6 +75,11 @@ def parse():
                     help="instead of the benchmark line: the paper's Table 4 / Table 5 sweep "
                          "(ILU(k), RAS blocks, overlap; BiCGSTAB and GMRES(30)) and CG with "
                          "damped Jacobi on the 150^3 3D Poisson matrix, on one GPU")
+    ap.add_argument("--formats", action="store_true",
+                    help="instead of the benchmark line: the SpMV format ablation (the split "
+                         "of Table 3's comparison): HEC SpMV with the ELL width forced to 1 "
+                         "(almost all CSR tail), chosen by the one-third rule (HEC), or the "
+                         "longest row (pure ELL), on regular, irregular and heavy-tailed rows")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
                          "--steps times (few launches before it, for ncu -k/-s/-c)")
@@ -807,6 +812,58 @@ def run_table4(args, local_rank):
                       "cg": [cg, cg_none]}), flush=True)
 
 
+# ------------------------------------------------------------------ SpMV format ablation
+def run_formats(args, local_rank):
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu as H
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    H.load_library()
+    peak, _ = measured_peaks()
+    mats = [("diffusion3d_7pt_128^3_lognormal", lambda: synth.diffusion3d_7pt_lognormal(128, 2.0, 2)),
+            ("stencil27_irregular_96^3", lambda: synth.stencil27_irregular(96, 4, 5)),
+            ("powerlaw_rows_2M_scale2.5_alpha1.5_max4000",
+             lambda: synth.random_powerlaw_rows(2_000_000, 2.5, 1.5, 4000, 7))]
+    out = []
+    for name, gen in mats:
+        A = gen()
+        lens = np.diff(A.row_ptr)
+        x = torch.tensor(synth.rhs_uniform(A.n, 1), device=dev)
+        y = torch.empty_like(x)
+        alg = A.nnz * 12 + A.n * 16
+        res = {"matrix": name, "n": A.n, "nnz": A.nnz, "max_row": int(lens.max()),
+               "mean_row": round(float(lens.mean()), 2)}
+        for label, K in (("csr_tail_K1", 1), ("hec_auto", 0), ("ell_only", int(lens.max()))):
+            ld = (A.n + 255) // 256 * 256
+            if K and K * ld * 12 > (16 << 30):
+                res[label] = {"K": K, "skipped": "ELL slab of %.0f GB" % (K * ld * 12 / 1e9)}
+                continue
+            M = H.hec_build(A.row_ptr, A.col, A.val, ell_width=K)
+            inf = M.info()
+            for _ in range(5):
+                H.hec_spmv(M, 1.0, x, 0.0, None, y)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(50):
+                H.hec_spmv(M, 1.0, x, 0.0, None, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 50
+            res[label] = {"K": inf["ell_width"], "tail_rows": inf["tail_rows"],
+                          "slab_bytes": inf["ell_width"] * inf["ell_ld"] * 12,
+                          "ms": round(ms, 4), "gbs": round(alg / (ms * 1e-3) / 1e9, 1),
+                          "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
+            M.destroy()
+        out.append(res)
+        print(json.dumps(res), file=sys.stderr, flush=True)
+    print(json.dumps({"spmv_formats": out, "alg_bytes": "nnz*12 + n*16 (stored entries only)",
+                      "peak_gbs": peak}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -820,6 +877,9 @@ def main():
         return
     if args.table4:
         run_table4(args, local_rank)
+        return
+    if args.formats:
+        run_formats(args, local_rank)
         return
     if world > 1:
         import torch

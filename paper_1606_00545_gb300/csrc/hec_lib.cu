@@ -142,6 +142,7 @@ struct hec_matrix_s {
     HostCSR csr;
     HecHost hec;
     DevBuf ell_col, ell_val, tail_rows, tail_ptr, tail_col, tail_val, tile_tail;
+    DevBuf tile_group, tile_long, tail_long;
     DevBuf ell_val32, tail_val32; // FP32 copies of the values, made on first FP32 use
     bool f32_ready = false;
     Reducer red;
@@ -149,7 +150,8 @@ struct hec_matrix_s {
     int64_t device_bytes() const
     {
         return (int64_t)(ell_col.bytes + ell_val.bytes + tail_rows.bytes + tail_ptr.bytes +
-                         tail_col.bytes + tail_val.bytes + tile_tail.bytes + red.partials.bytes +
+                         tail_col.bytes + tail_val.bytes + tile_tail.bytes + tile_group.bytes +
+                         tile_long.bytes + tail_long.bytes + red.partials.bytes +
                          ell_val32.bytes + tail_val32.bytes);
     }
     ~hec_matrix_s();
@@ -211,6 +213,9 @@ SpmvArgs spmv_args(const hec_matrix_s *A)
     a.tail_col = A->tail_col.as<int>();
     a.tail_val = A->tail_val.as<double>();
     a.tile_tail = A->tile_tail.as<int>();
+    a.tile_group = A->tile_group.as<int>();
+    a.tile_long = A->tile_long.as<int>();
+    a.tail_long = A->tail_long.as<int>();
     a.alpha = 1.0;
     a.beta = 0.0;
     a.op = FIN_STORE;
@@ -991,6 +996,9 @@ int upload_matrix(hec_matrix_s *A, cudaStream_t s)
     HEC_TRY(upload(A->tail_col, H.tail_col, s));
     HEC_TRY(upload(A->tail_val, H.tail_val, s));
     HEC_TRY(upload(A->tile_tail, H.tile_tail, s));
+    HEC_TRY(upload(A->tile_group, H.tile_group, s));
+    HEC_TRY(upload(A->tile_long, H.tile_long, s));
+    HEC_TRY(upload(A->tail_long, H.tail_long, s));
     HEC_TRY(A->red.init(s));
     HEC_CK(cudaStreamSynchronize(s));
     return HEC_OK;

@@ -132,6 +132,32 @@ void build_hec(const HostCSR &A, int K, int align, HecHost &H)
             ++t;
         H.tile_tail[tile] = (int)t;
     }
+    // The tail schedule.  A tile's short tail rows are read by groups of g
+    // lanes (g = 4..32, a power of two near half their mean length, so that
+    // a warp is busy on rows of a few entries as on rows of a hundred); rows
+    // longer than kSpmvLongRow are read by the whole CTA, one at a time.
+    H.tile_group.assign(ntiles, 32);
+    H.tile_long.assign(ntiles + 1, 0);
+    H.tail_long.clear();
+    for (int tile = 0; tile < ntiles; ++tile) {
+        H.tile_long[tile] = (int)H.tail_long.size();
+        int64_t len_sum = 0, nshort = 0;
+        for (int q = H.tile_tail[tile]; q < H.tile_tail[tile + 1]; ++q) {
+            const int len = H.tail_ptr[q + 1] - H.tail_ptr[q];
+            if (len > kSpmvLongRow) {
+                H.tail_long.push_back(q);
+            } else {
+                len_sum += len;
+                ++nshort;
+            }
+        }
+        int g = 4;
+        if (nshort > 0)
+            while (g < 32 && 2 * (int64_t)g * nshort < len_sum)
+                g *= 2;
+        H.tile_group[tile] = g;
+    }
+    H.tile_long[ntiles] = (int)H.tail_long.size();
 }
 
 // ---------------------------------------------------------------- RAS blocks

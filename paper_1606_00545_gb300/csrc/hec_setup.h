@@ -31,6 +31,9 @@ struct HecHost {
     std::vector<int> tail_col;
     std::vector<double> tail_val;
     std::vector<int> tile_tail;    // per SpMV tile: first tail row index (ntiles + 1)
+    std::vector<int> tile_group;   // per tile: lanes per short tail row (4, 8, 16 or 32)
+    std::vector<int> tile_long;    // per tile: first index into tail_long (ntiles + 1)
+    std::vector<int> tail_long;    // tail rows longer than kSpmvLongRow, by tile
 };
 int ell_width_auto(const HostCSR &A);
 void build_hec(const HostCSR &A, int K, int align, HecHost &H);

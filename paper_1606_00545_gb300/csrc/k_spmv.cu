@@ -60,13 +60,44 @@ __global__ void __launch_bounds__(kThreads) k_spmv_hec(SpmvArgs a)
             __syncthreads();
             const int t0 = a.tile_tail[tile], t1 = a.tile_tail[tile + 1];
             const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            for (int t = t0 + wid; t < t1; t += kThreads / 32) {
+            // short rows: groups of g lanes, 32 / g rows per warp at a time,
+            // reduced by xor shuffles inside each aligned group of g lanes
+            const int g = a.tile_group[tile];
+            const int rpw = 32 / g, gid = lane / g, lig = lane % g;
+            for (int tb = t0 + wid * rpw; tb < t1; tb += (kThreads / 32) * rpw) {
+                const int t = tb + gid;
                 T s = T(0);
-                for (int e = a.tail_ptr[t] + lane; e < a.tail_ptr[t + 1]; e += 32)
+                bool mine = false;
+                if (t < t1) {
+                    const int e0 = a.tail_ptr[t], e1 = a.tail_ptr[t + 1];
+                    mine = e1 - e0 <= kSpmvLongRow;
+                    if (mine)
+                        for (int e = e0 + lig; e < e1; e += g)
+                            s += tail_val[e] * __ldg(&x[a.tail_col[e]]);
+                }
+                for (int o = g >> 1; o > 0; o >>= 1)
+                    s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (mine && lig == 0)
+                    s_tail[a.tail_rows[t] - base] = s;
+            }
+            // long rows: the whole CTA, one row at a time, fixed-order sum
+            for (int q = a.tile_long[tile]; q < a.tile_long[tile + 1]; ++q) {
+                const int t = a.tail_long[q];
+                T s = T(0);
+                for (int e = a.tail_ptr[t] + threadIdx.x; e < a.tail_ptr[t + 1]; e += kThreads)
                     s += tail_val[e] * __ldg(&x[a.tail_col[e]]);
                 s = warp_sum_t(s);
+                __shared__ T s_red[kThreads / 32];
+                __syncthreads(); // s_red of the previous long row is read
                 if (lane == 0)
-                    s_tail[a.tail_rows[t] - base] = s;
+                    s_red[wid] = s;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    T tot = T(0);
+                    for (int w = 0; w < kThreads / 32; ++w)
+                        tot += s_red[w];
+                    s_tail[a.tail_rows[t] - base] = tot;
+                }
             }
             __syncthreads();
         }

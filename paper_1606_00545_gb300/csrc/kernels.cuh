@@ -9,6 +9,7 @@ namespace hec {
 
 constexpr int kThreads = 256;         // threads per CTA of the streaming kernels
 constexpr int kSpmvTile = 2 * kThreads; // rows per SpMV tile: 2 adjacent rows per thread
+constexpr int kSpmvLongRow = 256;       // tail rows longer than this take a whole CTA
 constexpr int kMaxRestart = 128;      // largest GMRES(m) supported
 constexpr int kMaxDots = 2;           // fused reductions per launch
 
@@ -74,6 +75,7 @@ struct SpmvArgs {
     const int *ell_col;
     const void *ell_val;
     const int *tail_rows, *tail_ptr, *tail_col, *tile_tail;
+    const int *tile_group, *tile_long, *tail_long; // tail schedule (see build_hec)
     const void *tail_val;
     const void *x;
     const void *y_in;

@@ -304,6 +304,31 @@ def random_sparse_rows(n: int, per_row: int, seed: int, dominance: float = 1.5) 
     return _assemble(n, rows, cols, vals)
 
 
+def random_powerlaw_rows(n: int, scale: float, alpha: float, max_len: int, seed: int,
+                         dominance: float = 1.5) -> CSR:
+    """Random nonsymmetric sparse matrix whose row lengths are heavy-tailed,
+    the shape that separates ELL, CSR and hybrid formats: row i draws
+    min(max_len, max(1, round(scale * u^(-1/alpha)))) off-diagonal columns
+    (u uniform on (0, 1], a Pareto law of shape alpha), uniformly among the
+    other columns (duplicates merged); values uniform on [-1, 1]; diagonal
+    ``dominance`` * off-diagonal abs row sum + 1."""
+    rng = np.random.default_rng(seed)
+    u = 1.0 - rng.random(n)
+    lens = np.minimum(max_len, np.maximum(1, np.rint(scale * u ** (-1.0 / alpha)))).astype(np.int64)
+    r = np.repeat(np.arange(n, dtype=np.int64), lens)
+    c = rng.integers(0, n, size=r.shape[0])
+    keep = r != c
+    r, c = r[keep], c[keep]
+    key = np.unique(r * n + c)
+    r, c = key // n, key % n
+    v = rng.uniform(-1.0, 1.0, size=r.shape[0])
+    absrow = np.bincount(r, weights=np.abs(v), minlength=n)
+    rows = np.concatenate([r, np.arange(n)])
+    cols = np.concatenate([c, np.arange(n)])
+    vals = np.concatenate([v, dominance * absrow + 1.0])
+    return _assemble(n, rows, cols, vals)
+
+
 def random_sparse(n: int, density: float, seed: int, dominance: float = 1.5,
                   integer: bool = False) -> CSR:
     """Random nonsymmetric sparse matrix with full diagonal.

@@ -52,6 +52,13 @@ SPMV_CASES = {
     "n3": lambda: (synth.tridiagonal(3, seed=1), 0),
     "n513": lambda: (synth.random_sparse(513, 0.01, seed=4), 0),
     "n1025_tail": lambda: (synth.random_sparse(1025, 0.02, seed=5), 4),
+    # the format ablation's splits: K = 1 (almost all CSR tail), K = the
+    # longest row (pure ELL), on heavy-tailed and irregular rows
+    "powerlaw_csr": lambda: (synth.random_powerlaw_rows(20000, 2.5, 1.5, 600, 3), 1),
+    "powerlaw_hec": lambda: (synth.random_powerlaw_rows(20000, 2.5, 1.5, 600, 3), 0),
+    "powerlaw_ell": lambda: (synth.random_powerlaw_rows(3000, 2.5, 1.5, 200, 4), 201),
+    "irregular27_csr": lambda: (synth.stencil27_irregular(12, 4, 5), 1),
+    "irregular27_ell": lambda: (synth.stencil27_irregular(12, 4, 5), 160),
 }
 
 
