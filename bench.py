@@ -145,6 +145,32 @@ def base_config(A, extra=None):
     return cfg
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(dist, value, device):
+    """The slowest rank's value (the job's time); the value itself on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device):
+    """The units all ranks processed; the value itself on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(dist, units, ms, device):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return sum_over_ranks(dist, units, device) / (max_over_ranks(dist, ms, device) * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -246,6 +272,27 @@ def profiled_traffic():
 
 
 # ------------------------------------------------------------------ CPU oracle
+def cpu_spmv_sample(A, reps=5):
+    """The oracle's SpMV row loop on one host core and on every core (row
+    ranges on threads): GB/s of stored-entry bytes, best of `reps`."""
+    import oracle
+    x = synth.rhs_uniform(A.n, 1)
+    nbytes = A.nnz * 12 + A.n * 16
+    cores = os.cpu_count() or 1
+    out = {}
+    for label, fn in (("one_core", lambda: oracle.spmv(A, x)),
+                      ("all_cores", lambda: oracle.spmv_threads(A, x, cores))):
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out[label] = {"ms": round(best * 1e3, 2), "gbs": round(nbytes / best / 1e9, 2)}
+    out["all_cores"]["cores"] = cores
+    return out
+
+
 def cpu_sample(A, b, iters):
     import oracle
     t0 = time.perf_counter()
@@ -559,12 +606,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, out
+        return max_over_ranks(dist, e0.elapsed_time(e1), dev), out
 
     for attempt in range(2):
         with ClockSampler(local_rank) as cs:
@@ -574,7 +616,7 @@ def run_ours(args, rank, world, local_rank):
             break
     tot_iters = sum(i["iters"] for i in infos)
     launches = sum(i["kernel_launches"] for i in infos)
-    value = world * tot_iters / (ms * 1e-3)
+    value = job_rate(dist, tot_iters, ms, dev)
     rel_resid = max(i["rel_resid"] for i in infos)
 
     # e2e: host (pinned) b and x through the C ABI, copies inside the region
@@ -588,7 +630,7 @@ def run_ours(args, rank, world, local_rank):
 
     solve_host()
     ms_e2e, infos_e2e = timed(solve_host, max(1, args.steps // 2))
-    e2e_value = world * sum(i["iters"] for i in infos_e2e) / (ms_e2e * 1e-3)
+    e2e_value = job_rate(dist, sum(i["iters"] for i in infos_e2e), ms_e2e, dev)
     xg = xh.numpy().copy()
 
     # dominant kernel: level-scheduled RAS triangular solve, timed alone
@@ -657,7 +699,8 @@ def run_ours(args, rank, world, local_rank):
         rate, it, dt, cpu_setup = cpu_sample(A, b, CPU_SAMPLE_ITERS)
         cpu = {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle",
                "sample": "%d BiCGSTAB iterations of the full 128^3 workload from x0 = 0 "
-                         "(%.1f s; RAS/ILU(1) setup %.1f s untimed)" % (it, dt, cpu_setup)}
+                         "(%.1f s; RAS/ILU(1) setup %.1f s untimed)" % (it, dt, cpu_setup),
+               "spmv": cpu_spmv_sample(A)}
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -67,6 +67,9 @@ def _load():
             lib = C.CDLL(build())
             lib.orc_spmv.argtypes = [C.c_int, _ip, _ip, _dp, C.c_double, _dp, C.c_double, _dp]
             lib.orc_spmv.restype = None
+            lib.orc_spmv_range.argtypes = [C.c_int, _ip, _ip, _dp, C.c_double, _dp, C.c_double,
+                                           _dp, C.c_int, C.c_int]
+            lib.orc_spmv_range.restype = None
             lib.orc_dot.argtypes = [C.c_int, _dp, _dp]
             lib.orc_dot.restype = C.c_double
             lib.orc_nrm2.argtypes = [C.c_int, _dp]
@@ -167,6 +170,21 @@ def spmv(A, x, alpha=1.0, beta=0.0, y=None):
     out = np.zeros(A.n) if y is None else np.array(y, dtype=np.float64, copy=True)
     _load().orc_spmv(A.n, rp, ci, va, float(alpha), x, float(beta), out)
     return out
+
+
+def spmv_threads(A, x, threads: int):
+    """y = A x with the oracle's row loop split into `threads` row ranges run
+    on host threads (the library call releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    rp, ci, va = _arrs(A)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.zeros(A.n)
+    cuts = np.linspace(0, A.n, threads + 1).astype(int)
+    lib = _load()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda t: lib.orc_spmv_range(A.n, rp, ci, va, 1.0, x, 0.0, y,
+                                                 int(cuts[t]), int(cuts[t + 1])), range(threads)))
+    return y
 
 
 def dot(x, y):

@@ -32,6 +32,21 @@ void orc_spmv(int n, const int *rp, const int *ci, const double *va, double alph
     }
 }
 
+/* The same row loop restricted to rows [lo, hi): the oracle's SpMV split
+ * over host threads for the all-cores CPU baseline (each row is summed as in
+ * orc_spmv, so the result is identical). */
+void orc_spmv_range(int n, const int *rp, const int *ci, const double *va, double alpha,
+                    const double *x, double beta, double *y, int lo, int hi)
+{
+    (void)n;
+    for (int i = lo; i < hi; ++i) {
+        double s = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            s += va[e] * x[ci[e]];
+        y[i] = (beta == 0.0) ? alpha * s : alpha * s + beta * y[i];
+    }
+}
+
 /* Eq. 5 */
 double orc_dot(int n, const double *x, const double *y)
 {

@@ -94,6 +94,11 @@ void orc_ras_block_rows(const orc_ras *M, int b, int *rows);
 const orc_csr *orc_ras_block_factor(const orc_ras *M, int b);
 void orc_ras_free(orc_ras *M);
 
+/* orc_spmv on rows [lo, hi) only (for running the row loop on several host
+ * threads; identical per-row arithmetic). */
+void orc_spmv_range(int n, const int *rp, const int *ci, const double *va, double alpha,
+                    const double *x, double beta, double *y, int lo, int hi);
+
 /* Solver outcome. */
 typedef struct {
     int iters;          /* BiCGSTAB: loop passes; GMRES: Arnoldi steps */

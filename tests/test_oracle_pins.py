@@ -600,3 +600,11 @@ def test_cg_breakdown_and_zero_rhs(orc):
     B = synth.poisson2d_5pt(4)
     x, info = orc.cg(B, np.zeros(B.n), x0=np.ones(B.n))
     assert info.status == orc.OK and np.all(x == 0) and info.iters == 0
+
+
+def test_spmv_on_host_threads_is_the_same_row_loop(orc):
+    # the all-cores CPU baseline splits the oracle's row loop over threads
+    A = synth.stencil27_irregular(16, 2, 3)
+    x = synth.rhs_uniform(A.n, 5)
+    for t in (1, 3, 8):
+        assert np.array_equal(orc.spmv_threads(A, x, t), orc.spmv(A, x))
