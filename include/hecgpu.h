@@ -295,6 +295,23 @@ int hec_precond_apply_noalloc(hec_precond_t M, const double *r, double *z, int64
 int hec_precond_apply_f32(hec_precond_t M, const float *r, float *z, int64_t spin_limit,
                           void *stream);
 void hec_precond_destroy(hec_precond_t M);
+/* Numeric refactorisation on the GPU: A keeps its sparsity pattern and takes
+ * the nnz new values `val` (host or device array of doubles, in the CSR
+ * order A was built from).  The HEC slab and tail (Section 2.1) are
+ * rewritten on the device (and their FP32 copies, if made).  When M is not
+ * NULL it must have been built from A: a damped-Jacobi handle recomputes
+ * omega / a_ii; an ILU(k)/RAS handle (level_schedule done) recomputes every
+ * block's factor on its existing fill pattern -- the pattern of Eqs. 9-10
+ * depends on the structure only -- by the elimination of Algorithm 2, one
+ * CTA per RAS block, rows of one L level (Eq. 11) in parallel, with the
+ * host's operation order and rounding (the factors are bit-identical to a
+ * fresh ilu_k_setup of the new matrix), and refills the values of its
+ * triangular-solve layouts.  Solve graphs and handles stay valid.  The first
+ * call per handle uploads index maps (about 12 bytes per matrix entry and 16
+ * per factor entry), later calls only stream values.  The call synchronises
+ * the stream.  Returns HEC_OK, HEC_ERR_ZERO_PIVOT (the factors are then
+ * unusable until the next successful refactor) or HEC_ERR_INVALID. */
+int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *stream);
 
 /* ---------------------------------------------------------------- Krylov */
 /* Section 2.7: solve A x = b with the right-preconditioned BiCGSTAB of
@@ -454,8 +471,12 @@ typedef struct {
     const double *b;  /* host, A.n values, copied                                   */
     int32_t ilu_k;    /* >= 0                                                       */
     int32_t reserved;
-    uint64_t key;     /* 0: nothing kept; else requests with equal keys must carry
-                         the same matrix and level and reuse its set-up form         */
+    uint64_t key;     /* 0: nothing kept; else requests with equal keys reuse the
+                         resident set-up form: without a matrix as it is; with a
+                         matrix of the same sparsity pattern and level, refactored
+                         on the GPU with the new values (hec_refactor); with
+                         another pattern (or for a one-CTA batched system), set
+                         up again                                                  */
     uint64_t tag;     /* returned with the result                                   */
 } hec_request_t;
 
@@ -471,7 +492,7 @@ typedef struct {
     int32_t lane;
     int32_t reused;     /* 1: the matrix and factors were resident already             */
     int32_t fp64_finish;/* 1: the mixed-precision solve was finished in FP64           */
-    int32_t reserved;
+    int32_t refactored; /* 1: a resident system took new values by hec_refactor         */
     int64_t device_bytes;
 } hec_result_t;
 

@@ -145,11 +145,17 @@ struct hec_matrix_s {
     DevBuf tile_group, tile_long, tail_long;
     DevBuf ell_val32, tail_val32; // FP32 copies of the values, made on first FP32 use
     bool f32_ready = false;
+    // hec_refactor: CSR entry -> slab / tail slot, CSR index of each diagonal,
+    // staging for host values; the host HEC copy is refreshed on demand
+    DevBuf d_slot, d_diagidx, d_newval;
+    const double *d_newval_view = nullptr; // the new values of the refactor in progress
+    bool hec_host_stale = false;
     Reducer red;
     std::vector<std::unique_ptr<Solver>> solvers; // solves without a preconditioner
     int64_t device_bytes() const
     {
-        return (int64_t)(ell_col.bytes + ell_val.bytes + tail_rows.bytes + tail_ptr.bytes +
+        return (int64_t)(d_slot.bytes + d_diagidx.bytes + d_newval.bytes +
+                         ell_col.bytes + ell_val.bytes + tail_rows.bytes + tail_ptr.bytes +
                          tail_col.bytes + tail_val.bytes + tile_tail.bytes + tile_group.bytes +
                          tile_long.bytes + tail_long.bytes + red.partials.bytes +
                          ell_val32.bytes + tail_val32.bytes);
@@ -162,13 +168,14 @@ struct hec_matrix_s {
 struct TrsvLayout {
     TrsvPack pack;
     DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc;
+    DevBuf d_row0, d_rms, d_rml, d_rmd; // value maps of hec_refactor (uploaded on first use)
     int nstages = 8;
     int vbytes = 8;
     bool built = false;
     int64_t device_bytes() const
     {
         return (int64_t)(d_pack.bytes + d_chunks.bytes + d_blocks.bytes + d_ysc.bytes +
-                         d_zsc.bytes);
+                         d_zsc.bytes + d_row0.bytes + d_rms.bytes + d_rml.bytes + d_rmd.bytes);
     }
 };
 
@@ -184,10 +191,19 @@ struct hec_precond_s {
     DevBuf d_err;
     int stage_bytes = 24576;
     std::vector<std::unique_ptr<Solver>> solvers;
+    // hec_refactor: every block's factor on the device (entries numbered over
+    // all blocks), its source map into A and the L level sets; the host copy
+    // of the factor values is refreshed on demand
+    DevBuf rf_rp, rf_ci, rf_dg, rf_f, rf_src, rf_row0, rf_lev0, rf_lptr, rf_lrows;
+    int64_t rf_nent = 0;
+    bool rf_ready = false, factor_host_stale = false;
     int64_t device_bytes() const
     {
         return lay[0].device_bytes() + lay[1].device_bytes() + (int64_t)d_err.bytes +
-               (int64_t)dinv.bytes + (int64_t)dinv32.bytes;
+               (int64_t)dinv.bytes + (int64_t)dinv32.bytes + (int64_t)rf_rp.bytes +
+               (int64_t)rf_ci.bytes + (int64_t)rf_dg.bytes + (int64_t)rf_f.bytes +
+               (int64_t)rf_src.bytes + (int64_t)rf_row0.bytes + (int64_t)rf_lev0.bytes +
+               (int64_t)rf_lptr.bytes + (int64_t)rf_lrows.bytes;
     }
     ~hec_precond_s();
 };
@@ -241,10 +257,14 @@ int ensure_f32(hec_matrix_s *A, cudaStream_t s)
 {
     if (A->f32_ready)
         return HEC_OK;
-    std::vector<float> ev(A->hec.ell_val.begin(), A->hec.ell_val.end());
-    std::vector<float> tv(A->hec.tail_val.begin(), A->hec.tail_val.end());
-    HEC_TRY(upload(A->ell_val32, ev, s));
-    HEC_TRY(upload(A->tail_val32, tv, s));
+    // rounded on the device from the current FP64 values (hec_refactor may
+    // have replaced them)
+    const int64_t ne = (int64_t)A->hec.ell_val.size(), nt = (int64_t)A->hec.tail_val.size();
+    HEC_TRY(A->ell_val32.alloc(ne * sizeof(float), s));
+    HEC_TRY(A->tail_val32.alloc(nt * sizeof(float), s));
+    launch_cast_f32(ne, A->ell_val.as<double>(), A->ell_val32.as<float>(), s);
+    launch_cast_f32(nt, A->tail_val.as<double>(), A->tail_val32.as<float>(), s);
+    HEC_TRY(check_launch("cast"));
     HEC_CK(cudaStreamSynchronize(s));
     A->f32_ready = true;
     return HEC_OK;
@@ -285,12 +305,32 @@ int run_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false)
     return check_launch("trsv");
 }
 
+// The host copy of the factor values after hec_refactor replaced them on the
+// device (factor queries and a layout packed later read it).
+int refresh_host_factors(hec_precond_s *M, cudaStream_t s)
+{
+    if (!M->factor_host_stale)
+        return HEC_OK;
+    std::vector<double> f((size_t)M->rf_nent);
+    HEC_CK(cudaMemcpyAsync(f.data(), M->rf_f.p, f.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           s));
+    HEC_CK(cudaStreamSynchronize(s));
+    size_t off = 0;
+    for (BlockFactor &B : M->blocks) {
+        std::memcpy(B.F.va.data(), f.data() + off, B.F.va.size() * sizeof(double));
+        off += B.F.va.size();
+    }
+    M->factor_host_stale = false;
+    return HEC_OK;
+}
+
 // Pack, upload and size the scratch of the layout with vb-byte values.
 int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
 {
     TrsvLayout &L = M->lay[idx];
     if (L.built)
         return HEC_OK;
+    HEC_TRY(refresh_host_factors(M, s));
     L.vbytes = idx == 0 ? 8 : 4;
     std::string msg;
     int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg);
@@ -1006,6 +1046,178 @@ int upload_matrix(hec_matrix_s *A, cudaStream_t s)
 
 } // namespace
 
+// ====================================================================== numeric refactorisation
+namespace {
+
+// A's new values (same pattern, CSR order of hec_build): the device slab and
+// tail, their FP32 copies if made, and the host CSR copy.  Stream-ordered.
+int refactor_matrix(hec_matrix_s *A, const double *val, cudaStream_t s)
+{
+    const int n = A->hec.n;
+    const int64_t nnz = (int64_t)A->csr.ci.size();
+    const HostCSR &C = A->csr;
+    const HecHost &H = A->hec;
+    if (!A->d_slot.p) {
+        // CSR entry -> ELL slot k * ld + i, or tail entry (encoded -t - 1)
+        std::vector<int64_t> slot(nnz);
+        int64_t t = 0;
+        for (int i = 0; i < n; ++i)
+            for (int e = C.rp[i]; e < C.rp[i + 1]; ++e) {
+                const int k = e - C.rp[i];
+                slot[e] = k < H.K ? (int64_t)k * H.ld + i : -(t++) - 1;
+            }
+        HEC_TRY(upload(A->d_slot, slot, s));
+    }
+    const double *dval = val;
+    const bool dev = is_device_ptr(val);
+    if (!dev) {
+        if (!A->d_newval.p)
+            HEC_TRY(A->d_newval.alloc(nnz * sizeof(double), s));
+        HEC_CK(cudaMemcpyAsync(A->d_newval.p, val, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+        dval = A->d_newval.as<double>();
+    }
+    launch_scatter_hec(nnz, dval, A->d_slot.as<int64_t>(), A->ell_val.as<double>(),
+                       A->tail_val.as<double>(), s);
+    HEC_TRY(check_launch("scatter"));
+    if (A->f32_ready) {
+        launch_cast_f32((int64_t)H.ell_val.size(), A->ell_val.as<double>(),
+                        A->ell_val32.as<float>(), s);
+        launch_cast_f32((int64_t)H.tail_val.size(), A->tail_val.as<double>(),
+                        A->tail_val32.as<float>(), s);
+        HEC_TRY(check_launch("cast"));
+    }
+    // the host CSR copy: later host-side setups read it
+    HEC_CK(cudaMemcpyAsync(A->csr.va.data(), val, nnz * sizeof(double),
+                           dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    A->hec_host_stale = true;
+    // the values the preconditioner step reads
+    A->d_newval_view = dval;
+    return HEC_OK;
+}
+
+// The factor data of every block on the device, built on the first refactor.
+int upload_refactor_data(const hec_matrix_s *A, hec_precond_s *M, cudaStream_t s)
+{
+    if (M->rf_ready)
+        return HEC_OK;
+    const int nb = M->nblocks;
+    std::vector<int> row0(nb + 1, 0), lev0(nb + 1, 0);
+    int64_t nent = 0;
+    for (int b = 0; b < nb; ++b) {
+        row0[b + 1] = row0[b] + M->blocks[b].F.n;
+        lev0[b + 1] = lev0[b] + (int)M->blocks[b].lptrL.size();
+        nent += (int64_t)M->blocks[b].F.ci.size();
+    }
+    if (nent >= INT32_MAX)
+        return fail(HEC_ERR_INVALID, "factors of %lld entries exceed the refactor index range",
+                    (long long)nent);
+    std::vector<int> rp((size_t)row0[nb] + 1), ci((size_t)nent), dg((size_t)row0[nb]),
+        src((size_t)nent), lptr((size_t)lev0[nb]), lrows((size_t)row0[nb]);
+    const HostCSR &C = A->csr;
+    parallel_for(nb, [&](int b) {
+        const BlockFactor &B = M->blocks[b];
+        const HostCSR &F = B.F;
+        int64_t e0 = 0;
+        for (int q = 0; q < b; ++q)
+            e0 += (int64_t)M->blocks[q].F.ci.size();
+        for (int i = 0; i < F.n; ++i) {
+            const int r = row0[b] + i;
+            rp[r] = (int)(e0 + F.rp[i]);
+            dg[r] = (int)(e0 + B.diag[i]);
+            lrows[r] = B.lrowsL[i];
+            const int g = B.rows[i];
+            for (int e = F.rp[i]; e < F.rp[i + 1]; ++e) {
+                ci[e0 + e] = F.ci[e];
+                int sidx = -1;
+                if (B.lev[e] == 0) { // an entry of A[V_b, V_b]
+                    const int gc = B.rows[F.ci[e]];
+                    const int *lo = C.ci.data() + C.rp[g], *hi = C.ci.data() + C.rp[g + 1];
+                    const int *it = std::lower_bound(lo, hi, gc);
+                    if (it != hi && *it == gc)
+                        sidx = (int)(it - C.ci.data());
+                }
+                src[e0 + e] = sidx;
+            }
+        }
+        for (size_t l = 0; l < B.lptrL.size(); ++l)
+            lptr[lev0[b] + l] = B.lptrL[l];
+    });
+    rp[row0[nb]] = (int)nent;
+    HEC_TRY(upload(M->rf_rp, rp, s));
+    HEC_TRY(upload(M->rf_ci, ci, s));
+    HEC_TRY(upload(M->rf_dg, dg, s));
+    HEC_TRY(upload(M->rf_src, src, s));
+    HEC_TRY(upload(M->rf_row0, row0, s));
+    HEC_TRY(upload(M->rf_lev0, lev0, s));
+    HEC_TRY(upload(M->rf_lptr, lptr, s));
+    HEC_TRY(upload(M->rf_lrows, lrows, s));
+    HEC_TRY(M->rf_f.alloc(nent * sizeof(double), s));
+    HEC_CK(cudaStreamSynchronize(s));
+    M->rf_nent = nent;
+    M->rf_ready = true;
+    return HEC_OK;
+}
+
+int refactor_precond(hec_matrix_s *A, hec_precond_s *M, cudaStream_t s)
+{
+    const double *dval = A->d_newval_view;
+    if (M->kind == kJacobi) {
+        if (!A->d_diagidx.p) {
+            std::vector<int64_t> d(M->n, -1);
+            const HostCSR &C = A->csr;
+            for (int i = 0; i < M->n; ++i)
+                for (int e = C.rp[i]; e < C.rp[i + 1]; ++e)
+                    if (C.ci[e] == i)
+                        d[i] = e;
+            HEC_TRY(upload(A->d_diagidx, d, s));
+        }
+        launch_jacobi_dinv(M->n, dval, A->d_diagidx.as<int64_t>(), M->omega, M->dinv.as<double>(),
+                           M->dinv32.p ? M->dinv32.as<float>() : nullptr, M->d_err.as<int>(), s);
+        return check_launch("jacobi dinv");
+    }
+    HEC_TRY(upload_refactor_data(A, M, s));
+    RefactorArgs ra{};
+    ra.nent = M->rf_nent;
+    ra.val = dval;
+    ra.src = M->rf_src.as<int>();
+    ra.f = M->rf_f.as<double>();
+    ra.rp = M->rf_rp.as<int>();
+    ra.ci = M->rf_ci.as<int>();
+    ra.dg = M->rf_dg.as<int>();
+    ra.blk_row0 = M->rf_row0.as<int>();
+    ra.blk_lev0 = M->rf_lev0.as<int>();
+    ra.lptr = M->rf_lptr.as<int>();
+    ra.lrows = M->rf_lrows.as<int>();
+    ra.err = M->d_err.as<int>();
+    launch_refactor(ra, M->nblocks, s);
+    HEC_TRY(check_launch("refactor"));
+    for (int idx = 0; idx < 2; ++idx) {
+        TrsvLayout &L = M->lay[idx];
+        if (!L.built)
+            continue;
+        if (!L.d_row0.p) {
+            HEC_TRY(upload(L.d_row0, L.pack.chunk_row0, s));
+            HEC_TRY(upload(L.d_rms, L.pack.rm_start, s));
+            HEC_TRY(upload(L.d_rml, L.pack.rm_len, s));
+            HEC_TRY(upload(L.d_rmd, L.pack.rm_diag, s));
+        }
+        FillArgs fa{};
+        fa.pack = L.d_pack.as<unsigned char>();
+        fa.chunks = L.d_chunks.as<uint2>();
+        fa.chunk_row0 = L.d_row0.as<int64_t>();
+        fa.rm_start = L.d_rms.as<int>();
+        fa.rm_len = L.d_rml.as<int>();
+        fa.rm_diag = L.d_rmd.as<int>();
+        fa.f = M->rf_f.as<double>();
+        launch_fill_pack(fa, (int)L.pack.chunks.size(), idx == 1, s);
+        HEC_TRY(check_launch("fill"));
+    }
+    M->factor_host_stale = true;
+    return HEC_OK;
+}
+
+} // namespace
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -1111,6 +1323,13 @@ int hec_matrix_export(hec_matrix_t A, int32_t *ell_col, double *ell_val, int32_t
 {
     if (!A)
         return fail(HEC_ERR_INVALID, "null matrix");
+    if (A->hec_host_stale) { // hec_refactor replaced the values on the device
+        HEC_CK(cudaMemcpy(A->hec.ell_val.data(), A->ell_val.p,
+                          A->hec.ell_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        HEC_CK(cudaMemcpy(A->hec.tail_val.data(), A->tail_val.p,
+                          A->hec.tail_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        A->hec_host_stale = false;
+    }
     const HecHost &H = A->hec;
     auto cp = [](void *dst, const void *src, size_t bytes) {
         if (dst && bytes)
@@ -1400,6 +1619,7 @@ int hec_precond_get_factor(hec_precond_t M, int32_t b, int32_t *nnz, int32_t *ro
 {
     if (!M || b < 0 || b >= M->nblocks || !nnz)
         return fail(HEC_ERR_INVALID, "bad arguments");
+    HEC_TRY(refresh_host_factors(M, nullptr));
     const BlockFactor &B = M->blocks[b];
     *nnz = (int32_t)B.F.ci.size();
     if (row_ptr)
@@ -1485,6 +1705,32 @@ int hec_precond_status(hec_precond_t M, void *stream)
 }
 
 void hec_precond_destroy(hec_precond_t M) { delete M; }
+
+int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *stream)
+{
+    if (!A || !val)
+        return fail(HEC_ERR_INVALID, "null argument");
+    if (A->host_only || (M && M->host_only))
+        return fail(HEC_ERR_INVALID, "host-only handle");
+    if (M && M->matrix_id != A->id)
+        return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
+    if (M && M->kind != kJacobi && !M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    cudaStream_t s = (cudaStream_t)stream;
+    HEC_TRY(refactor_matrix(A, val, s));
+    if (M)
+        HEC_TRY(refactor_precond(A, M, s));
+    HEC_CK(cudaStreamSynchronize(s));
+    if (M) {
+        int err = 0;
+        HEC_CK(cudaMemcpy(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            HEC_CK(cudaMemset(M->d_err.p, 0, sizeof(int)));
+            return fail(err, "numeric refactorisation: a pivot is zero");
+        }
+    }
+    return HEC_OK;
+}
 
 int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, double tol,
                  int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,

@@ -29,6 +29,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
     uint64_t ticket = 0, tag = 0, key = 0;
+    uint64_t pattern = 0; // hash of row_ptr and col (matrix requests)
     int n = 0, k = 0;
     bool has_matrix = true;
     std::vector<int32_t> rp, ci;
@@ -43,6 +44,7 @@ struct Resident {
     hec_batch_t B = nullptr;
     int64_t bytes = 0;
     int n = 0, k = 0;
+    uint64_t pattern = 0;
     int users = 0;
     std::list<uint64_t>::iterator lru;
     void destroy()
@@ -116,10 +118,27 @@ int64_t resident_bytes(const Resident &R)
     return t;
 }
 
+// FNV-1a over the sparsity pattern: equal patterns let a keyed request with
+// new values refactor its resident system instead of setting it up again.
+uint64_t pattern_hash(const std::vector<int32_t> &rp, const std::vector<int32_t> &ci)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const std::vector<int32_t> &v) {
+        for (int32_t x : v) {
+            h ^= (uint32_t)x;
+            h *= 1099511628211ull;
+        }
+    };
+    mix(rp);
+    mix(ci);
+    return h;
+}
+
 int setup(hec_server_s *S, const Request &q, cudaStream_t st, Resident &R)
 {
     R.n = q.n;
     R.k = q.k;
+    R.pattern = q.pattern;
     if (q.n <= S->o.small_rows) {
         const int64_t sp[2] = {0, q.n};
         std::vector<int64_t> rp(q.rp.begin(), q.rp.end());
@@ -220,11 +239,23 @@ void lane_main(hec_server_s *S, int lane)
         Resident *R = &local;
         int rc = HEC_OK;
         if (reuse) {
-            std::lock_guard<std::mutex> lk(S->mu);
-            R = &S->cache[q.key];
-            if (R->n != q.n || R->k != q.k)
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                R = &S->cache[q.key];
+            }
+            if (R->n != q.n || R->k != q.k) {
                 rc = fail(HEC_ERR_INVALID, "key %llu was set up for another matrix",
                           (unsigned long long)q.key);
+            } else if (q.has_matrix && R->A && R->pattern == q.pattern) {
+                // same pattern, new values: refactor on the device (HEC values,
+                // ILU(k) of every RAS block, triangular-solve layouts)
+                rc = hec_refactor(R->A, R->M, q.va.data(), st);
+                r.refactored = 1;
+            } else if (q.has_matrix) {
+                // another pattern, or a one-CTA batched system: set it up again
+                R->destroy();
+                rc = setup(S, q, st, *R);
+            }
         } else if (!q.has_matrix) {
             rc = fail(HEC_ERR_INVALID, "key %llu is not resident and the request has no matrix",
                       (unsigned long long)q.key);
@@ -280,6 +311,8 @@ void lane_main(hec_server_s *S, int lane)
             if (reuse) {
                 Resident &c = S->cache[q.key];
                 c.users = 0;
+                S->reserved += used - c.bytes; // refactor maps or a new set-up
+                c.bytes = used;
                 c.lru = S->lru.insert(S->lru.end(), q.key);
             } else if (q.key && rc >= 0 && S->cache.find(q.key) == S->cache.end()) {
                 local.bytes = used;
@@ -384,6 +417,7 @@ int hec_server_submit(hec_server_t S, const hec_request_t *req, uint64_t *ticket
         q.rp.assign(req->A.row_ptr, req->A.row_ptr + n + 1);
         q.ci.assign(req->A.col, req->A.col + req->A.nnz);
         q.va.assign(req->A.val, req->A.val + req->A.nnz);
+        q.pattern = pattern_hash(q.rp, q.ci);
     }
     q.b.assign(req->b, req->b + n);
     {

@@ -446,6 +446,7 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
         std::vector<unsigned char> bytes;
         std::vector<uint2> chunks; // offsets relative to this block
         int nL = 0, nU = 0, spanL = 0, spanU = 0, nchunksL = 0;
+        std::vector<int> rows_per_chunk, rm_start, rm_len, rm_diag; // block-local entries
         int64_t alg = 0;
         std::string err;
     };
@@ -584,6 +585,13 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                         }
                         seg += (size_t)wd * ls * (vb + 4);
                     }
+                    O.rows_per_chunk.push_back(nr);
+                    for (int t = 0; t < nr; ++t) {
+                        const int i = pr.order[q + t];
+                        O.rm_start.push_back(upass ? B.diag[i] + 1 : F.rp[i]);
+                        O.rm_len.push_back(row_len(upass, i));
+                        O.rm_diag.push_back(upass ? B.diag[i] : -1);
+                    }
                     src = reinterpret_cast<int *>(seg);
                     int *dst = src + npad;
                     unsigned char *dinv = reinterpret_cast<unsigned char *>(dst + npad);
@@ -637,6 +645,27 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
     for (auto &O : outs)
         total += O.bytes.size();
     P.pack.resize(total);
+    P.chunk_row0.clear();
+    P.rm_start.clear();
+    P.rm_len.clear();
+    P.rm_diag.clear();
+    {
+        int64_t ent0 = 0, r0 = 0;
+        for (int b = 0; b < nb; ++b) {
+            const BlockOut &O = outs[b];
+            for (int nr : O.rows_per_chunk) {
+                P.chunk_row0.push_back(r0);
+                r0 += nr;
+            }
+            for (size_t q = 0; q < O.rm_start.size(); ++q) {
+                P.rm_start.push_back((int)(ent0 + O.rm_start[q]));
+                P.rm_len.push_back(O.rm_len[q]);
+                P.rm_diag.push_back(O.rm_diag[q] < 0 ? -1 : (int)(ent0 + O.rm_diag[q]));
+            }
+            ent0 += (int64_t)Bs[b].F.ci.size();
+        }
+        P.chunk_row0.push_back(r0);
+    }
     size_t off = 0;
     int64_t yoff = 0, zoff = 0;
     bool any_global_u = false;

@@ -67,6 +67,11 @@ struct TrsvPack {
     int ring_slots = 0;         // power of two (>= 32)
     int64_t alg_bytes = 0;      // algorithmic bytes of one apply
     int64_t rows_L = 0, rows_U = 0;
+    // where every chunk row's values come from, for refilling them from new
+    // factor values on the device: factor entries are numbered over all
+    // blocks in order (block b's entries start after those of blocks < b)
+    std::vector<int64_t> chunk_row0; // per chunk: first index into the row maps
+    std::vector<int> rm_start, rm_len, rm_diag; // first value's entry, count, diagonal (U; -1 for L)
 };
 // vb: bytes per stored value, 8 (FP64 layout) or 4 (FP32 layout).
 int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,

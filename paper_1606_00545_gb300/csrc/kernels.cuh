@@ -187,6 +187,37 @@ size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes);
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false);
 
+// ------------------------------------------------------------------ numeric refactorisation
+// Factors of all RAS blocks, concatenated: rows by block (row0 of block b at
+// blk_row0[b]), entries by row (rp: global entry offsets, ci: block-local
+// columns, dg: global entry index of each row's diagonal).
+struct RefactorArgs {
+    int64_t nent;            // factor entries over all blocks
+    const double *val;       // the new CSR values of A
+    const int *src;          // per factor entry: its CSR index in A, -1 for fill
+    double *f;               // factor values (out)
+    const int *rp, *ci, *dg;
+    const int *blk_row0;     // nblocks + 1
+    const int *blk_lev0;     // nblocks + 1: offsets into lptr (each block: nlev + 1 entries)
+    const int *lptr, *lrows; // L level sets per block (local rows, by block row offset)
+    int *err;                // device error word (HEC_ERR_ZERO_PIVOT)
+};
+// Per row of every chunk of a triangular-solve layout: where its values come from.
+struct FillArgs {
+    unsigned char *pack;
+    const uint2 *chunks;     // {offset in 16-byte units, bytes}
+    const int64_t *chunk_row0;
+    const int *rm_start, *rm_len, *rm_diag; // factor entry of the pass's first value, count, diagonal
+    const double *f;
+};
+int launch_scatter_hec(int64_t nnz, const double *val, const int64_t *slot, double *ell,
+                       double *tail, cudaStream_t s);
+int launch_cast_f32(int64_t n, const double *x, float *y, cudaStream_t s);
+int launch_refactor(const RefactorArgs &a, int nblocks, cudaStream_t s);
+int launch_fill_pack(const FillArgs &a, int nchunks, bool fp32, cudaStream_t s);
+int launch_jacobi_dinv(int n, const double *val, const int64_t *diag, double omega, double *dinv,
+                       float *dinv32, int *err, cudaStream_t s);
+
 // ------------------------------------------------------------------ small solver kernels
 int launch_gmres_lsq(SolverState *st, cudaStream_t s);
 int launch_loopcond(SolverState *st, cudaStream_t s);

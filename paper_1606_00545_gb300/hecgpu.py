@@ -125,7 +125,7 @@ class Result_t(C.Structure):
                 ("iters", C.c_int32), ("rel_resid", C.c_double), ("t_submit", C.c_double),
                 ("t_start", C.c_double), ("t_setup", C.c_double), ("t_done", C.c_double),
                 ("lane", C.c_int32), ("reused", C.c_int32), ("fp64_finish", C.c_int32),
-                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+                ("refactored", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 _vp = C.c_void_p
@@ -150,6 +150,7 @@ _SIGS = {
     "hec_multidot": ([_i32, _i32, _vp, _i64, _vp, _vp, _vp], C.c_int),
     "ilu_k_setup": ([_vp, _i32, _i32, _i32, _vp, C.POINTER(_vp)], C.c_int),
     "hec_jacobi_setup": ([_vp, C.c_double, _vp, C.POINTER(_vp)], C.c_int),
+    "hec_refactor": ([_vp, _vp, _vp, _vp], C.c_int),
     "level_schedule": ([_vp, _vp], C.c_int),
     "hec_precond_info": ([_vp, C.POINTER(PrecondInfo_t)], C.c_int),
     "hec_precond_get_block": ([_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), _vp],
@@ -430,6 +431,15 @@ class Precond:
             self.destroy()
         except Exception:
             pass
+
+
+def hec_refactor(A: Matrix, M, val, stream=None):
+    """Same pattern, new values (numpy array or torch tensor in A's CSR
+    order): A and, if given, its preconditioner are refactored on the GPU."""
+    if not hasattr(val, "data_ptr"):
+        val = np.ascontiguousarray(val, np.float64)
+    _check(load_library().hec_refactor(A.handle, M.handle if M is not None else None, _ptr(val),
+                                       _stream(stream)), "hec_refactor")
 
 
 def jacobi_setup(A: Matrix, omega: float = 1.0, stream=None) -> Precond:

@@ -134,3 +134,39 @@ def test_serve_fp64_and_invalid(H, orc):
     with H.Server(lanes=1) as S:
         with pytest.raises(H.HecError):
             S.solution(12345, 10)
+
+
+def test_serve_keyed_new_values_refactor_on_device(H, orc):
+    """A keyed request carrying new values of the resident pattern is
+    refactored on the GPU (hec_refactor) instead of set up again; its result
+    is bit-identical to a cold solve of the new matrix.  A one-CTA batched
+    system with new values is set up again."""
+    big0 = synth.serving_matrix({"stencil": 7, "side": 36, "k": 1, "seed": 5})
+    big1 = synth.serving_matrix({"stencil": 7, "side": 36, "k": 1, "seed": 8})
+    small0 = synth.serving_matrix({"stencil": 5, "side": 40, "k": 0, "seed": 2})
+    small1 = synth.serving_matrix({"stencil": 5, "side": 40, "k": 0, "seed": 3})
+    assert np.array_equal(big0.col, big1.col) and not np.array_equal(big0.val, big1.val)
+    b_big = synth.rhs_uniform(big0.n, 4)
+    b_small = synth.rhs_uniform(small0.n, 5)
+
+    def solve_all(items):
+        out = []
+        with H.Server(lanes=1, flags=H.MIXED_FP32) as S:
+            for i, (A, b, k, key) in enumerate(items):
+                t = S.submit(A, b, ilu_k=k, key=key, tag=i)
+                r = []
+                while not r:
+                    r = S.poll(wait_ms=200)
+                out.append((r[0], S.solution(t, A.n)))
+        return out
+
+    keyed = solve_all([(big0, b_big, 1, 90), (big1, b_big, 1, 90),
+                       (small0, b_small, 0, 91), (small1, b_small, 0, 91)])
+    cold = solve_all([(big1, b_big, 1, 0), (small1, b_small, 0, 0)])
+    assert keyed[1][0]["reused"] == 1 and keyed[1][0]["refactored"] == 1
+    assert keyed[3][0]["reused"] == 1 and keyed[3][0]["refactored"] == 0
+    for (r, x), (rc, xc), (A, b) in ((keyed[1], cold[0], (big1, b_big)),
+                                     (keyed[3], cold[1], (small1, b_small))):
+        assert r["status"] == H.OK and rc["status"] == H.OK
+        assert np.array_equal(x, xc)
+        assert np.linalg.norm(b - orc.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
