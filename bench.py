@@ -545,6 +545,35 @@ def c5_section(H):
                                                 True)
         cap = out["mixed_lambda"]["solves_per_s"]
         out["mixed_half_capacity"] = open_loop(S, 0.5 * cap, stream(0.5 * cap, 40), True)
+        # new values for the resident systems of the single-system path (a
+        # time step of the same grids): keyed requests are refactored on the
+        # GPU; the same matrices sent without a key are set up on the host
+        big = [i for i, A in enumerate(pool) if A.n > 32768]
+
+        def one(A2, i, key):
+            S.submit(A2, rhs[i], ilu_k=specs[i]["k"], key=key, tag=i)
+            r = []
+            while not r:
+                r = S.poll(wait_ms=100)
+            return r[0]
+
+        first, rf, cold = [], [], []
+        for i in big:  # two time steps: the first also builds the handle's index maps
+            first.append(one(synth.serving_matrix(dict(specs[i], seed=specs[i]["seed"] + 500),
+                                                  SIGMA), i, i + 1))
+            A3 = synth.serving_matrix(dict(specs[i], seed=specs[i]["seed"] + 501), SIGMA)
+            rf.append(one(A3, i, i + 1))
+            cold.append(one(A3, i, 0))
+        ms = lambda r: 1e3 * (r["t_setup"] - r["t_start"])
+        out["new_values"] = {
+            "systems": len(big), "unknowns": [pool[i].n for i in big],
+            "refactored": int(sum(r["refactored"] for r in first + rf)),
+            "ok": int(sum(r["status"] == H.OK for r in first + rf + cold)),
+            "first_refactor_ms": [round(ms(r), 2) for r in first],
+            "refactor_setup_ms": [round(ms(r), 2) for r in rf],
+            "host_setup_ms": [round(ms(r), 1) for r in cold],
+            "median_speedup": float(np.median([ms(c) / max(1e-6, ms(r))
+                                               for r, c in zip(rf, cold)]))}
     # the plain form on the same request stream: FP64, one system at a time,
     # every solve through the single-system launch sequence
     with H.Server(lanes=1, flags=0, small_rows=1, keep_solutions=False) as S:

@@ -172,6 +172,15 @@ def spmv(A, x, alpha=1.0, beta=0.0, y=None):
     return out
 
 
+def spmv_rows(A, x, lo: int, hi: int):
+    """Rows [lo, hi) of A x (the oracle's row loop on that range)."""
+    rp, ci, va = _arrs(A)
+    y = np.zeros(A.n)
+    _load().orc_spmv_range(A.n, rp, ci, va, 1.0, np.ascontiguousarray(x, np.float64), 0.0, y,
+                           int(lo), int(hi))
+    return y[lo:hi]
+
+
 def spmv_threads(A, x, threads: int):
     """y = A x with the oracle's row loop split into `threads` row ranges run
     on host threads (the library call releases the GIL)."""
