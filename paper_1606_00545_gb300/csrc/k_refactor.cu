@@ -48,10 +48,97 @@ __global__ void k_gather_factor(int64_t nent, const double *val, const int *src,
     }
 }
 
+// Rows of at most kLocalRow entries are eliminated in per-thread arrays:
+// the row is read once and written once, and its merges against the pivot
+// rows read only the pivot rows from memory.  Longer rows run the same steps
+// on global memory.
+constexpr int kLocalRow = 48;
+
+__device__ __forceinline__ bool eliminate_row_local(const RefactorArgs &a, int row0, int r)
+{
+    const int b0 = a.rp[r], len = a.rp[r + 1] - b0, nl = a.dg[r] - b0;
+    int ci[kLocalRow];
+    double f[kLocalRow];
+    for (int q = 0; q < len; ++q) {
+        ci[q] = a.ci[b0 + q];
+        f[q] = a.f[b0 + q];
+    }
+    bool ok = true;
+    for (int k = 0; k < nl; ++k) {
+        const int p = row0 + ci[k]; // pivot row
+        const int dp = a.dg[p], ep = a.rp[p + 1];
+        const double upp = a.f[dp];
+        if (upp == 0.0) {
+            ok = false;
+            break;
+        }
+        const double lip = __ddiv_rn(f[k], upp);
+        f[k] = lip;
+        // row i's entries right of p against row p's U part (both ascending)
+        int x = k + 1, y = dp + 1;
+        int cy = y < ep ? a.ci[y] : 0x7fffffff;
+        double fy = y < ep ? a.f[y] : 0.0;
+        while (x < len && y < ep) {
+            const int cx = ci[x];
+            if (cx == cy) {
+                f[x] = __dsub_rn(f[x], __dmul_rn(lip, fy));
+                ++x;
+                ++y;
+                if (y < ep) {
+                    cy = a.ci[y];
+                    fy = a.f[y];
+                }
+            } else if (cx < cy) {
+                ++x;
+            } else {
+                ++y;
+                if (y < ep) {
+                    cy = a.ci[y];
+                    fy = a.f[y];
+                }
+            }
+        }
+    }
+    for (int q = 0; q < len; ++q)
+        a.f[b0 + q] = f[q];
+    return ok && f[nl] != 0.0;
+}
+
+__device__ __forceinline__ bool eliminate_row_global(const RefactorArgs &a, int row0, int r)
+{
+    double *f = a.f;
+    const int end_i = a.rp[r + 1];
+    for (int e = a.rp[r]; e < a.dg[r]; ++e) {
+        const int p = row0 + a.ci[e]; // pivot row
+        const double upp = f[a.dg[p]];
+        if (upp == 0.0)
+            return false;
+        const double lip = __ddiv_rn(f[e], upp);
+        f[e] = lip;
+        int x = e + 1, y = a.dg[p] + 1;
+        const int end_p = a.rp[p + 1];
+        while (x < end_i && y < end_p) {
+            const int cx = a.ci[x], cy = a.ci[y];
+            if (cx == cy) {
+                f[x] = __dsub_rn(f[x], __dmul_rn(lip, f[y]));
+                ++x;
+                ++y;
+            } else if (cx < cy) {
+                ++x;
+            } else {
+                ++y;
+            }
+        }
+    }
+    return f[a.dg[r]] != 0.0;
+}
+
 // One CTA per RAS block, one thread per row of the current L level, a CTA
 // barrier between levels.  Row data is global-entry indexed: row r (global
 // over all blocks) holds entries [rp[r], rp[r+1]), local columns ci, its
-// diagonal at dg[r].
+// diagonal at dg[r].  Within a row the pivots are taken in ascending order
+// and each update is a separately rounded multiply and subtract: the host's
+// operations in the host's order.
 __global__ void __launch_bounds__(kThreads) k_iluk_numeric(RefactorArgs a)
 {
     const int b = blockIdx.x;
@@ -59,38 +146,13 @@ __global__ void __launch_bounds__(kThreads) k_iluk_numeric(RefactorArgs a)
     const int *lptr = a.lptr + a.blk_lev0[b];
     const int nlev = a.blk_lev0[b + 1] - a.blk_lev0[b] - 1;
     const int *lrows = a.lrows + row0;
-    double *f = a.f;
     for (int l = 0; l < nlev; ++l) {
         for (int q = lptr[l] + threadIdx.x; q < lptr[l + 1]; q += blockDim.x) {
             const int r = row0 + lrows[q];
-            const int end_i = a.rp[r + 1];
-            for (int e = a.rp[r]; e < a.dg[r]; ++e) {
-                const int p = row0 + a.ci[e]; // pivot row
-                const double upp = f[a.dg[p]];
-                if (upp == 0.0) {
-                    atomicExch(a.err, HEC_ERR_ZERO_PIVOT);
-                    break;
-                }
-                const double lip = __ddiv_rn(f[e], upp);
-                f[e] = lip;
-                // row i's entries right of p against row p's U part (both
-                // ascending): a_ij -= l_ip u_pj where the columns meet
-                int x = e + 1, y = a.dg[p] + 1;
-                const int end_p = a.rp[p + 1];
-                while (x < end_i && y < end_p) {
-                    const int cx = a.ci[x], cy = a.ci[y];
-                    if (cx == cy) {
-                        f[x] = __dsub_rn(f[x], __dmul_rn(lip, f[y]));
-                        ++x;
-                        ++y;
-                    } else if (cx < cy) {
-                        ++x;
-                    } else {
-                        ++y;
-                    }
-                }
-            }
-            if (f[a.dg[r]] == 0.0)
+            const bool ok = (a.rp[r + 1] - a.rp[r] <= kLocalRow)
+                                ? eliminate_row_local(a, row0, r)
+                                : eliminate_row_global(a, row0, r);
+            if (!ok)
                 atomicExch(a.err, HEC_ERR_ZERO_PIVOT);
         }
         __syncthreads();
