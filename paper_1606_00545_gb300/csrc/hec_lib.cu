@@ -171,6 +171,7 @@ struct TrsvLayout {
     DevBuf d_row0, d_rms, d_rml, d_rmd; // value maps of hec_refactor (uploaded on first use)
     int nstages = 8;
     int vbytes = 8;
+    int fixed_width = 0; // FP32 layout: uniform warp width (0: per-warp widths)
     bool built = false;
     int64_t device_bytes() const
     {
@@ -293,6 +294,7 @@ TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
     a.ring_mask = L.pack.ring_slots - 1;
     a.stage_bytes = M->stage_bytes;
     a.nstages = L.nstages;
+    a.fixed_width = L.fixed_width;
     a.spin_limit = spin;
     a.err = M->d_err.as<int>();
     return a;
@@ -332,8 +334,15 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
         return HEC_OK;
     HEC_TRY(refresh_host_factors(M, s));
     L.vbytes = idx == 0 ? 8 : 4;
+    // FP32: pad every row to one short width when the factors allow it (the
+    // padding costs FP32 multiply-adds and bytes, and saves the per-warp
+    // width dispatch); FP64 keeps exact widths (its pipe is the bound)
+    L.fixed_width = idx == 1 ? trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
+                                                           max_factor_width(M->blocks, true)))
+                             : 0;
     std::string msg;
-    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg);
+    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg,
+                       L.fixed_width);
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
     if (!M->host_only) {

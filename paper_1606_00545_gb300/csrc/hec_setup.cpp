@@ -426,8 +426,17 @@ struct PassRows {
 // their L dependencies.  The other rows cannot influence the owned part of
 // the result and are left out of the device program (the result on the
 // owned rows is unchanged).
+int max_factor_width(const std::vector<BlockFactor> &Bs, bool upass)
+{
+    int w = 0;
+    for (const BlockFactor &B : Bs)
+        for (int i = 0; i < B.F.n; ++i)
+            w = std::max(w, upass ? B.F.rp[i + 1] - B.diag[i] - 1 : B.diag[i] - B.F.rp[i]);
+    return w;
+}
+
 int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int max_ring, int vb,
-              TrsvPack &P, std::string &msg)
+              TrsvPack &P, std::string &msg, int uniform_width)
 {
     (void)n;
     if (vb != 8 && vb != 4) {
@@ -520,7 +529,8 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                     while (q2 < end && q2 - q < kThreads) {
                         const int j = q2 - q;
                         if (j % kWarpRows == 0)
-                            widths.push_back(row_len(upass, pr.order[q2]));
+                            widths.push_back(uniform_width > 0 ? uniform_width
+                                                               : row_len(upass, pr.order[q2]));
                         if (chunk_bytes(widths, j + 1, upass, vb) > (size_t)stage_bytes) {
                             if (j % kWarpRows == 0)
                                 widths.pop_back();
@@ -569,15 +579,18 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                             const int i = pr.order[q + t];
                             const int e0 = upass ? B.diag[i] + 1 : F.rp[i];
                             const int len = row_len(upass, i);
-                            if (len == 0 && wd > 0) {
+                            if (len == 0 && wd > 0 && uniform_width == 0) {
                                 // a row of level >= 2 always has a dependency
                                 O.err = "internal: dependency-free row in a dependent level";
                                 return;
                             }
                             for (int kk = 0; kk < wd; ++kk) {
                                 // padding repeats the first dependency with value 0
+                                // (a row without one -- level 1 of a uniform-width
+                                // layout -- points at the chunk's first position:
+                                // 0 times a finite value)
                                 const int e = kk < len ? e0 + kk : e0;
-                                const int d = (upass ? posU : posL)[F.ci[e]];
+                                const int d = len > 0 ? (upass ? posU : posL)[F.ci[e]] : q;
                                 dep[(size_t)kk * ls + lane] = d;
                                 put_value(val, (size_t)kk * ls + lane, kk < len ? F.va[e] : 0.0, vb);
                                 mindep = std::min(mindep, d);

@@ -74,8 +74,13 @@ struct TrsvPack {
     std::vector<int> rm_start, rm_len, rm_diag; // first value's entry, count, diagonal (U; -1 for L)
 };
 // vb: bytes per stored value, 8 (FP64 layout) or 4 (FP32 layout).
+// uniform_width > 0: every warp segment of every chunk has this width (rows
+// padded with value 0), so the kernel can address and solve rows with a
+// width known at compile time; it must be >= the longest row.
 int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,
-              TrsvPack &out, std::string &msg);
+              TrsvPack &out, std::string &msg, int uniform_width = 0);
+// The longest off-diagonal row of any L_b (upass false) or U_b.
+int max_factor_width(const std::vector<BlockFactor> &B, bool upass);
 
 // Run f(i) for i in [0, count) on the host's cores.
 void parallel_for(int count, const std::function<void(int)> &f);

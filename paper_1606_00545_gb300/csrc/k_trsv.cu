@@ -213,7 +213,7 @@ __device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const 
 //             one thread releases empty[s] (and ldone after the last L chunk).
 // T = double: the FP64 path; T = float: the FP32 inner solves of the
 // mixed-precision mode (FP32 factors, products and accumulation).
-template <class T>
+template <class T, int FW>
 __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -339,11 +339,43 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
             if (t < v.nrows) {
                 const bool rm = v.upass ? blk.ring_U : blk.ring_L;
                 const T *gdep = v.upass ? zsc : ysc;
-                const Segment<T> g = warp_segment<T>(ch, v.nrows, t / kWarpRows);
                 const int lane = t % kWarpRows;
                 T sacc = rhs[(size_t)s * kThreads + t];
-                sacc = rm ? row_solve_any<true, T>(g, lane, ring, mask, gdep, sacc)
-                          : row_solve_any<false, T>(g, lane, ring, mask, gdep, sacc);
+                if constexpr (FW > 0) {
+                    // uniform-width layout: every warp's segment is FW entries
+                    // wide, so this thread's entries sit at a compile-time
+                    // offset from the chunk (all warps before the last are
+                    // full) and the row needs no width dispatch
+                    const int w = t / kWarpRows;
+                    const int stride = seg_stride(w, v.nrows);
+                    const T *val = reinterpret_cast<const T *>(
+                                       ch + 96 + (size_t)w * FW * kWarpRows * (sizeof(T) + 4)) +
+                                   lane;
+                    const int *dep = reinterpret_cast<const int *>(val - lane + FW * stride) + lane;
+                    T l[FW], y[FW];
+                    int d[FW];
+#pragma unroll
+                    for (int k = 0; k < FW; ++k) {
+                        l[k] = val[k * stride];
+                        d[k] = dep[k * stride];
+                    }
+                    if (rm) {
+#pragma unroll
+                        for (int k = 0; k < FW; ++k)
+                            y[k] = ring[d[k] & mask];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < FW; ++k)
+                            y[k] = gdep[d[k]];
+                    }
+#pragma unroll
+                    for (int k = 0; k < FW; ++k)
+                        sacc = fma(-l[k], y[k], sacc);
+                } else {
+                    const Segment<T> g = warp_segment<T>(ch, v.nrows, t / kWarpRows);
+                    sacc = rm ? row_solve_any<true, T>(g, lane, ring, mask, gdep, sacc)
+                              : row_solve_any<false, T>(g, lane, ring, mask, gdep, sacc);
+                }
                 const int pos = v.base + t;
                 if (v.upass) {
                     sacc *= v.dinv[t];
@@ -369,7 +401,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
             failed = 1; // the feeding warps' own waits run out
             break;
         }
-        if (t == 0)
+        // the release falls to the last thread: warp 7 holds the shortest rows
+        if (t == kThreads - 1)
             mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
         if (gout)
             *gout = out;
@@ -377,7 +410,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
             // every y of the L pass is written before the gatherer reads
             // the U pass's right-hand sides from them
             consumer_sync_or(0);
-            if (t == 0)
+            if (t == kThreads - 1)
                 mbar_arrive(ldone);
         }
         if (++s == S) {
@@ -404,7 +437,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
 // The dynamic shared memory limit is a process-wide attribute of the kernel:
 // raised once to the device's opt-in maximum, so that launches of different
 // sizes from several host threads never race on it.
-template <class T> static cudaError_t prepare_trsv()
+template <class T, int FW> static cudaError_t prepare_trsv()
 {
     static std::once_flag once;
     static cudaError_t e = cudaSuccess;
@@ -414,26 +447,38 @@ template <class T> static cudaError_t prepare_trsv()
         cudaFuncAttributes fa{};
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e == cudaSuccess)
-            e = cudaFuncGetAttributes(&fa, k_trsv_ras<T>);
+            e = cudaFuncGetAttributes(&fa, k_trsv_ras<T, FW>);
         if (e == cudaSuccess)  // the opt-in limit covers static and dynamic shared memory
-            e = cudaFuncSetAttribute(k_trsv_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_trsv_ras<T, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      optin - (int)fa.sharedSizeBytes);
     });
     return e;
 }
 
-template <class T> static int launch_t(const TrsvArgs &a, cudaStream_t s)
+template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s)
 {
     const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1, sizeof(T));
-    if (prepare_trsv<T>() != cudaSuccess)
+    if (prepare_trsv<T, FW>() != cudaSuccess)
         return -1;
-    k_trsv_ras<T><<<a.nblocks, kThreads + 64, smem, s>>>(a);
+    k_trsv_ras<T, FW><<<a.nblocks, kThreads + 64, smem, s>>>(a);
     return 0;
 }
 
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32)
 {
-    return fp32 ? launch_t<float>(a, s) : launch_t<double>(a, s);
+    if (!fp32)
+        return launch_t<double, 0>(a, s);
+    switch (a.fixed_width) { // FP32 layouts padded to a uniform width
+    case 4: return launch_t<float, 4>(a, s);
+    case 6: return launch_t<float, 6>(a, s);
+    case 8: return launch_t<float, 8>(a, s);
+    default: return launch_t<float, 0>(a, s);
+    }
+}
+
+int trsv_uniform_width(int longest_row)
+{
+    return longest_row <= 4 ? 4 : longest_row <= 6 ? 6 : longest_row <= 8 ? 8 : 0;
 }
 
 } // namespace hec

@@ -174,6 +174,7 @@ struct TrsvArgs {
     void *ysc, *zsc;            // scratch: y by L position, z by U position
     int ring_mask;              // ring slots - 1 (power of two)
     int stage_bytes, nstages;
+    int fixed_width;            // > 0: FP32 layout packed with this uniform warp width
     long long spin_limit;
     int *err;                   // device error word
     SolverState *st;            // nullable: skip / basis column / launch count
@@ -186,6 +187,9 @@ size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
 // Largest stage count (3..8) that fits the device's shared memory per CTA.
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes);
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false);
+// The uniform width (4, 6 or 8) the FP32 layout is padded to for rows of at
+// most longest_row entries; 0: longer rows, generic layout.
+int trsv_uniform_width(int longest_row);
 
 // ------------------------------------------------------------------ numeric refactorisation
 // Factors of all RAS blocks, concatenated: rows by block (row0 of block b at
