@@ -208,3 +208,26 @@ def test_invalid_arguments(H):
     B = H.hec_build(A.row_ptr, A.col, A.val)
     with pytest.raises(H.HecError):
         H.krylov_solve(B, P, b, x)  # preconditioner of another matrix
+
+
+@pytest.mark.parametrize("method,flags", [("bicgstab", 0), ("gmres", 0), ("gmres", "mixed"),
+                                          ("cg", 0)])
+def test_nan_rhs_ends_in_breakdown(H, orc, method, flags):
+    """Fault injected on the host: a NaN in b ends the solve with
+    HEC_BREAKDOWN (no hang, no device error); a clean solve on the same
+    handles still works afterwards and reports its device time."""
+    A = synth.diffusion2d_5pt_lognormal(32, 1.0, 4)
+    M, P = setup(H, A, 0, 1, 0)
+    b = synth.rhs_uniform(A.n, 8)
+    bad = b.copy()
+    bad[A.n // 3] = np.nan
+    m = {"bicgstab": H.BICGSTAB, "gmres": H.GMRES, "cg": H.CG}[method]
+    fl = H.MIXED_FP32 if flags == "mixed" else 0
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(bad), x, tol=1e-8, maxit=200, restart=30, method=m,
+                          flags=fl)
+    assert info["status"] == H.BREAKDOWN
+    x = dev(np.zeros(A.n))
+    info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=2000, restart=30, method=m, flags=fl)
+    assert info["status"] == H.OK and info["solve_ms"] > 0
+    assert true_rel_resid(orc, A, b, host(x)) <= 1e-8
