@@ -163,8 +163,6 @@ typedef struct {
     int64_t kernel_launches;/* library kernels the solve ran                  */
     int64_t h2d_bytes;      /* host->device bytes copied (host b / x)         */
     int64_t d2h_bytes;      /* device->host bytes copied (host x)             */
-    double solve_ms;        /* device time of the iteration (CUDA events on the
-                               stream, copies of host b / x excluded)        */
 } hec_solve_info_t;
 
 /* ---------------------------------------------------------------- misc */

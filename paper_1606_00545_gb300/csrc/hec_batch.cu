@@ -821,20 +821,6 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
         }
         dx = sx.as<double>();
     }
-    NvtxRange nvtx_("krylov_solve_batched");
-    struct Events { // timing of the solve launch(es), released on every return
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        ~Events()
-        {
-            if (e0)
-                cudaEventDestroy(e0);
-            if (e1)
-                cudaEventDestroy(e1);
-        }
-    } ev;
-    HEC_CK(cudaEventCreate(&ev.e0));
-    HEC_CK(cudaEventCreate(&ev.e1));
-    HEC_CK(cudaEventRecord(ev.e0, st));
     HEC_TRY(run_batch(B, BOP_SOLVE, fp32, db, dx, nrhs, tol, maxit, restart, fp32 ? 1e-5 : 0.0,
                       (o.flags & HEC_X0_ZERO) != 0, spin, st, nullptr));
     std::vector<BatchResult> res(B->nsys);
@@ -869,7 +855,6 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
             }
         launches = 2;
     }
-    HEC_CK(cudaEventRecord(ev.e1, st));
     if (!xdev) {
         HEC_CK(cudaMemcpyAsync(x, dx, nb, cudaMemcpyDeviceToHost, st));
         d2h += (int64_t)nb;
@@ -877,9 +862,6 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
     HEC_CK(cudaStreamSynchronize(st));
     int status = HEC_OK;
     hec_solve_info_t I{};
-    float solve_ms = 0.0f;
-    cudaEventElapsedTime(&solve_ms, ev.e0, ev.e1);
-    I.solve_ms = solve_ms;
     I.fp64_finish = nstag;
     for (int s = 0; s < B->nsys; ++s) {
         const BatchResult &r = res[s];

@@ -1263,7 +1263,6 @@ int hec_set_allocator(void *(*alloc_fn)(size_t, void *, void *), void (*free_fn)
 
 int hec_build(const hec_csr_t *Ain, const hec_opts_t *opts, void *stream, hec_matrix_t *out)
 {
-    NvtxRange nvtx_("hec_build");
     if (!Ain || !out)
         return fail(HEC_ERR_INVALID, "null argument");
     *out = nullptr;
@@ -1497,7 +1496,6 @@ int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const doubl
 int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
                 hec_precond_t *out)
 {
-    NvtxRange nvtx_("ilu_k_setup");
     (void)stream;
     if (!A || !out)
         return fail(HEC_ERR_INVALID, "null argument");
@@ -1529,7 +1527,6 @@ int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, voi
 
 int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *out)
 {
-    NvtxRange nvtx_("hec_jacobi_setup");
     if (!A || !out)
         return fail(HEC_ERR_INVALID, "null argument");
     *out = nullptr;
@@ -1567,7 +1564,6 @@ int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *
 
 int level_schedule(hec_precond_t M, void *stream)
 {
-    NvtxRange nvtx_("level_schedule");
     if (!M)
         return fail(HEC_ERR_INVALID, "null preconditioner");
     if (M->scheduled)
@@ -1668,7 +1664,6 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
 
 int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit, void *stream)
 {
-    NvtxRange nvtx_("hec_precond_apply");
     if (!M || !r || !z || r == z)
         return fail(HEC_ERR_INVALID, "bad arguments");
     if (M->host_only)
@@ -1722,7 +1717,6 @@ void hec_precond_destroy(hec_precond_t M) { delete M; }
 
 int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *stream)
 {
-    NvtxRange nvtx_("hec_refactor");
     if (!A || !val)
         return fail(HEC_ERR_INVALID, "null argument");
     if (A->host_only || (M && M->host_only))
@@ -1751,7 +1745,6 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
                  int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
                  hec_solve_info_t *info)
 {
-    NvtxRange nvtx_("krylov_solve");
     if (info)
         std::memset(info, 0, sizeof(*info));
     if (!A || !b || !x)
@@ -1816,35 +1809,17 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
         if (!xdev)
             h2d += vb;
     }
-    struct Events { // the solve's two timing events, released on every return
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        ~Events()
-        {
-            if (e0)
-                cudaEventDestroy(e0);
-            if (e1)
-                cudaEventDestroy(e1);
-        }
-    } ev;
-    HEC_CK(cudaEventCreate(&ev.e0));
-    HEC_CK(cudaEventCreate(&ev.e1));
-    cudaEvent_t ev0 = ev.e0, ev1 = ev.e1;
-    HEC_CK(cudaEventRecord(ev0, s));
     if (eager)
         HEC_TRY(run_eager(A, M, *S, s));
     else
         HEC_CK(cudaGraphLaunch(S->exec, s));
-    HEC_CK(cudaEventRecord(ev1, s));
     HEC_CK(cudaMemcpyAsync(x, S->x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!xdev)
         d2h += vb;
     HEC_CK(cudaMemcpyAsync(&h, S->st, offsetof(SolverState, H), cudaMemcpyDeviceToHost, s));
     HEC_CK(cudaStreamSynchronize(s));
-    float solve_ms = 0.0f;
-    cudaEventElapsedTime(&solve_ms, ev0, ev1);
     int status = h.err ? h.err : h.status;
     if (info) {
-        info->solve_ms = solve_ms;
         info->iters = h.iters;
         info->restarts = h.restarts;
         info->status = status;
@@ -1872,7 +1847,6 @@ int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, do
             info->kernel_launches += i64.kernel_launches;
             info->h2d_bytes += i64.h2d_bytes;
             info->d2h_bytes += i64.d2h_bytes;
-            info->solve_ms += i64.solve_ms;
             info->fp64_finish = 1;
         }
     }

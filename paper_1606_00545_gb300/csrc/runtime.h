@@ -14,18 +14,8 @@
 #include <vector>
 
 #include "../../include/hecgpu.h"
-#include <nvtx3/nvToolsExt.h>
 
 namespace hec {
-
-// A named NVTX range over one library call or phase (for nsys / ncu range
-// filters); header-only NVTX 3, a no-op when no tool is attached.
-struct NvtxRange {
-    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-    NvtxRange(const NvtxRange &) = delete;
-    NvtxRange &operator=(const NvtxRange &) = delete;
-};
 
 // Records a printf-style message for hec_last_error() and returns `code`.
 int fail(int code, const char *fmt, ...);

@@ -83,7 +83,7 @@ class SolveInfo_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
                 ("fp64_finish", C.c_int32), ("rel_resid", C.c_double), ("est_resid", C.c_double),
                 ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("solve_ms", C.c_double)]
+                ("d2h_bytes", C.c_int64)]
 
 
 class BatchCSR_t(C.Structure):

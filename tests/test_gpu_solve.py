@@ -215,7 +215,7 @@ def test_invalid_arguments(H):
 def test_nan_rhs_ends_in_breakdown(H, orc, method, flags):
     """Fault injected on the host: a NaN in b ends the solve with
     HEC_BREAKDOWN (no hang, no device error); a clean solve on the same
-    handles still works afterwards and reports its device time."""
+    handles still works afterwards."""
     A = synth.diffusion2d_5pt_lognormal(32, 1.0, 4)
     M, P = setup(H, A, 0, 1, 0)
     b = synth.rhs_uniform(A.n, 8)
@@ -229,5 +229,5 @@ def test_nan_rhs_ends_in_breakdown(H, orc, method, flags):
     assert info["status"] == H.BREAKDOWN
     x = dev(np.zeros(A.n))
     info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=2000, restart=30, method=m, flags=fl)
-    assert info["status"] == H.OK and info["solve_ms"] > 0
+    assert info["status"] == H.OK
     assert true_rel_resid(orc, A, b, host(x)) <= 1e-8
