@@ -70,7 +70,7 @@ def parse():
                          "device-side graph loop (ncu cannot profile kernels of graphs with "
                          "conditional nodes); same kernels and results, slower")
     ap.add_argument("--skip", default="",
-                    help="comma-separated sections to leave out of the JSON line: c3, c4, c5")
+                    help="comma-separated sections to leave out of the JSON line: c1, c3, c4, c5")
     ap.add_argument("--table4", action="store_true",
                     help="instead of the benchmark line: the paper's Table 4 / Table 5 sweep "
                          "(ILU(k), RAS blocks, overlap; BiCGSTAB and GMRES(30)) and CG with "
@@ -338,7 +338,67 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------ C3 and C4 sections
+# ------------------------------------------------------------------ C1, C3 and C4 sections
+def c1_section(H, torch, dev, with_cpu):
+    """The small single solve: 2D 5-point Poisson on 64x64 (n = 4,096), ILU(0)
+    on one block, GMRES(30) from x0 = 0 to 1e-8, rhs uniform[-1, 1] seed 1.
+    Matrix, factors and basis (about 1.5 MB) stay in L2, so this case is a
+    latency figure: per-solve device time (CUDA events around each solve),
+    host-buffer latency through the C ABI (wall clock, copies included) and
+    iterations/s, with no HBM fraction."""
+    A = synth.poisson2d_5pt(64)
+    b = synth.rhs_uniform(A.n, 1)
+    t0 = time.perf_counter()
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    H.level_schedule(P)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    stream = torch.cuda.current_stream()
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+    kw = dict(tol=1e-8, maxit=1000, restart=30, method=H.GMRES, flags=H.X0_ZERO)
+    for _ in range(5):
+        info = H.krylov_solve(M, P, bd, x, **kw)
+    assert info["status"] == H.OK, info
+    reps = 50
+    dev_ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = H.krylov_solve(M, P, bd, x, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    bh = b.copy()
+    xh = np.zeros(A.n)
+    host_ms = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ih = H.krylov_solve(M, P, bh, xh, **kw)
+        host_ms.append((time.perf_counter() - t0) * 1e3)
+    assert ih["status"] == H.OK and ih["iters"] == info["iters"], (ih, info)
+    p50 = statistics.median(dev_ms)
+    out = {"workload": "poisson2d_5pt_64x64_ilu0_gmres30_tol1e-8_fp64", "n": A.n,
+           "nnz": A.nnz, "iters": info["iters"], "rel_resid": info["rel_resid"],
+           "kernel_launches": info["kernel_launches"], "setup_ms": round(setup_ms, 2),
+           "solve_ms_p50": p50, "solve_ms_min": min(dev_ms),
+           "iters_per_s": info["iters"] / (p50 * 1e-3),
+           "e2e_host_buffers_ms_p50": statistics.median(host_ms), "solves_timed": reps}
+    if with_cpu:
+        import oracle
+        R = oracle.RAS(A, 0, 1, 0)
+        best = None
+        for _ in range(5):
+            t0 = time.perf_counter()
+            _, ir = oracle.gmres(A, b, M=R, tol=1e-8, maxit=1000, restart=30)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out["cpu_oracle_one_core"] = {"solve_ms": round(best * 1e3, 2), "iters": ir.iters}
+    return out
+
+
 def c3_section(H, torch, dev, timed):
     """96^3 27-point + 2% irregular rows: ILU(0) on 64 RAS blocks, GMRES(50),
     FP64 against mixed (FP32 inner cycles, FP64 refinement), manufactured
@@ -735,6 +795,8 @@ def run_ours(args, rank, world, local_rank):
     H.hec_refactor(Ah, P, v1)  # back to the benchmark's matrix
     pinf = P.info()
     skip = set(filter(None, args.skip.split(",")))
+    c1 = (c1_section(H, torch, dev, rank == 0 and not args.no_cpu_baseline)
+          if "c1" not in skip else None)
     c3 = c3_section(H, torch, dev, timed) if "c3" not in skip else None
     c4 = c4_section(H, torch, dev, timed, peak) if "c4" not in skip else None
     c5 = c5_section(H) if "c5" not in skip else None
@@ -791,6 +853,7 @@ def run_ours(args, rank, world, local_rank):
                          "trsv_alg_bytes": pinf["apply_bytes_f32"],
                          "spmv_ms": ms_s32 / reps,
                          "spmv_gbs": (A.nnz * 8 + A.n * 8) / (ms_s32 * 1e-3 / reps) / 1e9},
+        "c1_latency": c1,
         "c3_irregular_mixed": c3,
         "c4_batched": c4,
         "c5_serving": c5,

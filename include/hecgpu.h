@@ -258,6 +258,34 @@ int hec_precond_get_factor(hec_precond_t M, int32_t b, int32_t *nnz, int32_t *ro
  * level); arrays may be NULL. */
 int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *nlev,
                            int32_t *level_ptr, int32_t *level_rows);
+/* The level-major factor layout that the triangular solves stream (Section
+ * 2.6, Eq. 11: the rows of every level of L_b, then of U_b), host copies, for
+ * inspection and host-side checks.  fp32 = 0: the FP64 layout; fp32 = 1: the
+ * FP32 layout of the mixed-precision mode (packed, and on a device handle
+ * uploaded, on first request).  *pack_bytes, *nchunks, *ring_slots (the
+ * shared-memory window of solved values, a power of two) and *fixed_width
+ * (0, or the one segment width of every warp) are always set; pack
+ * (pack_bytes bytes), chunks (2 per chunk: byte offset / 16, byte count) and
+ * blocks (7 per RAS block: first chunk, first U chunk, end chunk, ring_L,
+ * ring_U -- 1 when that pass reads dependencies from the ring, 0 when from
+ * the global scratch -- and the block's y and z scratch offsets) may be NULL.
+ *
+ * A chunk holds rows of one level.  It starts with 24 int32: row count,
+ * warp count, level-major position of its first row, flags (bit 0: U pass),
+ * the entry width of each of 8 warp segments, each segment's byte offset,
+ * and the byte offsets of src, dst and dinv.  Segment w covers rows 32w ..
+ * 32w+31 as val[width][stride] (8- or 4-byte values) then dep[width][stride]
+ * (int32 level-major positions of the same pass); stride is 32, or for the
+ * last warp its row count rounded up to 4.  Row t of the L pass computes
+ * y[pos] = r[src[t]] - sum_k val[k] y[dep[k]]; of the U pass
+ * z[pos] = (y[src[t]] - sum_k val[k] z[dep[k]]) * dinv[t], written to
+ * global row dst[t] when dst[t] >= 0 (an owned row).  Padding entries have
+ * value 0.  The stream must be NULL or a CUDA stream; a device handle's
+ * layout is read back on it (synchronously).  HEC_ERR_INVALID for a
+ * damped-Jacobi handle or before level_schedule. */
+int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
+                           int32_t *ring_slots, int32_t *fixed_width, void *pack,
+                           uint32_t *chunks, int64_t *blocks, void *stream);
 /* z = M^{-1} r (Eq. 7 with M = the RAS combination of L_b U_b): every block
  * gathers r on V_b, solves L_b then U_b level by level, and writes z on its
  * owned rows only.  r, z: device arrays of n doubles, r != z.  Needs

@@ -1662,6 +1662,54 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
     return HEC_OK;
 }
 
+int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
+                           int32_t *ring_slots, int32_t *fixed_width, void *pack, uint32_t *chunks,
+                           int64_t *blocks, void *stream)
+{
+    if (!M || (fp32 != 0 && fp32 != 1) || !pack_bytes || !nchunks || !ring_slots || !fixed_width)
+        return fail(HEC_ERR_INVALID, "bad arguments");
+    if (M->kind == kJacobi)
+        return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no factor layout");
+    if (!M->scheduled)
+        return fail(HEC_ERR_INVALID, "level_schedule has not run");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HEC_TRY(build_layout(M, fp32, s));
+    const TrsvLayout &L = M->lay[fp32];
+    int64_t total = 0;
+    for (const uint2 &c : L.pack.chunks)
+        total = std::max<int64_t>(total, (int64_t)c.x * 16 + c.y);
+    *pack_bytes = total;
+    *nchunks = (int32_t)L.pack.chunks.size();
+    *ring_slots = L.pack.ring_slots;
+    *fixed_width = L.fixed_width;
+    if (pack && total > 0) {
+        if (!L.pack.pack.empty()) {
+            std::memcpy(pack, L.pack.pack.data(), (size_t)total);
+        } else { // uploaded (and possibly refilled by hec_refactor): the device copy
+            HEC_CK(cudaMemcpyAsync(pack, L.d_pack.p, (size_t)total, cudaMemcpyDeviceToHost, s));
+            HEC_CK(cudaStreamSynchronize(s));
+        }
+    }
+    if (chunks)
+        for (size_t c = 0; c < L.pack.chunks.size(); ++c) {
+            chunks[2 * c] = L.pack.chunks[c].x;
+            chunks[2 * c + 1] = L.pack.chunks[c].y;
+        }
+    if (blocks)
+        for (size_t b = 0; b < L.pack.blocks.size(); ++b) {
+            const TrsvBlock &T = L.pack.blocks[b];
+            int64_t *o = blocks + 7 * b;
+            o[0] = T.chunk_begin;
+            o[1] = T.chunk_mid;
+            o[2] = T.chunk_end;
+            o[3] = T.ring_L;
+            o[4] = T.ring_U;
+            o[5] = T.yoff;
+            o[6] = T.zoff;
+        }
+    return HEC_OK;
+}
+
 int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit, void *stream)
 {
     if (!M || !r || !z || r == z)

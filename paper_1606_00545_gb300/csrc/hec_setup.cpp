@@ -588,7 +588,9 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
                                 // padding repeats the first dependency with value 0
                                 // (a row without one -- level 1 of a uniform-width
                                 // layout -- points at the chunk's first position:
-                                // 0 times a finite value)
+                                // in the ring that slot holds a value of this
+                                // apply or 0; from the global scratch the kernel
+                                // does not read entries of value 0)
                                 const int e = kk < len ? e0 + kk : e0;
                                 const int d = len > 0 ? (upass ? posU : posL)[F.ci[e]] : q;
                                 dep[(size_t)kk * ls + lane] = d;

@@ -364,9 +364,14 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
                         for (int k = 0; k < FW; ++k)
                             y[k] = ring[d[k] & mask];
                     } else {
+                        // the padding of a dependency-free row points at the
+                        // chunk's first position, which this apply has not
+                        // written yet in the global scratch (it may hold
+                        // anything, NaN included): entries of value 0 are
+                        // not read
 #pragma unroll
                         for (int k = 0; k < FW; ++k)
-                            y[k] = gdep[d[k]];
+                            y[k] = l[k] != T(0) ? gdep[d[k]] : T(0);
                     }
 #pragma unroll
                     for (int k = 0; k < FW; ++k)

@@ -157,6 +157,8 @@ _SIGS = {
                               C.c_int),
     "hec_precond_get_factor": ([_vp, _i32, C.POINTER(_i32), _vp, _vp, _vp, _vp], C.c_int),
     "hec_precond_get_levels": ([_vp, _i32, _i32, C.POINTER(_i32), _vp, _vp], C.c_int),
+    "hec_precond_get_layout": ([_vp, _i32, C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32),
+                                C.POINTER(_i32), _vp, _vp, _vp, _vp], C.c_int),
     "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_status": ([_vp, _vp], C.c_int),
     "hec_precond_apply_noalloc": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
@@ -420,6 +422,24 @@ class Precond:
         _check(_lib.hec_precond_get_levels(self._h, b, which, C.byref(nlev), _ptr(ptr), _ptr(rows)),
                "hec_precond_get_levels")
         return ptr, rows
+
+    def layout(self, fp32=False, stream=None):
+        """The triangular solves' level-major chunk layout, host copies:
+        dict(pack=uint8 bytes, chunks=(nchunks, 2) uint32 {offset/16, bytes},
+        blocks=(nblocks, 7) int64, ring_slots, fixed_width, vbytes)."""
+        nb, nc, ring, fw = _i64(), _i32(), _i32(), _i32()
+        st = C.c_void_p(0) if self.A is not None and _is_host_only(self) else _stream(stream)
+        _check(_lib.hec_precond_get_layout(self._h, int(bool(fp32)), C.byref(nb), C.byref(nc),
+                                           C.byref(ring), C.byref(fw), None, None, None, st),
+               "hec_precond_get_layout")
+        pack = np.zeros(nb.value, np.uint8)
+        chunks = np.zeros((nc.value, 2), np.uint32)
+        blocks = np.zeros((self.info()["nblocks"], 7), np.int64)
+        _check(_lib.hec_precond_get_layout(self._h, int(bool(fp32)), C.byref(nb), C.byref(nc),
+                                           C.byref(ring), C.byref(fw), _ptr(pack), _ptr(chunks),
+                                           _ptr(blocks), st), "hec_precond_get_layout")
+        return {"pack": pack, "chunks": chunks, "blocks": blocks, "ring_slots": ring.value,
+                "fixed_width": fw.value, "vbytes": 4 if fp32 else 8}
 
     def destroy(self):
         if self._h and _lib is not None:

@@ -80,6 +80,37 @@ def test_precond_f32_vs_fp64_oracle(H, orc, case):
     assert err <= 1e-3
 
 
+def test_precond_global_scratch_after_nan_apply(H, orc):
+    """A pass whose dependency window exceeds the shared-memory ring reads its
+    dependencies from a global scratch that keeps the previous apply's values.
+    In the uniform-width FP32 layout the padding of a dependency-free row
+    points at a position not yet written in the current apply; after an apply
+    of an all-NaN right-hand side (which leaves NaN in every scratch slot) the
+    next apply must still be exact, in FP32 and FP64."""
+    import torch
+    A = synth.random_sparse_rows(24000, 6, seed=6)
+    M = H.hec_build(A.row_ptr, A.col, A.val)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    H.level_schedule(P)
+    assert P.info()["global_passes"] > 0
+    r = synth.rhs_uniform(A.n, 3)
+    ref = orc.RAS(A, 0, 1, 0).apply(r)
+    for fp32 in (True, False):
+        dt = torch.float32 if fp32 else torch.float64
+        apply = H.hec_precond_apply_f32 if fp32 else H.hec_precond_apply
+        z = torch.empty(A.n, dtype=dt, device="cuda:0")
+        apply(P, torch.full((A.n,), float("nan"), dtype=dt, device="cuda:0"), z)
+        assert H.hec_precond_status(P) == H.OK
+        assert not np.any(np.isfinite(host(z)))
+        apply(P, dev(r, dt), z)
+        assert H.hec_precond_status(P) == H.OK
+        got = host(z)
+        assert np.all(np.isfinite(got)), fp32
+        err = np.max(np.abs(got - ref)) / np.abs(ref).max()
+        assert err <= (1e-4 if fp32 else 1e-10), (fp32, err)
+    assert P.layout(fp32=True)["fixed_width"] > 0  # the uniform-width kernel ran
+
+
 def test_mixed_gmres_c1(H, orc):
     """64x64 Poisson, ILU(0), mixed GMRES(30): FP64 residual 1e-8."""
     A = synth.poisson2d_5pt(64)

@@ -138,3 +138,177 @@ def test_setup_errors(H):
     assert e.value.status == H.ERR_INVALID
     with pytest.raises(H.HecError):
         H.ilu_k_setup(Mb, 0, 3, 0)  # more blocks than rows
+
+
+# ------------------------------------------------------------------ factor layout
+# The level-major chunk layout that the triangular-solve kernel streams,
+# executed on the host from its bytes: a check of the packer (positions,
+# dependencies, ring window, padding, row maps, algorithmic bytes) that needs
+# no GPU.
+
+def _seg_stride(w, nr):
+    left = nr - 32 * w
+    return 32 if left >= 32 else (left + 3) & ~3
+
+
+def run_layout(lay, n, r):
+    """z = M^{-1} r by the chunk program of every RAS block, as the kernel
+    runs it: L chunks then U chunks, the rows of a chunk in parallel,
+    dependencies from the shared-memory ring (zeroed at launch, slot =
+    position mod ring size) or from the global scratch.  The scratch starts
+    as NaN here (the kernel never clears it), so a read of a position the
+    pass has not produced yet shows up; the kernel skips entries of value 0
+    of a uniform-width layout there.  Returns z and how often each row of z
+    was written."""
+    pack, chunks, R = lay["pack"], lay["chunks"], lay["ring_slots"]
+    FW, vb = lay["fixed_width"], lay["vbytes"]
+    dt = np.float64 if vb == 8 else np.float32
+    mask = R - 1
+    z = np.full(n, np.nan, dt)
+    writes = np.zeros(n, np.int64)
+    rv = r.astype(dt)
+    for c0, cm, c1, ring_l, ring_u, _, _ in lay["blocks"]:
+        ring = np.zeros(R, dt)
+        held = np.full(R, -1, np.int64)  # the position whose value a slot holds
+        y = None
+        for upass, lo, hi, use_ring in ((False, c0, cm, ring_l), (True, cm, c1, ring_u)):
+            heads = [np.frombuffer(pack, np.int32, 24, int(chunks[c, 0]) * 16) for c in range(lo, hi)]
+            npos = int(heads[-1][2] + heads[-1][0]) if heads else 0
+            sol = np.full(npos, np.nan, dt)
+            nxt = 0
+            for c, h in zip(range(lo, hi), heads):
+                base = int(chunks[c, 0]) * 16
+                nr, nw, q, flags = (int(v) for v in h[:4])
+                assert (flags & 1) == int(upass) and q == nxt and 0 < nr <= 256
+                assert nw == (nr + 31) // 32 and int(chunks[c, 1]) % 16 == 0
+                nxt = q + nr
+                src = np.frombuffer(pack, np.int32, nr, base + int(h[20]))
+                if upass:
+                    assert np.all((src >= 0) & (src < len(y)))
+                    acc = y[src].copy()
+                else:
+                    acc = rv[src].copy()
+                for w in range(nw):
+                    wd, so, ls = int(h[4 + w]), int(h[12 + w]), _seg_stride(w, nr)
+                    m = min(32, nr - 32 * w)
+                    if FW:  # the kernel computes these offsets at compile time
+                        assert wd == FW and so == 96 + w * FW * 32 * (vb + 4)
+                    if wd == 0:
+                        continue
+                    val = np.frombuffer(pack, dt, wd * ls, base + so).reshape(wd, ls)[:, :m]
+                    dep = np.frombuffer(pack, np.int32, wd * ls,
+                                        base + so + wd * ls * vb).reshape(wd, ls)[:, :m]
+                    rows = slice(32 * w, 32 * w + m)
+                    for k in range(wd):
+                        d, live = dep[k], val[k] != 0
+                        # rows of a chunk share a level: every dependency is earlier
+                        assert np.all((d >= 0) & (d <= q)) and np.all(d[live] < q)
+                        if use_ring:
+                            assert np.all(held[d[live] & mask] == d[live])  # in the window
+                            assert np.all(nxt - 1 - d[live] < R)  # not overwritten by the chunk
+                            yk = ring[d & mask]
+                        else:
+                            yk = sol[d]
+                            if FW:
+                                yk = np.where(live, yk, dt(0))
+                        acc[rows] -= val[k] * yk
+                if upass:
+                    acc *= np.frombuffer(pack, dt, nr, base + int(h[22]))
+                pos = np.arange(q, nxt)
+                sol[pos] = acc
+                if use_ring:
+                    ring[pos & mask] = acc
+                    held[pos & mask] = pos
+                if upass:
+                    dst = np.frombuffer(pack, np.int32, nr, base + int(h[21]))
+                    own = dst >= 0
+                    z[dst[own]] = acc[own]
+                    np.add.at(writes, dst[own], 1)
+            assert nxt == npos and np.all(np.isfinite(sol))
+            if not upass:
+                y = sol
+    return z, writes
+
+
+def needed_rows(rp, ci, rows, lo, hi):
+    """Rows of block V_b that can reach its owned part of z: the U solve needs
+    the owned rows and, transitively, their U dependencies; the L solve needs
+    those and, transitively, their L dependencies."""
+    nv = len(rows)
+    owned = (rows >= lo) & (rows < hi)
+    need_u = owned.copy()
+    for i in range(nv):
+        if need_u[i]:
+            cols = ci[rp[i]:rp[i + 1]]
+            need_u[cols[cols > i]] = True
+    need_l = need_u.copy()
+    for i in range(nv - 1, -1, -1):
+        if need_l[i]:
+            cols = ci[rp[i]:rp[i + 1]]
+            need_l[cols[cols < i]] = True
+    return owned, need_l, need_u
+
+
+LAYOUT_CASES = {
+    "poisson2d_ilu0": (lambda: synth.poisson2d_5pt(24), 0, 1, 0),
+    "diffusion3d_ilu1_ras4": (lambda: synth.diffusion3d_7pt_lognormal(10, 2.0, 2), 1, 4, 1),
+    "random_ilu2_ras3_ov2": (lambda: synth.random_sparse(600, 0.01, seed=2), 2, 3, 2),
+    "irregular27_ras2": (lambda: synth.stencil27_irregular(6, 2, 3, frac=0.05, extra_min=3,
+                                                           extra_max=9), 0, 2, 1),
+    "wide_window_global": (lambda: synth.random_sparse_rows(24000, 6, seed=6), 0, 1, 0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(LAYOUT_CASES))
+def test_factor_layout_runs_to_the_oracle_apply(H, orc, case):
+    make, k, nb, ov = LAYOUT_CASES[case]
+    A = make()
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P)
+    ref = orc.RAS(A, k, nb, ov).apply(synth.rhs_uniform(A.n, 1))
+    r = synth.rhs_uniform(A.n, 1)
+    for fp32 in (False, True):
+        lay = H.Precond.layout(P, fp32=fp32)
+        vb = lay["vbytes"]
+        z, writes = run_layout(lay, A.n, r)
+        assert np.all(writes == 1)  # every row of z written once, by its owner
+        err = np.max(np.abs(z - ref)) / np.abs(ref).max()
+        assert err <= (1e-5 if fp32 else 1e-13), (case, fp32, err)
+        # algorithmic bytes of one apply, counted from the factors
+        alg = 0
+        for b in range(nb):
+            rows, lo, hi = P.block(b)
+            rp, ci, _, _ = P.factor(b)
+            owned, need_l, need_u = needed_rows(rp, ci, rows, lo, hi)
+            c0, cm, c1 = (int(v) for v in lay["blocks"][b, :3])
+            npos = []
+            for a, e in ((c0, cm), (cm, c1)):
+                h = np.frombuffer(lay["pack"], np.int32, 4, int(lay["chunks"][e - 1, 0]) * 16)
+                npos.append(int(h[2] + h[0]))
+            assert npos == [int(need_l.sum()), int(need_u.sum())]
+            for i in range(len(rows)):
+                cols = ci[rp[i]:rp[i + 1]]
+                if need_l[i]:
+                    alg += (4 + vb) * int(np.sum(cols < i)) + 2 * vb + 4
+                if need_u[i]:
+                    alg += (4 + vb) * int(np.sum(cols > i)) + 2 * vb + 8 + (vb if owned[i] else 0)
+        inf = P.info()
+        assert alg == inf["apply_bytes_f32" if fp32 else "apply_bytes"]
+        if fp32:
+            assert lay["fixed_width"] in (0, 4, 6, 8)
+        else:
+            assert lay["fixed_width"] == 0
+    if case == "wide_window_global":
+        assert P.info()["global_passes"] > 0
+        assert H.Precond.layout(P, fp32=True)["fixed_width"] > 0
+
+
+def test_factor_layout_errors(H):
+    A = synth.poisson2d_5pt(8)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    with pytest.raises(H.HecError):
+        P.layout()  # before level_schedule
+    H.level_schedule(P)
+    assert P.layout()["chunks"].shape[0] > 0
