@@ -80,9 +80,11 @@ def parse():
                          "of Table 3's comparison): HEC SpMV with the ELL width forced to 1 "
                          "(almost all CSR tail), chosen by the one-third rule (HEC), or the "
                          "longest row (pure ELL), on regular, irregular and heavy-tailed rows")
-    ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32"], default=None,
+    ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32", "batch"],
+                    default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
-                         "--steps times (few launches before it, for ncu -k/-s/-c)")
+                         "--steps times (few launches before it, for ncu -k/-s/-c); batch: "
+                         "one wave of systems drawn like the 4096-system batch")
     return ap.parse_args()
 
 
@@ -127,6 +129,45 @@ def run_kernel_only(args, local_rank):
               "spmv": A.nnz * 12 + A.n * 16, "spmv32": A.nnz * 8 + A.n * 8}[args.kernel]
     print(json.dumps({"kernel": args.kernel, "launches": args.steps, "ms_per_launch": ms,
                       "alg_bytes": nbytes,
+                      "gbs": nbytes / (ms * 1e-3) / 1e9 if ms else None}))
+
+
+def run_batch_only(args, local_rank):
+    """Profiling mode of the batched solver: one wave of systems (152 SMs x 4
+    CTAs = 608) drawn like the 4096-system batch (sides uniform on 16..128,
+    log-normal sigma 2, seed 7), 4 right-hand sides, ILU(0), mixed GMRES(30)
+    to 1e-8, with the configuration the autotuner picks for the full batch
+    fixed (no tuning launches); --steps solves, one launch each."""
+    import torch
+    from paper_1606_00545_gb300 import build
+    build.build()
+    from paper_1606_00545_gb300 import hecgpu as H
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    nsys = 608
+    Bs = synth.batch_diffusion2d(nsys, C4_SMIN, C4_SMAX, SIGMA, C4_SEED)
+    Bh = H.hec_build_batched((Bs.sys_ptr, Bs.row_ptr, Bs.col, Bs.val), threads=128,
+                             ctas_per_sm=4, ell_width=0, nstages=4)
+    H.ilu_k_setup_batched(Bh, 0)
+    b = torch.tensor(synth.rhs_uniform(Bs.rows * C4_NRHS, C4_SEED + 1).reshape(-1, C4_NRHS),
+                     device=dev)
+    x = torch.zeros_like(b)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for i in range(args.steps):
+        if i == 1:
+            torch.cuda.synchronize()
+            e0.record()
+        inf, per = H.krylov_solve_batched(Bh, b, x, nrhs=C4_NRHS, tol=TOL, maxit=MAXIT,
+                                          restart=C4_RESTART, flags=H.X0_ZERO | H.MIXED_FP32,
+                                          per_system=True)
+    e1.record()
+    torch.cuda.synchronize()
+    assert all(p["status"] == H.OK for p in per), "a system did not converge"
+    ms = e0.elapsed_time(e1) / (args.steps - 1) if args.steps > 1 else None
+    nbytes = c4_bytes(Bs, per, C4_NRHS, C4_RESTART)
+    print(json.dumps({"kernel": "batch", "nsys": nsys, "rows": Bs.rows, "launches": args.steps,
+                      "ms_per_launch": ms, "alg_bytes": nbytes, "steps": inf["iters"],
                       "gbs": nbytes / (ms * 1e-3) / 1e9 if ms else None}))
 
 
@@ -1032,6 +1073,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.kernel == "batch":
+        run_batch_only(args, local_rank)
         return
     if args.kernel:
         run_kernel_only(args, local_rank)
