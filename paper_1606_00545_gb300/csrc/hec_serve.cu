@@ -44,6 +44,7 @@ struct Resident {
     hec_batch_t B = nullptr;
     int64_t bytes = 0;
     int n = 0, k = 0;
+    int64_t nnz = 0;
     uint64_t pattern = 0;
     int users = 0;
     std::list<uint64_t>::iterator lru;
@@ -138,6 +139,7 @@ int setup(hec_server_s *S, const Request &q, cudaStream_t st, Resident &R)
 {
     R.n = q.n;
     R.k = q.k;
+    R.nnz = (int64_t)q.ci.size();
     R.pattern = q.pattern;
     if (q.n <= S->o.small_rows) {
         const int64_t sp[2] = {0, q.n};
@@ -246,9 +248,12 @@ void lane_main(hec_server_s *S, int lane)
             if (R->n != q.n || R->k != q.k) {
                 rc = fail(HEC_ERR_INVALID, "key %llu was set up for another matrix",
                           (unsigned long long)q.key);
-            } else if (q.has_matrix && R->A && R->pattern == q.pattern) {
+            } else if (q.has_matrix && R->A && R->nnz == (int64_t)q.va.size() &&
+                       R->pattern == q.pattern) {
                 // same pattern, new values: refactor on the device (HEC values,
-                // ILU(k) of every RAS block, triangular-solve layouts)
+                // ILU(k) of every RAS block, triangular-solve layouts); the
+                // entry count is compared as well, since the refactor reads
+                // exactly the resident matrix's count of values
                 rc = hec_refactor(R->A, R->M, q.va.data(), st);
                 r.refactored = 1;
             } else if (q.has_matrix) {
