@@ -282,11 +282,23 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+LAYOUT_MARKER = b"// ---------------------------------------------------------------- RAS blocks"
+
+
 def kernel_source_sha():
+    """Hash of the triangular-solve kernel, its PTX helpers, and the part of the
+    host setup that decides the layout it streams (RAS blocks, ILU(k) pattern,
+    levels, chunk packing: hec_setup.cpp from its RAS section on; the input
+    checks and the HEC conversion before it do not touch that layout)."""
     h = hashlib.sha256()
-    for f in ("k_trsv.cu", "ptx.cuh", "hec_setup.cpp"):  # the kernel and the layout it streams
-        with open(os.path.join(ROOT, "paper_1606_00545_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1606_00545_gb300", "csrc")
+    for f in ("k_trsv.cu", "ptx.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "hec_setup.cpp"), "rb") as fh:
+        setup = fh.read()
+    at = setup.find(LAYOUT_MARKER)
+    h.update(setup[at:] if at >= 0 else setup)
     return h.hexdigest()[:16]
 
 

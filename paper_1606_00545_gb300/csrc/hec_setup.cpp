@@ -44,8 +44,9 @@ int check_csr(int n, const int *rp, const int *ci, int nnz, bool need_diag, std:
         return HEC_ERR_INVALID;
     }
     for (int i = 0; i < n; ++i) {
-        if (rp[i + 1] < rp[i]) {
-            msg = "row_ptr decreases at row " + std::to_string(i);
+        // checked before row i's columns are read: they must lie in [0, nnz)
+        if (rp[i + 1] < rp[i] || rp[i + 1] > nnz) {
+            msg = "row_ptr decreases or exceeds nnz at row " + std::to_string(i);
             return HEC_ERR_INVALID;
         }
         bool diag = false;

@@ -138,6 +138,13 @@ def test_setup_errors(H):
     assert e.value.status == H.ERR_INVALID
     with pytest.raises(H.HecError):
         H.ilu_k_setup(Mb, 0, 3, 0)  # more blocks than rows
+    # row_ptr past nnz in the middle (rejected before any column is read),
+    # decreasing row_ptr, a column out of range, a last entry that is not nnz
+    for rp, ci in (([0, 10, 5], [0, 1, 0, 1, 1]), ([0, 3, 2, 5], [0, 1, 2, 0, 2]),
+                   ([0, 2, 4], [0, 2, 0, 1]), ([0, 2, 3], [0, 1, 1, 0])):
+        with pytest.raises(H.HecError) as e:
+            H.hec_build(np.array(rp), np.array(ci), np.ones(len(ci)), host_only=True)
+        assert e.value.status in (H.ERR_INVALID, H.ERR_UNSORTED_CSR)
 
 
 # ------------------------------------------------------------------ factor layout
