@@ -585,318 +585,332 @@ bool valid_handle(const hec_batch_s *B) { return B != nullptr && B->nsys > 0; }
 int hec_build_batched(const hec_batch_csr_t *A, const hec_batch_config_t *cfg, void *stream,
                       hec_batch_t *out)
 {
-    (void)stream;
-    if (!A || !out || !A->sys_ptr || !A->row_ptr || !A->col || !A->val)
-        return fail(HEC_ERR_INVALID, "null argument");
-    *out = nullptr;
-    if (A->nsys < 1)
-        return fail(HEC_ERR_INVALID, "nsys must be >= 1");
-    hec_batch_config_t c{};
-    if (cfg)
-        c = *cfg;
-    HEC_TRY(check_config(c));
-    if (A->sys_ptr[0] != 0 || A->row_ptr[0] != 0)
-        return fail(HEC_ERR_INVALID, "sys_ptr[0] and row_ptr[0] must be 0");
-    for (int s = 0; s < A->nsys; ++s) {
-        const int64_t n = A->sys_ptr[s + 1] - A->sys_ptr[s];
-        if (n < 1 || n > (1 << 30))
-            return fail(HEC_ERR_INVALID, "system %d has %lld rows", s, (long long)n);
-    }
-    auto B = std::make_unique<hec_batch_s>();
-    B->nsys = A->nsys;
-    B->cfg = c;
-    B->sys.resize(A->nsys);
-    B->sys_ptr.assign(A->sys_ptr, A->sys_ptr + A->nsys + 1);
-    std::vector<int> rc(A->nsys, HEC_OK);
-    std::vector<std::string> msg(A->nsys);
-    parallel_for(A->nsys, [&](int s) {
-        const int64_t r0 = A->sys_ptr[s], r1 = A->sys_ptr[s + 1];
-        HostCSR &H = B->sys[s].A;
-        H.n = (int)(r1 - r0);
-        H.rp.resize(H.n + 1);
-        const int64_t e0 = A->row_ptr[r0];
-        for (int64_t i = r0; i <= r1; ++i) {
-            const int64_t e = A->row_ptr[i] - e0;
-            if (e < 0 || e > (int64_t)0x7fffffff || (i > r0 && A->row_ptr[i] < A->row_ptr[i - 1])) {
-                rc[s] = HEC_ERR_INVALID;
-                msg[s] = "row_ptr is not non-decreasing";
-                return;
-            }
-            H.rp[i - r0] = (int)e;
+    return abi_guard(__func__, [&]() -> int {
+        (void)stream;
+        if (!A || !out || !A->sys_ptr || !A->row_ptr || !A->col || !A->val)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *out = nullptr;
+        if (A->nsys < 1)
+            return fail(HEC_ERR_INVALID, "nsys must be >= 1");
+        hec_batch_config_t c{};
+        if (cfg)
+            c = *cfg;
+        HEC_TRY(check_config(c));
+        if (A->sys_ptr[0] != 0 || A->row_ptr[0] != 0)
+            return fail(HEC_ERR_INVALID, "sys_ptr[0] and row_ptr[0] must be 0");
+        for (int s = 0; s < A->nsys; ++s) {
+            const int64_t n = A->sys_ptr[s + 1] - A->sys_ptr[s];
+            if (n < 1 || n > (1 << 30))
+                return fail(HEC_ERR_INVALID, "system %d has %lld rows", s, (long long)n);
         }
-        const int64_t nnz = A->row_ptr[r1] - e0;
-        H.ci.assign(A->col + e0, A->col + e0 + nnz);
-        H.va.assign(A->val + e0, A->val + e0 + nnz);
-        rc[s] = check_csr(H.n, H.rp.data(), H.ci.data(), (int)nnz, true, msg[s]);
+        auto B = std::make_unique<hec_batch_s>();
+        B->nsys = A->nsys;
+        B->cfg = c;
+        B->sys.resize(A->nsys);
+        B->sys_ptr.assign(A->sys_ptr, A->sys_ptr + A->nsys + 1);
+        std::vector<int> rc(A->nsys, HEC_OK);
+        std::vector<std::string> msg(A->nsys);
+        parallel_for(A->nsys, [&](int s) {
+            const int64_t r0 = A->sys_ptr[s], r1 = A->sys_ptr[s + 1];
+            HostCSR &H = B->sys[s].A;
+            H.n = (int)(r1 - r0);
+            H.rp.resize(H.n + 1);
+            const int64_t e0 = A->row_ptr[r0];
+            for (int64_t i = r0; i <= r1; ++i) {
+                const int64_t e = A->row_ptr[i] - e0;
+                if (e < 0 || e > (int64_t)0x7fffffff || (i > r0 && A->row_ptr[i] < A->row_ptr[i - 1])) {
+                    rc[s] = HEC_ERR_INVALID;
+                    msg[s] = "row_ptr is not non-decreasing";
+                    return;
+                }
+                H.rp[i - r0] = (int)e;
+            }
+            const int64_t nnz = A->row_ptr[r1] - e0;
+            H.ci.assign(A->col + e0, A->col + e0 + nnz);
+            H.va.assign(A->val + e0, A->val + e0 + nnz);
+            rc[s] = check_csr(H.n, H.rp.data(), H.ci.data(), (int)nnz, true, msg[s]);
+        });
+        for (int s = 0; s < A->nsys; ++s)
+            if (rc[s] != HEC_OK)
+                return fail(rc[s], "system %d: %s", s, msg[s].c_str());
+        for (const SysHost &S : B->sys) {
+            B->rows += S.A.n;
+            B->nnz += (int64_t)S.A.ci.size();
+            B->max_n = std::max(B->max_n, S.A.n);
+        }
+        *out = B.release();
+        return HEC_OK;
     });
-    for (int s = 0; s < A->nsys; ++s)
-        if (rc[s] != HEC_OK)
-            return fail(rc[s], "system %d: %s", s, msg[s].c_str());
-    for (const SysHost &S : B->sys) {
-        B->rows += S.A.n;
-        B->nnz += (int64_t)S.A.ci.size();
-        B->max_n = std::max(B->max_n, S.A.n);
-    }
-    *out = B.release();
-    return HEC_OK;
 }
 
 int ilu_k_setup_batched(hec_batch_t B, int32_t k)
 {
-    if (!valid_handle(B))
-        return fail(HEC_ERR_INVALID, "invalid batch handle");
-    if (k < 0)
-        return fail(HEC_ERR_INVALID, "k must be >= 0");
-    std::vector<int> rc(B->nsys, HEC_OK);
-    std::vector<std::string> msg(B->nsys);
-    parallel_for(B->nsys, [&](int s) {
-        SysHost &S = B->sys[s];
-        BlockFactor &F = S.F;
-        F = BlockFactor();
-        F.own_lo = 0;
-        F.own_hi = S.A.n;
-        F.rows.resize(S.A.n);
-        std::iota(F.rows.begin(), F.rows.end(), 0);
-        F.F = S.A;
-        rc[s] = iluk_block(F, k, msg[s]);
-        if (rc[s] == HEC_OK)
-            levels_block(F);
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B))
+            return fail(HEC_ERR_INVALID, "invalid batch handle");
+        if (k < 0)
+            return fail(HEC_ERR_INVALID, "k must be >= 0");
+        std::vector<int> rc(B->nsys, HEC_OK);
+        std::vector<std::string> msg(B->nsys);
+        parallel_for(B->nsys, [&](int s) {
+            SysHost &S = B->sys[s];
+            BlockFactor &F = S.F;
+            F = BlockFactor();
+            F.own_lo = 0;
+            F.own_hi = S.A.n;
+            F.rows.resize(S.A.n);
+            std::iota(F.rows.begin(), F.rows.end(), 0);
+            F.F = S.A;
+            rc[s] = iluk_block(F, k, msg[s]);
+            if (rc[s] == HEC_OK)
+                levels_block(F);
+        });
+        for (int s = 0; s < B->nsys; ++s)
+            if (rc[s] != HEC_OK) {
+                B->ilu_k = -1;
+                return fail(rc[s], "system %d: %s", s, msg[s].c_str());
+            }
+        B->factor_nnz = 0;
+        for (const SysHost &S : B->sys)
+            B->factor_nnz += (int64_t)S.F.F.ci.size();
+        B->ilu_k = k;
+        B->layout_ok = false;
+        return HEC_OK;
     });
-    for (int s = 0; s < B->nsys; ++s)
-        if (rc[s] != HEC_OK) {
-            B->ilu_k = -1;
-            return fail(rc[s], "system %d: %s", s, msg[s].c_str());
-        }
-    B->factor_nnz = 0;
-    for (const SysHost &S : B->sys)
-        B->factor_nnz += (int64_t)S.F.F.ci.size();
-    B->ilu_k = k;
-    B->layout_ok = false;
-    return HEC_OK;
 }
 
 int hec_batch_info(hec_batch_t B, hec_batch_info_t *info)
 {
-    if (!valid_handle(B) || !info)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    std::memset(info, 0, sizeof(*info));
-    info->nsys = B->nsys;
-    info->ilu_k = B->ilu_k;
-    info->rows = B->rows;
-    info->nnz = B->nnz;
-    info->factor_nnz = B->factor_nnz;
-    info->max_n = B->max_n;
-    info->ring_slots = B->layout_ok ? B->ring_slots : 0;
-    info->device_bytes = B->device_bytes();
-    info->config = B->cfg;
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B) || !info)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        std::memset(info, 0, sizeof(*info));
+        info->nsys = B->nsys;
+        info->ilu_k = B->ilu_k;
+        info->rows = B->rows;
+        info->nnz = B->nnz;
+        info->factor_nnz = B->factor_nnz;
+        info->max_n = B->max_n;
+        info->ring_slots = B->layout_ok ? B->ring_slots : 0;
+        info->device_bytes = B->device_bytes();
+        info->config = B->cfg;
+        return HEC_OK;
+    });
 }
 
 int hec_batch_set_config(hec_batch_t B, const hec_batch_config_t *cfg)
 {
-    if (!valid_handle(B) || !cfg)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    HEC_TRY(check_config(*cfg));
-    if (cfg->ell_width != B->cfg.ell_width)
-        B->layout_ok = false;
-    B->cfg = *cfg;
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B) || !cfg)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        HEC_TRY(check_config(*cfg));
+        if (cfg->ell_width != B->cfg.ell_width)
+            B->layout_ok = false;
+        B->cfg = *cfg;
+        return HEC_OK;
+    });
 }
 
 int hec_batch_autotune(hec_batch_t B, int32_t nrhs, int32_t restart, const hec_solve_opts_t *opts,
                        void *stream, hec_batch_config_t *chosen)
 {
-    if (!valid_handle(B) || nrhs < 1 || restart < 1 || restart > kBatchMaxRestart)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool fp32 = opts && (opts->flags & HEC_MIXED_FP32);
-    // sample: about eight systems per SM, evenly spaced over the size ranking,
-    // so that every CTA of a trial works through several systems as in the
-    // full batch (a trial of one system per CTA would time the largest
-    // system's latency, not the throughput)
-    std::vector<int> bysize(B->nsys);
-    std::iota(bysize.begin(), bysize.end(), 0);
-    std::stable_sort(bysize.begin(), bysize.end(),
-                     [&](int x, int y) { return B->sys[x].A.n > B->sys[y].A.n; });
-    const int want = std::min(B->nsys, 8 * device_sms());
-    std::vector<int> idx;
-    for (int i = 0; i < want; ++i)
-        idx.push_back(bysize[(int64_t)i * B->nsys / want]);
-    auto S = sub_batch(B, idx);
-    S->factor_nnz = 0;
-    for (SysHost &h : S->sys)
-        S->factor_nnz += (int64_t)h.F.F.ci.size();
-    DevBuf db, dx;
-    const size_t vb = (size_t)S->rows * nrhs * sizeof(double);
-    HEC_TRY(db.alloc(vb, st));
-    HEC_TRY(dx.alloc(vb, st));
-    {
-        std::vector<double> ones((size_t)S->rows * nrhs, 1.0);
-        HEC_CK(cudaMemcpyAsync(db.p, ones.data(), vb, cudaMemcpyHostToDevice, st));
-    }
-    // ELL width candidates: per-system choice, and the largest row length
-    std::vector<int> kc = {0};
-    int maxlen = 0;
-    for (const SysHost &h : S->sys)
-        for (int i = 0; i < h.A.n; ++i)
-            maxlen = std::max(maxlen, h.A.rp[i + 1] - h.A.rp[i]);
-    bool differs = false;
-    for (const SysHost &h : S->sys)
-        differs |= ell_width_auto(h.A) != maxlen;
-    if (differs)
-        kc.push_back(maxlen);
-    hec_batch_config_t best = B->cfg;
-    float best_ms = 1e30f;
-    const int maxit = restart;  // one cycle per system
-    for (int K : kc) {
-        for (int threads : {128, 256, 512}) {
-            for (int ctas : {1, 2, 3, 4}) {
-                if (threads * ctas > 2048)
-                    continue;
-                for (int ns : {4, 8}) {
-                    hec_batch_config_t c{threads, ctas, K, ns};
-                    if (S->cfg.ell_width != K)
-                        S->layout_ok = false;
-                    S->cfg = c;
-                    Launch L;
-                    HEC_TRY(build_layout(S.get(), st));
-                    if (S->ilu_k >= 0)
-                        HEC_TRY(build_factors(S.get(), fp32 ? 4 : 8, st));
-                    if (resolve_launch(S.get(), fp32, nrhs, restart, L) != HEC_OK || L.ctas < ctas)
-                        continue;  // does not fit
-                    float ms = 0.f;
-                    const int rc = run_batch(S.get(), BOP_SOLVE, fp32, db.as<double>(), dx.as<double>(),
-                                             nrhs, 1e-30, maxit, restart, fp32 ? 1e-5 : 0.0, true,
-                                             kBatchSpin, st, &ms);
-                    if (rc < 0)
-                        return rc;
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best = c;
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B) || nrhs < 1 || restart < 1 || restart > kBatchMaxRestart)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        const bool fp32 = opts && (opts->flags & HEC_MIXED_FP32);
+        // sample: about eight systems per SM, evenly spaced over the size ranking,
+        // so that every CTA of a trial works through several systems as in the
+        // full batch (a trial of one system per CTA would time the largest
+        // system's latency, not the throughput)
+        std::vector<int> bysize(B->nsys);
+        std::iota(bysize.begin(), bysize.end(), 0);
+        std::stable_sort(bysize.begin(), bysize.end(),
+                         [&](int x, int y) { return B->sys[x].A.n > B->sys[y].A.n; });
+        const int want = std::min(B->nsys, 8 * device_sms());
+        std::vector<int> idx;
+        for (int i = 0; i < want; ++i)
+            idx.push_back(bysize[(int64_t)i * B->nsys / want]);
+        auto S = sub_batch(B, idx);
+        S->factor_nnz = 0;
+        for (SysHost &h : S->sys)
+            S->factor_nnz += (int64_t)h.F.F.ci.size();
+        DevBuf db, dx;
+        const size_t vb = (size_t)S->rows * nrhs * sizeof(double);
+        HEC_TRY(db.alloc(vb, st));
+        HEC_TRY(dx.alloc(vb, st));
+        {
+            std::vector<double> ones((size_t)S->rows * nrhs, 1.0);
+            HEC_CK(cudaMemcpyAsync(db.p, ones.data(), vb, cudaMemcpyHostToDevice, st));
+        }
+        // ELL width candidates: per-system choice, and the largest row length
+        std::vector<int> kc = {0};
+        int maxlen = 0;
+        for (const SysHost &h : S->sys)
+            for (int i = 0; i < h.A.n; ++i)
+                maxlen = std::max(maxlen, h.A.rp[i + 1] - h.A.rp[i]);
+        bool differs = false;
+        for (const SysHost &h : S->sys)
+            differs |= ell_width_auto(h.A) != maxlen;
+        if (differs)
+            kc.push_back(maxlen);
+        hec_batch_config_t best = B->cfg;
+        float best_ms = 1e30f;
+        const int maxit = restart;  // one cycle per system
+        for (int K : kc) {
+            for (int threads : {128, 256, 512}) {
+                for (int ctas : {1, 2, 3, 4}) {
+                    if (threads * ctas > 2048)
+                        continue;
+                    for (int ns : {4, 8}) {
+                        hec_batch_config_t c{threads, ctas, K, ns};
+                        if (S->cfg.ell_width != K)
+                            S->layout_ok = false;
+                        S->cfg = c;
+                        Launch L;
+                        HEC_TRY(build_layout(S.get(), st));
+                        if (S->ilu_k >= 0)
+                            HEC_TRY(build_factors(S.get(), fp32 ? 4 : 8, st));
+                        if (resolve_launch(S.get(), fp32, nrhs, restart, L) != HEC_OK || L.ctas < ctas)
+                            continue;  // does not fit
+                        float ms = 0.f;
+                        const int rc = run_batch(S.get(), BOP_SOLVE, fp32, db.as<double>(), dx.as<double>(),
+                                                 nrhs, 1e-30, maxit, restart, fp32 ? 1e-5 : 0.0, true,
+                                                 kBatchSpin, st, &ms);
+                        if (rc < 0)
+                            return rc;
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best = c;
+                        }
                     }
                 }
             }
         }
-    }
-    if (best.ell_width != B->cfg.ell_width)
-        B->layout_ok = false;
-    B->cfg = best;
-    if (chosen)
-        *chosen = best;
-    return HEC_OK;
+        if (best.ell_width != B->cfg.ell_width)
+            B->layout_ok = false;
+        B->cfg = best;
+        if (chosen)
+            *chosen = best;
+        return HEC_OK;
+    });
 }
 
 int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs, double tol,
                          int32_t maxit, int32_t restart, const hec_solve_opts_t *opts,
                          void *stream, hec_solve_info_t *info, hec_batch_sys_info_t *sys_info)
 {
-    if (!valid_handle(B) || !b || !x)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    if (nrhs < 1 || restart < 1 || restart > kBatchMaxRestart || maxit < 0 || !(tol >= 0.0))
-        return fail(HEC_ERR_INVALID, "nrhs >= 1, 1 <= restart <= %d, maxit >= 0, tol >= 0",
-                    kBatchMaxRestart);
-    cudaStream_t st = (cudaStream_t)stream;
-    hec_solve_opts_t o{};
-    if (opts)
-        o = *opts;
-    const bool fp32 = (o.flags & HEC_MIXED_FP32) != 0;
-    const long long spin = o.spin_limit > 0 ? o.spin_limit : kBatchSpin;
-    const size_t nb = (size_t)B->rows * nrhs * sizeof(double);
-    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    DevBuf sb, sx;
-    const double *db = b;
-    double *dx = x;
-    int64_t h2d = 0, d2h = 0;
-    if (!bdev) {
-        HEC_TRY(sb.alloc(nb, st));
-        HEC_CK(cudaMemcpyAsync(sb.p, b, nb, cudaMemcpyHostToDevice, st));
-        db = sb.as<double>();
-        h2d += (int64_t)nb;
-    }
-    if (!xdev) {
-        HEC_TRY(sx.alloc(nb, st));
-        if (!(o.flags & HEC_X0_ZERO)) {
-            HEC_CK(cudaMemcpyAsync(sx.p, x, nb, cudaMemcpyHostToDevice, st));
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B) || !b || !x)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        if (nrhs < 1 || restart < 1 || restart > kBatchMaxRestart || maxit < 0 || !(tol >= 0.0))
+            return fail(HEC_ERR_INVALID, "nrhs >= 1, 1 <= restart <= %d, maxit >= 0, tol >= 0",
+                        kBatchMaxRestart);
+        cudaStream_t st = (cudaStream_t)stream;
+        hec_solve_opts_t o{};
+        if (opts)
+            o = *opts;
+        const bool fp32 = (o.flags & HEC_MIXED_FP32) != 0;
+        const long long spin = o.spin_limit > 0 ? o.spin_limit : kBatchSpin;
+        const size_t nb = (size_t)B->rows * nrhs * sizeof(double);
+        const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+        DevBuf sb, sx;
+        const double *db = b;
+        double *dx = x;
+        int64_t h2d = 0, d2h = 0;
+        if (!bdev) {
+            HEC_TRY(sb.alloc(nb, st));
+            HEC_CK(cudaMemcpyAsync(sb.p, b, nb, cudaMemcpyHostToDevice, st));
+            db = sb.as<double>();
             h2d += (int64_t)nb;
         }
-        dx = sx.as<double>();
-    }
-    HEC_TRY(run_batch(B, BOP_SOLVE, fp32, db, dx, nrhs, tol, maxit, restart, fp32 ? 1e-5 : 0.0,
-                      (o.flags & HEC_X0_ZERO) != 0, spin, st, nullptr));
-    std::vector<BatchResult> res(B->nsys);
-    HEC_CK(cudaMemcpyAsync(res.data(), B->res.p, sizeof(BatchResult) * res.size(),
-                           cudaMemcpyDeviceToHost, st));
-    HEC_CK(cudaStreamSynchronize(st));
-    // systems whose FP32 cycles stopped refining: finish them in FP64, from
-    // their current x, in one more launch restricted to them
-    std::vector<unsigned char> only(B->nsys, 0);
-    int nstag = 0;
-    for (int s = 0; s < B->nsys; ++s)
-        if (res[s].status == kBatchStagnated) {
-            only[s] = 1;
-            ++nstag;
+        if (!xdev) {
+            HEC_TRY(sx.alloc(nb, st));
+            if (!(o.flags & HEC_X0_ZERO)) {
+                HEC_CK(cudaMemcpyAsync(sx.p, x, nb, cudaMemcpyHostToDevice, st));
+                h2d += (int64_t)nb;
+            }
+            dx = sx.as<double>();
         }
-    int launches = 1;
-    if (nstag > 0) {
-        DevBuf donly;
-        HEC_TRY(upload(donly, only, st));
-        HEC_TRY(run_batch(B, BOP_SOLVE, false, db, dx, nrhs, tol, maxit, restart, 0.0, false, spin,
-                          st, nullptr, donly.as<unsigned char>()));
-        std::vector<BatchResult> r64(B->nsys);
-        HEC_CK(cudaMemcpyAsync(r64.data(), B->res.p, sizeof(BatchResult) * r64.size(),
+        HEC_TRY(run_batch(B, BOP_SOLVE, fp32, db, dx, nrhs, tol, maxit, restart, fp32 ? 1e-5 : 0.0,
+                          (o.flags & HEC_X0_ZERO) != 0, spin, st, nullptr));
+        std::vector<BatchResult> res(B->nsys);
+        HEC_CK(cudaMemcpyAsync(res.data(), B->res.p, sizeof(BatchResult) * res.size(),
                                cudaMemcpyDeviceToHost, st));
         HEC_CK(cudaStreamSynchronize(st));
+        // systems whose FP32 cycles stopped refining: finish them in FP64, from
+        // their current x, in one more launch restricted to them
+        std::vector<unsigned char> only(B->nsys, 0);
+        int nstag = 0;
         for (int s = 0; s < B->nsys; ++s)
-            if (only[s]) {
-                res[s].iters += r64[s].iters;
-                res[s].cycles += r64[s].cycles;
-                res[s].status = r64[s].status;
-                res[s].rel_resid = r64[s].rel_resid;
+            if (res[s].status == kBatchStagnated) {
+                only[s] = 1;
+                ++nstag;
             }
-        launches = 2;
-    }
-    if (!xdev) {
-        HEC_CK(cudaMemcpyAsync(x, dx, nb, cudaMemcpyDeviceToHost, st));
-        d2h += (int64_t)nb;
-    }
-    HEC_CK(cudaStreamSynchronize(st));
-    int status = HEC_OK;
-    hec_solve_info_t I{};
-    I.fp64_finish = nstag;
-    for (int s = 0; s < B->nsys; ++s) {
-        const BatchResult &r = res[s];
-        I.iters += r.iters;
-        I.restarts += r.cycles;
-        I.rel_resid = std::max(I.rel_resid, r.rel_resid);
-        if (status == HEC_OK && r.status != HEC_OK)
-            status = r.status;
-        if (sys_info) {
-            sys_info[s].iters = r.iters;
-            sys_info[s].cycles = r.cycles;
-            sys_info[s].status = r.status;
-            sys_info[s].reserved = 0;
-            sys_info[s].rel_resid = r.rel_resid;
+        int launches = 1;
+        if (nstag > 0) {
+            DevBuf donly;
+            HEC_TRY(upload(donly, only, st));
+            HEC_TRY(run_batch(B, BOP_SOLVE, false, db, dx, nrhs, tol, maxit, restart, 0.0, false, spin,
+                              st, nullptr, donly.as<unsigned char>()));
+            std::vector<BatchResult> r64(B->nsys);
+            HEC_CK(cudaMemcpyAsync(r64.data(), B->res.p, sizeof(BatchResult) * r64.size(),
+                                   cudaMemcpyDeviceToHost, st));
+            HEC_CK(cudaStreamSynchronize(st));
+            for (int s = 0; s < B->nsys; ++s)
+                if (only[s]) {
+                    res[s].iters += r64[s].iters;
+                    res[s].cycles += r64[s].cycles;
+                    res[s].status = r64[s].status;
+                    res[s].rel_resid = r64[s].rel_resid;
+                }
+            launches = 2;
         }
-    }
-    I.status = status;
-    I.kernel_launches = launches;
-    I.h2d_bytes = h2d;
-    I.d2h_bytes = d2h;
-    if (info)
-        *info = I;
-    return status;
+        if (!xdev) {
+            HEC_CK(cudaMemcpyAsync(x, dx, nb, cudaMemcpyDeviceToHost, st));
+            d2h += (int64_t)nb;
+        }
+        HEC_CK(cudaStreamSynchronize(st));
+        int status = HEC_OK;
+        hec_solve_info_t I{};
+        I.fp64_finish = nstag;
+        for (int s = 0; s < B->nsys; ++s) {
+            const BatchResult &r = res[s];
+            I.iters += r.iters;
+            I.restarts += r.cycles;
+            I.rel_resid = std::max(I.rel_resid, r.rel_resid);
+            if (status == HEC_OK && r.status != HEC_OK)
+                status = r.status;
+            if (sys_info) {
+                sys_info[s].iters = r.iters;
+                sys_info[s].cycles = r.cycles;
+                sys_info[s].status = r.status;
+                sys_info[s].reserved = 0;
+                sys_info[s].rel_resid = r.rel_resid;
+            }
+        }
+        I.status = status;
+        I.kernel_launches = launches;
+        I.h2d_bytes = h2d;
+        I.d2h_bytes = d2h;
+        if (info)
+            *info = I;
+        return status;
+    });
 }
 
 int hec_batch_apply(hec_batch_t B, int32_t op, const double *b, double *x, int32_t nrhs, void *stream)
 {
-    if (!valid_handle(B) || !b || !x || nrhs < 1 || op < 0 || op > 3)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    if ((op == 2 || op == 3) && B->ilu_k < 0)
-        return fail(HEC_ERR_INVALID, "no factors: call ilu_k_setup_batched first");
-    static const int kop[4] = {BOP_SPMV64, BOP_SPMV_IN, BOP_PRECOND, BOP_PRECOND};
-    const bool fp32 = op == 1 || op == 2;
-    return run_batch(B, kop[op], fp32, b, x, nrhs, 0.0, 0, 1, 0.0, true, kBatchSpin,
-                     (cudaStream_t)stream, nullptr);
+    return abi_guard(__func__, [&]() -> int {
+        if (!valid_handle(B) || !b || !x || nrhs < 1 || op < 0 || op > 3)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        if ((op == 2 || op == 3) && B->ilu_k < 0)
+            return fail(HEC_ERR_INVALID, "no factors: call ilu_k_setup_batched first");
+        static const int kop[4] = {BOP_SPMV64, BOP_SPMV_IN, BOP_PRECOND, BOP_PRECOND};
+        const bool fp32 = op == 1 || op == 2;
+        return run_batch(B, kop[op], fp32, b, x, nrhs, 0.0, 0, 1, 0.0, true, kBatchSpin,
+                         (cudaStream_t)stream, nullptr);
+    });
 }
 
 void hec_batch_destroy(hec_batch_t B) { delete B; }

@@ -1251,106 +1251,114 @@ const char *hec_last_error(void) { return hec::last_error_text(); }
 int hec_set_allocator(void *(*alloc_fn)(size_t, void *, void *), void (*free_fn)(void *, void *, void *),
                       void *ctx)
 {
-    if ((alloc_fn == nullptr) != (free_fn == nullptr))
-        return fail(HEC_ERR_INVALID, "allocator needs both functions or neither");
-    AllocFns f;
-    f.alloc = alloc_fn;
-    f.free_ = free_fn;
-    f.ctx = ctx;
-    set_allocator(f);
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if ((alloc_fn == nullptr) != (free_fn == nullptr))
+            return fail(HEC_ERR_INVALID, "allocator needs both functions or neither");
+        AllocFns f;
+        f.alloc = alloc_fn;
+        f.free_ = free_fn;
+        f.ctx = ctx;
+        set_allocator(f);
+        return HEC_OK;
+    });
 }
 
 int hec_build(const hec_csr_t *Ain, const hec_opts_t *opts, void *stream, hec_matrix_t *out)
 {
-    if (!Ain || !out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    *out = nullptr;
-    hec_opts_t o{};
-    if (opts)
-        o = *opts;
-    const int align = o.ell_ld_align ? o.ell_ld_align : 256;
-    if (align < 32 || align % 32 != 0)
-        return fail(HEC_ERR_INVALID, "ell_ld_align must be a positive multiple of 32");
-    if (o.ell_width < 0)
-        return fail(HEC_ERR_INVALID, "ell_width must be >= 0");
-    const int n = Ain->n, nnz = Ain->nnz;
-    if (n < 1 || nnz < 0)
-        return fail(HEC_ERR_INVALID, "bad sizes n=%d nnz=%d", n, nnz);
-    cudaStream_t s = (cudaStream_t)stream;
-    std::unique_ptr<hec_matrix_s> A(new hec_matrix_s());
-    A->id = g_next_id++;
-    A->host_only = (o.flags & HEC_HOST_ONLY) != 0;
-    HostCSR &C = A->csr;
-    C.n = n;
-    C.rp.resize(n + 1);
-    C.ci.resize(nnz);
-    C.va.resize(nnz);
-    if (Ain->on_device) {
-        HEC_CK(cudaMemcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
-        if (nnz) {
-            HEC_CK(cudaMemcpy(C.ci.data(), Ain->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
-            HEC_CK(cudaMemcpy(C.va.data(), Ain->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+    return abi_guard(__func__, [&]() -> int {
+        if (!Ain || !out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *out = nullptr;
+        hec_opts_t o{};
+        if (opts)
+            o = *opts;
+        const int align = o.ell_ld_align ? o.ell_ld_align : 256;
+        if (align < 32 || align % 32 != 0)
+            return fail(HEC_ERR_INVALID, "ell_ld_align must be a positive multiple of 32");
+        if (o.ell_width < 0)
+            return fail(HEC_ERR_INVALID, "ell_width must be >= 0");
+        const int n = Ain->n, nnz = Ain->nnz;
+        if (n < 1 || nnz < 0)
+            return fail(HEC_ERR_INVALID, "bad sizes n=%d nnz=%d", n, nnz);
+        cudaStream_t s = (cudaStream_t)stream;
+        std::unique_ptr<hec_matrix_s> A(new hec_matrix_s());
+        A->id = g_next_id++;
+        A->host_only = (o.flags & HEC_HOST_ONLY) != 0;
+        HostCSR &C = A->csr;
+        C.n = n;
+        C.rp.resize(n + 1);
+        C.ci.resize(nnz);
+        C.va.resize(nnz);
+        if (Ain->on_device) {
+            HEC_CK(cudaMemcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+            if (nnz) {
+                HEC_CK(cudaMemcpy(C.ci.data(), Ain->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+                HEC_CK(cudaMemcpy(C.va.data(), Ain->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+            }
+        } else {
+            if (!Ain->row_ptr || (nnz && (!Ain->col || !Ain->val)))
+                return fail(HEC_ERR_INVALID, "null CSR array");
+            std::memcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1));
+            if (nnz) {
+                std::memcpy(C.ci.data(), Ain->col, sizeof(int) * nnz);
+                std::memcpy(C.va.data(), Ain->val, sizeof(double) * nnz);
+            }
         }
-    } else {
-        if (!Ain->row_ptr || (nnz && (!Ain->col || !Ain->val)))
-            return fail(HEC_ERR_INVALID, "null CSR array");
-        std::memcpy(C.rp.data(), Ain->row_ptr, sizeof(int) * (n + 1));
-        if (nnz) {
-            std::memcpy(C.ci.data(), Ain->col, sizeof(int) * nnz);
-            std::memcpy(C.va.data(), Ain->val, sizeof(double) * nnz);
-        }
-    }
-    std::string msg;
-    int rc = check_csr(n, C.rp.data(), C.ci.data(), nnz, false, msg);
-    if (rc != HEC_OK)
-        return fail(rc, "%s", msg.c_str());
-    const int K = o.ell_width ? o.ell_width : ell_width_auto(C);
-    build_hec(C, K, align, A->hec);
-    if (!A->host_only)
-        HEC_TRY(upload_matrix(A.get(), s));
-    *out = A.release();
-    return HEC_OK;
+        std::string msg;
+        int rc = check_csr(n, C.rp.data(), C.ci.data(), nnz, false, msg);
+        if (rc != HEC_OK)
+            return fail(rc, "%s", msg.c_str());
+        const int K = o.ell_width ? o.ell_width : ell_width_auto(C);
+        build_hec(C, K, align, A->hec);
+        if (!A->host_only)
+            HEC_TRY(upload_matrix(A.get(), s));
+        *out = A.release();
+        return HEC_OK;
+    });
 }
 
 int hec_matrix_info(hec_matrix_t A, hec_matrix_info_t *info)
 {
-    if (!A || !info)
-        return fail(HEC_ERR_INVALID, "null argument");
-    info->n = A->hec.n;
-    info->nnz = (int32_t)A->csr.ci.size();
-    info->ell_width = A->hec.K;
-    info->ell_ld = A->hec.ld;
-    info->tail_rows = (int32_t)A->hec.tail_rows.size();
-    info->tail_nnz = (int32_t)A->hec.tail_col.size();
-    info->device_bytes = A->device_bytes();
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !info)
+            return fail(HEC_ERR_INVALID, "null argument");
+        info->n = A->hec.n;
+        info->nnz = (int32_t)A->csr.ci.size();
+        info->ell_width = A->hec.K;
+        info->ell_ld = A->hec.ld;
+        info->tail_rows = (int32_t)A->hec.tail_rows.size();
+        info->tail_nnz = (int32_t)A->hec.tail_col.size();
+        info->device_bytes = A->device_bytes();
+        return HEC_OK;
+    });
 }
 
 int hec_matrix_export(hec_matrix_t A, int32_t *ell_col, double *ell_val, int32_t *tail_rows,
                       int32_t *tail_ptr, int32_t *tail_col, double *tail_val)
 {
-    if (!A)
-        return fail(HEC_ERR_INVALID, "null matrix");
-    if (A->hec_host_stale) { // hec_refactor replaced the values on the device
-        HEC_CK(cudaMemcpy(A->hec.ell_val.data(), A->ell_val.p,
-                          A->hec.ell_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        HEC_CK(cudaMemcpy(A->hec.tail_val.data(), A->tail_val.p,
-                          A->hec.tail_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        A->hec_host_stale = false;
-    }
-    const HecHost &H = A->hec;
-    auto cp = [](void *dst, const void *src, size_t bytes) {
-        if (dst && bytes)
-            std::memcpy(dst, src, bytes);
-    };
-    cp(ell_col, H.ell_col.data(), H.ell_col.size() * sizeof(int));
-    cp(ell_val, H.ell_val.data(), H.ell_val.size() * sizeof(double));
-    cp(tail_rows, H.tail_rows.data(), H.tail_rows.size() * sizeof(int));
-    cp(tail_ptr, H.tail_ptr.data(), H.tail_ptr.size() * sizeof(int));
-    cp(tail_col, H.tail_col.data(), H.tail_col.size() * sizeof(int));
-    cp(tail_val, H.tail_val.data(), H.tail_val.size() * sizeof(double));
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!A)
+            return fail(HEC_ERR_INVALID, "null matrix");
+        if (A->hec_host_stale) { // hec_refactor replaced the values on the device
+            HEC_CK(cudaMemcpy(A->hec.ell_val.data(), A->ell_val.p,
+                              A->hec.ell_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            HEC_CK(cudaMemcpy(A->hec.tail_val.data(), A->tail_val.p,
+                              A->hec.tail_val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            A->hec_host_stale = false;
+        }
+        const HecHost &H = A->hec;
+        auto cp = [](void *dst, const void *src, size_t bytes) {
+            if (dst && bytes)
+                std::memcpy(dst, src, bytes);
+        };
+        cp(ell_col, H.ell_col.data(), H.ell_col.size() * sizeof(int));
+        cp(ell_val, H.ell_val.data(), H.ell_val.size() * sizeof(double));
+        cp(tail_rows, H.tail_rows.data(), H.tail_rows.size() * sizeof(int));
+        cp(tail_ptr, H.tail_ptr.data(), H.tail_ptr.size() * sizeof(int));
+        cp(tail_col, H.tail_col.data(), H.tail_col.size() * sizeof(int));
+        cp(tail_val, H.tail_val.data(), H.tail_val.size() * sizeof(double));
+        return HEC_OK;
+    });
 }
 
 void hec_matrix_destroy(hec_matrix_t A) { delete A; }
@@ -1358,547 +1366,587 @@ void hec_matrix_destroy(hec_matrix_t A) { delete A; }
 int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const double *y_in,
              double *y_out, const double *w, double *dots, void *stream)
 {
-    if (!A || !x || !y_out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    if (A->host_only)
-        return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
-    if (beta != 0.0 && !y_in)
-        return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
-    if (x == y_out)
-        return fail(HEC_ERR_INVALID, "x and y_out must not alias");
-    SpmvArgs a = spmv_args(A);
-    a.x = x;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.y_in = y_in;
-    a.y_out = y_out;
-    a.red = A->red.r;
-    a.w0 = w;
-    a.w1 = nullptr;
-    a.result = dots;
-    a.op = FIN_STORE;
-    const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
-    return run_spmv(A, a, mode, dots ? 2 : 0, (cudaStream_t)stream);
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !x || !y_out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        if (A->host_only)
+            return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
+        if (beta != 0.0 && !y_in)
+            return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
+        if (x == y_out)
+            return fail(HEC_ERR_INVALID, "x and y_out must not alias");
+        SpmvArgs a = spmv_args(A);
+        a.x = x;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.y_in = y_in;
+        a.y_out = y_out;
+        a.red = A->red.r;
+        a.w0 = w;
+        a.w1 = nullptr;
+        a.result = dots;
+        a.op = FIN_STORE;
+        const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
+        return run_spmv(A, a, mode, dots ? 2 : 0, (cudaStream_t)stream);
+    });
 }
 
 int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const float *y_in,
                  float *y_out, void *stream)
 {
-    if (!A || !x || !y_out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    if (A->host_only)
-        return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
-    if (beta != 0.0f && !y_in)
-        return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
-    if ((const void *)x == (const void *)y_out)
-        return fail(HEC_ERR_INVALID, "x and y_out must not alias");
-    cudaStream_t s = (cudaStream_t)stream;
-    HEC_TRY(ensure_f32(A, s));
-    SpmvArgs a = spmv_args(A);
-    a.x = x;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.y_in = y_in;
-    a.y_out = y_out;
-    const int mode = (beta != 0.0f) ? 2 : (alpha != 1.0f ? 1 : 0);
-    return run_spmv(A, a, mode, 0, s, true);
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !x || !y_out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        if (A->host_only)
+            return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
+        if (beta != 0.0f && !y_in)
+            return fail(HEC_ERR_INVALID, "y_in is needed when beta != 0");
+        if ((const void *)x == (const void *)y_out)
+            return fail(HEC_ERR_INVALID, "x and y_out must not alias");
+        cudaStream_t s = (cudaStream_t)stream;
+        HEC_TRY(ensure_f32(A, s));
+        SpmvArgs a = spmv_args(A);
+        a.x = x;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.y_in = y_in;
+        a.y_out = y_out;
+        const int mode = (beta != 0.0f) ? 2 : (alpha != 1.0f ? 1 : 0);
+        return run_spmv(A, a, mode, 0, s, true);
+    });
 }
 
 int hec_axpby(int32_t n, double a, const double *x, double b, double *y, void *stream)
 {
-    if (n < 0 || (n > 0 && (!x || !y)))
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (n == 0)
-        return HEC_OK;
-    VecArgs v{};
-    v.n = n;
-    v.a = a;
-    v.b = b;
-    v.x = x;
-    v.z = y;
-    return run_vec(V_AXPBY, v, (cudaStream_t)stream);
+    return abi_guard(__func__, [&]() -> int {
+        if (n < 0 || (n > 0 && (!x || !y)))
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (n == 0)
+            return HEC_OK;
+        VecArgs v{};
+        v.n = n;
+        v.a = a;
+        v.b = b;
+        v.x = x;
+        v.z = y;
+        return run_vec(V_AXPBY, v, (cudaStream_t)stream);
+    });
 }
 
 int hec_waxpby(int32_t n, double a, const double *x, double b, const double *y, double *z,
                void *stream)
 {
-    if (n < 0 || (n > 0 && (!x || !y || !z)))
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (n == 0)
-        return HEC_OK;
-    VecArgs v{};
-    v.n = n;
-    v.a = a;
-    v.b = b;
-    v.x = x;
-    v.y = y;
-    v.z = z;
-    return run_vec(V_WAXPBY, v, (cudaStream_t)stream);
+    return abi_guard(__func__, [&]() -> int {
+        if (n < 0 || (n > 0 && (!x || !y || !z)))
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (n == 0)
+            return HEC_OK;
+        VecArgs v{};
+        v.n = n;
+        v.a = a;
+        v.b = b;
+        v.x = x;
+        v.y = y;
+        v.z = z;
+        return run_vec(V_WAXPBY, v, (cudaStream_t)stream);
+    });
 }
 
 int hec_dot(int32_t n, const double *x, const double *y, double *result, void *stream)
 {
-    if (n < 0 || !result || (n > 0 && (!x || !y)))
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (n == 0) {
-        HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
-        return HEC_OK;
-    }
-    VecArgs v{};
-    v.n = n;
-    v.x = x;
-    v.y = y;
-    v.result = result;
-    v.op = FIN_STORE;
-    HEC_TRY(global_reducer(s, v.red));
-    return run_vec(V_DOT, v, s);
+    return abi_guard(__func__, [&]() -> int {
+        if (n < 0 || !result || (n > 0 && (!x || !y)))
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (n == 0) {
+            HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
+            return HEC_OK;
+        }
+        VecArgs v{};
+        v.n = n;
+        v.x = x;
+        v.y = y;
+        v.result = result;
+        v.op = FIN_STORE;
+        HEC_TRY(global_reducer(s, v.red));
+        return run_vec(V_DOT, v, s);
+    });
 }
 
 int hec_nrm2(int32_t n, const double *x, double *result, void *stream)
 {
-    if (n < 0 || !result || (n > 0 && !x))
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (n == 0) {
-        HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
-        return HEC_OK;
-    }
-    VecArgs v{};
-    v.n = n;
-    v.x = x;
-    v.result = result;
-    v.op = FIN_STORE;
-    HEC_TRY(global_reducer(s, v.red));
-    v.op = FIN_STORE_SQRT;
-    return run_vec(V_NRM2SQ, v, s);
+    return abi_guard(__func__, [&]() -> int {
+        if (n < 0 || !result || (n > 0 && !x))
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (n == 0) {
+            HEC_CK(cudaMemsetAsync(result, 0, sizeof(double), s));
+            return HEC_OK;
+        }
+        VecArgs v{};
+        v.n = n;
+        v.x = x;
+        v.result = result;
+        v.op = FIN_STORE;
+        HEC_TRY(global_reducer(s, v.red));
+        v.op = FIN_STORE_SQRT;
+        return run_vec(V_NRM2SQ, v, s);
+    });
 }
 
 int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const double *w, double *h,
                  void *stream)
 {
-    if (n < 1 || k < 1 || k > kMaxRestart + 1 || ldv < n || !V || !w || !h)
-        return fail(HEC_ERR_INVALID, "bad arguments (k must be in 1..%d)", kMaxRestart + 1);
-    cudaStream_t s = (cudaStream_t)stream;
-    BasisArgs a{};
-    a.n = n;
-    a.k = k;
-    a.V = V;
-    a.ldv = ldv;
-    a.w = w;
-    a.result = h;
-    a.op = FIN_STORE;
-    HEC_TRY(global_reducer(s, a.red));
-    launch_multidot(a, grid_for(n, kThreads, 2), s);
-    return check_launch("multidot");
+    return abi_guard(__func__, [&]() -> int {
+        if (n < 1 || k < 1 || k > kMaxRestart + 1 || ldv < n || !V || !w || !h)
+            return fail(HEC_ERR_INVALID, "bad arguments (k must be in 1..%d)", kMaxRestart + 1);
+        cudaStream_t s = (cudaStream_t)stream;
+        BasisArgs a{};
+        a.n = n;
+        a.k = k;
+        a.V = V;
+        a.ldv = ldv;
+        a.w = w;
+        a.result = h;
+        a.op = FIN_STORE;
+        HEC_TRY(global_reducer(s, a.red));
+        launch_multidot(a, grid_for(n, kThreads, 2), s);
+        return check_launch("multidot");
+    });
 }
 
 int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
                 hec_precond_t *out)
 {
-    (void)stream;
-    if (!A || !out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    *out = nullptr;
-    const int n = A->hec.n;
-    if (k < 0 || overlap < 0 || nblocks < 1 || nblocks > n)
-        return fail(HEC_ERR_INVALID, "need k >= 0, overlap >= 0, 1 <= nblocks <= n");
-    std::string msg;
-    int rc = check_csr(n, A->csr.rp.data(), A->csr.ci.data(), (int)A->csr.ci.size(), true, msg);
-    if (rc != HEC_OK)
-        return fail(rc, "%s", msg.c_str());
-    std::unique_ptr<hec_precond_s> M(new hec_precond_s());
-    M->matrix_id = A->id;
-    M->n = n;
-    M->k = k;
-    M->nblocks = nblocks;
-    M->overlap = overlap;
-    M->host_only = A->host_only;
-    ras_blocks(A->csr, nblocks, overlap, M->blocks);
-    std::vector<int> rcs(nblocks, HEC_OK);
-    std::vector<std::string> msgs(nblocks);
-    parallel_for(nblocks, [&](int b) { rcs[b] = iluk_block(M->blocks[b], k, msgs[b]); });
-    for (int b = 0; b < nblocks; ++b)
-        if (rcs[b] != HEC_OK)
-            return fail(rcs[b], "block %d: %s", b, msgs[b].c_str());
-    *out = M.release();
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        (void)stream;
+        if (!A || !out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *out = nullptr;
+        const int n = A->hec.n;
+        if (k < 0 || overlap < 0 || nblocks < 1 || nblocks > n)
+            return fail(HEC_ERR_INVALID, "need k >= 0, overlap >= 0, 1 <= nblocks <= n");
+        std::string msg;
+        int rc = check_csr(n, A->csr.rp.data(), A->csr.ci.data(), (int)A->csr.ci.size(), true, msg);
+        if (rc != HEC_OK)
+            return fail(rc, "%s", msg.c_str());
+        std::unique_ptr<hec_precond_s> M(new hec_precond_s());
+        M->matrix_id = A->id;
+        M->n = n;
+        M->k = k;
+        M->nblocks = nblocks;
+        M->overlap = overlap;
+        M->host_only = A->host_only;
+        ras_blocks(A->csr, nblocks, overlap, M->blocks);
+        std::vector<int> rcs(nblocks, HEC_OK);
+        std::vector<std::string> msgs(nblocks);
+        parallel_for(nblocks, [&](int b) { rcs[b] = iluk_block(M->blocks[b], k, msgs[b]); });
+        for (int b = 0; b < nblocks; ++b)
+            if (rcs[b] != HEC_OK)
+                return fail(rcs[b], "block %d: %s", b, msgs[b].c_str());
+        *out = M.release();
+        return HEC_OK;
+    });
 }
 
 int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *out)
 {
-    if (!A || !out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    *out = nullptr;
-    if (!(omega > 0.0) || !std::isfinite(omega))
-        return fail(HEC_ERR_INVALID, "omega must be a finite positive number");
-    const int n = A->hec.n;
-    const HostCSR &C = A->csr;
-    std::vector<double> d(n);
-    for (int i = 0; i < n; ++i) {
-        double a = 0.0;
-        for (int e = C.rp[i]; e < C.rp[i + 1]; ++e)
-            if (C.ci[e] == i)
-                a = C.va[e];
-        if (a == 0.0)
-            return fail(HEC_ERR_ZERO_PIVOT, "row %d has a zero or missing diagonal entry", i);
-        d[i] = omega / a;
-    }
-    std::unique_ptr<hec_precond_s> M(new hec_precond_s());
-    M->matrix_id = A->id;
-    M->kind = kJacobi;
-    M->omega = omega;
-    M->n = n;
-    M->host_only = A->host_only;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!M->host_only) {
-        HEC_TRY(upload(M->dinv, d, s));
-        HEC_TRY(M->d_err.alloc(sizeof(int), s));
-        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
-        HEC_CK(cudaStreamSynchronize(s));
-    }
-    M->scheduled = true;
-    *out = M.release();
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *out = nullptr;
+        if (!(omega > 0.0) || !std::isfinite(omega))
+            return fail(HEC_ERR_INVALID, "omega must be a finite positive number");
+        const int n = A->hec.n;
+        const HostCSR &C = A->csr;
+        std::vector<double> d(n);
+        for (int i = 0; i < n; ++i) {
+            double a = 0.0;
+            for (int e = C.rp[i]; e < C.rp[i + 1]; ++e)
+                if (C.ci[e] == i)
+                    a = C.va[e];
+            if (a == 0.0)
+                return fail(HEC_ERR_ZERO_PIVOT, "row %d has a zero or missing diagonal entry", i);
+            d[i] = omega / a;
+        }
+        std::unique_ptr<hec_precond_s> M(new hec_precond_s());
+        M->matrix_id = A->id;
+        M->kind = kJacobi;
+        M->omega = omega;
+        M->n = n;
+        M->host_only = A->host_only;
+        cudaStream_t s = (cudaStream_t)stream;
+        if (!M->host_only) {
+            HEC_TRY(upload(M->dinv, d, s));
+            HEC_TRY(M->d_err.alloc(sizeof(int), s));
+            HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+            HEC_CK(cudaStreamSynchronize(s));
+        }
+        M->scheduled = true;
+        *out = M.release();
+        return HEC_OK;
+    });
 }
 
 int level_schedule(hec_precond_t M, void *stream)
 {
-    if (!M)
-        return fail(HEC_ERR_INVALID, "null preconditioner");
-    if (M->scheduled)
-        return HEC_OK; // also every damped-Jacobi handle: nothing to schedule
-    cudaStream_t s = (cudaStream_t)stream;
-    parallel_for(M->nblocks, [&](int b) { levels_block(M->blocks[b]); });
-    HEC_TRY(build_layout(M, 0, s));
-    if (!M->host_only) {
-        HEC_TRY(M->d_err.alloc(sizeof(int), s));
-        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
-        HEC_CK(cudaStreamSynchronize(s));
-    }
-    M->scheduled = true;
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!M)
+            return fail(HEC_ERR_INVALID, "null preconditioner");
+        if (M->scheduled)
+            return HEC_OK; // also every damped-Jacobi handle: nothing to schedule
+        cudaStream_t s = (cudaStream_t)stream;
+        parallel_for(M->nblocks, [&](int b) { levels_block(M->blocks[b]); });
+        HEC_TRY(build_layout(M, 0, s));
+        if (!M->host_only) {
+            HEC_TRY(M->d_err.alloc(sizeof(int), s));
+            HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+            HEC_CK(cudaStreamSynchronize(s));
+        }
+        M->scheduled = true;
+        return HEC_OK;
+    });
 }
 
 int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
 {
-    if (!M || !info)
-        return fail(HEC_ERR_INVALID, "null argument");
-    std::memset(info, 0, sizeof(*info));
-    info->nblocks = M->nblocks;
-    info->overlap = M->overlap;
-    info->k = M->kind == kJacobi ? -1 : M->k;
-    info->scheduled = M->scheduled ? 1 : 0;
-    for (const BlockFactor &B : M->blocks) {
-        info->rows_total += B.F.n;
-        info->factor_nnz += (int64_t)B.F.ci.size();
-        info->max_levels_L = std::max(info->max_levels_L, B.nlevL);
-        info->max_levels_U = std::max(info->max_levels_U, B.nlevU);
-    }
-    info->apply_bytes = M->kind == kJacobi ? (int64_t)M->n * 24 // r, d read; z written
-                        : M->scheduled          ? M->lay[0].pack.alg_bytes
-                                                : 0;
-    info->device_bytes = M->device_bytes();
-    info->ring_slots = M->scheduled ? M->lay[0].pack.ring_slots : 0;
-    info->apply_bytes_f32 = M->lay[1].built ? M->lay[1].pack.alg_bytes : 0;
-    for (const TrsvBlock &T : M->lay[0].pack.blocks)
-        info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || !info)
+            return fail(HEC_ERR_INVALID, "null argument");
+        std::memset(info, 0, sizeof(*info));
+        info->nblocks = M->nblocks;
+        info->overlap = M->overlap;
+        info->k = M->kind == kJacobi ? -1 : M->k;
+        info->scheduled = M->scheduled ? 1 : 0;
+        for (const BlockFactor &B : M->blocks) {
+            info->rows_total += B.F.n;
+            info->factor_nnz += (int64_t)B.F.ci.size();
+            info->max_levels_L = std::max(info->max_levels_L, B.nlevL);
+            info->max_levels_U = std::max(info->max_levels_U, B.nlevU);
+        }
+        info->apply_bytes = M->kind == kJacobi ? (int64_t)M->n * 24 // r, d read; z written
+                            : M->scheduled          ? M->lay[0].pack.alg_bytes
+                                                    : 0;
+        info->device_bytes = M->device_bytes();
+        info->ring_slots = M->scheduled ? M->lay[0].pack.ring_slots : 0;
+        info->apply_bytes_f32 = M->lay[1].built ? M->lay[1].pack.alg_bytes : 0;
+        for (const TrsvBlock &T : M->lay[0].pack.blocks)
+            info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
+        return HEC_OK;
+    });
 }
 
 int hec_precond_get_block(hec_precond_t M, int32_t b, int32_t *nv, int32_t *own_lo,
                           int32_t *own_hi, int32_t *rows)
 {
-    if (!M || b < 0 || b >= M->nblocks)
-        return fail(HEC_ERR_INVALID, "bad block");
-    const BlockFactor &B = M->blocks[b];
-    if (nv)
-        *nv = (int32_t)B.rows.size();
-    if (own_lo)
-        *own_lo = B.own_lo;
-    if (own_hi)
-        *own_hi = B.own_hi;
-    if (rows)
-        std::memcpy(rows, B.rows.data(), B.rows.size() * sizeof(int));
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || b < 0 || b >= M->nblocks)
+            return fail(HEC_ERR_INVALID, "bad block");
+        const BlockFactor &B = M->blocks[b];
+        if (nv)
+            *nv = (int32_t)B.rows.size();
+        if (own_lo)
+            *own_lo = B.own_lo;
+        if (own_hi)
+            *own_hi = B.own_hi;
+        if (rows)
+            std::memcpy(rows, B.rows.data(), B.rows.size() * sizeof(int));
+        return HEC_OK;
+    });
 }
 
 int hec_precond_get_factor(hec_precond_t M, int32_t b, int32_t *nnz, int32_t *row_ptr,
                            int32_t *col, double *val, int32_t *lev)
 {
-    if (!M || b < 0 || b >= M->nblocks || !nnz)
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    HEC_TRY(refresh_host_factors(M, nullptr));
-    const BlockFactor &B = M->blocks[b];
-    *nnz = (int32_t)B.F.ci.size();
-    if (row_ptr)
-        std::memcpy(row_ptr, B.F.rp.data(), B.F.rp.size() * sizeof(int));
-    if (col)
-        std::memcpy(col, B.F.ci.data(), B.F.ci.size() * sizeof(int));
-    if (val)
-        std::memcpy(val, B.F.va.data(), B.F.va.size() * sizeof(double));
-    if (lev)
-        std::memcpy(lev, B.lev.data(), B.lev.size() * sizeof(int));
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || b < 0 || b >= M->nblocks || !nnz)
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        HEC_TRY(refresh_host_factors(M, nullptr));
+        const BlockFactor &B = M->blocks[b];
+        *nnz = (int32_t)B.F.ci.size();
+        if (row_ptr)
+            std::memcpy(row_ptr, B.F.rp.data(), B.F.rp.size() * sizeof(int));
+        if (col)
+            std::memcpy(col, B.F.ci.data(), B.F.ci.size() * sizeof(int));
+        if (val)
+            std::memcpy(val, B.F.va.data(), B.F.va.size() * sizeof(double));
+        if (lev)
+            std::memcpy(lev, B.lev.data(), B.lev.size() * sizeof(int));
+        return HEC_OK;
+    });
 }
 
 int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *nlev,
                            int32_t *level_ptr, int32_t *level_rows)
 {
-    if (!M || b < 0 || b >= M->nblocks || (which != HEC_FACTOR_L && which != HEC_FACTOR_U))
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (!M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    const BlockFactor &B = M->blocks[b];
-    const bool u = which == HEC_FACTOR_U;
-    if (nlev)
-        *nlev = u ? B.nlevU : B.nlevL;
-    const std::vector<int> &p = u ? B.lptrU : B.lptrL;
-    const std::vector<int> &r = u ? B.lrowsU : B.lrowsL;
-    if (level_ptr)
-        std::memcpy(level_ptr, p.data(), p.size() * sizeof(int));
-    if (level_rows)
-        std::memcpy(level_rows, r.data(), r.size() * sizeof(int));
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || b < 0 || b >= M->nblocks || (which != HEC_FACTOR_L && which != HEC_FACTOR_U))
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (!M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        const BlockFactor &B = M->blocks[b];
+        const bool u = which == HEC_FACTOR_U;
+        if (nlev)
+            *nlev = u ? B.nlevU : B.nlevL;
+        const std::vector<int> &p = u ? B.lptrU : B.lptrL;
+        const std::vector<int> &r = u ? B.lrowsU : B.lrowsL;
+        if (level_ptr)
+            std::memcpy(level_ptr, p.data(), p.size() * sizeof(int));
+        if (level_rows)
+            std::memcpy(level_rows, r.data(), r.size() * sizeof(int));
+        return HEC_OK;
+    });
 }
 
 int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
                            int32_t *ring_slots, int32_t *fixed_width, void *pack, uint32_t *chunks,
                            int64_t *blocks, void *stream)
 {
-    if (!M || (fp32 != 0 && fp32 != 1) || !pack_bytes || !nchunks || !ring_slots || !fixed_width)
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (M->kind == kJacobi)
-        return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no factor layout");
-    if (!M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    HEC_TRY(build_layout(M, fp32, s));
-    const TrsvLayout &L = M->lay[fp32];
-    int64_t total = 0;
-    for (const uint2 &c : L.pack.chunks)
-        total = std::max<int64_t>(total, (int64_t)c.x * 16 + c.y);
-    *pack_bytes = total;
-    *nchunks = (int32_t)L.pack.chunks.size();
-    *ring_slots = L.pack.ring_slots;
-    *fixed_width = L.fixed_width;
-    if (pack && total > 0) {
-        if (!L.pack.pack.empty()) {
-            std::memcpy(pack, L.pack.pack.data(), (size_t)total);
-        } else { // uploaded (and possibly refilled by hec_refactor): the device copy
-            HEC_CK(cudaMemcpyAsync(pack, L.d_pack.p, (size_t)total, cudaMemcpyDeviceToHost, s));
-            HEC_CK(cudaStreamSynchronize(s));
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || (fp32 != 0 && fp32 != 1) || !pack_bytes || !nchunks || !ring_slots || !fixed_width)
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (M->kind == kJacobi)
+            return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no factor layout");
+        if (!M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        HEC_TRY(build_layout(M, fp32, s));
+        const TrsvLayout &L = M->lay[fp32];
+        int64_t total = 0;
+        for (const uint2 &c : L.pack.chunks)
+            total = std::max<int64_t>(total, (int64_t)c.x * 16 + c.y);
+        *pack_bytes = total;
+        *nchunks = (int32_t)L.pack.chunks.size();
+        *ring_slots = L.pack.ring_slots;
+        *fixed_width = L.fixed_width;
+        if (pack && total > 0) {
+            if (!L.pack.pack.empty()) {
+                std::memcpy(pack, L.pack.pack.data(), (size_t)total);
+            } else { // uploaded (and possibly refilled by hec_refactor): the device copy
+                HEC_CK(cudaMemcpyAsync(pack, L.d_pack.p, (size_t)total, cudaMemcpyDeviceToHost, s));
+                HEC_CK(cudaStreamSynchronize(s));
+            }
         }
-    }
-    if (chunks)
-        for (size_t c = 0; c < L.pack.chunks.size(); ++c) {
-            chunks[2 * c] = L.pack.chunks[c].x;
-            chunks[2 * c + 1] = L.pack.chunks[c].y;
-        }
-    if (blocks)
-        for (size_t b = 0; b < L.pack.blocks.size(); ++b) {
-            const TrsvBlock &T = L.pack.blocks[b];
-            int64_t *o = blocks + 7 * b;
-            o[0] = T.chunk_begin;
-            o[1] = T.chunk_mid;
-            o[2] = T.chunk_end;
-            o[3] = T.ring_L;
-            o[4] = T.ring_U;
-            o[5] = T.yoff;
-            o[6] = T.zoff;
-        }
-    return HEC_OK;
+        if (chunks)
+            for (size_t c = 0; c < L.pack.chunks.size(); ++c) {
+                chunks[2 * c] = L.pack.chunks[c].x;
+                chunks[2 * c + 1] = L.pack.chunks[c].y;
+            }
+        if (blocks)
+            for (size_t b = 0; b < L.pack.blocks.size(); ++b) {
+                const TrsvBlock &T = L.pack.blocks[b];
+                int64_t *o = blocks + 7 * b;
+                o[0] = T.chunk_begin;
+                o[1] = T.chunk_mid;
+                o[2] = T.chunk_end;
+                o[3] = T.ring_L;
+                o[4] = T.ring_U;
+                o[5] = T.yoff;
+                o[6] = T.zoff;
+            }
+        return HEC_OK;
+    });
 }
 
 int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit, void *stream)
 {
-    if (!M || !r || !z || r == z)
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (M->host_only)
-        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
-    if (!M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    if (M->kind == kJacobi)
-        return run_jacobi(M, r, z, false, (cudaStream_t)stream);
-    TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
-    a.r = r;
-    a.z = z;
-    return run_trsv(a, (cudaStream_t)stream);
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || !r || !z || r == z)
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (M->host_only)
+            return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+        if (!M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        if (M->kind == kJacobi)
+            return run_jacobi(M, r, z, false, (cudaStream_t)stream);
+        TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
+        a.r = r;
+        a.z = z;
+        return run_trsv(a, (cudaStream_t)stream);
+    });
 }
 
 int hec_precond_apply_f32(hec_precond_t M, const float *r, float *z, int64_t spin_limit,
                           void *stream)
 {
-    if (!M || !r || !z || (const void *)r == (const void *)z)
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (M->host_only)
-        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
-    if (!M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    cudaStream_t s = (cudaStream_t)stream;
-    HEC_TRY(ensure_precond_f32(M, s));
-    if (M->kind == kJacobi)
-        return run_jacobi(M, r, z, true, s);
-    TrsvArgs a = trsv_args(M, M->lay[1], spin_limit ? spin_limit : kDefaultSpin);
-    a.r = r;
-    a.z = z;
-    return run_trsv(a, s, true);
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || !r || !z || (const void *)r == (const void *)z)
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (M->host_only)
+            return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+        if (!M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        cudaStream_t s = (cudaStream_t)stream;
+        HEC_TRY(ensure_precond_f32(M, s));
+        if (M->kind == kJacobi)
+            return run_jacobi(M, r, z, true, s);
+        TrsvArgs a = trsv_args(M, M->lay[1], spin_limit ? spin_limit : kDefaultSpin);
+        a.r = r;
+        a.z = z;
+        return run_trsv(a, s, true);
+    });
 }
 
 int hec_precond_status(hec_precond_t M, void *stream)
 {
-    if (!M || M->host_only || !M->scheduled)
-        return fail(HEC_ERR_INVALID, "bad preconditioner");
-    cudaStream_t s = (cudaStream_t)stream;
-    int err = 0;
-    HEC_CK(cudaMemcpyAsync(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HEC_CK(cudaStreamSynchronize(s));
-    if (err) {
-        HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || M->host_only || !M->scheduled)
+            return fail(HEC_ERR_INVALID, "bad preconditioner");
+        cudaStream_t s = (cudaStream_t)stream;
+        int err = 0;
+        HEC_CK(cudaMemcpyAsync(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         HEC_CK(cudaStreamSynchronize(s));
-        return fail(err, "a bounded device wait ran out");
-    }
-    return HEC_OK;
+        if (err) {
+            HEC_CK(cudaMemsetAsync(M->d_err.p, 0, sizeof(int), s));
+            HEC_CK(cudaStreamSynchronize(s));
+            return fail(err, "a bounded device wait ran out");
+        }
+        return HEC_OK;
+    });
 }
 
 void hec_precond_destroy(hec_precond_t M) { delete M; }
 
 int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *stream)
 {
-    if (!A || !val)
-        return fail(HEC_ERR_INVALID, "null argument");
-    if (A->host_only || (M && M->host_only))
-        return fail(HEC_ERR_INVALID, "host-only handle");
-    if (M && M->matrix_id != A->id)
-        return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
-    if (M && M->kind != kJacobi && !M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    cudaStream_t s = (cudaStream_t)stream;
-    HEC_TRY(refactor_matrix(A, val, s));
-    if (M)
-        HEC_TRY(refactor_precond(A, M, s));
-    HEC_CK(cudaStreamSynchronize(s));
-    if (M) {
-        int err = 0;
-        HEC_CK(cudaMemcpy(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) {
-            HEC_CK(cudaMemset(M->d_err.p, 0, sizeof(int)));
-            return fail(err, "numeric refactorisation: a pivot is zero");
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !val)
+            return fail(HEC_ERR_INVALID, "null argument");
+        if (A->host_only || (M && M->host_only))
+            return fail(HEC_ERR_INVALID, "host-only handle");
+        if (M && M->matrix_id != A->id)
+            return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
+        if (M && M->kind != kJacobi && !M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        cudaStream_t s = (cudaStream_t)stream;
+        HEC_TRY(refactor_matrix(A, val, s));
+        if (M)
+            HEC_TRY(refactor_precond(A, M, s));
+        HEC_CK(cudaStreamSynchronize(s));
+        if (M) {
+            int err = 0;
+            HEC_CK(cudaMemcpy(&err, M->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+            if (err) {
+                HEC_CK(cudaMemset(M->d_err.p, 0, sizeof(int)));
+                return fail(err, "numeric refactorisation: a pivot is zero");
+            }
         }
-    }
-    return HEC_OK;
+        return HEC_OK;
+    });
 }
 
 int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, double tol,
                  int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
                  hec_solve_info_t *info)
 {
-    if (info)
-        std::memset(info, 0, sizeof(*info));
-    if (!A || !b || !x)
-        return fail(HEC_ERR_INVALID, "null argument");
-    if (A->host_only || (M && M->host_only))
-        return fail(HEC_ERR_INVALID, "host-only handle");
-    if (M && (M->matrix_id != A->id))
-        return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
-    if (M && !M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    hec_solve_opts_t o{};
-    if (opts)
-        o = *opts;
-    if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB && o.method != HEC_CG)
-        return fail(HEC_ERR_INVALID, "unknown method");
-    if (!(tol >= 0.0) || maxit < 0)
-        return fail(HEC_ERR_INVALID, "tol >= 0 and maxit >= 0 required");
-    if (o.method == HEC_GMRES && (restart < 1 || restart > kMaxRestart))
-        return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
-    if (o.method != HEC_GMRES)
-        restart = 0;
-    const bool mixed = (o.flags & HEC_MIXED_FP32) != 0;
-    if (mixed && o.method != HEC_GMRES)
-        return fail(HEC_ERR_INVALID, "HEC_MIXED_FP32 needs method HEC_GMRES");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (mixed) {
-        HEC_TRY(ensure_f32(A, s));
-        if (M)
-            HEC_TRY(ensure_precond_f32(M, s));
-    }
-    Solver *S = nullptr;
-    HEC_TRY(make_solver(A, M, o.method, restart, mixed, s, S));
-    const int n = S->n;
-    const size_t vb = sizeof(double) * (size_t)n;
-    // state header
-    std::unique_ptr<SolverState> hp(new SolverState());
-    SolverState &h = *hp;
-    std::memset(&h, 0, offsetof(SolverState, H));
-    h.tol = tol;
-    h.maxit = maxit;
-    h.restart = restart;
-    h.method = o.method;
-    h.flags = o.flags;
-    h.h_while = S->h_while;
-    h.h_if = S->h_if;
-    const bool eager = (o.flags & HEC_SOLVE_EAGER) != 0;
-    h.graph_mode = eager ? 0 : 1;
-    // an FP32 inner cycle also ends once it has reduced its FP32 residual by
-    // this factor: below it the FP32 arithmetic cannot be trusted, the FP64
-    // refinement (next cycle start) takes over
-    h.inner_rtol = mixed ? 1e-5 : 0.0;
-    HEC_CK(cudaMemcpyAsync(S->st, &h, offsetof(SolverState, H), cudaMemcpyHostToDevice, s));
-    int64_t h2d = 0, d2h = 0;
-    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    HEC_CK(cudaMemcpyAsync(S->b, b, vb, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (!bdev)
-        h2d += vb;
-    if (o.flags & HEC_X0_ZERO) {
-        HEC_CK(cudaMemsetAsync(S->x, 0, vb, s));
-    } else {
-        HEC_CK(cudaMemcpyAsync(S->x, x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        if (!xdev)
-            h2d += vb;
-    }
-    if (eager)
-        HEC_TRY(run_eager(A, M, *S, s));
-    else
-        HEC_CK(cudaGraphLaunch(S->exec, s));
-    HEC_CK(cudaMemcpyAsync(x, S->x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    if (!xdev)
-        d2h += vb;
-    HEC_CK(cudaMemcpyAsync(&h, S->st, offsetof(SolverState, H), cudaMemcpyDeviceToHost, s));
-    HEC_CK(cudaStreamSynchronize(s));
-    int status = h.err ? h.err : h.status;
-    if (info) {
-        info->iters = h.iters;
-        info->restarts = h.restarts;
-        info->status = status;
-        info->rel_resid = h.rel_resid;
-        info->est_resid = h.est;
-        info->kernel_launches = (int64_t)h.launches;
-        info->h2d_bytes = h2d;
-        info->d2h_bytes = d2h;
-    }
-    if (h.err)
-        return fail(h.err, "a bounded device wait ran out during the solve");
-    if (mixed && h.stagnated && !h.err) {
-        // the FP32 cycles stopped refining: finish in FP64 from the current x
-        hec_solve_opts_t o64 = o;
-        o64.flags &= ~(HEC_MIXED_FP32 | HEC_X0_ZERO);
-        hec_solve_info_t i64{};
-        status = krylov_solve(A, M, b, x, tol, std::max(0, maxit - h.iters), restart, &o64, stream,
-                              &i64);
-        if (info) {
-            info->iters += i64.iters;
-            info->restarts += i64.restarts;
-            info->status = i64.status;
-            info->rel_resid = i64.rel_resid;
-            info->est_resid = i64.est_resid;
-            info->kernel_launches += i64.kernel_launches;
-            info->h2d_bytes += i64.h2d_bytes;
-            info->d2h_bytes += i64.d2h_bytes;
-            info->fp64_finish = 1;
+    return abi_guard(__func__, [&]() -> int {
+        if (info)
+            std::memset(info, 0, sizeof(*info));
+        if (!A || !b || !x)
+            return fail(HEC_ERR_INVALID, "null argument");
+        if (A->host_only || (M && M->host_only))
+            return fail(HEC_ERR_INVALID, "host-only handle");
+        if (M && (M->matrix_id != A->id))
+            return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
+        if (M && !M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        hec_solve_opts_t o{};
+        if (opts)
+            o = *opts;
+        if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB && o.method != HEC_CG)
+            return fail(HEC_ERR_INVALID, "unknown method");
+        if (!(tol >= 0.0) || maxit < 0)
+            return fail(HEC_ERR_INVALID, "tol >= 0 and maxit >= 0 required");
+        if (o.method == HEC_GMRES && (restart < 1 || restart > kMaxRestart))
+            return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
+        if (o.method != HEC_GMRES)
+            restart = 0;
+        const bool mixed = (o.flags & HEC_MIXED_FP32) != 0;
+        if (mixed && o.method != HEC_GMRES)
+            return fail(HEC_ERR_INVALID, "HEC_MIXED_FP32 needs method HEC_GMRES");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (mixed) {
+            HEC_TRY(ensure_f32(A, s));
+            if (M)
+                HEC_TRY(ensure_precond_f32(M, s));
         }
-    }
-    return status;
+        Solver *S = nullptr;
+        HEC_TRY(make_solver(A, M, o.method, restart, mixed, s, S));
+        const int n = S->n;
+        const size_t vb = sizeof(double) * (size_t)n;
+        // state header
+        std::unique_ptr<SolverState> hp(new SolverState());
+        SolverState &h = *hp;
+        std::memset(&h, 0, offsetof(SolverState, H));
+        h.tol = tol;
+        h.maxit = maxit;
+        h.restart = restart;
+        h.method = o.method;
+        h.flags = o.flags;
+        h.h_while = S->h_while;
+        h.h_if = S->h_if;
+        const bool eager = (o.flags & HEC_SOLVE_EAGER) != 0;
+        h.graph_mode = eager ? 0 : 1;
+        // an FP32 inner cycle also ends once it has reduced its FP32 residual by
+        // this factor: below it the FP32 arithmetic cannot be trusted, the FP64
+        // refinement (next cycle start) takes over
+        h.inner_rtol = mixed ? 1e-5 : 0.0;
+        HEC_CK(cudaMemcpyAsync(S->st, &h, offsetof(SolverState, H), cudaMemcpyHostToDevice, s));
+        int64_t h2d = 0, d2h = 0;
+        const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+        HEC_CK(cudaMemcpyAsync(S->b, b, vb, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (!bdev)
+            h2d += vb;
+        if (o.flags & HEC_X0_ZERO) {
+            HEC_CK(cudaMemsetAsync(S->x, 0, vb, s));
+        } else {
+            HEC_CK(cudaMemcpyAsync(S->x, x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+            if (!xdev)
+                h2d += vb;
+        }
+        if (eager)
+            HEC_TRY(run_eager(A, M, *S, s));
+        else
+            HEC_CK(cudaGraphLaunch(S->exec, s));
+        HEC_CK(cudaMemcpyAsync(x, S->x, vb, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        if (!xdev)
+            d2h += vb;
+        HEC_CK(cudaMemcpyAsync(&h, S->st, offsetof(SolverState, H), cudaMemcpyDeviceToHost, s));
+        HEC_CK(cudaStreamSynchronize(s));
+        int status = h.err ? h.err : h.status;
+        if (info) {
+            info->iters = h.iters;
+            info->restarts = h.restarts;
+            info->status = status;
+            info->rel_resid = h.rel_resid;
+            info->est_resid = h.est;
+            info->kernel_launches = (int64_t)h.launches;
+            info->h2d_bytes = h2d;
+            info->d2h_bytes = d2h;
+        }
+        if (h.err)
+            return fail(h.err, "a bounded device wait ran out during the solve");
+        if (mixed && h.stagnated && !h.err) {
+            // the FP32 cycles stopped refining: finish in FP64 from the current x
+            hec_solve_opts_t o64 = o;
+            o64.flags &= ~(HEC_MIXED_FP32 | HEC_X0_ZERO);
+            hec_solve_info_t i64{};
+            status = krylov_solve(A, M, b, x, tol, std::max(0, maxit - h.iters), restart, &o64, stream,
+                                  &i64);
+            if (info) {
+                info->iters += i64.iters;
+                info->restarts += i64.restarts;
+                info->status = i64.status;
+                info->rel_resid = i64.rel_resid;
+                info->est_resid = i64.est_resid;
+                info->kernel_launches += i64.kernel_launches;
+                info->h2d_bytes += i64.h2d_bytes;
+                info->d2h_bytes += i64.d2h_bytes;
+                info->fp64_finish = 1;
+            }
+        }
+        return status;
+    });
 }
 
 } // extern "C"
@@ -1944,29 +1992,31 @@ int noalloc_scratch(double **out)
 extern "C" int hec_precond_apply_noalloc(hec_precond_t M, const double *r, double *z,
                                          int64_t spin_limit, void *stream)
 {
-    if (!M || !r || !z || r == z)
-        return fail(HEC_ERR_INVALID, "bad arguments");
-    if (M->host_only)
-        return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
-    if (!M->scheduled)
-        return fail(HEC_ERR_INVALID, "level_schedule has not run");
-    if (M->kind == kJacobi) // no scratch at all
-        return run_jacobi(M, r, z, false, (cudaStream_t)stream);
-    const TrsvPack &P = M->lay[0].pack;
-    const long long need = (long long)P.ysz + (long long)P.zsz;
-    if (need > kNoallocScratchDoubles)
-        return fail(HEC_ERR_INVALID,
-                    "preconditioner needs %lld scratch doubles; the static array of "
-                    "hec_precond_apply_noalloc holds %lld (use hec_precond_apply)",
-                    need, kNoallocScratchDoubles);
-    double *scratch = nullptr;
-    HEC_TRY(noalloc_scratch(&scratch));
-    // y and z scratch are written before they are read inside one launch, so
-    // nothing in the shared array has to start at zero.
-    TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
-    a.r = r;
-    a.z = z;
-    a.ysc = scratch;
-    a.zsc = P.zsz ? scratch + P.ysz : nullptr;
-    return run_trsv(a, (cudaStream_t)stream);
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || !r || !z || r == z)
+            return fail(HEC_ERR_INVALID, "bad arguments");
+        if (M->host_only)
+            return fail(HEC_ERR_INVALID, "host-only preconditioner has no device data");
+        if (!M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        if (M->kind == kJacobi) // no scratch at all
+            return run_jacobi(M, r, z, false, (cudaStream_t)stream);
+        const TrsvPack &P = M->lay[0].pack;
+        const long long need = (long long)P.ysz + (long long)P.zsz;
+        if (need > kNoallocScratchDoubles)
+            return fail(HEC_ERR_INVALID,
+                        "preconditioner needs %lld scratch doubles; the static array of "
+                        "hec_precond_apply_noalloc holds %lld (use hec_precond_apply)",
+                        need, kNoallocScratchDoubles);
+        double *scratch = nullptr;
+        HEC_TRY(noalloc_scratch(&scratch));
+        // y and z scratch are written before they are read inside one launch, so
+        // nothing in the shared array has to start at zero.
+        TrsvArgs a = trsv_args(M, M->lay[0], spin_limit ? spin_limit : kDefaultSpin);
+        a.r = r;
+        a.z = z;
+        a.ysc = scratch;
+        a.zsc = P.zsz ? scratch + P.ysz : nullptr;
+        return run_trsv(a, (cudaStream_t)stream);
+    });
 }

@@ -259,13 +259,13 @@ void lane_main(hec_server_s *S, int lane)
             } else if (q.has_matrix) {
                 // another pattern, or a one-CTA batched system: set it up again
                 R->destroy();
-                rc = setup(S, q, st, *R);
+                rc = abi_guard("hec_server set-up", [&]() { return setup(S, q, st, *R); });
             }
         } else if (!q.has_matrix) {
             rc = fail(HEC_ERR_INVALID, "key %llu is not resident and the request has no matrix",
                       (unsigned long long)q.key);
         } else {
-            rc = setup(S, q, st, local);
+            rc = abi_guard("hec_server set-up", [&]() { return setup(S, q, st, local); });
         }
         r.t_setup = S->now();
         const size_t nb = (size_t)q.n * sizeof(double);
@@ -294,10 +294,14 @@ void lane_main(hec_server_s *S, int lane)
         }
         std::vector<double> x;
         if (rc >= 0 && S->o.keep_solutions) {
-            x.resize(q.n);
-            if (cudaMemcpyAsync(x.data(), dx, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                rc = HEC_ERR_CUDA;
+            rc = abi_guard("hec_server solution copy", [&]() -> int {
+                x.resize(q.n);
+                if (cudaMemcpyAsync(x.data(), dx, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return fail(HEC_ERR_CUDA, "solution copy of request %llu",
+                                (unsigned long long)q.ticket);
+                return rc;
+            });
         }
         if (rc < 0 && S->verbose)
             fprintf(stderr, "hec_server: request %llu (n = %d) failed: %s\n",
@@ -350,125 +354,133 @@ void lane_main(hec_server_s *S, int lane)
 
 int hec_server_create(const hec_server_opts_t *opts, hec_server_t *out)
 {
-    if (!out)
-        return fail(HEC_ERR_INVALID, "null argument");
-    *out = nullptr;
-    hec_server_opts_t o{};
-    if (opts)
-        o = *opts;
-    if (o.lanes < 0 || o.lanes > 64 || o.restart < 0 || o.restart > 31 || o.maxit < 0 ||
-        o.small_rows < 0 || o.block_rows < 0 || o.device_budget < 0 || !(o.tol >= 0.0))
-        return fail(HEC_ERR_INVALID, "bad server options");
-    if (o.lanes == 0)
-        o.lanes = 8;
-    if (o.restart == 0)
-        o.restart = 30;
-    if (o.maxit == 0)
-        o.maxit = 20000;
-    if (o.tol == 0.0)
-        o.tol = 1e-8;
-    if (o.small_rows == 0)
-        o.small_rows = 32768;
-    if (o.block_rows == 0)
-        o.block_rows = 16384;
-    if (o.device_budget == 0) {
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(HEC_ERR_CUDA, "no CUDA device");
+    return abi_guard(__func__, [&]() -> int {
+        if (!out)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *out = nullptr;
+        hec_server_opts_t o{};
+        if (opts)
+            o = *opts;
+        if (o.lanes < 0 || o.lanes > 64 || o.restart < 0 || o.restart > 31 || o.maxit < 0 ||
+            o.small_rows < 0 || o.block_rows < 0 || o.device_budget < 0 || !(o.tol >= 0.0))
+            return fail(HEC_ERR_INVALID, "bad server options");
+        if (o.lanes == 0)
+            o.lanes = 8;
+        if (o.restart == 0)
+            o.restart = 30;
+        if (o.maxit == 0)
+            o.maxit = 20000;
+        if (o.tol == 0.0)
+            o.tol = 1e-8;
+        if (o.small_rows == 0)
+            o.small_rows = 32768;
+        if (o.block_rows == 0)
+            o.block_rows = 16384;
+        if (o.device_budget == 0) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(HEC_ERR_CUDA, "no CUDA device");
+            }
+            o.device_budget = (int64_t)(fr / 2);
         }
-        o.device_budget = (int64_t)(fr / 2);
-    }
-    auto S = new hec_server_s();
-    S->o = o;
-    S->t0 = Clock::now();
-    S->verbose = std::getenv("HEC_SERVER_VERBOSE") != nullptr;
-    for (int i = 0; i < o.lanes; ++i) {
-        cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            for (cudaStream_t t : S->streams)
-                cudaStreamDestroy(t);
-            delete S;
-            return fail(HEC_ERR_CUDA, "cannot create a lane stream");
+        auto S = new hec_server_s();
+        S->o = o;
+        S->t0 = Clock::now();
+        S->verbose = std::getenv("HEC_SERVER_VERBOSE") != nullptr;
+        for (int i = 0; i < o.lanes; ++i) {
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                for (cudaStream_t t : S->streams)
+                    cudaStreamDestroy(t);
+                delete S;
+                return fail(HEC_ERR_CUDA, "cannot create a lane stream");
+            }
+            S->streams.push_back(st);
         }
-        S->streams.push_back(st);
-    }
-    for (int i = 0; i < o.lanes; ++i)
-        S->lanes.emplace_back(lane_main, S, i);
-    *out = S;
-    return HEC_OK;
+        for (int i = 0; i < o.lanes; ++i)
+            S->lanes.emplace_back(lane_main, S, i);
+        *out = S;
+        return HEC_OK;
+    });
 }
 
 int hec_server_submit(hec_server_t S, const hec_request_t *req, uint64_t *ticket)
 {
-    if (!S || !req || !req->b || req->A.on_device)
-        return fail(HEC_ERR_INVALID, "invalid request (host arrays required)");
-    const bool has = req->A.row_ptr != nullptr;
-    if (!has && req->key == 0)
-        return fail(HEC_ERR_INVALID, "a request without a matrix needs a key");
-    if (has && (!req->A.col || !req->A.val))
-        return fail(HEC_ERR_INVALID, "invalid request matrix");
-    const int n = req->A.n;
-    if (n < 1 || req->ilu_k < 0 || (has && (req->A.row_ptr[0] != 0 || req->A.row_ptr[n] != req->A.nnz)))
-        return fail(HEC_ERR_INVALID, "invalid request matrix");
-    Request q;
-    q.tag = req->tag;
-    q.key = req->key;
-    q.n = n;
-    q.k = req->ilu_k;
-    q.has_matrix = has;
-    if (has) {
-        q.rp.assign(req->A.row_ptr, req->A.row_ptr + n + 1);
-        q.ci.assign(req->A.col, req->A.col + req->A.nnz);
-        q.va.assign(req->A.val, req->A.val + req->A.nnz);
-        q.pattern = pattern_hash(q.rp, q.ci);
-    }
-    q.b.assign(req->b, req->b + n);
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        if (S->stopping)
-            return fail(HEC_ERR_INVALID, "server is shutting down");
-        q.ticket = S->next_ticket++;
-        q.t_submit = S->now();
-        if (ticket)
-            *ticket = q.ticket;
-        S->pending.push_back(std::move(q));
-    }
-    S->cv_work.notify_one();
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!S || !req || !req->b || req->A.on_device)
+            return fail(HEC_ERR_INVALID, "invalid request (host arrays required)");
+        const bool has = req->A.row_ptr != nullptr;
+        if (!has && req->key == 0)
+            return fail(HEC_ERR_INVALID, "a request without a matrix needs a key");
+        if (has && (!req->A.col || !req->A.val))
+            return fail(HEC_ERR_INVALID, "invalid request matrix");
+        const int n = req->A.n;
+        if (n < 1 || req->ilu_k < 0 || (has && (req->A.row_ptr[0] != 0 || req->A.row_ptr[n] != req->A.nnz)))
+            return fail(HEC_ERR_INVALID, "invalid request matrix");
+        Request q;
+        q.tag = req->tag;
+        q.key = req->key;
+        q.n = n;
+        q.k = req->ilu_k;
+        q.has_matrix = has;
+        if (has) {
+            q.rp.assign(req->A.row_ptr, req->A.row_ptr + n + 1);
+            q.ci.assign(req->A.col, req->A.col + req->A.nnz);
+            q.va.assign(req->A.val, req->A.val + req->A.nnz);
+            q.pattern = pattern_hash(q.rp, q.ci);
+        }
+        q.b.assign(req->b, req->b + n);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->stopping)
+                return fail(HEC_ERR_INVALID, "server is shutting down");
+            q.ticket = S->next_ticket++;
+            q.t_submit = S->now();
+            if (ticket)
+                *ticket = q.ticket;
+            S->pending.push_back(std::move(q));
+        }
+        S->cv_work.notify_one();
+        return HEC_OK;
+    });
 }
 
 int hec_server_poll(hec_server_t S, hec_result_t *out, int32_t max, int32_t *count, int32_t wait_ms)
 {
-    if (!S || !count || (max > 0 && !out))
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    std::unique_lock<std::mutex> lk(S->mu);
-    if (S->finished.empty() && wait_ms > 0)
-        S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms),
-                            [&]() { return !S->finished.empty(); });
-    int c = 0;
-    while (c < max && !S->finished.empty()) {
-        out[c++] = S->finished.front();
-        S->finished.pop_front();
-    }
-    *count = c;
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!S || !count || (max > 0 && !out))
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->finished.empty() && wait_ms > 0)
+            S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms),
+                                [&]() { return !S->finished.empty(); });
+        int c = 0;
+        while (c < max && !S->finished.empty()) {
+            out[c++] = S->finished.front();
+            S->finished.pop_front();
+        }
+        *count = c;
+        return HEC_OK;
+    });
 }
 
 int hec_server_solution(hec_server_t S, uint64_t ticket, double *x, int32_t n)
 {
-    if (!S || !x)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->solutions.find(ticket);
-    if (it == S->solutions.end())
-        return fail(HEC_ERR_INVALID, "no stored solution for ticket %llu", (unsigned long long)ticket);
-    if ((size_t)n != it->second.size())
-        return fail(HEC_ERR_INVALID, "solution has %zu values, not %d", it->second.size(), n);
-    std::memcpy(x, it->second.data(), sizeof(double) * it->second.size());
-    S->solutions.erase(it);
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!S || !x)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->solutions.find(ticket);
+        if (it == S->solutions.end())
+            return fail(HEC_ERR_INVALID, "no stored solution for ticket %llu", (unsigned long long)ticket);
+        if ((size_t)n != it->second.size())
+            return fail(HEC_ERR_INVALID, "solution has %zu values, not %d", it->second.size(), n);
+        std::memcpy(x, it->second.data(), sizeof(double) * it->second.size());
+        S->solutions.erase(it);
+        return HEC_OK;
+    });
 }
 
 double hec_server_clock(hec_server_t S) { return S ? S->now() : 0.0; }
@@ -476,18 +488,20 @@ double hec_server_clock(hec_server_t S) { return S ? S->now() : 0.0; }
 int hec_server_stats(hec_server_t S, int32_t *queued, int32_t *running, int32_t *finished,
                      int64_t *reserved_bytes)
 {
-    if (!S)
-        return fail(HEC_ERR_INVALID, "invalid argument");
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (queued)
-        *queued = (int32_t)S->pending.size();
-    if (running)
-        *running = S->running;
-    if (finished)
-        *finished = (int32_t)S->finished.size();
-    if (reserved_bytes)
-        *reserved_bytes = S->reserved;
-    return HEC_OK;
+    return abi_guard(__func__, [&]() -> int {
+        if (!S)
+            return fail(HEC_ERR_INVALID, "invalid argument");
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (queued)
+            *queued = (int32_t)S->pending.size();
+        if (running)
+            *running = S->running;
+        if (finished)
+            *finished = (int32_t)S->finished.size();
+        if (reserved_bytes)
+            *reserved_bytes = S->reserved;
+        return HEC_OK;
+    });
 }
 
 void hec_server_destroy(hec_server_t S)

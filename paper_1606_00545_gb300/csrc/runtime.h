@@ -9,7 +9,9 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -36,6 +38,22 @@ int check_launch(const char *what);
         if (r_ != HEC_OK)                                                                         \
             return r_;                                                                            \
     } while (0)
+
+// Runs the body of a C ABI entry point.  A C++ exception (a host allocation
+// that failed, a vector larger than it can be, a thread that could not start)
+// becomes an error code and a message instead of crossing the ABI.
+template <class F> int abi_guard(const char *where, F &&body) noexcept
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return fail(HEC_ERR_OOM, "%s: host memory exhausted", where);
+    } catch (const std::exception &e) {
+        return fail(HEC_ERR_INVALID, "%s: %s", where, e.what());
+    } catch (...) {
+        return fail(HEC_ERR_INVALID, "%s: unknown exception", where);
+    }
+}
 
 // The allocator registered with hec_set_allocator (both null: cudaMalloc).
 struct AllocFns {

@@ -147,6 +147,20 @@ def test_setup_errors(H):
         assert e.value.status in (H.ERR_INVALID, H.ERR_UNSORTED_CSR)
 
 
+def test_cpp_exception_does_not_cross_the_abi(H):
+    """An ELL slab larger than a host vector can hold makes the C++ setup
+    throw; the entry point returns an error code with a message instead (the
+    process keeps running, the next call works)."""
+    A = synth.poisson2d_5pt(4)
+    with pytest.raises(H.HecError) as e:
+        H.hec_build(A.row_ptr, A.col, A.val, ell_width=2 ** 31 - 1,
+                    ell_ld_align=2 ** 31 - 32, host_only=True)
+    assert e.value.status in (H.ERR_INVALID, H.ERR_OOM)
+    assert "hec_build" in str(e.value)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    assert M.info()["n"] == A.n
+
+
 # ------------------------------------------------------------------ factor layout
 # The level-major chunk layout that the triangular-solve kernel streams,
 # executed on the host from its bytes: a check of the packer (positions,
