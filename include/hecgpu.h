@@ -472,7 +472,8 @@ void hec_batch_destroy(hec_batch_t B);
  * nonzero key they stay resident afterwards too (least recently used evicted
  * first when the budget needs room), and later requests with the same key
  * reuse them without setup (a key serves one request at a time: a request
- * whose key is in use waits, and later requests may start before it).  Systems of at most small_rows unknowns run on
+ * whose key is in use waits, and later requests may start before it).
+ * Systems of at most small_rows unknowns run on
  * the batched kernel as one-CTA launches, larger ones on the single-system
  * path with RAS blocks of about block_rows rows.  A request's result depends
  * only on the request: it is bit-identical alone and in any mix.  The paper
@@ -501,7 +502,9 @@ typedef struct {
     int32_t reserved;
     uint64_t key;     /* 0: nothing kept; else requests with equal keys reuse the
                          resident set-up form: without a matrix as it is; with a
-                         matrix of the same sparsity pattern and level, refactored
+                         matrix of the same sparsity pattern (row_ptr and col,
+                         compared by entry count and a 64-bit FNV-1a hash) and
+                         level, refactored
                          on the GPU with the new values (hec_refactor); with
                          another pattern (or for a one-CTA batched system), set
                          up again                                                  */
