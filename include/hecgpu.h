@@ -48,7 +48,7 @@ extern "C" {
 /* ---------------------------------------------------------------- status */
 #define HEC_OK 0
 #define HEC_ERR_INVALID (-1)      /* bad argument or handle state            */
-#define HEC_ERR_OOM (-2)          /* the allocator returned NULL             */
+#define HEC_ERR_OOM (-2)          /* device or host memory exhausted         */
 #define HEC_ERR_ZERO_PIVOT (-3)   /* ILU(k) met a pivot equal to zero        */
 #define HEC_ERR_UNSORTED_CSR (-4) /* columns not strictly ascending / range  */
 #define HEC_ERR_CUDA (-5)         /* a CUDA runtime call failed              */
