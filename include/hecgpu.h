@@ -346,8 +346,9 @@ int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *strea
  * Algorithm 4, restarted GMRES(restart) or preconditioned CG (opts->method),
  * M == NULL meaning no preconditioner; M is an ILU(k)/RAS or a damped-Jacobi
  * handle.  Convergence: ||r|| <= tol ||b|| (BiCGSTAB, CG: the recursive
- * residual; GMRES: the true residual checked at every cycle end).  b and x are device or host arrays of n doubles (host arrays are
- * staged through device memory; the byte counts are reported in info);
+ * residual; GMRES: the true residual checked at every cycle end).  b and x
+ * are device or host arrays of n doubles (host arrays are staged through
+ * device memory; the byte counts are reported in info);
  * x holds x0 on entry unless HEC_X0_ZERO, and the solution on exit.  The
  * whole iteration runs on the device as one CUDA graph with a device-side
  * loop condition; the call synchronises the stream at the end.  Returns
@@ -355,6 +356,22 @@ int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *strea
 int krylov_solve(hec_matrix_t A, hec_precond_t M, const double *b, double *x, double tol,
                  int32_t maxit, int32_t restart, const hec_solve_opts_t *opts, void *stream,
                  hec_solve_info_t *info);
+/* Device bytes that the first krylov_solve(A, M, ..., restart, opts) with
+ * these method, restart and precision arguments allocates beyond what the
+ * handles already hold (*bytes; 0 once such a solve has run, since the
+ * workspace stays cached in the handles):
+ *   - the solver's FP64 vectors and Krylov basis (and, for HEC_MIXED_FP32,
+ *     its FP32 ones), padded to a multiple of 32 entries;
+ *   - its device-resident state and the reduction scratch, which scales with
+ *     the device's SM count;
+ *   - with HEC_MIXED_FP32, the FP32 copies of A's values and of M's factor
+ *     layout (or Jacobi diagonal) that the first mixed solve makes.  The
+ *     FP32 layout is packed on the host here to be counted.
+ * A mixed solve that finishes in FP64 also allocates what this call
+ * reports without HEC_MIXED_FP32.  Host work only; host-only handles
+ * work.  HEC_ERR_INVALID for arguments krylov_solve would reject. */
+int hec_workspace_bytes(hec_matrix_t A, hec_precond_t M, int32_t restart,
+                        const hec_solve_opts_t *opts, int64_t *bytes);
 
 /* ---------------------------------------------------------------- batches */
 /* Many independent systems A_s x_s = b_s (s = 0 .. nsys-1), each with nrhs

@@ -116,9 +116,13 @@ namespace {
 struct Reducer {
     DevBuf partials, ticket;
     RedScratch r{};
+    static int capacity()
+    {
+        return std::max(device_sms() * 8 * kMaxDots, device_sms() * 4 * (kMaxRestart + 1));
+    }
     int init(cudaStream_t s)
     {
-        const int cap = std::max(device_sms() * 8 * kMaxDots, device_sms() * 4 * (kMaxRestart + 1));
+        const int cap = capacity();
         HEC_TRY(partials.alloc((size_t)cap * sizeof(double), s));
         HEC_TRY(ticket.alloc(sizeof(unsigned), s));
         HEC_CK(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
@@ -948,16 +952,32 @@ int run_eager(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t s)
     return seq_exit(A, S, s);
 }
 
-int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool mixed,
-                cudaStream_t s, Solver *&out)
+// FP64 and FP32 vectors (of the padded length) of a solver's workspace.
+int solver_vecs64(int method, int restart, bool mixed)
+{
+    return method == HEC_BICGSTAB ? 10 : method == HEC_CG ? 6 : (mixed ? 3 : (restart + 1) + 7);
+}
+int solver_vecs32(int restart, bool mixed) { return mixed ? (restart + 1) + 4 : 0; }
+
+// The solver (workspace, graph) cached in the handles for these arguments.
+Solver *cached_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool mixed)
 {
     auto &cache = M ? M->solvers : A->solvers;
     for (auto &p : cache)
         if (p->matrix_id == A->id && p->method == method && p->mixed == mixed &&
-            (method != HEC_GMRES || p->restart == restart)) {
-            out = p.get();
-            return HEC_OK;
-        }
+            (method != HEC_GMRES || p->restart == restart))
+            return p.get();
+    return nullptr;
+}
+
+int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool mixed,
+                cudaStream_t s, Solver *&out)
+{
+    auto &cache = M ? M->solvers : A->solvers;
+    if (Solver *c = cached_solver(A, M, method, restart, mixed)) {
+        out = c;
+        return HEC_OK;
+    }
     std::unique_ptr<Solver> S(new Solver());
     S->matrix_id = A->id;
     S->method = method;
@@ -966,14 +986,12 @@ int make_solver(hec_matrix_s *A, hec_precond_s *M, int method, int restart, bool
     S->n = A->hec.n;
     S->ldv = ((int64_t)S->n + 31) / 32 * 32;
     const int64_t nv = S->ldv;
-    const int nvec = method == HEC_BICGSTAB ? 10
-                     : method == HEC_CG  ? 6
-                                         : (mixed ? 3 : (restart + 1) + 7);
+    const int nvec = solver_vecs64(method, restart, mixed);
     HEC_TRY(S->ws.alloc((size_t)nvec * nv * sizeof(double), s));
     HEC_CK(cudaMemsetAsync(S->ws.p, 0, S->ws.bytes, s));
     if (mixed) {
         // FP32 basis and step vectors of the inner cycles
-        HEC_TRY(S->ws32.alloc((size_t)((restart + 1) + 4) * nv * sizeof(float), s));
+        HEC_TRY(S->ws32.alloc((size_t)solver_vecs32(restart, mixed) * nv * sizeof(float), s));
         HEC_CK(cudaMemsetAsync(S->ws32.p, 0, S->ws32.bytes, s));
     }
     HEC_TRY(S->st_buf.alloc(sizeof(SolverState), s));
@@ -1831,6 +1849,63 @@ int hec_refactor(hec_matrix_t A, hec_precond_t M, const double *val, void *strea
                 return fail(err, "numeric refactorisation: a pivot is zero");
             }
         }
+        return HEC_OK;
+    });
+}
+
+int hec_workspace_bytes(hec_matrix_t A, hec_precond_t M, int32_t restart,
+                        const hec_solve_opts_t *opts, int64_t *bytes)
+{
+    return abi_guard(__func__, [&]() -> int {
+        if (!A || !bytes)
+            return fail(HEC_ERR_INVALID, "null argument");
+        *bytes = 0;
+        if (M && (M->matrix_id != A->id))
+            return fail(HEC_ERR_INVALID, "preconditioner was built from another matrix");
+        if (M && !M->scheduled)
+            return fail(HEC_ERR_INVALID, "level_schedule has not run");
+        hec_solve_opts_t o{};
+        if (opts)
+            o = *opts;
+        if (o.method != HEC_GMRES && o.method != HEC_BICGSTAB && o.method != HEC_CG)
+            return fail(HEC_ERR_INVALID, "unknown method");
+        if (o.method == HEC_GMRES && (restart < 1 || restart > kMaxRestart))
+            return fail(HEC_ERR_INVALID, "restart must be in 1..%d", kMaxRestart);
+        if (o.method != HEC_GMRES)
+            restart = 0;
+        const bool mixed = (o.flags & HEC_MIXED_FP32) != 0;
+        if (mixed && o.method != HEC_GMRES)
+            return fail(HEC_ERR_INVALID, "HEC_MIXED_FP32 needs method HEC_GMRES");
+        // a device allocation of 0 bytes takes 16 (DevBuf)
+        auto dev = [](int64_t b) { return b > 0 ? b : (int64_t)16; };
+        int64_t total = 0;
+        if (!cached_solver(A, M, o.method, restart, mixed)) {
+            const int64_t nv = ((int64_t)A->hec.n + 31) / 32 * 32;
+            total += dev(solver_vecs64(o.method, restart, mixed) * nv * (int64_t)sizeof(double));
+            if (mixed)
+                total += dev(solver_vecs32(restart, mixed) * nv * (int64_t)sizeof(float));
+            total += (int64_t)sizeof(SolverState) + (int64_t)Reducer::capacity() * 8 +
+                     (int64_t)sizeof(unsigned);
+        }
+        if (mixed && !A->f32_ready)
+            total += dev((int64_t)A->hec.ell_val.size() * 4) + dev((int64_t)A->hec.tail_val.size() * 4);
+        if (mixed && M && M->kind == kJacobi && !M->dinv32.p)
+            total += dev((int64_t)M->n * 4);
+        if (mixed && M && M->kind != kJacobi && !M->lay[1].built) {
+            // the FP32 layout the first mixed solve packs and uploads, packed
+            // here on the host to be counted
+            TrsvPack P;
+            std::string msg;
+            const int fw = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
+                                                       max_factor_width(M->blocks, true)));
+            const int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw);
+            if (rc != HEC_OK)
+                return fail(rc, "%s", msg.c_str());
+            total += dev((int64_t)P.pack.size()) + dev((int64_t)(P.chunks.size() * sizeof(uint2))) +
+                     dev((int64_t)(P.blocks.size() * sizeof(TrsvBlock))) +
+                     std::max<int64_t>(P.ysz, 1) * 4 + std::max<int64_t>(P.zsz, 1) * 4;
+        }
+        *bytes = total;
         return HEC_OK;
     });
 }

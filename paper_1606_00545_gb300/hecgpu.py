@@ -166,6 +166,7 @@ _SIGS = {
     "hec_precond_destroy": ([_vp], None),
     "krylov_solve": ([_vp, _vp, _vp, _vp, _dbl, _i32, _i32, C.POINTER(SolveOpts_t), _vp,
                       C.POINTER(SolveInfo_t)], C.c_int),
+    "hec_workspace_bytes": ([_vp, _vp, _i32, C.POINTER(SolveOpts_t), C.POINTER(_i64)], C.c_int),
     "hec_build_batched": ([C.POINTER(BatchCSR_t), C.POINTER(BatchConfig_t), _vp, C.POINTER(_vp)],
                           C.c_int),
     "ilu_k_setup_batched": ([_vp, _i32], C.c_int),
@@ -522,6 +523,17 @@ def krylov_solve(A: Matrix, M, b, x, tol=1e-8, maxit=1000, restart=30, method=GM
                                      _stream(stream), C.byref(inf))
     _check(rc, "krylov_solve", ok=(OK, MAXIT, BREAKDOWN))
     return {f: getattr(inf, f) for f, _ in SolveInfo_t._fields_ if f != "reserved"}
+
+
+def hec_workspace_bytes(A: Matrix, M, restart=30, method=GMRES, flags=0) -> int:
+    """Device bytes the first krylov_solve with these arguments allocates
+    beyond what the handles hold (0 once such a solve has run)."""
+    o = SolveOpts_t(int(method), int(flags), 0)
+    nb = _i64()
+    _check(load_library().hec_workspace_bytes(A.handle, M.handle if M is not None else None,
+                                              int(restart), C.byref(o), C.byref(nb)),
+           "hec_workspace_bytes")
+    return nb.value
 
 
 # ------------------------------------------------------------------ batches

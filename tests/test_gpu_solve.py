@@ -231,3 +231,22 @@ def test_nan_rhs_ends_in_breakdown(H, orc, method, flags):
     info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=2000, restart=30, method=m, flags=fl)
     assert info["status"] == H.OK
     assert true_rel_resid(orc, A, b, host(x)) <= 1e-8
+
+
+def test_workspace_bytes_zero_once_solved(H):
+    """hec_workspace_bytes counts what the first solve with given arguments
+    allocates; once that solve has run, its workspace (and, for the mixed
+    form, the FP32 copies) stays cached in the handles and the count is 0."""
+    A = synth.diffusion2d_5pt_lognormal(30, 1.0, 2)
+    b = synth.rhs_uniform(A.n, 3)
+    M, P = setup(H, A, 0, 2, 1)
+    for method, restart, flags in ((H.GMRES, 20, 0), (H.GMRES, 20, H.MIXED_FP32),
+                                   (H.BICGSTAB, 0, 0)):
+        assert H.hec_workspace_bytes(M, P, restart, method, flags) > 0
+        x = dev(np.zeros(A.n))
+        info = H.krylov_solve(M, P, dev(b), x, tol=1e-8, maxit=500, restart=max(restart, 1),
+                              method=method, flags=flags)
+        assert info["status"] == H.OK
+        assert H.hec_workspace_bytes(M, P, restart, method, flags) == 0
+    assert H.hec_workspace_bytes(M, P, 25, H.GMRES) > 0  # another restart length
+    assert H.hec_workspace_bytes(M, None, 0, H.CG) > 0  # no preconditioner: its own cache

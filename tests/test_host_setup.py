@@ -333,3 +333,35 @@ def test_factor_layout_errors(H):
         P.layout()  # before level_schedule
     H.level_schedule(P)
     assert P.layout()["chunks"].shape[0] > 0
+
+
+def test_workspace_bytes_query(H):
+    """hec_workspace_bytes on host-only handles: each extra GMRES restart step
+    costs one padded basis vector (FP64, or FP32 in the mixed form), BiCGSTAB
+    keeps four vectors more than CG, and the mixed count drops by exactly
+    the FP32 layout's device bytes once that layout exists."""
+    A = synth.diffusion3d_7pt_lognormal(9, 2.0, 1)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, 1, 3, 1)
+    H.level_schedule(P)
+    nv = (A.n + 31) // 32 * 32
+    q = H.hec_workspace_bytes
+    assert q(M, P, 50, H.GMRES) - q(M, P, 30, H.GMRES) == 20 * nv * 8
+    assert q(M, P, 0, H.BICGSTAB) - q(M, P, 0, H.CG) == 4 * nv * 8
+    assert q(M, None, 0, H.CG) == q(M, P, 0, H.CG)
+    m30 = q(M, P, 30, H.GMRES, H.MIXED_FP32)
+    assert q(M, P, 50, H.GMRES, H.MIXED_FP32) - m30 == 20 * nv * 4
+    lay = P.layout(fp32=True)  # packs the FP32 layout (host-only: nothing uploaded)
+    heads = [np.frombuffer(lay["pack"], np.int32, 4, int(c) * 16) for c in lay["chunks"][:, 0]]
+    ysz = zsz = 0
+    for c0, cm, c1, _, ring_u, _, _ in lay["blocks"]:
+        ysz += int(heads[cm - 1][2] + heads[cm - 1][0])
+        if not ring_u:
+            zsz += int(heads[c1 - 1][2] + heads[c1 - 1][0])
+    layout_bytes = (len(lay["pack"]) + 8 * len(lay["chunks"]) + 40 * len(lay["blocks"]) +
+                    4 * max(ysz, 1) + 4 * max(zsz, 1))
+    assert m30 - q(M, P, 30, H.GMRES, H.MIXED_FP32) == layout_bytes
+    for bad in (dict(restart=0, method=H.GMRES), dict(restart=500, method=H.GMRES),
+                dict(restart=0, method=H.BICGSTAB, flags=H.MIXED_FP32), dict(restart=30, method=7)):
+        with pytest.raises(H.HecError):
+            q(M, P, **bad)
