@@ -190,8 +190,10 @@ int hec_matrix_export(hec_matrix_t A, int32_t *ell_col, double *ell_val, int32_t
 void hec_matrix_destroy(hec_matrix_t A);
 
 /* Eq. 2 (Algorithm 1): y_out = alpha * A x + beta * y_in on the device.
- * y_in may equal y_out; it is not read when beta == 0; x must not overlap y_out.  x, y_in, y_out:
- * device arrays of n doubles.  When dots != NULL (device, 2 doubles) the
+ * y_in may equal y_out; it is not read when beta == 0; x must not overlap
+ * y_out.  x, y_in, y_out: device arrays of n doubles; y_out must be 16-byte
+ * aligned (rows are stored in pairs; HEC_ERR_INVALID otherwise, before any
+ * device work).  When dots != NULL (device, 2 doubles) the
  * reductions of the result are fused into the same launch:
  * dots[0] = (w, y_out) (w: device array of n doubles; NULL means y_out) and
  * dots[1] = (y_out, y_out), each summed in a fixed order (deterministic). */
@@ -201,7 +203,7 @@ int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const d
 /* The FP32 SpMV of the mixed-precision inner solves, Eq. 2 with FP32 values
  * (the matrix's values rounded once to FP32, kept beside the FP64 ones after
  * the first FP32 call), FP32 products and accumulation.  x, y_in, y_out:
- * device arrays of n floats; no fused dots. */
+ * device arrays of n floats, y_out 8-byte aligned; no fused dots. */
 int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const float *y_in,
                  float *y_out, void *stream);
 

@@ -1387,6 +1387,9 @@ int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const d
     return abi_guard(__func__, [&]() -> int {
         if (!A || !x || !y_out)
             return fail(HEC_ERR_INVALID, "null argument");
+        // a thread stores its two adjacent rows with one 16-byte store
+        if (reinterpret_cast<uintptr_t>(y_out) % (2 * sizeof(double)) != 0)
+            return fail(HEC_ERR_INVALID, "y_out must be 16-byte aligned");
         if (A->host_only)
             return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
         if (beta != 0.0 && !y_in)
@@ -1415,6 +1418,9 @@ int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const 
     return abi_guard(__func__, [&]() -> int {
         if (!A || !x || !y_out)
             return fail(HEC_ERR_INVALID, "null argument");
+        // a thread stores its two adjacent rows with one 8-byte store
+        if (reinterpret_cast<uintptr_t>(y_out) % (2 * sizeof(float)) != 0)
+            return fail(HEC_ERR_INVALID, "y_out must be 8-byte aligned");
         if (A->host_only)
             return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
         if (beta != 0.0f && !y_in)

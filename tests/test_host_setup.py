@@ -365,3 +365,25 @@ def test_workspace_bytes_query(H):
                 dict(restart=0, method=H.BICGSTAB, flags=H.MIXED_FP32), dict(restart=30, method=7)):
         with pytest.raises(H.HecError):
             q(M, P, **bad)
+
+
+def test_spmv_rejects_misaligned_output(H):
+    """The SpMV stores two adjacent rows per thread with one vector store, so
+    y_out must be 16-byte (FP64) or 8-byte (FP32) aligned; a misaligned
+    output is rejected before any device work (the addresses below are
+    never dereferenced)."""
+    import ctypes
+    A = synth.poisson2d_5pt(4)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    lib = H.load_library()
+    x = ctypes.c_void_p(0x10000)
+    for y, f32 in ((0x20008, False), (0x20004, True)):
+        if f32:
+            rc = lib.hec_spmv_f32(M.handle, 1.0, x, 0.0, None, ctypes.c_void_p(y), None)
+        else:
+            rc = lib.hec_spmv(M.handle, 1.0, x, 0.0, None, ctypes.c_void_p(y), None, None, None)
+        assert rc == H.ERR_INVALID
+        assert b"aligned" in lib.hec_last_error()
+    # aligned: rejected for the host-only handle instead, after the alignment check
+    rc = lib.hec_spmv(M.handle, 1.0, x, 0.0, None, ctypes.c_void_p(0x20010), None, None, None)
+    assert rc == H.ERR_INVALID and b"host-only" in lib.hec_last_error()
