@@ -6,6 +6,7 @@ are rebuilt when a source or header is newer than the library.
 """
 from __future__ import annotations
 
+import fcntl
 import glob
 import os
 import subprocess
@@ -33,13 +34,29 @@ def _deps():
         os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "hecgpu.h"), __file__]
 
 
+def _current() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(d) <= t for d in _deps())
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library if anything changed; return its path."""
+    """Compile and link the library if anything changed; return its path.
+    Processes that build at the same time (the ranks of one launch, parallel
+    test workers) take turns on a lock file: one compiles, the others then
+    find the library current."""
     os.makedirs(OUT, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(d) <= t for d in _deps()):
+    if not force and _current():
+        return LIB
+    with open(os.path.join(OUT, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and _current():
             return LIB
+        return _compile(verbose)
+
+
+def _compile(verbose: bool) -> str:
     nvcc = _nvcc()
     common = ["-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
