@@ -80,6 +80,8 @@ def parse():
                          "of Table 3's comparison): HEC SpMV with the ELL width forced to 1 "
                          "(almost all CSR tail), chosen by the one-third rule (HEC), or the "
                          "longest row (pure ELL), on regular, irregular and heavy-tailed rows")
+    ap.add_argument("--parts", type=int, default=0,
+                    help="CTAs per RAS block of the triangular solve (0: automatic)")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32", "batch"],
                     default=None,
                     help="profiling mode: set up the workload, then launch only this kernel "
@@ -98,7 +100,7 @@ def run_kernel_only(args, local_rank):
     A, b = workload()
     Ah = H.hec_build(A.row_ptr, A.col, A.val)
     P = H.ilu_k_setup(Ah, K_FILL, NBLOCKS, OVERLAP)
-    H.level_schedule(P)
+    H.level_schedule(P, parts=args.parts)
     fp32 = args.kernel.endswith("32")
     r = torch.tensor(b, device=dev, dtype=torch.float32 if fp32 else torch.float64)
     z = torch.empty_like(r)
@@ -128,7 +130,7 @@ def run_kernel_only(args, local_rank):
     nbytes = {"trsv": inf["apply_bytes"], "trsv32": inf["apply_bytes_f32"],
               "spmv": A.nnz * 12 + A.n * 16, "spmv32": A.nnz * 8 + A.n * 8}[args.kernel]
     print(json.dumps({"kernel": args.kernel, "launches": args.steps, "ms_per_launch": ms,
-                      "alg_bytes": nbytes,
+                      "alg_bytes": nbytes, "trsv_parts": inf["trsv_parts"],
                       "gbs": nbytes / (ms * 1e-3) / 1e9 if ms else None}))
 
 
@@ -286,13 +288,14 @@ LAYOUT_MARKER = b"// -----------------------------------------------------------
 
 
 def kernel_source_sha():
-    """Hash of the triangular-solve kernel, its PTX helpers, and the part of the
-    host setup that decides the layout it streams (RAS blocks, ILU(k) pattern,
-    levels, chunk packing: hec_setup.cpp from its RAS section on; the input
-    checks and the HEC conversion before it do not touch that layout)."""
+    """Hash of the triangular-solve kernel, its PTX helpers, the chunk packer
+    (trsv_layout.cpp) and the part of the host setup that decides the rows it
+    packs (RAS blocks, ILU(k) pattern, levels: hec_setup.cpp from its RAS
+    section on; the input checks and the HEC conversion before it do not
+    touch that layout)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1606_00545_gb300", "csrc")
-    for f in ("k_trsv.cu", "ptx.cuh"):
+    for f in ("k_trsv.cu", "ptx.cuh", "trsv_layout.cpp"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "hec_setup.cpp"), "rb") as fh:

@@ -53,6 +53,9 @@ extern "C" {
 #define HEC_ERR_UNSORTED_CSR (-4) /* columns not strictly ascending / range  */
 #define HEC_ERR_CUDA (-5)         /* a CUDA runtime call failed              */
 #define HEC_ERR_TIMEOUT (-6)      /* a bounded device wait ran out           */
+#define HEC_ERR_DEBUG (-7)        /* a device-side check of the debug build
+                                     (compiled with HEC_DEBUG) failed; see
+                                     hec_debug_record                       */
 #define HEC_MAXIT 1               /* solver stopped at maxit                 */
 #define HEC_BREAKDOWN 2           /* BiCGSTAB rho = 0, (r0,v) = 0, omega = 0  */
 
@@ -109,6 +112,11 @@ typedef struct {
                                 not fit the window and are read from global
                                 memory instead                                */
     int64_t apply_bytes_f32; /* the same for the FP32 layout (0 until built)   */
+    int32_t trsv_parts;      /* CTAs per RAS block of the triangular solve     */
+    int32_t import_slots;    /* shared-memory window of values received from a
+                                neighbouring CTA (0: no block is split)        */
+    int32_t split_blocks;    /* RAS blocks solved by more than one CTA         */
+    int32_t reserved;
 } hec_precond_info_t;
 
 #define HEC_GMRES 0
@@ -264,30 +272,66 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
  * 2.6, Eq. 11: the rows of every level of L_b, then of U_b), host copies, for
  * inspection and host-side checks.  fp32 = 0: the FP64 layout; fp32 = 1: the
  * FP32 layout of the mixed-precision mode (packed, and on a device handle
- * uploaded, on first request).  *pack_bytes, *nchunks, *ring_slots (the
- * shared-memory window of solved values, a power of two) and *fixed_width
+ * uploaded, on first request).  *pack_bytes, *nchunks, *ring_slots (R, the
+ * shared-memory window of a CTA's own solved values, a power of two),
+ * *import_slots (RI, the window of values received from a neighbouring CTA;
+ * 0 when no block is split), *parts (P, CTAs per RAS block) and *fixed_width
  * (0, or the one segment width of every warp) are always set; pack
  * (pack_bytes bytes), chunks (2 per chunk: byte offset / 16, byte count) and
- * blocks (7 per RAS block: first chunk, first U chunk, end chunk, ring_L,
- * ring_U -- 1 when that pass reads dependencies from the ring, 0 when from
- * the global scratch -- and the block's y and z scratch offsets) may be NULL.
+ * programs (8 per CTA, nblocks * P of them, block b's part p at b * P + p:
+ * first chunk, first U chunk, end chunk, ring_L, ring_U -- 1 when that pass
+ * reads dependencies from shared memory, 0 when from the global scratch --
+ * the program's y and z scratch offsets, and links: bit 0 when part p - 1 of
+ * the block exists, bit 1 when part p + 1 does) may be NULL.
  *
- * A chunk holds rows of one level.  It starts with 24 int32: row count,
- * warp count, level-major position of its first row, flags (bit 0: U pass),
- * the entry width of each of 8 warp segments, each segment's byte offset,
- * and the byte offsets of src, dst and dinv.  Segment w covers rows 32w ..
- * 32w+31 as val[width][stride] (8- or 4-byte values) then dep[width][stride]
- * (int32 level-major positions of the same pass); stride is 32, or for the
- * last warp its row count rounded up to 4.  Row t of the L pass computes
+ * A part is a contiguous range of the block's local rows; L_b is lower
+ * triangular in that order, so in the L pass part p reads only its own and
+ * part p - 1's values, in the U pass its own and part p + 1's.  A block is
+ * split only when no dependency reaches further.
+ *
+ * A chunk holds rows of one level.  It starts with 28 int32: row count,
+ * warp count, position (in the part's level-major order) of its first row,
+ * flags (bit 0: U pass, bit 1: exports, bit 2: no warp segment wider than
+ * 8 entries), the entry width of each of 8 warp
+ * segments, each segment's byte offset, the byte offsets of src, dst, dinv
+ * and exp, need_prev and need_next (the completed-chunk counts of parts
+ * p - 1 and p + 1 this chunk waits for), and two zeros.  Segment w covers
+ * rows 32w .. 32w+31 as val[width][stride] (8- or 4-byte values) then
+ * dep[width][stride] (int32); stride is 32, or for the last warp its row
+ * count rounded up to 4.  In a pass read from shared memory dep is a slot:
+ * own values at slot position & (R - 1), values from the neighbouring part
+ * at R + (import position & (RI - 1)); otherwise dep is a position of the
+ * same pass in the global scratch.  Row t of the L pass computes
  * y[pos] = r[src[t]] - sum_k val[k] y[dep[k]]; of the U pass
  * z[pos] = (y[src[t]] - sum_k val[k] z[dep[k]]) * dinv[t], written to
- * global row dst[t] when dst[t] >= 0 (an owned row).  Padding entries have
- * value 0.  The stream must be NULL or a CUDA stream; a device handle's
- * layout is read back on it (synchronously).  HEC_ERR_INVALID for a
- * damped-Jacobi handle or before level_schedule. */
+ * global row dst[t] when dst[t] >= 0 (an owned row).  exp[t] >= 0 is the
+ * slot that row's value takes in the neighbour's ring (L: part p + 1, U:
+ * part p - 1).  Padding entries have value 0.  The stream must be NULL or a
+ * CUDA stream; a device handle's layout is read back on it (synchronously).
+ * HEC_ERR_INVALID for a damped-Jacobi handle or before level_schedule. */
 int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
-                           int32_t *ring_slots, int32_t *fixed_width, void *pack,
-                           uint32_t *chunks, int64_t *blocks, void *stream);
+                           int32_t *ring_slots, int32_t *import_slots, int32_t *parts,
+                           int32_t *fixed_width, void *pack, uint32_t *chunks, int64_t *programs,
+                           void *stream);
+/* CTAs that solve each RAS block's triangular systems (Section 2.6: the
+ * rows of one level are independent, so they may be spread over several
+ * SMs): 0 = automatic (split while the widest block's levels hold more than
+ * 128 rows per CTA and nblocks * P CTAs fit on the device's SMs), or 1, 2, 4
+ * or 8.  The CTAs of one block run as one thread-block cluster.  A block
+ * whose dependencies do not allow the split gets fewer parts.  Call it
+ * between ilu_k_setup and level_schedule; HEC_ERR_INVALID afterwards, for a
+ * damped-Jacobi handle or another value. */
+int hec_precond_set_trsv_parts(hec_precond_t M, int32_t parts);
+/* Debug builds (compiled with HEC_DEBUG; not a counterpart of anything in the
+ * paper): the triangular-solve kernel checks every chunk header against the
+ * position its program has reached, every gathered index against n, and
+ * every dependency slot against the ring, and on a violation skips the
+ * access, sets the error word to HEC_ERR_DEBUG and records the first one.
+ * record: 8 int32 -- code (1 pass flag, 2 row count, 3 gathered index,
+ * 4 chunk position, 5 ring slot, 6 scratch position, 7 destination row;
+ * 0 = none), program, chunk, thread, value, bound, 0, 0.  clear != 0 resets
+ * it.  HEC_ERR_INVALID in a release build. */
+int hec_debug_record(int32_t *record, int32_t clear);
 /* z = M^{-1} r (Eq. 7 with M = the RAS combination of L_b U_b): every block
  * gathers r on V_b, solves L_b then U_b level by level, and writes z on its
  * owned rows only.  r, z: device arrays of n doubles, r != z.  Needs

@@ -2,7 +2,9 @@
 
 Each translation unit is compiled in parallel (one ``-gencode``), then linked
 into one shared library with the CUDA runtime linked statically.  Object files
-are rebuilt when a source or header is newer than the library.
+are rebuilt when a source or header is newer than the library.  ``debug=True``
+builds the same sources with ``-DHEC_DEBUG`` (device-side checks) into
+``_build/debug/libhecgpu.so``.
 """
 from __future__ import annotations
 
@@ -34,35 +36,44 @@ def _deps():
         os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "hecgpu.h"), __file__]
 
 
-def _current() -> bool:
-    if not os.path.exists(LIB):
+def _paths(debug: bool):
+    out = os.path.join(OUT, "debug") if debug else OUT
+    return out, os.path.join(out, "libhecgpu.so")
+
+
+def _current(lib: str) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     """Compile and link the library if anything changed; return its path.
     Processes that build at the same time (the ranks of one launch, parallel
     test workers) take turns on a lock file: one compiles, the others then
     find the library current."""
-    os.makedirs(OUT, exist_ok=True)
-    if not force and _current():
-        return LIB
-    with open(os.path.join(OUT, ".build.lock"), "w") as lock:
+    out, lib = _paths(debug)
+    os.makedirs(out, exist_ok=True)
+    if not force and _current(lib):
+        return lib
+    with open(os.path.join(out, ".build.lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
-        if not force and _current():
-            return LIB
-        return _compile(verbose)
+        if not force and _current(lib):
+            return lib
+        return _compile(verbose, debug)
 
 
-def _compile(verbose: bool) -> str:
+def _compile(verbose: bool, debug: bool = False) -> str:
+    out, lib = _paths(debug)
     nvcc = _nvcc()
     common = ["-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
+    if debug:
+        common.append("-DHEC_DEBUG")
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out, os.path.basename(src) + ".o")
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "c++"]
@@ -75,13 +86,13 @@ def _compile(verbose: bool) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc, "-gencode", GENCODE, "-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -175,7 +175,7 @@ struct TrsvLayout {
     DevBuf d_row0, d_rms, d_rml, d_rmd; // value maps of hec_refactor (uploaded on first use)
     int nstages = 8;
     int vbytes = 8;
-    int fixed_width = 0; // FP32 layout: uniform warp width (0: per-warp widths)
+    int fixed_width = 0; // uniform row width of the fixed-slot format (0: per-warp widths)
     bool built = false;
     int64_t device_bytes() const
     {
@@ -195,6 +195,7 @@ struct hec_precond_s {
     TrsvLayout lay[2]; // [0] FP64 values (level_schedule), [1] FP32 (built on first use)
     DevBuf d_err;
     int stage_bytes = 24576;
+    int trsv_parts = 0; // CTAs per RAS block of the triangular solve (0: automatic)
     std::vector<std::unique_ptr<Solver>> solvers;
     // hec_refactor: every block's factor on the device (entries numbered over
     // all blocks), its source map into A and the L level sets; the host copy
@@ -289,18 +290,22 @@ int run_vec(VecOp op, const VecArgs &a, cudaStream_t s)
 TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
 {
     TrsvArgs a{};
-    a.nblocks = M->nblocks;
+    a.nblocks = (int)L.pack.blocks.size();
+    a.parts = L.pack.parts;
+    a.import_slots = L.pack.import_slots;
     a.blocks = L.d_blocks.as<TrsvBlock>();
     a.chunks = L.d_chunks.as<uint2>();
     a.pack = L.d_pack.as<unsigned char>();
     a.ysc = L.d_ysc.p;
     a.zsc = L.pack.zsz ? L.d_zsc.p : nullptr;
     a.ring_mask = L.pack.ring_slots - 1;
-    a.stage_bytes = M->stage_bytes;
+    a.stage_bytes = L.pack.stage_bytes;
     a.nstages = L.nstages;
     a.fixed_width = L.fixed_width;
+    a.exp_arrays = L.pack.exp_arrays;
     a.spin_limit = spin;
     a.err = M->d_err.as<int>();
+    a.n = M->n;
     return a;
 }
 
@@ -330,6 +335,15 @@ int refresh_host_factors(hec_precond_s *M, cudaStream_t s)
     return HEC_OK;
 }
 
+// CTAs per RAS block: the handle's choice, else split while levels are wide
+// and the CTAs fit on the device's SMs (host-only handles: 152, GB300's count).
+int layout_parts(const hec_precond_s *M)
+{
+    if (M->trsv_parts > 0)
+        return M->trsv_parts;
+    return trsv_auto_parts(M->blocks, M->host_only ? 152 : device_sms());
+}
+
 // Pack, upload and size the scratch of the layout with vb-byte values.
 int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
 {
@@ -338,19 +352,20 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
         return HEC_OK;
     HEC_TRY(refresh_host_factors(M, s));
     L.vbytes = idx == 0 ? 8 : 4;
-    // FP32: pad every row to one short width when the factors allow it (the
-    // padding costs FP32 multiply-adds and bytes, and saves the per-warp
-    // width dispatch); FP64 keeps exact widths (its pipe is the bound)
-    L.fixed_width = idx == 1 ? trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
-                                                           max_factor_width(M->blocks, true)))
-                             : 0;
+    // pad every row to one short width when the factors allow it: the
+    // fixed-slot chunks that the kernel streams from registers one chunk ahead
+    // (the padding costs multiply-adds only where a warp's rows are shorter
+    // than the width)
+    L.fixed_width = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
+                                                max_factor_width(M->blocks, true)));
     std::string msg;
     int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg,
-                       L.fixed_width);
+                       L.fixed_width, layout_parts(M));
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
     if (!M->host_only) {
-        L.nstages = trsv_stages_for(M->stage_bytes, L.pack.ring_slots, L.vbytes);
+        L.nstages = trsv_stages_for(L.pack.stage_bytes,
+                                    L.pack.ring_slots + 2 * L.pack.import_slots, L.vbytes);
         HEC_TRY(upload(L.d_pack, L.pack.pack, s));
         HEC_TRY(upload(L.d_chunks, L.pack.chunks, s));
         HEC_TRY(upload(L.d_blocks, L.pack.blocks, s));
@@ -1656,6 +1671,13 @@ int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
         info->apply_bytes_f32 = M->lay[1].built ? M->lay[1].pack.alg_bytes : 0;
         for (const TrsvBlock &T : M->lay[0].pack.blocks)
             info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
+        info->trsv_parts = M->scheduled && M->kind != kJacobi ? M->lay[0].pack.parts : 0;
+        info->import_slots = M->scheduled && M->kind != kJacobi ? M->lay[0].pack.import_slots : 0;
+        {
+            const TrsvPack &P = M->lay[0].pack;
+            for (size_t q = 0; q < P.blocks.size(); q += (size_t)std::max(P.parts, 1))
+                info->split_blocks += (P.blocks[q].links & 2) ? 1 : 0;
+        }
         return HEC_OK;
     });
 }
@@ -1723,11 +1745,13 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
 }
 
 int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
-                           int32_t *ring_slots, int32_t *fixed_width, void *pack, uint32_t *chunks,
-                           int64_t *blocks, void *stream)
+                           int32_t *ring_slots, int32_t *import_slots, int32_t *parts,
+                           int32_t *fixed_width, void *pack, uint32_t *chunks, int64_t *programs,
+                           void *stream)
 {
     return abi_guard(__func__, [&]() -> int {
-        if (!M || (fp32 != 0 && fp32 != 1) || !pack_bytes || !nchunks || !ring_slots || !fixed_width)
+        if (!M || (fp32 != 0 && fp32 != 1) || !pack_bytes || !nchunks || !ring_slots ||
+            !import_slots || !parts || !fixed_width)
             return fail(HEC_ERR_INVALID, "bad arguments");
         if (M->kind == kJacobi)
             return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no factor layout");
@@ -1742,6 +1766,8 @@ int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, i
         *pack_bytes = total;
         *nchunks = (int32_t)L.pack.chunks.size();
         *ring_slots = L.pack.ring_slots;
+        *import_slots = L.pack.import_slots;
+        *parts = L.pack.parts;
         *fixed_width = L.fixed_width;
         if (pack && total > 0) {
             if (!L.pack.pack.empty()) {
@@ -1756,10 +1782,10 @@ int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, i
                 chunks[2 * c] = L.pack.chunks[c].x;
                 chunks[2 * c + 1] = L.pack.chunks[c].y;
             }
-        if (blocks)
+        if (programs)
             for (size_t b = 0; b < L.pack.blocks.size(); ++b) {
                 const TrsvBlock &T = L.pack.blocks[b];
-                int64_t *o = blocks + 7 * b;
+                int64_t *o = programs + 8 * b;
                 o[0] = T.chunk_begin;
                 o[1] = T.chunk_mid;
                 o[2] = T.chunk_end;
@@ -1767,7 +1793,37 @@ int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, i
                 o[4] = T.ring_U;
                 o[5] = T.yoff;
                 o[6] = T.zoff;
+                o[7] = T.links;
             }
+        return HEC_OK;
+    });
+}
+
+int hec_debug_record(int32_t *record, int32_t clear)
+{
+    return abi_guard(__func__, [&]() -> int {
+        if (!record)
+            return fail(HEC_ERR_INVALID, "null record");
+        if (!trsv_debug_build())
+            return fail(HEC_ERR_INVALID, "not a debug build (compile with HEC_DEBUG)");
+        int r[8];
+        if (trsv_debug_read(r, clear != 0) != 0)
+            return fail(HEC_ERR_CUDA, "cannot read the debug record");
+        std::memcpy(record, r, sizeof(r));
+        return HEC_OK;
+    });
+}
+
+int hec_precond_set_trsv_parts(hec_precond_t M, int32_t parts)
+{
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || (parts != 0 && parts != 1 && parts != 2 && parts != 4 && parts != 8))
+            return fail(HEC_ERR_INVALID, "parts must be 0 (automatic), 1, 2, 4 or 8");
+        if (M->kind == kJacobi)
+            return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no triangular solve");
+        if (M->scheduled)
+            return fail(HEC_ERR_INVALID, "set the parts before level_schedule");
+        M->trsv_parts = parts;
         return HEC_OK;
     });
 }
@@ -1904,7 +1960,8 @@ int hec_workspace_bytes(hec_matrix_t A, hec_precond_t M, int32_t restart,
             std::string msg;
             const int fw = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
                                                        max_factor_width(M->blocks, true)));
-            const int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw);
+            const int rc =
+                pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw, layout_parts(M));
             if (rc != HEC_OK)
                 return fail(rc, "%s", msg.c_str());
             total += dev((int64_t)P.pack.size()) + dev((int64_t)(P.chunks.size() * sizeof(uint2))) +

@@ -1,6 +1,6 @@
 // hec_setup.cpp -- host setup: HEC conversion (Section 2.1), RAS blocks
 // (Section 2.5), ILU(k) (Section 2.4, Eqs. 9-10, Algorithm 2), level schedule
-// (Section 2.6, Eq. 11) and the chunk layout of the triangular-solve kernel.
+// (Section 2.6, Eq. 11).  The triangular-solve layout is in trsv_layout.cpp.
 #include "hec_setup.h"
 
 #include <algorithm>
@@ -365,356 +365,6 @@ void levels_block(BlockFactor &B)
     }
     level_sets(B.levL, B.nlevL, B.lptrL, B.lrowsL);
     level_sets(B.levU, B.nlevU, B.lptrU, B.lrowsU);
-}
-
-// ---------------------------------------------------------------- chunk layout
-
-namespace {
-
-constexpr int kWarpRows = 32;
-constexpr int kMaxWarps = kThreads / kWarpRows;
-// counts, one width and one segment offset per warp, section offsets
-constexpr int kChunkHeader = 16 + 4 * kMaxWarps + 4 * kMaxWarps + 16;
-
-inline int r32(int x) { return (x + kWarpRows - 1) & ~(kWarpRows - 1); }
-
-// Lane stride of warp w's segment: 32 for a full warp, the row count rounded
-// up to 4 for the last, partial one.
-inline int seg_stride(int w, int nrows)
-{
-    const int left = nrows - w * kWarpRows;
-    return left >= kWarpRows ? kWarpRows : (left + 3) & ~3;
-}
-
-// Chunk layout (offsets in bytes, every section 16-byte aligned):
-//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass)
-//   [16, 48)  width of every warp's segment (entries per row, uniform in the warp)
-//   [48, 80)  byte offset of every warp's segment
-//   [80, 96)  byte offsets of src, dst, dinv, and 0
-//   per warp w < nwarps: val[width_w][stride_w] (value), dep[width_w][stride_w] (int32)
-//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (value)
-// Values are vb bytes: 8 (FP64 layout) or 4 (FP32 layout of the mixed-precision
-// mode).  Row t of the chunk is handled by thread t (warp t / 32, lane t % 32).
-size_t chunk_bytes(const std::vector<int> &widths, int nrows, bool upass, int vb)
-{
-    size_t b = kChunkHeader;
-    for (size_t w = 0; w < widths.size(); ++w)
-        b += (size_t)widths[w] * seg_stride((int)w, nrows) * (vb + 4);
-    b += 4 * (size_t)r32(nrows);
-    if (upass)
-        b += (4 + vb) * (size_t)r32(nrows);
-    return (b + 15) & ~(size_t)15;
-}
-
-inline void put_value(unsigned char *base, size_t i, double v, int vb)
-{
-    if (vb == 8)
-        reinterpret_cast<double *>(base)[i] = v;
-    else
-        reinterpret_cast<float *>(base)[i] = (float)v;
-}
-
-struct PassRows {
-    std::vector<int> order;     // needed rows in level-major order
-    std::vector<int> level_end; // end offsets into order, one per level
-};
-
-} // namespace
-
-// Which rows a block must solve: the U solve needs the owned rows and,
-// transitively, the rows they depend on through U (higher local indices);
-// the L solve needs every row whose y the U solve reads and, transitively,
-// their L dependencies.  The other rows cannot influence the owned part of
-// the result and are left out of the device program (the result on the
-// owned rows is unchanged).
-int max_factor_width(const std::vector<BlockFactor> &Bs, bool upass)
-{
-    int w = 0;
-    for (const BlockFactor &B : Bs)
-        for (int i = 0; i < B.F.n; ++i)
-            w = std::max(w, upass ? B.F.rp[i + 1] - B.diag[i] - 1 : B.diag[i] - B.F.rp[i]);
-    return w;
-}
-
-int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int max_ring, int vb,
-              TrsvPack &P, std::string &msg, int uniform_width)
-{
-    (void)n;
-    if (vb != 8 && vb != 4) {
-        msg = "value size must be 8 or 4 bytes";
-        return HEC_ERR_INVALID;
-    }
-    const int nb = (int)Bs.size();
-    P.pack.clear();
-    P.chunks.clear();
-    P.blocks.assign(nb, TrsvBlock());
-    P.ysz = P.zsz = 0;
-    P.alg_bytes = 0;
-    P.rows_L = P.rows_U = 0;
-    int ring_need = 32;
-    struct BlockOut {
-        std::vector<unsigned char> bytes;
-        std::vector<uint2> chunks; // offsets relative to this block
-        int nL = 0, nU = 0, spanL = 0, spanU = 0, nchunksL = 0;
-        std::vector<int> rows_per_chunk, rm_start, rm_len, rm_diag; // block-local entries
-        int64_t alg = 0;
-        std::string err;
-    };
-    std::vector<BlockOut> outs(nb);
-    parallel_for(nb, [&](int b) {
-        const BlockFactor &B = Bs[b];
-        const HostCSR &F = B.F;
-        const int nv = F.n;
-        BlockOut &O = outs[b];
-        std::vector<char> needU(nv, 0), needL(nv, 0), owned(nv, 0);
-        for (int i = 0; i < nv; ++i)
-            owned[i] = (B.rows[i] >= B.own_lo && B.rows[i] < B.own_hi);
-        for (int i = 0; i < nv; ++i) {
-            needU[i] |= owned[i];
-            if (needU[i])
-                for (int e = B.diag[i] + 1; e < F.rp[i + 1]; ++e)
-                    needU[F.ci[e]] = 1;
-        }
-        for (int i = nv - 1; i >= 0; --i) {
-            needL[i] |= needU[i];
-            if (needL[i])
-                for (int e = F.rp[i]; e < B.diag[i]; ++e)
-                    needL[F.ci[e]] = 1;
-        }
-        std::vector<int> posL(nv, -1), posU(nv, -1);
-        // off-diagonal entries of row i in the L (upass false) or U factor
-        auto row_len = [&](bool upass, int i) {
-            return upass ? F.rp[i + 1] - B.diag[i] - 1 : B.diag[i] - F.rp[i];
-        };
-        auto order_pass = [&](bool upass, std::vector<int> &pos) {
-            const std::vector<int> &ptr = upass ? B.lptrU : B.lptrL;
-            const std::vector<int> &rows = upass ? B.lrowsU : B.lrowsL;
-            const std::vector<char> &need = upass ? needU : needL;
-            PassRows pr;
-            std::vector<int> lvl;
-            for (size_t l = 0; l + 1 < ptr.size(); ++l) {
-                lvl.clear();
-                for (int q = ptr[l]; q < ptr[l + 1]; ++q)
-                    if (need[rows[q]])
-                        lvl.push_back(rows[q]);
-                // inside a level rows are independent: longest first, so each
-                // warp's segment pads little (stable: ties keep row order)
-                std::stable_sort(lvl.begin(), lvl.end(), [&](int x, int y) {
-                    return row_len(upass, x) > row_len(upass, y);
-                });
-                for (int i : lvl) {
-                    pos[i] = (int)pr.order.size();
-                    pr.order.push_back(i);
-                }
-                pr.level_end.push_back((int)pr.order.size());
-            }
-            return pr;
-        };
-        PassRows pl = order_pass(false, posL);
-        PassRows pu = order_pass(true, posU);
-        O.nL = (int)pl.order.size();
-        O.nU = (int)pu.order.size();
-        auto emit = [&](bool upass, const PassRows &pr, const std::vector<int> &pos, int &span) {
-            (void)pos;
-            int start = 0;
-            span = 0;
-            std::vector<int> widths;
-            for (int end : pr.level_end) {
-                int q = start;
-                while (q < end) {
-                    // greedy chunk: rows [q, q2) of this level, warp w takes rows
-                    // 32w .. 32w+31; rows are sorted longest first, so a warp's
-                    // width is the length of its first row
-                    int q2 = q;
-                    widths.clear();
-                    while (q2 < end && q2 - q < kThreads) {
-                        const int j = q2 - q;
-                        if (j % kWarpRows == 0)
-                            widths.push_back(uniform_width > 0 ? uniform_width
-                                                               : row_len(upass, pr.order[q2]));
-                        if (chunk_bytes(widths, j + 1, upass, vb) > (size_t)stage_bytes) {
-                            if (j % kWarpRows == 0)
-                                widths.pop_back();
-                            break;
-                        }
-                        ++q2;
-                    }
-                    if (q2 == q) {
-                        O.err = "a factor row is too long for one shared-memory stage";
-                        return;
-                    }
-                    const int nr = q2 - q, npad = r32(nr), nw = (int)widths.size();
-                    const size_t bytes = chunk_bytes(widths, nr, upass, vb);
-                    const size_t off = O.bytes.size();
-                    O.bytes.resize(off + bytes, 0);
-                    unsigned char *ch = O.bytes.data() + off;
-                    int hdr[kChunkHeader / 4] = {nr, nw, q, upass ? 1 : 0};
-                    int segoff = kChunkHeader;
-                    for (int w = 0; w < nw; ++w) {
-                        hdr[4 + w] = widths[w];
-                        hdr[4 + kMaxWarps + w] = segoff;
-                        segoff += widths[w] * seg_stride(w, nr) * (vb + 4);
-                    }
-                    hdr[4 + 2 * kMaxWarps + 0] = segoff;                  // src
-                    hdr[4 + 2 * kMaxWarps + 1] = segoff + 4 * npad;       // dst
-                    hdr[4 + 2 * kMaxWarps + 2] = segoff + 8 * npad;       // dinv
-                    std::memcpy(ch, hdr, kChunkHeader);
-                    unsigned char *seg = ch + kChunkHeader;
-                    int *src = nullptr;
-                    int mindep = q;
-                    for (int w = 0; w < nw; ++w) {
-                        const int wd = widths[w];
-                        const int ls = seg_stride(w, nr);
-                        unsigned char *val = seg;
-                        int *dep = reinterpret_cast<int *>(seg + (size_t)wd * ls * vb);
-                        for (int lane = 0; lane < ls; ++lane) {
-                            const int t = w * kWarpRows + lane;
-                            if (t >= nr) {
-                                // rows past the chunk: never read, keep them valid
-                                for (int kk = 0; kk < wd; ++kk) {
-                                    dep[(size_t)kk * ls + lane] = q;
-                                    put_value(val, (size_t)kk * ls + lane, 0.0, vb);
-                                }
-                                continue;
-                            }
-                            const int i = pr.order[q + t];
-                            const int e0 = upass ? B.diag[i] + 1 : F.rp[i];
-                            const int len = row_len(upass, i);
-                            if (len == 0 && wd > 0 && uniform_width == 0) {
-                                // a row of level >= 2 always has a dependency
-                                O.err = "internal: dependency-free row in a dependent level";
-                                return;
-                            }
-                            for (int kk = 0; kk < wd; ++kk) {
-                                // padding repeats the first dependency with value 0
-                                // (a row without one -- level 1 of a uniform-width
-                                // layout -- points at the chunk's first position:
-                                // in the ring that slot holds a value of this
-                                // apply or 0; from the global scratch the kernel
-                                // does not read entries of value 0)
-                                const int e = kk < len ? e0 + kk : e0;
-                                const int d = len > 0 ? (upass ? posU : posL)[F.ci[e]] : q;
-                                dep[(size_t)kk * ls + lane] = d;
-                                put_value(val, (size_t)kk * ls + lane, kk < len ? F.va[e] : 0.0, vb);
-                                mindep = std::min(mindep, d);
-                            }
-                        }
-                        seg += (size_t)wd * ls * (vb + 4);
-                    }
-                    O.rows_per_chunk.push_back(nr);
-                    for (int t = 0; t < nr; ++t) {
-                        const int i = pr.order[q + t];
-                        O.rm_start.push_back(upass ? B.diag[i] + 1 : F.rp[i]);
-                        O.rm_len.push_back(row_len(upass, i));
-                        O.rm_diag.push_back(upass ? B.diag[i] : -1);
-                    }
-                    src = reinterpret_cast<int *>(seg);
-                    int *dst = src + npad;
-                    unsigned char *dinv = reinterpret_cast<unsigned char *>(dst + npad);
-                    for (int t = 0; t < nr; ++t) {
-                        const int i = pr.order[q + t];
-                        const int len = row_len(upass, i);
-                        if (upass) {
-                            src[t] = posL[i];
-                            dst[t] = owned[i] ? B.rows[i] : -1;
-                            put_value(dinv, t, 1.0 / F.va[B.diag[i]], vb);
-                            O.alg += (4ll + vb) * len + vb /*y*/ + vb /*dinv*/ + 4 /*src*/ +
-                                     4 /*dst*/ + (owned[i] ? vb : 0);
-                        } else {
-                            src[t] = B.rows[i];
-                            O.alg += (4ll + vb) * len + vb /*r*/ + vb /*y*/ + 4 /*src*/;
-                        }
-                    }
-                    span = std::max(span, (q + nr) - mindep);
-                    O.chunks.push_back(make_uint2((unsigned)(off / 16), (unsigned)bytes));
-                    q = q2;
-                }
-                start = end;
-            }
-        };
-        emit(false, pl, posL, O.spanL);
-        if (!O.err.empty())
-            return;
-        O.nchunksL = (int)O.chunks.size();
-        emit(true, pu, posU, O.spanU);
-    });
-    for (int b = 0; b < nb; ++b)
-        if (!outs[b].err.empty()) {
-            msg = outs[b].err;
-            return HEC_ERR_INVALID;
-        }
-    // ring size: the largest window that fits, power of two
-    auto pow2 = [](int v) {
-        int p = 32;
-        while (p < v)
-            p <<= 1;
-        return p;
-    };
-    for (int b = 0; b < nb; ++b) {
-        if (pow2(outs[b].spanL + 1) <= max_ring)
-            ring_need = std::max(ring_need, pow2(outs[b].spanL + 1));
-        if (pow2(outs[b].spanU + 1) <= max_ring)
-            ring_need = std::max(ring_need, pow2(outs[b].spanU + 1));
-    }
-    P.ring_slots = ring_need;
-    size_t total = 0;
-    for (auto &O : outs)
-        total += O.bytes.size();
-    P.pack.resize(total);
-    P.chunk_row0.clear();
-    P.rm_start.clear();
-    P.rm_len.clear();
-    P.rm_diag.clear();
-    {
-        int64_t ent0 = 0, r0 = 0;
-        for (int b = 0; b < nb; ++b) {
-            const BlockOut &O = outs[b];
-            for (int nr : O.rows_per_chunk) {
-                P.chunk_row0.push_back(r0);
-                r0 += nr;
-            }
-            for (size_t q = 0; q < O.rm_start.size(); ++q) {
-                P.rm_start.push_back((int)(ent0 + O.rm_start[q]));
-                P.rm_len.push_back(O.rm_len[q]);
-                P.rm_diag.push_back(O.rm_diag[q] < 0 ? -1 : (int)(ent0 + O.rm_diag[q]));
-            }
-            ent0 += (int64_t)Bs[b].F.ci.size();
-        }
-        P.chunk_row0.push_back(r0);
-    }
-    size_t off = 0;
-    int64_t yoff = 0, zoff = 0;
-    bool any_global_u = false;
-    for (int b = 0; b < nb; ++b) {
-        BlockOut &O = outs[b];
-        TrsvBlock &T = P.blocks[b];
-        T.chunk_begin = (int)P.chunks.size();
-        for (const uint2 &c : O.chunks)
-            P.chunks.push_back(make_uint2((unsigned)(c.x + off / 16), c.y));
-        T.chunk_end = (int)P.chunks.size();
-        T.chunk_mid = T.chunk_begin + O.nchunksL;
-        std::memcpy(P.pack.data() + off, O.bytes.data(), O.bytes.size());
-        off += O.bytes.size();
-        T.ring_L = (O.spanL + 1 <= ring_need) ? 1 : 0;
-        T.ring_U = (O.spanU + 1 <= ring_need) ? 1 : 0;
-        T.yoff = yoff;
-        yoff += O.nL;
-        T.zoff = zoff;
-        if (!T.ring_U) {
-            zoff += O.nU;
-            any_global_u = true;
-        }
-        P.alg_bytes += O.alg;
-        P.rows_L += O.nL;
-        P.rows_U += O.nU;
-    }
-    if (off / 16 > 0xffffffffull) {
-        msg = "factor layout exceeds 64 GiB";
-        return HEC_ERR_INVALID;
-    }
-    P.ysz = yoff;
-    P.zsz = any_global_u ? zoff : 0;
-    return HEC_OK;
 }
 
 } // namespace hec

@@ -59,12 +59,17 @@ int iluk_block(BlockFactor &B, int k, std::string &msg);
 void levels_block(BlockFactor &B);
 
 // --------------------------------------------------------------- device layout
+// (trsv_layout.cpp)
 struct TrsvPack {
     std::vector<unsigned char> pack;
     std::vector<uint2> chunks;
-    std::vector<TrsvBlock> blocks;
-    int64_t ysz = 0, zsz = 0;   // scratch lengths (doubles)
-    int ring_slots = 0;         // power of two (>= 32)
+    std::vector<TrsvBlock> blocks; // one program per (RAS block, part): block b, part p at b * parts + p
+    int parts = 1;              // CTAs per RAS block (the cluster size of the launch)
+    int stage_bytes = 0;        // shared-memory stage the kernel streams chunks into
+    int exp_arrays = 0;         // fixed-slot chunks carry export slots
+    int64_t ysz = 0, zsz = 0;   // scratch lengths (values)
+    int ring_slots = 0;         // own ring R: power of two (>= 32)
+    int import_slots = 0;       // import ring RI: power of two, 0 when no block is split
     int64_t alg_bytes = 0;      // algorithmic bytes of one apply
     int64_t rows_L = 0, rows_U = 0;
     // where every chunk row's values come from, for refilling them from new
@@ -74,11 +79,17 @@ struct TrsvPack {
     std::vector<int> rm_start, rm_len, rm_diag; // first value's entry, count, diagonal (U; -1 for L)
 };
 // vb: bytes per stored value, 8 (FP64 layout) or 4 (FP32 layout).
-// uniform_width > 0: every warp segment of every chunk has this width (rows
-// padded with value 0), so the kernel can address and solve rows with a
-// width known at compile time; it must be >= the longest row.
+// uniform_width > 0 (at most 8): every row is padded to this width (value 0)
+// and chunks use the fixed-slot format, so the kernel addresses every row's
+// data at compile-time offsets; it must be >= the longest row.  stage_bytes
+// is raised, if needed, to hold the largest fixed-slot chunk (out.stage_bytes).
+// parts (1, 2, 4 or 8): CTAs per RAS block; a block whose dependencies do
+// not allow that split gets fewer (its remaining programs are empty).
 int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,
-              TrsvPack &out, std::string &msg, int uniform_width = 0);
+              TrsvPack &out, std::string &msg, int uniform_width = 0, int parts = 1);
+// The parts per block worth launching: split while the widest block's levels
+// hold more than four warps of rows per part and the CTAs fit on sm_count SMs.
+int trsv_auto_parts(const std::vector<BlockFactor> &B, int sm_count);
 // The longest off-diagonal row of any L_b (upass false) or U_b.
 int max_factor_width(const std::vector<BlockFactor> &B, bool upass);
 

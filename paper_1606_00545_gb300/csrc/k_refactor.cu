@@ -162,7 +162,9 @@ __global__ void __launch_bounds__(kThreads) k_iluk_numeric(RefactorArgs a)
 // The triangular-solve layout's value slots from the new factor values: one
 // CTA per chunk, thread t on row t.  Row t of chunk c takes the factor
 // entries [start, start + len) of its pass (L: the multipliers; U: the
-// entries right of the diagonal) and, for U, 1 / u_tt.
+// entries right of the diagonal) and, for U, 1 / u_tt.  Both chunk formats
+// of trsv_layout.cpp: fixed-slot (flag bit 3: every row padded to FW entries
+// in per-warp blocks) and generic (per-warp widths).
 template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillArgs a)
 {
     const int c = blockIdx.x;
@@ -174,12 +176,24 @@ template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillA
     if (t >= nrows)
         return;
     const int w = t / 32, lane = t % 32;
+    const int64_t q = a.chunk_row0[c] + t;
+    const int start = a.rm_start[q], len = a.rm_len[q];
+    if (hdr[3] & 8) {
+        const int FW = hdr[6];
+        const bool exps = (hdr[3] & 16) != 0;
+        const int vb = (int)sizeof(T);
+        const int blk = FW * 32 * vb + (FW + 1) * 128 + (upass ? 32 * vb + 128 : 0) + (exps ? 128 : 0);
+        T *val = reinterpret_cast<T *>(ch + 32 + (size_t)w * blk);
+        for (int k = 0; k < FW; ++k)
+            val[k * 32 + lane] = k < len ? T(a.f[start + k]) : T(0);
+        if (upass)
+            val[FW * 32 + lane] = T(__ddiv_rn(1.0, a.f[a.rm_diag[q]]));
+        return;
+    }
     const int left = nrows - w * 32;
     const int stride = left >= 32 ? 32 : (left + 3) & ~3;
     const int width = hdr[4 + w];
     T *val = reinterpret_cast<T *>(ch + hdr[4 + 8 + w]);
-    const int64_t q = a.chunk_row0[c] + t;
-    const int start = a.rm_start[q], len = a.rm_len[q];
     for (int k = 0; k < width; ++k)
         val[k * stride + lane] = k < len ? T(a.f[start + k]) : T(0);
     if (upass) {

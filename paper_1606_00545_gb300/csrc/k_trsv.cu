@@ -3,27 +3,43 @@
 // level (Eq. 11, Algorithm 3), solve U_b z = y level by level, write z on the
 // rows the block owns.
 //
-// Design for sm_103a.  One persistent CTA per RAS block walks the block's
-// "program": the rows of every level of L_b, then of U_b, packed level-major
-// into chunks (a chunk holds rows of one level only; rows inside a level are
-// independent).  A chunk is one contiguous byte range in HBM holding, for its
-// rows, the factor entries column-major (value, dependency position), the
-// source index of the right-hand side, and for U the destination row and the
-// inverted diagonal.  Rows of a level are sorted longest first and every warp
-// gets its own segment width, so little FP64 work is spent on padding.
+// Design for sm_103a.  Each RAS block is solved by one CTA, or by a chain of
+// P CTAs of one thread-block cluster ("parts": contiguous ranges of the
+// block's rows, see trsv_layout.cpp).  A CTA walks its "program": its rows of
+// every level of L_b, then of U_b, packed level-major into chunks (a chunk
+// holds rows of one level only; rows inside a level are independent).  A
+// chunk is one contiguous byte range in HBM holding, for its rows, the factor
+// entries (value, dependency slot), the source index of the right-hand side,
+// for U the destination row and the inverted diagonal, and for rows a
+// neighbouring part reads, the slot they go to there.  Two chunk formats:
+//   - fixed-slot (every row padded to one width FW <= 8): each thread's data
+//     sits at a compile-time offset from the stage, so the solving warps copy
+//     their rows of the next chunk into registers while the current chunk's
+//     multiply-add chain runs -- a level's critical path is then the ring
+//     loads, the chain and the barrier;
+//   - generic (wider rows): per-warp widths, rows solved from shared memory.
 // Nothing on a level's critical path waits for HBM:
 //   - an issuer warp streams chunks into a ring of shared-memory stages with
 //     cp.async.bulk (the TMA bulk-copy engine) completing on mbarriers, S
 //     chunks ahead of the solving warps;
-//   - a gatherer warp, once a chunk has landed, gathers its right-hand sides
-//     (L pass: from r; U pass: from the L results, once the L pass is
-//     complete) with 4- or 8-byte cp.async completing on a per-stage
-//     mbarrier -- a separate warp, so that a stage the issuer waits to
-//     refill never holds back the gathers of chunks already in flight;
+//   - two gatherer warps, taking chunks in turn, gather each landed chunk's
+//     right-hand sides (L pass: from r; U pass: from the L results, once the
+//     L pass is complete) with 4- or 8-byte cp.async, one chunk ahead, and
+//     hand the chunk over (a per-stage mbarrier) once the copies have
+//     completed and the neighbouring parts have completed the chunks its
+//     thresholds name;
 //   - solved values of the last few levels live in a shared-memory ring
 //     indexed by level-major position (the setup checks that every
 //     dependency of a chunk lies within the ring's window; passes whose
-//     window does not fit read dependencies from the global scratch).
+//     window does not fit read dependencies from the global scratch); values
+//     a neighbouring part reads are also kept in a local export ring;
+//   - one signaller thread copies the exports of completed chunks into the
+//     neighbour's import ring (distributed shared memory), fences at cluster
+//     scope, and only then stores the completed-chunk count into the
+//     neighbour's shared memory -- off the solving warps' path.  (A release
+//     orders the releasing thread's own stores: measured on this GPU, a
+//     fence by one thread after a CTA barrier did not order the
+//     distributed-shared-memory stores of the other threads.)
 // Levels are separated by a barrier of the solving warps only -- no
 // grid-wide synchronisation.  Every wait is bounded: a wait that runs out
 // sets the device error word, one thread waits (bounded) for the copies still
@@ -35,26 +51,14 @@
 
 namespace hec {
 
-// Barrier of the consumer warps only (named barrier 1), OR-reducing a flag.
-__device__ __forceinline__ int consumer_sync_or(int flag)
-{
-    int any;
-    asm volatile("{\n\t.reg .pred p, q;\n\t"
-                 "setp.ne.s32 p, %1, 0;\n\t"
-                 "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
-                 "selp.s32 %0, 1, 0, q;\n\t}"
-                 : "=r"(any)
-                 : "r"(flag), "n"(kThreads)
-                 : "memory");
-    return any;
-}
-
 // Shared memory of one CTA: S stages, S right-hand-side slots of kThreads
-// values, the ring, and 3 S + 1 mbarriers.  vbytes: 8 (FP64) or 4 (FP32).
+// values, the ring (own, import and export slots: ring_slots in all), 3 S + 1
+// mbarriers and two progress counters.  vbytes: 8 (FP64) or 4 (FP32).
 size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
 {
-    return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * vbytes +
-           (size_t)ring_slots * vbytes + (size_t)(3 * nstages + 1) * sizeof(uint64_t);
+    const size_t ring = ((size_t)ring_slots * vbytes + 7) & ~(size_t)7;
+    return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * vbytes + ring +
+           (size_t)(3 * nstages + 1) * sizeof(uint64_t) + 2 * sizeof(uint32_t);
 }
 
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes)
@@ -69,21 +73,53 @@ int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes)
     return S;
 }
 
+// ------------------------------------------------------------------ debug build
+// Compiled with HEC_DEBUG, the kernel checks what it reads before it uses it:
+// every chunk's header against the position the program has reached, every
+// gathered index against the array it indexes, every dependency slot against
+// the ring.  A failed check records the first violation (code, program,
+// chunk, thread, value, bound), sets the error word to HEC_ERR_DEBUG and
+// skips the access; nothing traps.
+__device__ int g_trsv_debug[8];
+
+#ifdef HEC_DEBUG
+__device__ __noinline__ void debug_fail(int *err, int code, int c, int val, int bound)
+{
+    if (atomicCAS(&g_trsv_debug[0], 0, code) == 0) {
+        g_trsv_debug[1] = (int)blockIdx.x;
+        g_trsv_debug[2] = c;
+        g_trsv_debug[3] = (int)threadIdx.x;
+        g_trsv_debug[4] = val;
+        g_trsv_debug[5] = bound;
+    }
+    atomicExch(err, HEC_ERR_DEBUG);
+}
+#define HEC_CHECK(cond, code, c, val, bound)                                                     \
+    ((cond) ? true : (debug_fail(a.err, (code), (c), (int)(val), (int)(bound)), false))
+#else
+#define HEC_CHECK(cond, code, c, val, bound) true
+#endif
+
 // Drain bound for copies already issued when a wait ran out: copies complete
 // in microseconds, this only guarantees that the CTA never waits forever.
 constexpr long long kDrainPolls = 1ll << 24;
 
-// A chunk in shared memory (layout written by the setup's packer; T is the
+// A chunk in shared memory (layout written by trsv_layout.cpp; T is the
 // value type, double or float):
-//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass)
+//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 1: exports)
 //   [16, 48)  width of every warp's segment
 //   [48, 80)  byte offset of every warp's segment
-//   [80, 96)  byte offsets of src, dst, dinv
+//   [80, 96)  byte offsets of src, dst, dinv, exp
+//   [96, 112) need_prev, need_next: completed chunks of part p - 1 / p + 1 to wait for
 //   per warp w < nwarps: val[width_w][stride_w] (T), dep[width_w][stride_w] (int32),
 //     stride_w = 32 for a full warp, the row count rounded up to 4 for the last one
-//   src[r32(nrows)] (int32), and for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (T)
+//   src[r32(nrows)] (int32); for U: dst[r32(nrows)] (int32), dinv[r32(nrows)] (T);
+//   with exports: exp[r32(nrows)] (int32), the row's slot in the neighbour's ring
+// A dependency is a slot of the ring in ring mode (own values below R,
+// imported ones from R on), else a position in the block's global scratch.
 constexpr int kWarpRows = 32;
 constexpr int kMaxWarps = kThreads / kWarpRows;
+constexpr int kFeedThreads = 128; // issuer, two gatherers and the signaller
 
 __device__ __forceinline__ int seg_stride(int w, int nrows)
 {
@@ -93,8 +129,8 @@ __device__ __forceinline__ int seg_stride(int w, int nrows)
 
 template <class T> struct ChunkView {
     int nrows, nwarps, base;
-    bool upass;
-    const int *src, *dst;
+    bool upass, exports;
+    const int *src, *dst, *exp;
     const T *dinv;
 };
 
@@ -107,9 +143,11 @@ template <class T> __device__ __forceinline__ ChunkView<T> view_chunk(const unsi
     v.nwarps = hdr.y;
     v.base = hdr.z;
     v.upass = (hdr.w & 1) != 0;
+    v.exports = (hdr.w & 2) != 0;
     v.src = reinterpret_cast<const int *>(ch + off.x);
     v.dst = reinterpret_cast<const int *>(ch + off.y);
     v.dinv = reinterpret_cast<const T *>(ch + off.z);
+    v.exp = reinterpret_cast<const int *>(ch + off.w);
     return v;
 }
 
@@ -132,14 +170,15 @@ __device__ __forceinline__ Segment<T> warp_segment(const unsigned char *ch, int 
     return g;
 }
 
-// s - sum_k val[k] * y[dep[k]] for one row in ascending column order, width W
+// s - sum_k val[k] * y[dep[k]] for one row in ascending column order (y: the
+// ring slot dep[k], or the global-scratch position dep[k]), width W
 // known at compile time: every shared-memory load of the row is issued before
 // the first multiply.  One accumulator: in FP64 the pipe's throughput, not
 // the 64-cycle latency of a dependent DFMA, bounds a level once several warps
 // are busy, and a second accumulator would cost one more FP64 add per row.
 template <int W, bool RING, class T>
-__device__ __forceinline__ T row_solve(const Segment<T> &g, int lane, const T *ring, int mask,
-                                       const T *gdep, T s)
+__device__ __forceinline__ T row_solve(const Segment<T> &g, int lane, const T *ring, const T *gdep,
+                                       T s)
 {
     if constexpr (W == 0) {
         return s;
@@ -153,7 +192,7 @@ __device__ __forceinline__ T row_solve(const Segment<T> &g, int lane, const T *r
         }
 #pragma unroll
         for (int k = 0; k < W; ++k)
-            y[k] = RING ? ring[d[k] & mask] : gdep[d[k]];
+            y[k] = RING ? ring[d[k]] : gdep[d[k]];
 #pragma unroll
         for (int k = 0; k < W; ++k)
             s = fma(-l[k], y[k], s);
@@ -162,19 +201,19 @@ __device__ __forceinline__ T row_solve(const Segment<T> &g, int lane, const T *r
 }
 
 template <bool RING, class T>
-__device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const T *ring, int mask,
+__device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const T *ring,
                                            const T *gdep, T s)
 {
     switch (g.width) {
     case 0: return s;
-    case 1: return row_solve<1, RING>(g, lane, ring, mask, gdep, s);
-    case 2: return row_solve<2, RING>(g, lane, ring, mask, gdep, s);
-    case 3: return row_solve<3, RING>(g, lane, ring, mask, gdep, s);
-    case 4: return row_solve<4, RING>(g, lane, ring, mask, gdep, s);
-    case 5: return row_solve<5, RING>(g, lane, ring, mask, gdep, s);
-    case 6: return row_solve<6, RING>(g, lane, ring, mask, gdep, s);
-    case 7: return row_solve<7, RING>(g, lane, ring, mask, gdep, s);
-    case 8: return row_solve<8, RING>(g, lane, ring, mask, gdep, s);
+    case 1: return row_solve<1, RING>(g, lane, ring, gdep, s);
+    case 2: return row_solve<2, RING>(g, lane, ring, gdep, s);
+    case 3: return row_solve<3, RING>(g, lane, ring, gdep, s);
+    case 4: return row_solve<4, RING>(g, lane, ring, gdep, s);
+    case 5: return row_solve<5, RING>(g, lane, ring, gdep, s);
+    case 6: return row_solve<6, RING>(g, lane, ring, gdep, s);
+    case 7: return row_solve<7, RING>(g, lane, ring, gdep, s);
+    case 8: return row_solve<8, RING>(g, lane, ring, gdep, s);
     default: {
         // wide rows: loads in blocks of 8 entries
         int k = 0;
@@ -184,7 +223,7 @@ __device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const 
             for (int q = 0; q < 8; ++q) {
                 l[q] = g.val[(k + q) * g.stride + lane];
                 const int d = g.dep[(k + q) * g.stride + lane];
-                y[q] = RING ? ring[d & mask] : gdep[d];
+                y[q] = RING ? ring[d] : gdep[d];
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q)
@@ -192,50 +231,157 @@ __device__ __forceinline__ T row_solve_any(const Segment<T> &g, int lane, const 
         }
         for (; k < g.width; ++k) {
             const int d = g.dep[k * g.stride + lane];
-            s = fma(-g.val[k * g.stride + lane], RING ? ring[d & mask] : gdep[d], s);
+            s = fma(-g.val[k * g.stride + lane], RING ? ring[d] : gdep[d], s);
         }
         return s;
     }
     }
 }
 
+// Barrier of the consumer warps only (named barrier 1), AND-reducing a flag.
+__device__ __forceinline__ int consumer_sync_and(int flag)
+{
+    int all;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.s32 p, %1, 0;\n\t"
+                 "barrier.cta.red.and.pred q, 1, %2, p;\n\t"
+                 "selp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(all)
+                 : "r"(flag), "n"(kThreads)
+                 : "memory");
+    return all;
+}
+
+// ------------------------------------------------------------------ generic format
+// The row of a chunk solved from shared memory: s - sum_k l_k y_dep(k), times
+// dinv in the U pass.
+template <class T>
+__device__ __forceinline__ T solve_row_smem(const unsigned char *ch, const ChunkView<T> &v, int t,
+                                            bool rm, const T *ring, const T *gdep, T sacc)
+{
+    const Segment<T> g = warp_segment<T>(ch, v.nrows, t / kWarpRows);
+    const int lane = t % kWarpRows;
+    sacc = rm ? row_solve_any<true, T>(g, lane, ring, gdep, sacc)
+              : row_solve_any<false, T>(g, lane, ring, gdep, sacc);
+    if (v.upass)
+        sacc *= v.dinv[t];
+    return sacc;
+}
+
+// ------------------------------------------------------------------ fixed-slot format
+// (written by trsv_layout.cpp; every row padded to FW entries)
+//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 1: exports)
+//   [16, 32)  need_prev, need_next, FW, xend (exports of the pass so far)
+//   per warp w < nwarps a block, lane l = row 32w + l: val[FW][32] (T);
+//   U: dinv[32] (T); dep[FW][32], src[32] (int32); U: dst[32]; exp[32]
+//   (export positions, -1: none) in launches with exp_arrays
+constexpr int kFixedHeader = 32;
+
+template <class T, int FW> struct Fixed {
+    __device__ static constexpr int dinv(bool) { return FW * 32 * (int)sizeof(T); }
+    __device__ static constexpr int dep(bool u) { return FW * 32 * (int)sizeof(T) + (u ? 32 * (int)sizeof(T) : 0); }
+    __device__ static constexpr int src(bool u) { return dep(u) + FW * 128; }
+    __device__ static constexpr int dst(bool u) { return src(u) + 128; }
+    __device__ static constexpr int exp(bool u) { return src(u) + 128 + (u ? 128 : 0); }
+    __device__ static constexpr int block(bool u, bool e) { return exp(u) + (e ? 128 : 0); }
+};
+
+// A solving thread's copy of its row of one fixed-slot chunk, with the
+// chunk's header fields.
+template <class T, int FW> struct RowRegs {
+    int nrows, nwarps, base, xend, flags;
+    T l[FW];
+    int d[FW];
+    T rhs, dinv;
+    int dst, exp;
+};
+
+// Every address below depends only on the stage, the thread and the pass,
+// never on a value read from the stage: all loads issue back to back.
+template <class T, int FW>
+__device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rslot, int w, int lane,
+                                           int t, bool upass, bool exps, RowRegs<T, FW> &R)
+{
+    const int4 hdr = *reinterpret_cast<const int4 *>(ch);
+    R.nrows = hdr.x;
+    R.nwarps = hdr.y;
+    R.base = hdr.z;
+    R.flags = hdr.w;
+    R.xend = reinterpret_cast<const int4 *>(ch)[1].w;
+    const unsigned char *blk = ch + kFixedHeader + (size_t)w * Fixed<T, FW>::block(upass, exps);
+    const T *val = reinterpret_cast<const T *>(blk) + lane;
+    const int *dep = reinterpret_cast<const int *>(blk + Fixed<T, FW>::dep(upass)) + lane;
+#pragma unroll
+    for (int k = 0; k < FW; ++k) {
+        R.l[k] = val[k * 32];
+        R.d[k] = dep[k * 32];
+    }
+    R.rhs = rslot[t];
+    if (upass) {
+        R.dinv = reinterpret_cast<const T *>(blk + Fixed<T, FW>::dinv(true))[lane];
+        R.dst = reinterpret_cast<const int *>(blk + Fixed<T, FW>::dst(true))[lane];
+    }
+    R.exp = exps ? reinterpret_cast<const int *>(blk + Fixed<T, FW>::exp(upass))[lane] : -1;
+}
+
 // Warp-specialised CTA: warps 0-7 solve rows (one row per thread per chunk),
-// warps 8 and 9 feed them.  Per chunk c in stage s = c mod S:
+// warps 8-11 feed them.  Per chunk c in stage s = c mod S:
 //   issuer (warp 8): wait empty[s] (chunk c - S released) -> arm full[s] with
 //             the chunk's byte count -> cp.async.bulk the chunk;
-//   gatherer (warp 9): wait full[s] -> gather the chunk's right-hand sides
-//             into slot s with cp.async (a U chunk waits for ldone first: its
-//             right-hand side is the L pass's output); ready[s] completes
-//             when the 32 lanes' gathers have landed (cp.async arrivals) and
-//             lane 0 -- which has seen the chunk's data land -- has arrived,
-//             so one barrier covers both;
-//   consumers: wait ready[s] -> solve -> consumer barrier ->
-//             one thread releases empty[s] (and ldone after the last L chunk).
+//   gatherers (warps 9 and 10, chunks alternating): wait full[s] -> gather
+//             the chunk's right-hand sides into slot s with cp.async, one
+//             commit group per chunk (a U chunk waits for ldone first: its
+//             right-hand side is the L pass's output) -> once the group has
+//             completed (waited for while the warp's next chunk is gathered)
+//             and lane 0 has seen the neighbouring parts' progress counters
+//             reach the chunk's thresholds, every lane arrives on ready[s];
+//   consumers: fixed-slot chunks are software-pipelined by one chunk: while
+//             chunk c's multiply-add chain runs, every thread copies its row
+//             of chunk c + 1 into registers (when that chunk is ready
+//             already).  The level's results go to the ring (and, for
+//             exports, into the neighbour's import ring), the consumer
+//             barrier closes the level, and the last thread frees the stages
+//             every thread is done with -- chunk c, and chunk c + 1 once all
+//             threads hold it -- and publishes the completed count.  Generic
+//             chunks are solved from shared memory, one at a time;
+//   signaller (warp 11): for a split block, forwards the completed count to
+//             the neighbouring parts (a release at cluster scope, then the
+//             count stored into their shared memory) as often as the fence
+//             allows -- the count may jump several chunks at once.
 // T = double: the FP64 path; T = float: the FP32 inner solves of the
 // mixed-precision mode (FP32 factors, products and accumulation).
 template <class T, int FW>
-__global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
+__global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     count_launch(a.st);
     if (a.st && a.st->skip)
-        return;
+        return; // uniform over the grid: no CTA of a cluster reaches a cluster barrier
     const T *r = reinterpret_cast<const T *>(a.r);
     if (a.r_from_j)
         r += (int64_t)a.st->j * a.ldv;
 
+    const bool clustered = a.parts > 1;
+    const int part = clustered ? (int)cluster_ctarank() : 0;
     const TrsvBlock blk = a.blocks[blockIdx.x];
     const int S = a.nstages;
     unsigned char *stages = smem;
     T *rhs = reinterpret_cast<T *>(smem + (size_t)S * a.stage_bytes);
     T *ring = rhs + (size_t)S * kThreads;
-    const int mask = a.ring_mask;
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + mask + 1);
+    const int nown = a.ring_mask + 1;
+    const int RI = a.import_slots;
+    const int nring = nown + 2 * RI; // own values, imports, exports
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) +
+                                                  (((size_t)nring * sizeof(T) + 7) & ~(size_t)7));
     uint64_t *empty = full + S;
     uint64_t *ready = empty + S;
     uint64_t *ldone = ready + S;
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(ldone + 1); // [0]: from part p - 1, [1]: from p + 1
     const int nch = blk.chunk_end - blk.chunk_begin;
     const int nL = blk.chunk_mid - blk.chunk_begin; // chunks of the L pass
+    const bool has_prev = (blk.links & 1) != 0, has_next = (blk.links & 2) != 0;
+    const bool signal = has_prev || has_next;
+    const bool exps = FW > 0 && a.exp_arrays != 0;
     const bool stall_test = a.spin_limit < 0;       // fault injection: nothing is issued
     const long long limit = stall_test ? -a.spin_limit : a.spin_limit;
     const uint2 *chunks = a.chunks + blk.chunk_begin;
@@ -244,25 +390,33 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
     T *zsc = a.zsc ? reinterpret_cast<T *>(a.zsc) + blk.zoff : nullptr;
     T *z = reinterpret_cast<T *>(a.z);
     const int t = threadIdx.x;
+    T *xring = ring + nown + RI; // this CTA's exports, slot = export position & (RI - 1)
+    // shared state of the roles (written before the final barrier)
+    __shared__ int s_issued, s_err;
+    __shared__ uint64_t s_prog;          // chunks completed | exports of that pass << 32
+    __shared__ uint32_t s_sent[2];       // exports copied to the neighbour: L, U
 
     if (t == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&ready[s], 33); // 32 gather arrivals + 1 data arrival
+            mbar_init(&ready[s], 32); // every gatherer lane, once its copies have landed
         }
         mbar_init(ldone, 1);
+        ctr[0] = ctr[1] = 0;
+        s_issued = 0;
+        s_err = 0;
+        s_prog = 0;
+        s_sent[0] = s_sent[1] = 0;
         fence_mbar_init();
     }
-    for (int i = t; i <= mask; i += blockDim.x)
+    for (int i = t; i < nown; i += blockDim.x)
         ring[i] = T(0);
     __syncthreads();
-
-    // shared state of the two feeding warps (written before the final barrier)
-    __shared__ int s_issued;
-    if (t == 0)
-        s_issued = 0;
-    __syncthreads();
+    // the neighbours store into this CTA's ring and counters only after they
+    // are initialised
+    if (clustered)
+        cluster_sync_all();
     int failed = 0;
 
     if (t >= kThreads && t < kThreads + 32 && !stall_test) {
@@ -271,8 +425,9 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
         const int lane = t - kThreads;
         uint2 win = make_uint2(0, 0);
         int wbase = -64;
+        int s = 0;
+        uint32_t par = 1; // parity of the release of the stage's previous chunk
         for (int c = 0; c < nch; ++c) {
-            const int s = c % S;
             if (c >= wbase + 32) { // 32 descriptors per warp-wide load
                 wbase = c;
                 win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
@@ -280,9 +435,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
             const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
             const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
             // every wait decision is a warp vote: the lanes must stay converged
-            if (c >= S &&
-                __any_sync(0xffffffffu,
-                           !bounded_wait(&empty[s], (uint32_t)((c / S) - 1) & 1u, limit))) {
+            if (c >= S && __any_sync(0xffffffffu, !bounded_wait(&empty[s], par, limit))) {
                 failed = 1;
                 break;
             }
@@ -292,20 +445,91 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
                          &full[s]);
                 s_issued = c + 1;
             }
+            if (++s == S) {
+                s = 0;
+                par ^= 1u;
+            }
         }
-    } else if (t >= kThreads + 32 && !stall_test) {
-        // ------------------------------------------------------------ gatherer warp
-        // follows the chunks as they land: gathers each one's right-hand sides
-        const int lane = t - kThreads - 32;
+    } else if (t >= kThreads + 32 && t < kThreads + 96 && !stall_test) {
+        // ------------------------------------------------------------ gatherer warps
+        // follow the chunks as they land (even chunks: warp 9, odd: warp 10):
+        // gather each one's right-hand sides as one cp.async group, and hand
+        // the chunk over once its group has completed and the neighbours'
+        // progress allows it.  Each warp keeps one chunk's gathers in flight
+        // while it issues the next one's.  Every lane arrives itself, after
+        // waiting for its own copies (an arrive-on-completion of the copies,
+        // measured on this GPU, did not make them visible to the solving
+        // warps in time).
+        const int gw = (t - kThreads - 32) / 32;
+        const int lane = t % 32;
         bool ldone_seen = false;
-        for (int g = 0; g < nch; ++g) {
-            const int sg = g % S;
-            if (__any_sync(0xffffffffu, !bounded_wait(&full[sg], (uint32_t)(g / S) & 1u, limit))) {
+        int sg = gw; // S >= 3: chunk gw lies in stage gw, phase 0
+        uint32_t par = 0;
+        int gp = -1, sgp = 0; // the chunk whose gathers are in flight, and its stage
+        // hand chunk gp over: lane 0 first waits for the neighbours' progress
+        auto finish = [&]() -> bool {
+            int late = 0;
+            const unsigned char *ch = stages + (size_t)sgp * a.stage_bytes;
+            if (lane == 0 && clustered) {
+                // the values this chunk imports are in the ring, and the
+                // import slots its exports overwrite have been read
+                const int4 hdr = *reinterpret_cast<const int4 *>(ch);
+                const bool upass = (hdr.w & 1) != 0;
+                const int4 need = *reinterpret_cast<const int4 *>(ch + (FW > 0 ? 16 : 96));
+                const int xend = FW > 0 ? need.w : need.z;
+                long long it = 0;
+                if (need.x > 0)
+                    while ((int)ld_acquire_cluster_u32(&ctr[0]) < need.x && ++it < limit) {
+                    }
+                if (need.y > 0)
+                    while ((int)ld_acquire_cluster_u32(&ctr[1]) < need.y && ++it < limit) {
+                    }
+                if (hdr.w & 2) {
+                    // the export slots this chunk writes have been sent on:
+                    // the L pass's exports before any U chunk writes the ring
+                    if (upass && blk.nexp_L > 0)
+                        while ((int)ld_acquire_cta_u32(&s_sent[0]) < blk.nexp_L && ++it < limit) {
+                        }
+                    while ((int)ld_acquire_cta_u32(&s_sent[upass ? 1 : 0]) < xend - RI &&
+                           ++it < limit) {
+                    }
+                }
+                late = it >= limit;
+            }
+            if (__any_sync(0xffffffffu, late))
+                return false;
+            mbar_arrive(&ready[sgp]); // this lane's gathers of chunk gp have landed
+            return true;
+        };
+        for (int g = gw; g < nch; g += 2) {
+            // a chunk in flight is handed over first when the next one has not landed
+            if (gp >= 0 && !__all_sync(0xffffffffu, mbar_test_wait(&full[sg], par))) {
+                cp_async_wait_group<0>();
+                if (!finish()) {
+                    failed = 1;
+                    break;
+                }
+                gp = -1;
+            }
+            if (__any_sync(0xffffffffu, !bounded_wait(&full[sg], par, limit))) {
                 failed = 1;
                 break;
             }
-            const ChunkView<T> v = view_chunk<T>(stages + (size_t)sg * a.stage_bytes);
-            if (v.upass && !ldone_seen) {
+            const unsigned char *ch = stages + (size_t)sg * a.stage_bytes;
+            int4 hdr = *reinterpret_cast<const int4 *>(ch);
+            const bool upass = (hdr.w & 1) != 0;
+            if (!HEC_CHECK(upass == (g >= nL), 1, g, hdr.w, nL) ||
+                !HEC_CHECK(hdr.x >= 1 && hdr.x <= kThreads, 2, g, hdr.x, kThreads))
+                hdr.x = 0; // nothing gathered from a chunk that is not the expected one
+            if (upass && !ldone_seen) {
+                if (gp >= 0) { // the last L chunk in flight goes first
+                    cp_async_wait_group<0>();
+                    if (!finish()) {
+                        failed = 1;
+                        break;
+                    }
+                    gp = -1;
+                }
                 if (__any_sync(0xffffffffu, !bounded_wait(ldone, 0u, limit))) {
                     failed = 1;
                     break;
@@ -313,114 +537,277 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
                 ldone_seen = true;
             }
             T *slot = rhs + (size_t)sg * kThreads;
-            for (int i = lane; i < v.nrows; i += 32)
-                cp_async_v<sizeof(T)>(&slot[i], v.upass ? ysc + v.src[i] : r + v.src[i]);
-            cp_async_arrive_noinc(&ready[sg]); // when this lane's gathers land
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&ready[sg]); // the chunk's data has landed (seen above)
-        }
-        cp_async_wait_all();
-    } else if (t < kThreads) {
-    // ---------------------------------------------------------------- consumer warps
-    int err = 0;
-    int s = 0;
-    uint32_t par = 0;
-    for (int c = 0; c < nch; ++c) {
-        if (!bounded_wait(&ready[s], par, limit))
-            err = 1;
-        // results leave the critical path: global stores are issued after the
-        // stage is released, so the release does not wait for them
-        T out = T(0);
-        T *gout = nullptr;
-        if (!err) {
-            const unsigned char *ch = stages + (size_t)s * a.stage_bytes;
-            const ChunkView<T> v = view_chunk<T>(ch);
-            if (t < v.nrows) {
-                const bool rm = v.upass ? blk.ring_U : blk.ring_L;
-                const T *gdep = v.upass ? zsc : ysc;
-                const int lane = t % kWarpRows;
-                T sacc = rhs[(size_t)s * kThreads + t];
-                if constexpr (FW > 0) {
-                    // uniform-width layout: every warp's segment is FW entries
-                    // wide, so this thread's entries sit at a compile-time
-                    // offset from the chunk (all warps before the last are
-                    // full) and the row needs no width dispatch
-                    const int w = t / kWarpRows;
-                    const int stride = seg_stride(w, v.nrows);
-                    const T *val = reinterpret_cast<const T *>(
-                                       ch + 96 + (size_t)w * FW * kWarpRows * (sizeof(T) + 4)) +
-                                   lane;
-                    const int *dep = reinterpret_cast<const int *>(val - lane + FW * stride) + lane;
-                    T l[FW], y[FW];
-                    int d[FW];
-#pragma unroll
-                    for (int k = 0; k < FW; ++k) {
-                        l[k] = val[k * stride];
-                        d[k] = dep[k * stride];
-                    }
-                    if (rm) {
-#pragma unroll
-                        for (int k = 0; k < FW; ++k)
-                            y[k] = ring[d[k] & mask];
-                    } else {
-                        // the padding of a dependency-free row points at the
-                        // chunk's first position, which this apply has not
-                        // written yet in the global scratch (it may hold
-                        // anything, NaN included): entries of value 0 are
-                        // not read
-#pragma unroll
-                        for (int k = 0; k < FW; ++k)
-                            y[k] = l[k] != T(0) ? gdep[d[k]] : T(0);
-                    }
-#pragma unroll
-                    for (int k = 0; k < FW; ++k)
-                        sacc = fma(-l[k], y[k], sacc);
-                } else {
-                    const Segment<T> g = warp_segment<T>(ch, v.nrows, t / kWarpRows);
-                    sacc = rm ? row_solve_any<true, T>(g, lane, ring, mask, gdep, sacc)
-                              : row_solve_any<false, T>(g, lane, ring, mask, gdep, sacc);
+            const T *from = upass ? ysc : r;
+            if constexpr (FW > 0) {
+                const int blkb = Fixed<T, FW>::block(upass, exps);
+                const int *src = reinterpret_cast<const int *>(ch + kFixedHeader +
+                                                               Fixed<T, FW>::src(upass)) +
+                                 lane;
+                for (int i = lane, j = 0; i < hdr.x; i += 32, ++j) {
+                    const int si = *reinterpret_cast<const int *>(
+                        reinterpret_cast<const unsigned char *>(src) + (size_t)j * blkb);
+                    if (HEC_CHECK(si >= 0 && (upass || si < a.n), 3, g, si, a.n))
+                        cp_async_v<sizeof(T)>(&slot[i], from + si);
                 }
-                const int pos = v.base + t;
-                if (v.upass) {
-                    sacc *= v.dinv[t];
-                    if (rm)
-                        ring[pos & mask] = sacc;
-                    else
-                        zsc[pos] = sacc; // read by later levels of this pass
-                    const int d = v.dst[t];
-                    if (d >= 0)
-                        gout = z + d;
-                } else {
-                    if (rm) {
-                        ring[pos & mask] = sacc;
-                        gout = ysc_w + pos;
-                    } else {
-                        ysc_w[pos] = sacc; // read by later levels of this pass
-                    }
+            } else {
+                const ChunkView<T> v = view_chunk<T>(ch);
+                for (int i = lane; i < hdr.x; i += 32)
+                    if (HEC_CHECK(v.src[i] >= 0 && (upass || v.src[i] < a.n), 3, g, v.src[i], a.n))
+                        cp_async_v<sizeof(T)>(&slot[i], from + v.src[i]);
+            }
+            cp_async_commit();
+            if (gp >= 0) { // the previous chunk's group: all but the newest have completed
+                cp_async_wait_group<1>();
+                if (!finish()) {
+                    failed = 1;
+                    break;
                 }
-                out = sacc;
+            }
+            gp = g;
+            sgp = sg;
+            sg += 2;
+            if (sg >= S) {
+                sg -= S;
+                par ^= 1u;
             }
         }
-        if (consumer_sync_or(err)) {
-            failed = 1; // the feeding warps' own waits run out
-            break;
+        if (!failed && gp >= 0) {
+            cp_async_wait_group<0>();
+            if (!finish())
+                failed = 1;
         }
-        // the release falls to the last thread: warp 7 holds the shortest rows
-        if (t == kThreads - 1)
-            mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
+        cp_async_wait_all();
+    } else if (t >= kThreads + 96) {
+        // ------------------------------------------------------------ signaller warp
+        // one thread sends the exports of completed chunks on, then their
+        // count: a release orders the releasing thread's own earlier stores
+        // only, so the stores and the count come from the same thread
+        if (signal && t == kThreads + 96) {
+            const uint32_t to_prev = has_prev ? mapa_shared(smem_u32(&ctr[1]), part - 1) : 0;
+            const uint32_t to_next = has_next ? mapa_shared(smem_u32(&ctr[0]), part + 1) : 0;
+            // the neighbours' import rings: L values go to part p + 1, U to p - 1
+            const uint32_t imp_next = has_next ? mapa_shared(smem_u32(ring + nown), part + 1) : 0;
+            const uint32_t imp_prev = has_prev ? mapa_shared(smem_u32(ring + nown), part - 1) : 0;
+            uint32_t pub = 0;
+            int sentL = 0, sentU = 0;
+            long long it = 0;
+            while (pub < (uint32_t)nch) {
+                const uint64_t prog = ld_acquire_cta_u64(&s_prog);
+                const uint32_t v = (uint32_t)prog;
+                if (v > pub) {
+                    const int xe = (int)(prog >> 32);
+                    const int endL = (int)v > nL ? blk.nexp_L : xe;
+                    for (int i = sentL; i < endL; ++i)
+                        st_cluster(imp_next + (uint32_t)((i & (RI - 1)) * sizeof(T)),
+                                   xring[i & (RI - 1)]);
+                    sentL = endL;
+                    if ((int)v > nL) {
+                        for (int i = sentU; i < xe; ++i)
+                            st_cluster(imp_prev + (uint32_t)((i & (RI - 1)) * sizeof(T)),
+                                       xring[i & (RI - 1)]);
+                        sentU = xe;
+                    }
+                    fence_acq_rel_cluster();
+                    if (has_prev)
+                        st_relaxed_cluster_u32(to_prev, v);
+                    if (has_next)
+                        st_relaxed_cluster_u32(to_next, v);
+                    st_release_cta_u32(&s_sent[0], (uint32_t)sentL);
+                    st_release_cta_u32(&s_sent[1], (uint32_t)sentU);
+                    pub = v;
+                    it = 0;
+                } else if (*reinterpret_cast<volatile int *>(&s_err) || ++it >= limit) {
+                    failed = 1;
+                    break;
+                }
+            }
+        }
+    } else if (t < kThreads) {
+    // ---------------------------------------------------------------- consumer warps
+    volatile int *verr = &s_err;
+    int s = 0;        // stage of chunk c
+    uint32_t par = 0; // phase parity of chunk c's ready barrier
+    int err = 0;
+    // a solved row leaves: ring or scratch, neighbour's import ring; returns
+    // where its global copy goes (written after the level's barrier)
+    auto put = [&](bool upass, bool rm, int pos, int dst, int e, T acc) -> T * {
+        T *gout = nullptr;
+        if (upass) {
+            if (rm)
+                ring[pos & a.ring_mask] = acc;
+            else
+                zsc[pos] = acc; // read by later levels of this pass
+            if (dst >= 0)
+                gout = z + dst;
+        } else if (rm) {
+            ring[pos & a.ring_mask] = acc;
+            gout = ysc_w + pos;
+        } else {
+            ysc_w[pos] = acc; // read by later levels of this pass
+        }
+        if (e >= 0)
+            xring[e & (RI - 1)] = acc; // sent on by the signaller
+        return gout;
+    };
+    // after the level's barrier: global copies, end of the L pass, progress
+    auto close = [&](int c, int xend, T *gout, T out) {
         if (gout)
             *gout = out;
         if (c == nL - 1) {
-            // every y of the L pass is written before the gatherer reads
+            // every y of the L pass is written before the gatherers read
             // the U pass's right-hand sides from them
-            consumer_sync_or(0);
+            consumer_sync_and(1);
             if (t == kThreads - 1)
                 mbar_arrive(ldone);
         }
-        if (++s == S) {
-            s = 0;
-            par ^= 1u;
+        if (t == kThreads - 1 && signal)
+            st_release_cta_u64(&s_prog, ((uint64_t)(uint32_t)xend << 32) | (uint32_t)(c + 1));
+    };
+    if constexpr (FW > 0) {
+        const int w = t / kWarpRows, lane = t % kWarpRows;
+        RowRegs<T, FW> A, B;
+        bool have = false; // this thread holds its row of chunk c
+        bool held = true;  // chunk c's stage has not been released (uniform)
+        int c = 0;
+        int xbase = 0;     // position the program has reached in its pass
+        // one level; cur holds chunk c (if have), nxt receives chunk c + 1
+        auto step = [&](RowRegs<T, FW> &cur, RowRegs<T, FW> &nxt) -> bool {
+            const bool upass = c >= nL;
+            const bool rm = upass ? blk.ring_U : blk.ring_L;
+            if (!have) {
+                if (!bounded_wait(&ready[s], par, limit)) {
+                    err = 1;
+                    *verr = 1;
+                } else {
+                    load_fixed<T, FW>(stages + (size_t)s * a.stage_bytes,
+                                      rhs + (size_t)s * kThreads, w, lane, t, upass, exps, cur);
+                }
+            }
+            int sn = s + 1;
+            uint32_t parn = par;
+            if (sn == S) {
+                sn = 0;
+                parn ^= 1u;
+            }
+            bool pref = c + 1 >= nch;
+            T out = T(0);
+            T *gout = nullptr;
+            if (c == nL)
+                xbase = 0;
+            bool rows_ok = true;
+#ifdef HEC_DEBUG
+            if (!err) {
+                rows_ok = HEC_CHECK(cur.base == xbase, 4, c, cur.base, xbase) &&
+                          HEC_CHECK((cur.flags & 1) == (upass ? 1 : 0), 1, c, cur.flags, nL) &&
+                          HEC_CHECK(cur.nrows >= 1 && cur.nrows <= kThreads &&
+                                        cur.nwarps == (cur.nrows + 31) / 32,
+                                    2, c, cur.nrows, cur.nwarps);
+                if (rows_ok && w < cur.nwarps)
+                    for (int k = 0; k < FW; ++k)
+                        rows_ok &= rm ? HEC_CHECK(cur.d[k] >= 0 && cur.d[k] < nring - RI, 5, c,
+                                                  cur.d[k], nring - RI)
+                                      : HEC_CHECK(cur.l[k] == T(0) ||
+                                                      (cur.d[k] >= 0 && cur.d[k] < cur.base),
+                                                  6, c, cur.d[k], cur.base);
+                if (rows_ok && t < cur.nrows && upass)
+                    rows_ok &= HEC_CHECK(cur.dst < a.n, 7, c, cur.dst, a.n);
+            }
+#endif
+            xbase += cur.nrows;
+            if (!err) {
+                // warps past the chunk's last one hold no rows: their slots in
+                // the stage are stale bytes and are never used as indices
+                const bool rows = w < cur.nwarps && rows_ok;
+                // this level's dependencies (the previous level's barrier has
+                // passed); padding lanes of the last warp carry valid slots
+                const T *gdep = upass ? zsc : ysc;
+                T y[FW];
+                if (rows) {
+#pragma unroll
+                    for (int k = 0; k < FW; ++k)
+                        // global scratch: padding of a dependency-free row points
+                        // at a position this apply has not written (it may hold
+                        // NaN); entries of value 0 are not read
+                        y[k] = rm ? ring[cur.d[k]] : (cur.l[k] != T(0) ? gdep[cur.d[k]] : T(0));
+                }
+                // the next chunk's rows: loads only, nothing waits for them here
+                const bool okn = mbar_test_wait(&ready[sn], parn);
+                load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
+                                  rhs + (size_t)sn * kThreads, w, lane, t, c + 1 >= nL, exps, nxt);
+                pref = pref || okn;
+                if (rows) { // warps without rows issue no multiply-adds
+                    T acc = cur.rhs;
+#pragma unroll
+                    for (int k = 0; k < FW; ++k)
+                        acc = fma(-cur.l[k], y[k], acc);
+                    if (upass)
+                        acc *= cur.dinv;
+                    if (t < cur.nrows) {
+                        gout = put(upass, rm, cur.base + t, upass ? cur.dst : -1, cur.exp, acc);
+                        out = acc;
+                    }
+                }
+            }
+            const int all = consumer_sync_and(pref && !err);
+            if (!all && *verr)
+                return true; // the feeding warps' own waits run out
+            // stages every thread is done with: chunk c (unless it was freed
+            // with the previous level), and chunk c + 1 when every thread
+            // holds its row of it
+            const bool free_next = all && c + 1 < nch;
+            if (t == kThreads - 1) {
+                if (held)
+                    mbar_arrive(&empty[s]);
+                if (free_next)
+                    mbar_arrive(&empty[sn]);
+            }
+            close(c, cur.xend, gout, out);
+            held = !free_next;
+            have = pref && c + 1 < nch;
+            s = sn;
+            par = parn;
+            ++c;
+            return false;
+        };
+        while (c < nch) {
+            if (step(A, B) || (c < nch && step(B, A))) {
+                failed = 1;
+                break;
+            }
+        }
+    } else {
+        for (int c = 0; c < nch; ++c) {
+            if (!bounded_wait(&ready[s], par, limit)) {
+                err = 1;
+                *verr = 1;
+            }
+            T out = T(0);
+            T *gout = nullptr;
+            int xend = 0;
+            if (!err) {
+                const unsigned char *ch = stages + (size_t)s * a.stage_bytes;
+                const ChunkView<T> v = view_chunk<T>(ch);
+                xend = reinterpret_cast<const int *>(ch)[26];
+                if (t < v.nrows) {
+                    const bool rm = v.upass ? blk.ring_U : blk.ring_L;
+                    const T acc = solve_row_smem<T>(ch, v, t, rm, ring, v.upass ? zsc : ysc,
+                                                    rhs[(size_t)s * kThreads + t]);
+                    gout = put(v.upass, rm, v.base + t, v.upass ? v.dst[t] : -1,
+                               v.exports ? v.exp[t] : -1, acc);
+                    out = acc;
+                }
+            }
+            if (!consumer_sync_and(!err)) {
+                failed = 1; // the feeding warps' own waits run out
+                break;
+            }
+            if (t == kThreads - 1)
+                mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
+            close(c, xend, gout, out);
+            if (++s == S) {
+                s = 0;
+                par ^= 1u;
+            }
         }
     }
     }
@@ -437,6 +824,9 @@ __global__ void __launch_bounds__(kThreads + 64, 1) k_trsv_ras(TrsvArgs a)
         if (a.st)
             a.st->err = HEC_ERR_TIMEOUT;
     }
+    // no CTA leaves while a neighbour may still store into its shared memory
+    if (clustered)
+        cluster_sync_all();
 }
 
 // The dynamic shared memory limit is a process-wide attribute of the kernel:
@@ -462,18 +852,58 @@ template <class T, int FW> static cudaError_t prepare_trsv()
 
 template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s)
 {
-    const size_t smem = trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1, sizeof(T));
+    const size_t smem =
+        trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1 + 2 * a.import_slots, sizeof(T));
     if (prepare_trsv<T, FW>() != cudaSuccess)
         return -1;
-    k_trsv_ras<T, FW><<<a.nblocks, kThreads + 64, smem, s>>>(a);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)a.nblocks);
+    cfg.blockDim = dim3(kThreads + kFeedThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.parts;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.parts > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_trsv_ras<T, FW>, a) == cudaSuccess ? 0 : -1;
+}
+
+int trsv_debug_read(int *out, bool clear)
+{
+    if (cudaMemcpyFromSymbol(out, g_trsv_debug, sizeof(g_trsv_debug)) != cudaSuccess)
+        return -1;
+    if (clear) {
+        static const int zero[8] = {};
+        if (cudaMemcpyToSymbol(g_trsv_debug, zero, sizeof(zero)) != cudaSuccess)
+            return -1;
+    }
     return 0;
+}
+
+bool trsv_debug_build()
+{
+#ifdef HEC_DEBUG
+    return true;
+#else
+    return false;
+#endif
 }
 
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32)
 {
-    if (!fp32)
-        return launch_t<double, 0>(a, s);
-    switch (a.fixed_width) { // FP32 layouts padded to a uniform width
+    // fixed-slot layouts by their uniform width; generic layouts
+    if (!fp32) {
+        switch (a.fixed_width) {
+        case 4: return launch_t<double, 4>(a, s);
+        case 6: return launch_t<double, 6>(a, s);
+        case 8: return launch_t<double, 8>(a, s);
+        default: return launch_t<double, 0>(a, s);
+        }
+    }
+    switch (a.fixed_width) {
     case 4: return launch_t<float, 4>(a, s);
     case 6: return launch_t<float, 6>(a, s);
     case 8: return launch_t<float, 8>(a, s);

@@ -159,34 +159,45 @@ int launch_basis_combine(const BasisArgs &a, int grid, cudaStream_t s, bool fp32
 
 // ------------------------------------------------------------------ TRSV (RAS)
 struct TrsvBlock {
-    int chunk_begin, chunk_end; // chunk ids of this RAS block (L chunks then U chunks)
-    int chunk_mid, pad_;        // first U chunk
+    int chunk_begin, chunk_end; // chunk ids of this program (L chunks then U chunks)
+    int chunk_mid;              // first U chunk
+    int links;                  // bit 0: part p - 1 of the same RAS block exists, bit 1: part p + 1
     int ring_L, ring_U;         // 1: dependencies read from the shared-memory ring
-    int64_t yoff, zoff;         // offsets of this block in the y / z scratch
+    int nexp_L, pad_;           // values of the L pass part p + 1 imports
+    int64_t yoff, zoff;         // offsets of this program in the y / z scratch
 };
 struct TrsvArgs {
-    int nblocks;
+    int nblocks;                // programs: RAS blocks x parts
+    int parts;                  // CTAs per RAS block = cluster size (1: no cluster)
     const TrsvBlock *blocks;
     const uint2 *chunks;        // {offset in 16-byte units, bytes}
     const unsigned char *pack;  // packed chunk data
     const void *r;              // FP64, or FP32 for the FP32 layout
     void *z;
     void *ysc, *zsc;            // scratch: y by L position, z by U position
-    int ring_mask;              // ring slots - 1 (power of two)
+    int ring_mask;              // own ring slots R - 1 (power of two)
+    int import_slots;           // import ring slots RI (0 without split blocks)
     int stage_bytes, nstages;
-    int fixed_width;            // > 0: FP32 layout packed with this uniform warp width
+    int fixed_width;            // > 0: fixed-slot layout of this uniform row width (4, 6 or 8)
+    int exp_arrays;             // fixed-slot chunks carry export slots
     long long spin_limit;
     int *err;                   // device error word
     SolverState *st;            // nullable: skip / basis column / launch count
+    int n;                      // rows of z (bounds checks of the debug build)
     int r_from_j;
     int64_t ldv;
 };
-// Shared memory of one CTA: stages, ring, right-hand-side slots, barriers
-// (vbytes: 8 for FP64 values, 4 for FP32).
+// Shared memory of one CTA: stages, right-hand-side slots, own and import
+// ring, barriers and the two progress counters (vbytes: 8 for FP64, 4 for FP32).
 size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes);
-// Largest stage count (3..8) that fits the device's shared memory per CTA.
+// Largest stage count (3..8) that fits the device's shared memory per CTA
+// (ring_slots: own + import slots).
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes);
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false);
+// The first violation a debug build (HEC_DEBUG) recorded: code, program,
+// chunk, thread, value, bound, 0, 0 (all 0: none); clear resets it.
+int trsv_debug_read(int *out, bool clear);
+bool trsv_debug_build();
 // The uniform width (4, 6 or 8) the FP32 layout is padded to for rows of at
 // most longest_row entries; 0: longer rows, generic layout.
 int trsv_uniform_width(int longest_row);

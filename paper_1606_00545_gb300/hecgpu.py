@@ -17,6 +17,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhecgpu.so")
+# the same library compiled with HEC_DEBUG (device-side checks, see hec_debug_record)
+DEBUG_LIB_PATH = os.path.join(_HERE, "_build", "debug", "libhecgpu.so")
 
 OK = 0
 ERR_INVALID = -1
@@ -25,6 +27,7 @@ ERR_ZERO_PIVOT = -3
 ERR_UNSORTED_CSR = -4
 ERR_CUDA = -5
 ERR_TIMEOUT = -6
+ERR_DEBUG = -7
 MAXIT = 1
 BREAKDOWN = 2
 GMRES = 0
@@ -47,7 +50,7 @@ class HecError(RuntimeError):
 def _status_name(s):
     return {OK: "ok", ERR_INVALID: "invalid", ERR_OOM: "oom", ERR_ZERO_PIVOT: "zero pivot",
             ERR_UNSORTED_CSR: "unsorted csr", ERR_CUDA: "cuda", ERR_TIMEOUT: "timeout",
-            MAXIT: "maxit", BREAKDOWN: "breakdown"}.get(s, "?")
+            ERR_DEBUG: "debug check", MAXIT: "maxit", BREAKDOWN: "breakdown"}.get(s, "?")
 
 
 class CSR_t(C.Structure):
@@ -72,7 +75,9 @@ class PrecondInfo_t(C.Structure):
                 ("max_levels_L", C.c_int32), ("max_levels_U", C.c_int32),
                 ("apply_bytes", C.c_int64), ("device_bytes", C.c_int64),
                 ("ring_slots", C.c_int32), ("global_passes", C.c_int32),
-                ("apply_bytes_f32", C.c_int64)]
+                ("apply_bytes_f32", C.c_int64), ("trsv_parts", C.c_int32),
+                ("import_slots", C.c_int32), ("split_blocks", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class SolveOpts_t(C.Structure):
@@ -158,7 +163,10 @@ _SIGS = {
     "hec_precond_get_factor": ([_vp, _i32, C.POINTER(_i32), _vp, _vp, _vp, _vp], C.c_int),
     "hec_precond_get_levels": ([_vp, _i32, _i32, C.POINTER(_i32), _vp, _vp], C.c_int),
     "hec_precond_get_layout": ([_vp, _i32, C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32),
-                                C.POINTER(_i32), _vp, _vp, _vp, _vp], C.c_int),
+                                C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), _vp, _vp, _vp,
+                                _vp], C.c_int),
+    "hec_precond_set_trsv_parts": ([_vp, _i32], C.c_int),
+    "hec_debug_record": ([_vp, _i32], C.c_int),
     "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_status": ([_vp, _vp], C.c_int),
     "hec_precond_apply_noalloc": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
@@ -427,20 +435,23 @@ class Precond:
     def layout(self, fp32=False, stream=None):
         """The triangular solves' level-major chunk layout, host copies:
         dict(pack=uint8 bytes, chunks=(nchunks, 2) uint32 {offset/16, bytes},
-        blocks=(nblocks, 7) int64, ring_slots, fixed_width, vbytes)."""
-        nb, nc, ring, fw = _i64(), _i32(), _i32(), _i32()
+        programs=(nblocks * parts, 8) int64, ring_slots, import_slots, parts,
+        fixed_width, vbytes)."""
+        nb, nc, ring, imp, parts, fw = _i64(), _i32(), _i32(), _i32(), _i32(), _i32()
         st = C.c_void_p(0) if self.A is not None and _is_host_only(self) else _stream(stream)
-        _check(_lib.hec_precond_get_layout(self._h, int(bool(fp32)), C.byref(nb), C.byref(nc),
-                                           C.byref(ring), C.byref(fw), None, None, None, st),
-               "hec_precond_get_layout")
+
+        def call(*arrays):
+            _check(_lib.hec_precond_get_layout(self._h, int(bool(fp32)), C.byref(nb), C.byref(nc),
+                                               C.byref(ring), C.byref(imp), C.byref(parts),
+                                               C.byref(fw), *arrays, st), "hec_precond_get_layout")
+        call(None, None, None)
         pack = np.zeros(nb.value, np.uint8)
         chunks = np.zeros((nc.value, 2), np.uint32)
-        blocks = np.zeros((self.info()["nblocks"], 7), np.int64)
-        _check(_lib.hec_precond_get_layout(self._h, int(bool(fp32)), C.byref(nb), C.byref(nc),
-                                           C.byref(ring), C.byref(fw), _ptr(pack), _ptr(chunks),
-                                           _ptr(blocks), st), "hec_precond_get_layout")
-        return {"pack": pack, "chunks": chunks, "blocks": blocks, "ring_slots": ring.value,
-                "fixed_width": fw.value, "vbytes": 4 if fp32 else 8}
+        programs = np.zeros((self.info()["nblocks"] * parts.value, 8), np.int64)
+        call(_ptr(pack), _ptr(chunks), _ptr(programs))
+        return {"pack": pack, "chunks": chunks, "programs": programs, "ring_slots": ring.value,
+                "import_slots": imp.value, "parts": parts.value, "fixed_width": fw.value,
+                "vbytes": 4 if fp32 else 8}
 
     def destroy(self):
         if self._h and _lib is not None:
@@ -478,7 +489,12 @@ def ilu_k_setup(A: Matrix, k: int, nblocks: int, overlap: int, stream=None) -> P
     return Precond(h, A)
 
 
-def level_schedule(M: Precond, stream=None):
+def level_schedule(M: Precond, stream=None, parts: int = 0):
+    """Eq. 11 level sets and the triangular-solve layout.  parts: CTAs per
+    RAS block of the triangular solve (0: automatic; 1, 2, 4 or 8)."""
+    if parts:
+        _check(load_library().hec_precond_set_trsv_parts(M.handle, int(parts)),
+               "hec_precond_set_trsv_parts")
     st = C.c_void_p(0) if M.A is not None and _is_host_only(M) else _stream(stream)
     _check(load_library().level_schedule(M.handle, st), "level_schedule")
 

@@ -74,8 +74,8 @@ def test_refactor_equals_fresh_setup_bit_for_bit(H, orc, k, nb, ov):
     # the layouts refilled on the device equal those packed from scratch, byte for byte
     for fp32 in (False, True):
         la, lb = P.layout(fp32=fp32), P1.layout(fp32=fp32)
-        assert np.array_equal(la["chunks"], lb["chunks"]) and np.array_equal(la["blocks"],
-                                                                              lb["blocks"])
+        assert np.array_equal(la["chunks"], lb["chunks"]) and np.array_equal(la["programs"],
+                                                                              lb["programs"])
         assert np.array_equal(la["pack"], lb["pack"]), fp32
     # SpMV on the new values
     y = dev(np.zeros(A0.n))
