@@ -364,8 +364,8 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
     if (!M->host_only) {
-        L.nstages = trsv_stages_for(L.pack.stage_bytes,
-                                    L.pack.ring_slots + 2 * L.pack.import_slots, L.vbytes);
+        L.nstages = trsv_stages_for(L.pack.stage_bytes, L.pack.ring_slots + L.pack.import_slots,
+                                    L.vbytes);
         HEC_TRY(upload(L.d_pack, L.pack.pack, s));
         HEC_TRY(upload(L.d_chunks, L.pack.chunks, s));
         HEC_TRY(upload(L.d_blocks, L.pack.blocks, s));

@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(kThreads) k_iluk_numeric(RefactorArgs a)
 // CTA per chunk, thread t on row t.  Row t of chunk c takes the factor
 // entries [start, start + len) of its pass (L: the multipliers; U: the
 // entries right of the diagonal) and, for U, 1 / u_tt.  Both chunk formats
-// of trsv_layout.cpp: fixed-slot (flag bit 3: every row padded to FW entries
-// in per-warp blocks) and generic (per-warp widths).
+// of trsv_layout.cpp: fixed-slot (flag bit 3: every row padded to FW entries,
+// 16-byte vectors per lane in per-warp blocks) and generic (per-warp widths).
 template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillArgs a)
 {
     const int c = blockIdx.x;
@@ -178,16 +178,18 @@ template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillA
     const int w = t / 32, lane = t % 32;
     const int64_t q = a.chunk_row0[c] + t;
     const int start = a.rm_start[q], len = a.rm_len[q];
-    if (hdr[3] & 8) {
+    if (hdr[3] & 8) { // fixed-slot: 16-byte vectors of VW values per lane
         const int FW = hdr[6];
         const bool exps = (hdr[3] & 16) != 0;
-        const int vb = (int)sizeof(T);
-        const int blk = FW * 32 * vb + (FW + 1) * 128 + (upass ? 32 * vb + 128 : 0) + (exps ? 128 : 0);
+        constexpr int vb = (int)sizeof(T), VW = 16 / vb;
+        const int NV = (FW + VW - 1) / VW, ND = (FW + 3) / 4;
+        const int blk = (NV + ND) * 512 + 128 + (upass ? 32 * vb + 128 : 0) + (exps ? 128 : 0);
         T *val = reinterpret_cast<T *>(ch + 32 + (size_t)w * blk);
-        for (int k = 0; k < FW; ++k)
-            val[k * 32 + lane] = k < len ? T(a.f[start + k]) : T(0);
+        for (int k = 0; k < NV * VW; ++k)
+            val[(k / VW) * 32 * VW + lane * VW + k % VW] = k < len ? T(a.f[start + k]) : T(0);
         if (upass)
-            val[FW * 32 + lane] = T(__ddiv_rn(1.0, a.f[a.rm_diag[q]]));
+            reinterpret_cast<T *>(ch + 32 + (size_t)w * blk + (NV + ND) * 512)[lane] =
+                T(__ddiv_rn(1.0, a.f[a.rm_diag[q]]));
         return;
     }
     const int left = nrows - w * 32;

@@ -32,14 +32,11 @@
 //     indexed by level-major position (the setup checks that every
 //     dependency of a chunk lies within the ring's window; passes whose
 //     window does not fit read dependencies from the global scratch); values
-//     a neighbouring part reads are also kept in a local export ring;
-//   - one signaller thread copies the exports of completed chunks into the
-//     neighbour's import ring (distributed shared memory), fences at cluster
-//     scope, and only then stores the completed-chunk count into the
-//     neighbour's shared memory -- off the solving warps' path.  (A release
-//     orders the releasing thread's own stores: measured on this GPU, a
-//     fence by one thread after a CTA barrier did not order the
-//     distributed-shared-memory stores of the other threads.)
+//     a neighbouring part reads are also stored straight into that part's
+//     import ring (distributed shared memory);
+//   - a signaller warp forwards the completed-chunk count to the neighbouring
+//     parts (a release at cluster scope, then the count stored into their
+//     shared memory), off the solving warps' path.
 // Levels are separated by a barrier of the solving warps only -- no
 // grid-wide synchronisation.  Every wait is bounded: a wait that runs out
 // sets the device error word, one thread waits (bounded) for the copies still
@@ -52,13 +49,13 @@
 namespace hec {
 
 // Shared memory of one CTA: S stages, S right-hand-side slots of kThreads
-// values, the ring (own, import and export slots: ring_slots in all), 3 S + 1
+// values, the ring (own and import slots: ring_slots in all), 2 S + 1
 // mbarriers and two progress counters.  vbytes: 8 (FP64) or 4 (FP32).
 size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
 {
     const size_t ring = ((size_t)ring_slots * vbytes + 7) & ~(size_t)7;
     return (size_t)stage_bytes * nstages + (size_t)nstages * kThreads * vbytes + ring +
-           (size_t)(3 * nstages + 1) * sizeof(uint64_t) + 2 * sizeof(uint32_t);
+           (size_t)(2 * nstages + 1) * sizeof(uint64_t) + 2 * sizeof(uint32_t);
 }
 
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes)
@@ -120,6 +117,7 @@ constexpr long long kDrainPolls = 1ll << 24;
 constexpr int kWarpRows = 32;
 constexpr int kMaxWarps = kThreads / kWarpRows;
 constexpr int kFeedThreads = 128; // issuer, two gatherers and the signaller
+constexpr int kMaxStages = 8;
 
 __device__ __forceinline__ int seg_stride(int w, int nrows)
 {
@@ -272,15 +270,37 @@ __device__ __forceinline__ T solve_row_smem(const unsigned char *ch, const Chunk
 // (written by trsv_layout.cpp; every row padded to FW entries)
 //   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 1: exports)
 //   [16, 32)  need_prev, need_next, FW, xend (exports of the pass so far)
-//   per warp w < nwarps a block, lane l = row 32w + l: val[FW][32] (T);
-//   U: dinv[32] (T); dep[FW][32], src[32] (int32); U: dst[32]; exp[32]
-//   (export positions, -1: none) in launches with exp_arrays
+//   per warp w < nwarps a block, lane l = row 32w + l: val (ceil(FW / VW)
+//   vectors of 32 lanes x 16 bytes, VW = 16 / sizeof(T)), dep (ceil(FW / 4)
+//   vectors of 32 lanes x 4 int32), U: dinv[32] (T), src[32] (int32), U:
+//   dst[32] (int32), exp[32] (int32 export positions, -1: none) in launches
+//   with exp_arrays
 constexpr int kFixedHeader = 32;
 
+template <class T> struct Vec16;
+template <> struct Vec16<double> {
+    using type = double2;
+    __device__ static double get(const double2 &v, int j) { return j == 0 ? v.x : v.y; }
+};
+template <> struct Vec16<float> {
+    using type = float4;
+    __device__ static float get(const float4 &v, int j)
+    {
+        return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    }
+};
+__device__ __forceinline__ int get4(const int4 &v, int j)
+{
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
 template <class T, int FW> struct Fixed {
-    __device__ static constexpr int dinv(bool) { return FW * 32 * (int)sizeof(T); }
-    __device__ static constexpr int dep(bool u) { return FW * 32 * (int)sizeof(T) + (u ? 32 * (int)sizeof(T) : 0); }
-    __device__ static constexpr int src(bool u) { return dep(u) + FW * 128; }
+    static constexpr int VW = 16 / (int)sizeof(T);
+    static constexpr int NV = (FW + VW - 1) / VW; // value vectors per lane
+    static constexpr int ND = (FW + 3) / 4;       // dependency vectors per lane
+    __device__ static constexpr int dep() { return NV * 512; }
+    __device__ static constexpr int dinv() { return (NV + ND) * 512; }
+    __device__ static constexpr int src(bool u) { return dinv() + (u ? 32 * (int)sizeof(T) : 0); }
     __device__ static constexpr int dst(bool u) { return src(u) + 128; }
     __device__ static constexpr int exp(bool u) { return src(u) + 128 + (u ? 128 : 0); }
     __device__ static constexpr int block(bool u, bool e) { return exp(u) + (e ? 128 : 0); }
@@ -289,39 +309,50 @@ template <class T, int FW> struct Fixed {
 // A solving thread's copy of its row of one fixed-slot chunk, with the
 // chunk's header fields.
 template <class T, int FW> struct RowRegs {
-    int nrows, nwarps, base, xend, flags;
-    T l[FW];
-    int d[FW];
+    int nrows, nwarps, base, flags;
+    typename Vec16<T>::type lv[Fixed<T, FW>::NV];
+    int4 dv[Fixed<T, FW>::ND];
     T rhs, dinv;
     int dst, exp;
+    __device__ T l(int k) const { return Vec16<T>::get(lv[k / Fixed<T, FW>::VW], k % Fixed<T, FW>::VW); }
+    __device__ int d(int k) const { return get4(dv[k / 4], k % 4); }
 };
 
 // Every address below depends only on the stage, the thread and the pass,
-// never on a value read from the stage: all loads issue back to back.
+// never on a value read from the stage: all loads issue back to back, 16
+// bytes each for the row's entries.
 template <class T, int FW>
 __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rslot, int w, int lane,
                                            int t, bool upass, bool exps, RowRegs<T, FW> &R)
 {
+    using F = Fixed<T, FW>;
     const int4 hdr = *reinterpret_cast<const int4 *>(ch);
     R.nrows = hdr.x;
     R.nwarps = hdr.y;
     R.base = hdr.z;
     R.flags = hdr.w;
-    R.xend = reinterpret_cast<const int4 *>(ch)[1].w;
-    const unsigned char *blk = ch + kFixedHeader + (size_t)w * Fixed<T, FW>::block(upass, exps);
-    const T *val = reinterpret_cast<const T *>(blk) + lane;
-    const int *dep = reinterpret_cast<const int *>(blk + Fixed<T, FW>::dep(upass)) + lane;
+    const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(upass, exps);
+    const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
 #pragma unroll
-    for (int k = 0; k < FW; ++k) {
-        R.l[k] = val[k * 32];
-        R.d[k] = dep[k * 32];
-    }
+    for (int v = 0; v < F::NV; ++v)
+        R.lv[v] = val[v * 32];
+    const int4 *dep = reinterpret_cast<const int4 *>(blk + F::dep()) + lane;
+#pragma unroll
+    for (int v = 0; v < F::ND; ++v)
+        R.dv[v] = dep[v * 32];
     R.rhs = rslot[t];
     if (upass) {
-        R.dinv = reinterpret_cast<const T *>(blk + Fixed<T, FW>::dinv(true))[lane];
-        R.dst = reinterpret_cast<const int *>(blk + Fixed<T, FW>::dst(true))[lane];
+        R.dinv = reinterpret_cast<const T *>(blk + F::dinv())[lane];
+        R.dst = reinterpret_cast<const int *>(blk + F::dst(true))[lane];
     }
-    R.exp = exps ? reinterpret_cast<const int *>(blk + Fixed<T, FW>::exp(upass))[lane] : -1;
+    R.exp = exps ? reinterpret_cast<const int *>(blk + F::exp(upass))[lane] : -1;
+}
+
+// Release-add by one thread to a shared counter (the handover of a chunk).
+__device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+                 : "memory");
 }
 
 // Warp-specialised CTA: warps 0-7 solve rows (one row per thread per chunk),
@@ -334,16 +365,18 @@ __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rsl
 //             right-hand side is the L pass's output) -> once the group has
 //             completed (waited for while the warp's next chunk is gathered)
 //             and lane 0 has seen the neighbouring parts' progress counters
-//             reach the chunk's thresholds, every lane arrives on ready[s];
+//             reach the chunk's thresholds, every lane adds 1 to the stage's
+//             handover counter (release): 32 per chunk;
 //   consumers: fixed-slot chunks are software-pipelined by one chunk: while
 //             chunk c's multiply-add chain runs, every thread copies its row
-//             of chunk c + 1 into registers (when that chunk is ready
-//             already).  The level's results go to the ring (and, for
-//             exports, into the neighbour's import ring), the consumer
-//             barrier closes the level, and the last thread frees the stages
-//             every thread is done with -- chunk c, and chunk c + 1 once all
-//             threads hold it -- and publishes the completed count.  Generic
-//             chunks are solved from shared memory, one at a time;
+//             of chunk c + 1 into registers, and keeps the copy if the
+//             handover counter it read (acquire) shows that chunk complete.
+//             The level's results go to the ring (and, for exports, into the
+//             neighbour's import ring), the consumer barrier closes the
+//             level, and the last thread frees the stages every thread is
+//             done with -- chunk c, and chunk c + 1 once all threads hold it
+//             -- and publishes the completed count.  Generic chunks are
+//             solved from shared memory, one at a time;
 //   signaller (warp 11): for a split block, forwards the completed count to
 //             the neighbouring parts (a release at cluster scope, then the
 //             count stored into their shared memory) as often as the fence
@@ -370,12 +403,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
     T *ring = rhs + (size_t)S * kThreads;
     const int nown = a.ring_mask + 1;
     const int RI = a.import_slots;
-    const int nring = nown + 2 * RI; // own values, imports, exports
+    const int nring = nown + RI; // own values, then values imported from a neighbour
     uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) +
                                                   (((size_t)nring * sizeof(T) + 7) & ~(size_t)7));
     uint64_t *empty = full + S;
-    uint64_t *ready = empty + S;
-    uint64_t *ldone = ready + S;
+    uint64_t *ldone = empty + S;
     uint32_t *ctr = reinterpret_cast<uint32_t *>(ldone + 1); // [0]: from part p - 1, [1]: from p + 1
     const int nch = blk.chunk_end - blk.chunk_begin;
     const int nL = blk.chunk_mid - blk.chunk_begin; // chunks of the L pass
@@ -390,26 +422,25 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
     T *zsc = a.zsc ? reinterpret_cast<T *>(a.zsc) + blk.zoff : nullptr;
     T *z = reinterpret_cast<T *>(a.z);
     const int t = threadIdx.x;
-    T *xring = ring + nown + RI; // this CTA's exports, slot = export position & (RI - 1)
     // shared state of the roles (written before the final barrier)
     __shared__ int s_issued, s_err;
-    __shared__ uint64_t s_prog;          // chunks completed | exports of that pass << 32
-    __shared__ uint32_t s_sent[2];       // exports copied to the neighbour: L, U
+    __shared__ uint32_t s_done;             // chunks the consumers have completed
+    __shared__ uint32_t s_hand[kMaxStages]; // handover count of every stage: 32 per chunk
 
     if (t == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&ready[s], 32); // every gatherer lane, once its copies have landed
         }
         mbar_init(ldone, 1);
         ctr[0] = ctr[1] = 0;
         s_issued = 0;
         s_err = 0;
-        s_prog = 0;
-        s_sent[0] = s_sent[1] = 0;
+        s_done = 0;
         fence_mbar_init();
     }
+    if (t < kMaxStages)
+        s_hand[t] = 0;
     for (int i = t; i < nown; i += blockDim.x)
         ring[i] = T(0);
     __syncthreads();
@@ -456,10 +487,10 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         // gather each one's right-hand sides as one cp.async group, and hand
         // the chunk over once its group has completed and the neighbours'
         // progress allows it.  Each warp keeps one chunk's gathers in flight
-        // while it issues the next one's.  Every lane arrives itself, after
-        // waiting for its own copies (an arrive-on-completion of the copies,
-        // measured on this GPU, did not make them visible to the solving
-        // warps in time).
+        // while it issues the next one's.  Every lane hands over for itself,
+        // after waiting for its own copies (an arrive-on-completion of the
+        // copies, measured on this GPU, did not make them visible to the
+        // solving warps in time).
         const int gw = (t - kThreads - 32) / 32;
         const int lane = t % 32;
         bool ldone_seen = false;
@@ -469,14 +500,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         // hand chunk gp over: lane 0 first waits for the neighbours' progress
         auto finish = [&]() -> bool {
             int late = 0;
-            const unsigned char *ch = stages + (size_t)sgp * a.stage_bytes;
             if (lane == 0 && clustered) {
                 // the values this chunk imports are in the ring, and the
                 // import slots its exports overwrite have been read
-                const int4 hdr = *reinterpret_cast<const int4 *>(ch);
-                const bool upass = (hdr.w & 1) != 0;
-                const int4 need = *reinterpret_cast<const int4 *>(ch + (FW > 0 ? 16 : 96));
-                const int xend = FW > 0 ? need.w : need.z;
+                const unsigned char *ch = stages + (size_t)sgp * a.stage_bytes;
+                const int2 need = *reinterpret_cast<const int2 *>(ch + (FW > 0 ? 16 : 96));
                 long long it = 0;
                 if (need.x > 0)
                     while ((int)ld_acquire_cluster_u32(&ctr[0]) < need.x && ++it < limit) {
@@ -484,21 +512,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 if (need.y > 0)
                     while ((int)ld_acquire_cluster_u32(&ctr[1]) < need.y && ++it < limit) {
                     }
-                if (hdr.w & 2) {
-                    // the export slots this chunk writes have been sent on:
-                    // the L pass's exports before any U chunk writes the ring
-                    if (upass && blk.nexp_L > 0)
-                        while ((int)ld_acquire_cta_u32(&s_sent[0]) < blk.nexp_L && ++it < limit) {
-                        }
-                    while ((int)ld_acquire_cta_u32(&s_sent[upass ? 1 : 0]) < xend - RI &&
-                           ++it < limit) {
-                    }
-                }
                 late = it >= limit;
             }
             if (__any_sync(0xffffffffu, late))
                 return false;
-            mbar_arrive(&ready[sgp]); // this lane's gathers of chunk gp have landed
+            red_release_add(&s_hand[sgp], 1u); // this lane's gathers of chunk gp have landed
             return true;
         };
         for (int g = gw; g < nch; g += 2) {
@@ -540,12 +558,9 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             const T *from = upass ? ysc : r;
             if constexpr (FW > 0) {
                 const int blkb = Fixed<T, FW>::block(upass, exps);
-                const int *src = reinterpret_cast<const int *>(ch + kFixedHeader +
-                                                               Fixed<T, FW>::src(upass)) +
-                                 lane;
+                const unsigned char *src = ch + kFixedHeader + Fixed<T, FW>::src(upass) + 4 * lane;
                 for (int i = lane, j = 0; i < hdr.x; i += 32, ++j) {
-                    const int si = *reinterpret_cast<const int *>(
-                        reinterpret_cast<const unsigned char *>(src) + (size_t)j * blkb);
+                    const int si = *reinterpret_cast<const int *>(src + (size_t)j * blkb);
                     if (HEC_CHECK(si >= 0 && (upass || si < a.n), 3, g, si, a.n))
                         cp_async_v<sizeof(T)>(&slot[i], from + si);
                 }
@@ -579,41 +594,22 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         cp_async_wait_all();
     } else if (t >= kThreads + 96) {
         // ------------------------------------------------------------ signaller warp
-        // one thread sends the exports of completed chunks on, then their
-        // count: a release orders the releasing thread's own earlier stores
-        // only, so the stores and the count come from the same thread
+        // publishes the completed-chunk count to the neighbours: the release
+        // at cluster scope covers the consumers' stores into the neighbours'
+        // import rings, ordered before the count by the consumer barrier
         if (signal && t == kThreads + 96) {
             const uint32_t to_prev = has_prev ? mapa_shared(smem_u32(&ctr[1]), part - 1) : 0;
             const uint32_t to_next = has_next ? mapa_shared(smem_u32(&ctr[0]), part + 1) : 0;
-            // the neighbours' import rings: L values go to part p + 1, U to p - 1
-            const uint32_t imp_next = has_next ? mapa_shared(smem_u32(ring + nown), part + 1) : 0;
-            const uint32_t imp_prev = has_prev ? mapa_shared(smem_u32(ring + nown), part - 1) : 0;
             uint32_t pub = 0;
-            int sentL = 0, sentU = 0;
             long long it = 0;
             while (pub < (uint32_t)nch) {
-                const uint64_t prog = ld_acquire_cta_u64(&s_prog);
-                const uint32_t v = (uint32_t)prog;
+                const uint32_t v = ld_acquire_cta_u32(&s_done);
                 if (v > pub) {
-                    const int xe = (int)(prog >> 32);
-                    const int endL = (int)v > nL ? blk.nexp_L : xe;
-                    for (int i = sentL; i < endL; ++i)
-                        st_cluster(imp_next + (uint32_t)((i & (RI - 1)) * sizeof(T)),
-                                   xring[i & (RI - 1)]);
-                    sentL = endL;
-                    if ((int)v > nL) {
-                        for (int i = sentU; i < xe; ++i)
-                            st_cluster(imp_prev + (uint32_t)((i & (RI - 1)) * sizeof(T)),
-                                       xring[i & (RI - 1)]);
-                        sentU = xe;
-                    }
                     fence_acq_rel_cluster();
                     if (has_prev)
                         st_relaxed_cluster_u32(to_prev, v);
                     if (has_next)
                         st_relaxed_cluster_u32(to_next, v);
-                    st_release_cta_u32(&s_sent[0], (uint32_t)sentL);
-                    st_release_cta_u32(&s_sent[1], (uint32_t)sentU);
                     pub = v;
                     it = 0;
                 } else if (*reinterpret_cast<volatile int *>(&s_err) || ++it >= limit) {
@@ -625,9 +621,22 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
     } else if (t < kThreads) {
     // ---------------------------------------------------------------- consumer warps
     volatile int *verr = &s_err;
-    int s = 0;        // stage of chunk c
-    uint32_t par = 0; // phase parity of chunk c's ready barrier
+    // the neighbours' import rings: L values go to part p + 1, U values to p - 1
+    const uint32_t imp_next =
+        has_next ? mapa_shared(smem_u32(ring + nown), part + 1) : 0;
+    const uint32_t imp_prev =
+        has_prev ? mapa_shared(smem_u32(ring + nown), part - 1) : 0;
+    int s = 0;         // stage of chunk c
+    uint32_t hneed = 32; // the stage's handover count once chunk c is handed over
     int err = 0;
+    // wait (bounded) until chunk c, in stage s, has been handed over
+    auto handed = [&](int st, uint32_t need) -> bool {
+        long long it = 0;
+        while (ld_acquire_cta_u32(&s_hand[st]) < need)
+            if (++it >= limit)
+                return false;
+        return true;
+    };
     // a solved row leaves: ring or scratch, neighbour's import ring; returns
     // where its global copy goes (written after the level's barrier)
     auto put = [&](bool upass, bool rm, int pos, int dst, int e, T acc) -> T * {
@@ -646,11 +655,12 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             ysc_w[pos] = acc; // read by later levels of this pass
         }
         if (e >= 0)
-            xring[e & (RI - 1)] = acc; // sent on by the signaller
+            st_cluster((upass ? imp_prev : imp_next) + (uint32_t)((e & (RI - 1)) * sizeof(T)),
+                       acc);
         return gout;
     };
     // after the level's barrier: global copies, end of the L pass, progress
-    auto close = [&](int c, int xend, T *gout, T out) {
+    auto close = [&](int c, T *gout, T out) {
         if (gout)
             *gout = out;
         if (c == nL - 1) {
@@ -661,7 +671,7 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 mbar_arrive(ldone);
         }
         if (t == kThreads - 1 && signal)
-            st_release_cta_u64(&s_prog, ((uint64_t)(uint32_t)xend << 32) | (uint32_t)(c + 1));
+            st_release_cta_u32(&s_done, (uint32_t)(c + 1));
     };
     if constexpr (FW > 0) {
         const int w = t / kWarpRows, lane = t % kWarpRows;
@@ -675,7 +685,7 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             const bool upass = c >= nL;
             const bool rm = upass ? blk.ring_U : blk.ring_L;
             if (!have) {
-                if (!bounded_wait(&ready[s], par, limit)) {
+                if (!handed(s, hneed)) {
                     err = 1;
                     *verr = 1;
                 } else {
@@ -684,10 +694,10 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 }
             }
             int sn = s + 1;
-            uint32_t parn = par;
+            uint32_t hneedn = hneed;
             if (sn == S) {
                 sn = 0;
-                parn ^= 1u;
+                hneedn += 32;
             }
             bool pref = c + 1 >= nch;
             T out = T(0);
@@ -704,11 +714,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                                     2, c, cur.nrows, cur.nwarps);
                 if (rows_ok && w < cur.nwarps)
                     for (int k = 0; k < FW; ++k)
-                        rows_ok &= rm ? HEC_CHECK(cur.d[k] >= 0 && cur.d[k] < nring - RI, 5, c,
-                                                  cur.d[k], nring - RI)
-                                      : HEC_CHECK(cur.l[k] == T(0) ||
-                                                      (cur.d[k] >= 0 && cur.d[k] < cur.base),
-                                                  6, c, cur.d[k], cur.base);
+                        rows_ok &= rm ? HEC_CHECK(cur.d(k) >= 0 && cur.d(k) < nring, 5, c,
+                                                  cur.d(k), nring)
+                                      : HEC_CHECK(cur.l(k) == T(0) ||
+                                                      (cur.d(k) >= 0 && cur.d(k) < cur.base),
+                                                  6, c, cur.d(k), cur.base);
                 if (rows_ok && t < cur.nrows && upass)
                     rows_ok &= HEC_CHECK(cur.dst < a.n, 7, c, cur.dst, a.n);
             }
@@ -728,18 +738,18 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                         // global scratch: padding of a dependency-free row points
                         // at a position this apply has not written (it may hold
                         // NaN); entries of value 0 are not read
-                        y[k] = rm ? ring[cur.d[k]] : (cur.l[k] != T(0) ? gdep[cur.d[k]] : T(0));
+                        y[k] = rm ? ring[cur.d(k)] : (cur.l(k) != T(0) ? gdep[cur.d(k)] : T(0));
                 }
-                // the next chunk's rows: loads only, nothing waits for them here
-                const bool okn = mbar_test_wait(&ready[sn], parn);
+                // the next chunk's rows: loads only, kept if the handover
+                // count (read first, with acquire) shows the chunk complete
+                const uint32_t hn = ld_acquire_cta_u32(&s_hand[sn]);
                 load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
                                   rhs + (size_t)sn * kThreads, w, lane, t, c + 1 >= nL, exps, nxt);
-                pref = pref || okn;
                 if (rows) { // warps without rows issue no multiply-adds
                     T acc = cur.rhs;
 #pragma unroll
                     for (int k = 0; k < FW; ++k)
-                        acc = fma(-cur.l[k], y[k], acc);
+                        acc = fma(-cur.l(k), y[k], acc);
                     if (upass)
                         acc *= cur.dinv;
                     if (t < cur.nrows) {
@@ -747,6 +757,7 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                         out = acc;
                     }
                 }
+                pref = pref || hn >= hneedn;
             }
             const int all = consumer_sync_and(pref && !err);
             if (!all && *verr)
@@ -761,11 +772,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 if (free_next)
                     mbar_arrive(&empty[sn]);
             }
-            close(c, cur.xend, gout, out);
+            close(c, gout, out);
             held = !free_next;
             have = pref && c + 1 < nch;
             s = sn;
-            par = parn;
+            hneed = hneedn;
             ++c;
             return false;
         };
@@ -777,17 +788,15 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         }
     } else {
         for (int c = 0; c < nch; ++c) {
-            if (!bounded_wait(&ready[s], par, limit)) {
+            if (!handed(s, hneed)) {
                 err = 1;
                 *verr = 1;
             }
             T out = T(0);
             T *gout = nullptr;
-            int xend = 0;
             if (!err) {
                 const unsigned char *ch = stages + (size_t)s * a.stage_bytes;
                 const ChunkView<T> v = view_chunk<T>(ch);
-                xend = reinterpret_cast<const int *>(ch)[26];
                 if (t < v.nrows) {
                     const bool rm = v.upass ? blk.ring_U : blk.ring_L;
                     const T acc = solve_row_smem<T>(ch, v, t, rm, ring, v.upass ? zsc : ysc,
@@ -803,10 +812,10 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             }
             if (t == kThreads - 1)
                 mbar_arrive(&empty[s]); // stage s and its right-hand-side slot are free
-            close(c, xend, gout, out);
+            close(c, gout, out);
             if (++s == S) {
                 s = 0;
-                par ^= 1u;
+                hneed += 32;
             }
         }
     }
@@ -853,7 +862,7 @@ template <class T, int FW> static cudaError_t prepare_trsv()
 template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s)
 {
     const size_t smem =
-        trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1 + 2 * a.import_slots, sizeof(T));
+        trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1 + a.import_slots, sizeof(T));
     if (prepare_trsv<T, FW>() != cudaSuccess)
         return -1;
     cudaLaunchConfig_t cfg{};

@@ -163,7 +163,6 @@ struct TrsvBlock {
     int chunk_mid;              // first U chunk
     int links;                  // bit 0: part p - 1 of the same RAS block exists, bit 1: part p + 1
     int ring_L, ring_U;         // 1: dependencies read from the shared-memory ring
-    int nexp_L, pad_;           // values of the L pass part p + 1 imports
     int64_t yoff, zoff;         // offsets of this program in the y / z scratch
 };
 struct TrsvArgs {

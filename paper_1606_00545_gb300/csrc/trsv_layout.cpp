@@ -94,20 +94,27 @@ size_t chunk_bytes(const std::vector<int> &widths, int nrows, bool upass, bool e
 }
 
 // Fixed-slot format (layouts of one uniform width FW <= 8): every row's data
-// sits at an offset that depends only on its thread, so the kernel can copy
-// the next chunk's row into registers without reading the header first.
+// sits at an offset that depends only on its thread, and a thread reads its
+// row with 16-byte loads, so the kernel can copy the next chunk's row into
+// registers without reading the header first.  VW = 16 / vb values per vector.
 //   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 1:
 //             exports, bit 2: narrow, bit 3: fixed-slot format, bit 4: the
 //             blocks carry exp arrays)
 //   [16, 32)  need_prev, need_next, FW, xend (exports of the pass so far)
 //   per warp w < nwarps, a block of fixed_block() bytes, lane l = row 32w + l:
-//     val[FW][32] (value); U: dinv[32] (value); dep[FW][32], src[32] (int32);
-//     U: dst[32] (int32); with exp arrays: exp[32] (int32)
-// Rows past nrows in the last warp are padding (value 0, dependency = the
-// chunk's padding slot, dst = exp = -1).
+//     val: ceil(FW / VW) vectors of 32 lanes x 16 bytes (vector v of lane l:
+//          entries v VW .. v VW + VW - 1); dep: ceil(FW / 4) vectors of 32
+//          lanes x 4 int32; U: dinv[32] (value); src[32] (int32); U: dst[32]
+//          (int32); with exp arrays: exp[32] (int32)
+// Entries past FW in the last vector and rows past nrows in the last warp
+// are padding (value 0, dependency = the chunk's padding slot, dst = exp = -1).
+inline int fixed_vw(int vb) { return 16 / vb; }
+inline int fixed_nv(int FW, int vb) { return (FW + fixed_vw(vb) - 1) / fixed_vw(vb); }
+inline int fixed_nd(int FW) { return (FW + 3) / 4; }
+
 size_t fixed_block(int FW, bool upass, bool exps, int vb)
 {
-    size_t b = (size_t)FW * 32 * vb + (size_t)(FW + 1) * 128;
+    size_t b = (size_t)(fixed_nv(FW, vb) + fixed_nd(FW)) * 512 + 128;
     if (upass)
         b += (size_t)32 * vb + 128;
     if (exps)
@@ -461,7 +468,6 @@ struct BlockOut {
     std::vector<std::vector<uint2>> chunks; // per part, offsets relative to this block
     std::vector<int> nchunksL, nL, nU;      // per part
     std::vector<int> ringL, ringU;          // per part
-    std::vector<int> nexpL;                 // per part: exports of the L pass
     std::vector<int> rows_per_chunk, rm_start, rm_len, rm_diag; // block-local entries
     int64_t alg = 0;
 };
@@ -476,7 +482,6 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
     O.nU.assign(P, 0);
     O.ringL.assign(P, 1);
     O.ringU.assign(P, 1);
-    O.nexpL.assign(P, 0);
     for (int p = 0; p < bp.nparts; ++p) {
         const PartPlan &pp = bp.parts[p];
         O.nchunksL[p] = pp.nchunksL;
@@ -484,7 +489,6 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
         O.nU[p] = (int)pp.U.order.size();
         O.ringL[p] = pp.spanL + 1 <= R;
         O.ringU[p] = pp.spanU + 1 <= R;
-        O.nexpL[p] = (int)pp.expL.size();
         bool xpass = false;
         int xcount = 0;
         for (const ChunkPlan &ch : pp.chunks) {
@@ -537,28 +541,43 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
                     nr, nw, q, (upass ? 1 : 0) | (ch.exp ? 2 : 0) | 4 | 8 | (exps ? 16 : 0),
                     ch.need_prev, ch.need_next, FW, xend};
                 std::memcpy(cb, hdr, kFixedHeader);
+                const int VW = fixed_vw(vb), NV = fixed_nv(FW, vb), ND = fixed_nd(FW);
                 for (int w = 0; w < nw; ++w) {
                     unsigned char *base = cb + kFixedHeader + w * blk;
-                    unsigned char *val = base;
-                    size_t o = (size_t)FW * 32 * vb;
+                    unsigned char *val = base;                          // [NV][32][VW]
+                    int *dep = reinterpret_cast<int *>(base + NV * 512); // [ND][32][4]
+                    size_t o = (size_t)(NV + ND) * 512;
                     unsigned char *dinv = base + o;
                     if (upass)
                         o += (size_t)32 * vb;
-                    int *dep = reinterpret_cast<int *>(base + o);
-                    o += (size_t)FW * 128;
                     int *src = reinterpret_cast<int *>(base + o);
                     o += 128;
                     int *dst = reinterpret_cast<int *>(base + o);
                     if (upass)
                         o += 128;
                     int *exp = reinterpret_cast<int *>(base + o);
+                    auto at_val = [&](int k, int lane) {
+                        return (size_t)(k / VW) * 32 * VW + (size_t)lane * VW + k % VW;
+                    };
+                    auto at_dep = [&](int k, int lane) {
+                        return (size_t)(k / 4) * 128 + (size_t)lane * 4 + k % 4;
+                    };
                     for (int lane = 0; lane < kWarpRows; ++lane) {
                         const int t = w * kWarpRows + lane;
-                        if (t >= nr) { // padding rows: never used
-                            for (int kk = 0; kk < FW; ++kk) {
-                                dep[kk * 32 + lane] = pad_dep;
-                                put_value(val, (size_t)kk * 32 + lane, 0.0, vb);
-                            }
+                        const int i = t < nr ? po.order[q + t] : -1;
+                        const int e0 = i >= 0 ? row_first(B, upass, i) : 0;
+                        const int len = i >= 0 ? row_len(B, upass, i) : 0;
+                        for (int kk = 0; kk < NV * VW; ++kk) {
+                            // padding repeats the first dependency with value 0 (a row
+                            // without one, or a padding row, points at the padding slot)
+                            const int e = kk < len ? e0 + kk : e0;
+                            put_value(val, at_val(kk, lane), kk < len ? F.va[e] : 0.0, vb);
+                        }
+                        for (int kk = 0; kk < ND * 4; ++kk) {
+                            const int e = kk < len ? e0 + kk : e0;
+                            dep[at_dep(kk, lane)] = len > 0 ? dep_of(F.ci[e]) : pad_dep;
+                        }
+                        if (i < 0) { // padding rows: never used
                             src[lane] = 0;
                             if (upass) {
                                 dst[lane] = -1;
@@ -567,13 +586,6 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
                             if (exps)
                                 exp[lane] = -1;
                             continue;
-                        }
-                        const int i = po.order[q + t];
-                        const int e0 = row_first(B, upass, i), len = row_len(B, upass, i);
-                        for (int kk = 0; kk < FW; ++kk) {
-                            const int e = kk < len ? e0 + kk : e0;
-                            dep[kk * 32 + lane] = len > 0 ? dep_of(F.ci[e]) : pad_dep;
-                            put_value(val, (size_t)kk * 32 + lane, kk < len ? F.va[e] : 0.0, vb);
                         }
                         if (upass) {
                             src[lane] = bp.posL[i];
@@ -854,7 +866,6 @@ int pack_trsv(const std::vector<BlockFactor> &Bs, int n, int stage_bytes, int ma
             T.chunk_mid = T.chunk_begin + O.nchunksL[p];
             T.links = (p > 0 && p < plans[b].nparts ? 1 : 0) |
                       (p + 1 < plans[b].nparts ? 2 : 0);
-            T.nexp_L = O.nexpL[p];
             T.ring_L = O.ringL[p];
             T.ring_U = O.ringU[p];
             T.yoff = yoff;

@@ -190,19 +190,23 @@ def parse_chunk(pack, chunks, c, vb):
     if fixed:
         FW, exps = int(h[6]), bool(flags & 16)
         out.update(need_prev=int(h[4]), need_next=int(h[5]), FW=FW, xend=int(h[7]))
-        blk = FW * 32 * vb + (FW + 1) * 128 + (32 * vb + 128 if upass else 0) + (128 if exps else 0)
+        VW = 16 // vb
+        NV, ND = (FW + VW - 1) // VW, (FW + 3) // 4
+        blk = (NV + ND) * 512 + 128 + (32 * vb + 128 if upass else 0) + (128 if exps else 0)
         assert int(chunks[c, 1]) == 32 + nw * blk
         src, dst, dinv, exp = [], [], [], []
         for w in range(nw):
             o = base + 32 + w * blk
             m = min(32, nr - 32 * w)
-            val = np.frombuffer(pack, dt, FW * 32, o).reshape(FW, 32)
-            o2 = o + FW * 32 * vb
+            # [NV][32 lanes][VW] -> [entry][lane]
+            v = np.frombuffer(pack, dt, NV * 32 * VW, o).reshape(NV, 32, VW)
+            val = v.transpose(0, 2, 1).reshape(NV * VW, 32)[:FW]
+            d = np.frombuffer(pack, np.int32, ND * 128, o + NV * 512).reshape(ND, 32, 4)
+            dep = d.transpose(0, 2, 1).reshape(ND * 4, 32)[:FW]
+            o2 = o + (NV + ND) * 512
             if upass:
                 dinv.append(np.frombuffer(pack, dt, 32, o2)[:m])
                 o2 += 32 * vb
-            dep = np.frombuffer(pack, np.int32, FW * 32, o2).reshape(FW, 32)
-            o2 += FW * 128
             src.append(np.frombuffer(pack, np.int32, 32, o2)[:m])
             o2 += 128
             if upass:
@@ -519,7 +523,7 @@ def test_workspace_bytes_query(H):
             ysz += int(heads[cm - 1][2] + heads[cm - 1][0])
         if not ring_u and c1 > cm:
             zsz += int(heads[c1 - 1][2] + heads[c1 - 1][0])
-    layout_bytes = (len(lay["pack"]) + 8 * len(lay["chunks"]) + 48 * len(lay["programs"]) +
+    layout_bytes = (len(lay["pack"]) + 8 * len(lay["chunks"]) + 40 * len(lay["programs"]) +
                     4 * max(ysz, 1) + 4 * max(zsz, 1))
     assert m30 - q(M, P, 30, H.GMRES, H.MIXED_FP32) == layout_bytes
     for bad in (dict(restart=0, method=H.GMRES), dict(restart=500, method=H.GMRES),
