@@ -42,6 +42,7 @@
 // sets the device error word, one thread waits (bounded) for the copies still
 // in flight, and the CTA returns.
 #include <mutex>
+#include <type_traits>
 
 #include "ptx.cuh"
 #include "reduce.cuh"
@@ -331,6 +332,8 @@ __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rsl
     R.nwarps = hdr.y;
     R.base = hdr.z;
     R.flags = hdr.w;
+    if (w >= hdr.y)
+        return; // a warp without rows in this chunk needs its header only
     const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(upass, exps);
     const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
 #pragma unroll
@@ -506,12 +509,13 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 const unsigned char *ch = stages + (size_t)sgp * a.stage_bytes;
                 const int2 need = *reinterpret_cast<const int2 *>(ch + (FW > 0 ? 16 : 96));
                 long long it = 0;
+                // polls back off, leaving the issue slots to the solving warps
                 if (need.x > 0)
-                    while ((int)ld_acquire_cluster_u32(&ctr[0]) < need.x && ++it < limit) {
-                    }
+                    while ((int)ld_acquire_cluster_u32(&ctr[0]) < need.x && ++it < limit)
+                        __nanosleep(32);
                 if (need.y > 0)
-                    while ((int)ld_acquire_cluster_u32(&ctr[1]) < need.y && ++it < limit) {
-                    }
+                    while ((int)ld_acquire_cluster_u32(&ctr[1]) < need.y && ++it < limit)
+                        __nanosleep(32);
                 late = it >= limit;
             }
             if (__any_sync(0xffffffffu, late))
@@ -615,6 +619,8 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 } else if (*reinterpret_cast<volatile int *>(&s_err) || ++it >= limit) {
                     failed = 1;
                     break;
+                } else {
+                    __nanosleep(64);
                 }
             }
         }
@@ -632,9 +638,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
     // wait (bounded) until chunk c, in stage s, has been handed over
     auto handed = [&](int st, uint32_t need) -> bool {
         long long it = 0;
-        while (ld_acquire_cta_u32(&s_hand[st]) < need)
+        while (ld_acquire_cta_u32(&s_hand[st]) < need) {
             if (++it >= limit)
                 return false;
+            __nanosleep(16);
+        }
         return true;
     };
     // a solved row leaves: ring or scratch, neighbour's import ring; returns
@@ -678,19 +686,22 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         RowRegs<T, FW> A, B;
         bool have = false; // this thread holds its row of chunk c
         bool held = true;  // chunk c's stage has not been released (uniform)
-        int c = 0;
+#ifdef HEC_DEBUG
         int xbase = 0;     // position the program has reached in its pass
-        // one level; cur holds chunk c (if have), nxt receives chunk c + 1
-        auto step = [&](RowRegs<T, FW> &cur, RowRegs<T, FW> &nxt) -> bool {
-            const bool upass = c >= nL;
-            const bool rm = upass ? blk.ring_U : blk.ring_L;
+#endif
+        // the chunks [c0, c1) of one pass (U: upper-triangular); cur holds
+        // chunk c (if have), nxt receives chunk c + 1 of the same pass
+        auto step = [&](auto Ucst, int c, int c1, RowRegs<T, FW> &cur,
+                        RowRegs<T, FW> &nxt) -> bool {
+            constexpr bool U = decltype(Ucst)::value;
+            const bool rm = U ? blk.ring_U : blk.ring_L;
             if (!have) {
                 if (!handed(s, hneed)) {
                     err = 1;
                     *verr = 1;
                 } else {
                     load_fixed<T, FW>(stages + (size_t)s * a.stage_bytes,
-                                      rhs + (size_t)s * kThreads, w, lane, t, upass, exps, cur);
+                                      rhs + (size_t)s * kThreads, w, lane, t, U, exps, cur);
                 }
             }
             int sn = s + 1;
@@ -699,16 +710,15 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 sn = 0;
                 hneedn += 32;
             }
-            bool pref = c + 1 >= nch;
+            const bool more = c + 1 < c1; // the next chunk belongs to this pass
+            bool pref = !more;
             T out = T(0);
             T *gout = nullptr;
-            if (c == nL)
-                xbase = 0;
             bool rows_ok = true;
 #ifdef HEC_DEBUG
             if (!err) {
                 rows_ok = HEC_CHECK(cur.base == xbase, 4, c, cur.base, xbase) &&
-                          HEC_CHECK((cur.flags & 1) == (upass ? 1 : 0), 1, c, cur.flags, nL) &&
+                          HEC_CHECK((cur.flags & 1) == (U ? 1 : 0), 1, c, cur.flags, nL) &&
                           HEC_CHECK(cur.nrows >= 1 && cur.nrows <= kThreads &&
                                         cur.nwarps == (cur.nrows + 31) / 32,
                                     2, c, cur.nrows, cur.nwarps);
@@ -719,45 +729,65 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                                       : HEC_CHECK(cur.l(k) == T(0) ||
                                                       (cur.d(k) >= 0 && cur.d(k) < cur.base),
                                                   6, c, cur.d(k), cur.base);
-                if (rows_ok && t < cur.nrows && upass)
+                if (rows_ok && t < cur.nrows && U)
                     rows_ok &= HEC_CHECK(cur.dst < a.n, 7, c, cur.dst, a.n);
             }
+            xbase = more ? xbase + cur.nrows : 0;
 #endif
-            xbase += cur.nrows;
             if (!err) {
                 // warps past the chunk's last one hold no rows: their slots in
                 // the stage are stale bytes and are never used as indices
                 const bool rows = w < cur.nwarps && rows_ok;
                 // this level's dependencies (the previous level's barrier has
                 // passed); padding lanes of the last warp carry valid slots
-                const T *gdep = upass ? zsc : ysc;
                 T y[FW];
                 if (rows) {
+                    if (rm) {
 #pragma unroll
-                    for (int k = 0; k < FW; ++k)
-                        // global scratch: padding of a dependency-free row points
-                        // at a position this apply has not written (it may hold
-                        // NaN); entries of value 0 are not read
-                        y[k] = rm ? ring[cur.d(k)] : (cur.l(k) != T(0) ? gdep[cur.d(k)] : T(0));
+                        for (int k = 0; k < FW; ++k)
+                            y[k] = ring[cur.d(k)];
+                    } else {
+                        // global scratch: padding of a dependency-free row
+                        // points at a position this apply has not written (it
+                        // may hold NaN); entries of value 0 are not read
+                        const T *gdep = U ? zsc : ysc;
+#pragma unroll
+                        for (int k = 0; k < FW; ++k)
+                            y[k] = cur.l(k) != T(0) ? gdep[cur.d(k)] : T(0);
+                    }
                 }
                 // the next chunk's rows: loads only, kept if the handover
                 // count (read first, with acquire) shows the chunk complete
-                const uint32_t hn = ld_acquire_cta_u32(&s_hand[sn]);
-                load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
-                                  rhs + (size_t)sn * kThreads, w, lane, t, c + 1 >= nL, exps, nxt);
+                if (more) {
+                    const uint32_t hn = ld_acquire_cta_u32(&s_hand[sn]);
+                    load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
+                                      rhs + (size_t)sn * kThreads, w, lane, t, U, exps, nxt);
+                    pref = hn >= hneedn;
+                }
                 if (rows) { // warps without rows issue no multiply-adds
                     T acc = cur.rhs;
 #pragma unroll
                     for (int k = 0; k < FW; ++k)
                         acc = fma(-cur.l(k), y[k], acc);
-                    if (upass)
+                    if (U)
                         acc *= cur.dinv;
                     if (t < cur.nrows) {
-                        gout = put(upass, rm, cur.base + t, upass ? cur.dst : -1, cur.exp, acc);
+                        const int pos = cur.base + t;
+                        if (rm)
+                            ring[pos & a.ring_mask] = acc;
+                        else
+                            (U ? zsc : ysc_w)[pos] = acc; // read by later levels of this pass
+                        if (U)
+                            gout = cur.dst >= 0 ? z + cur.dst : nullptr;
+                        else if (rm)
+                            gout = ysc_w + pos;
+                        if (cur.exp >= 0) // exports (-1 without export slots)
+                            st_cluster((U ? imp_prev : imp_next) +
+                                           (uint32_t)((cur.exp & (RI - 1)) * sizeof(T)),
+                                       acc);
                         out = acc;
                     }
                 }
-                pref = pref || hn >= hneedn;
             }
             const int all = consumer_sync_and(pref && !err);
             if (!all && *verr)
@@ -765,27 +795,48 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             // stages every thread is done with: chunk c (unless it was freed
             // with the previous level), and chunk c + 1 when every thread
             // holds its row of it
-            const bool free_next = all && c + 1 < nch;
+            const bool free_next = all && more;
             if (t == kThreads - 1) {
                 if (held)
                     mbar_arrive(&empty[s]);
                 if (free_next)
                     mbar_arrive(&empty[sn]);
+                if (signal)
+                    st_release_cta_u32(&s_done, (uint32_t)(c + 1));
             }
-            close(c, gout, out);
+            if (gout)
+                *gout = out;
             held = !free_next;
-            have = pref && c + 1 < nch;
+            have = pref && more;
             s = sn;
             hneed = hneedn;
-            ++c;
             return false;
         };
-        while (c < nch) {
-            if (step(A, B) || (c < nch && step(B, A))) {
-                failed = 1;
-                break;
+        // one pass: chunks [c0, c1), two levels per trip (register sets swap)
+        auto run = [&](auto Ucst, int c0, int c1) -> bool {
+            have = false;
+            for (int c = c0; c < c1; c += 2) {
+                if (step(Ucst, c, c1, A, B))
+                    return true;
+                if (c + 1 < c1 && step(Ucst, c + 1, c1, B, A))
+                    return true;
             }
+            return false;
+        };
+        if (run(std::integral_constant<bool, false>(), 0, nL)) {
+            failed = 1;
+        } else {
+            if (nL > 0) {
+                // every y of the L pass is written before the gatherers read
+                // the U pass's right-hand sides from them
+                consumer_sync_and(1);
+                if (t == kThreads - 1)
+                    mbar_arrive(ldone);
+            }
+            if (run(std::integral_constant<bool, true>(), nL, nch))
+                failed = 1;
         }
+
     } else {
         for (int c = 0; c < nch; ++c) {
             if (!handed(s, hneed)) {
