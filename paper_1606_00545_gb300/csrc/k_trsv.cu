@@ -370,16 +370,16 @@ __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v)
 //             and lane 0 has seen the neighbouring parts' progress counters
 //             reach the chunk's thresholds, every lane adds 1 to the stage's
 //             handover counter (release): 32 per chunk;
-//   consumers: fixed-slot chunks are software-pipelined by one chunk: while
-//             chunk c's multiply-add chain runs, every thread copies its row
-//             of chunk c + 1 into registers, and keeps the copy if the
-//             handover counter it read (acquire) shows that chunk complete.
-//             The level's results go to the ring (and, for exports, into the
+//   consumers: fixed-slot chunks are software-pipelined by one chunk: after
+//             issuing chunk c's dependency loads, every thread waits until
+//             chunk c + 1 has been handed over (an acquire load of the
+//             counter; in the steady state it has) and copies its row of it
+//             into registers, then runs chunk c's multiply-add chain.  The
+//             level's results go to the ring (and, for exports, into the
 //             neighbour's import ring), the consumer barrier closes the
-//             level, and the last thread frees the stages every thread is
-//             done with -- chunk c, and chunk c + 1 once all threads hold it
-//             -- and publishes the completed count.  Generic chunks are
-//             solved from shared memory, one at a time;
+//             level, and the last thread frees chunk c + 1's stage and
+//             publishes the completed count.  Generic chunks are solved from
+//             shared memory, one at a time;
 //   signaller (warp 11): for a split block, forwards the completed count to
 //             the neighbouring parts (a release at cluster scope, then the
 //             count stored into their shared memory) as often as the fence
@@ -684,60 +684,57 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
     if constexpr (FW > 0) {
         const int w = t / kWarpRows, lane = t % kWarpRows;
         RowRegs<T, FW> A, B;
-        bool have = false; // this thread holds its row of chunk c
-        bool held = true;  // chunk c's stage has not been released (uniform)
-#ifdef HEC_DEBUG
-        int xbase = 0;     // position the program has reached in its pass
-#endif
-        // the chunks [c0, c1) of one pass (U: upper-triangular); cur holds
-        // chunk c (if have), nxt receives chunk c + 1 of the same pass
-        auto step = [&](auto Ucst, int c, int c1, RowRegs<T, FW> &cur,
-                        RowRegs<T, FW> &nxt) -> bool {
+        // one pass: chunks [c0, c1), U: the upper-triangular pass.  Before a
+        // level's barrier every thread has copied its row of the next chunk
+        // of the pass into registers, so that chunk's stage is free after
+        // the barrier, and the next level starts with its dependencies.
+        auto run = [&](auto Ucst, int c0, int c1) -> bool {
             constexpr bool U = decltype(Ucst)::value;
+            if (c0 >= c1)
+                return false;
             const bool rm = U ? blk.ring_U : blk.ring_L;
-            if (!have) {
-                if (!handed(s, hneed)) {
-                    err = 1;
-                    *verr = 1;
-                } else {
-                    load_fixed<T, FW>(stages + (size_t)s * a.stage_bytes,
-                                      rhs + (size_t)s * kThreads, w, lane, t, U, exps, cur);
-                }
+            const T *gdep = U ? zsc : ysc;
+            T *scr = U ? zsc : ysc_w;
+            const uint32_t imp = U ? imp_prev : imp_next;
+            // the pass's first chunk
+            if (!handed(s, hneed)) {
+                *verr = 1;
+                return true;
             }
-            int sn = s + 1;
-            uint32_t hneedn = hneed;
-            if (sn == S) {
-                sn = 0;
-                hneedn += 32;
-            }
-            const bool more = c + 1 < c1; // the next chunk belongs to this pass
-            bool pref = !more;
-            T out = T(0);
-            T *gout = nullptr;
-            bool rows_ok = true;
+            load_fixed<T, FW>(stages + (size_t)s * a.stage_bytes, rhs + (size_t)s * kThreads, w,
+                              lane, t, U, exps, A);
+            consumer_sync_and(1);
+            if (t == kThreads - 1)
+                mbar_arrive(&empty[s]);
 #ifdef HEC_DEBUG
-            if (!err) {
-                rows_ok = HEC_CHECK(cur.base == xbase, 4, c, cur.base, xbase) &&
-                          HEC_CHECK((cur.flags & 1) == (U ? 1 : 0), 1, c, cur.flags, nL) &&
-                          HEC_CHECK(cur.nrows >= 1 && cur.nrows <= kThreads &&
-                                        cur.nwarps == (cur.nrows + 31) / 32,
-                                    2, c, cur.nrows, cur.nwarps);
-                if (rows_ok && w < cur.nwarps)
-                    for (int k = 0; k < FW; ++k)
-                        rows_ok &= rm ? HEC_CHECK(cur.d(k) >= 0 && cur.d(k) < nring, 5, c,
-                                                  cur.d(k), nring)
-                                      : HEC_CHECK(cur.l(k) == T(0) ||
-                                                      (cur.d(k) >= 0 && cur.d(k) < cur.base),
-                                                  6, c, cur.d(k), cur.base);
-                if (rows_ok && t < cur.nrows && U)
-                    rows_ok &= HEC_CHECK(cur.dst < a.n, 7, c, cur.dst, a.n);
-            }
-            xbase = more ? xbase + cur.nrows : 0;
+            int xbase = 0; // position the program has reached in its pass
 #endif
-            if (!err) {
-                // warps past the chunk's last one hold no rows: their slots in
-                // the stage are stale bytes and are never used as indices
-                const bool rows = w < cur.nwarps && rows_ok;
+            auto level = [&](int c, RowRegs<T, FW> &cur, RowRegs<T, FW> &nxt) -> bool {
+                int sn = s + 1;
+                uint32_t hneedn = hneed;
+                if (sn == S) {
+                    sn = 0;
+                    hneedn += 32;
+                }
+                const bool more = c + 1 < c1;
+                bool rows = w < cur.nwarps; // warps past the chunk's last one hold no rows
+#ifdef HEC_DEBUG
+                rows = rows && HEC_CHECK(cur.base == xbase, 4, c, cur.base, xbase) &&
+                       HEC_CHECK((cur.flags & 1) == (U ? 1 : 0), 1, c, cur.flags, nL) &&
+                       HEC_CHECK(cur.nrows >= 1 && cur.nrows <= kThreads &&
+                                     cur.nwarps == (cur.nrows + 31) / 32,
+                                 2, c, cur.nrows, cur.nwarps);
+                if (rows)
+                    for (int k = 0; k < FW; ++k)
+                        rows &= rm ? HEC_CHECK(cur.d(k) >= 0 && cur.d(k) < nring, 5, c, cur.d(k),
+                                               nring)
+                                   : HEC_CHECK(cur.l(k) == T(0) ||
+                                                   (cur.d(k) >= 0 && cur.d(k) < cur.base),
+                                               6, c, cur.d(k), cur.base);
+                if (rows && t < cur.nrows && U)
+                    rows &= HEC_CHECK(cur.dst < a.n, 7, c, cur.dst, a.n);
+                xbase += cur.nrows;
+#endif
                 // this level's dependencies (the previous level's barrier has
                 // passed); padding lanes of the last warp carry valid slots
                 T y[FW];
@@ -750,20 +747,25 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                         // global scratch: padding of a dependency-free row
                         // points at a position this apply has not written (it
                         // may hold NaN); entries of value 0 are not read
-                        const T *gdep = U ? zsc : ysc;
 #pragma unroll
                         for (int k = 0; k < FW; ++k)
                             y[k] = cur.l(k) != T(0) ? gdep[cur.d(k)] : T(0);
                     }
                 }
-                // the next chunk's rows: loads only, kept if the handover
-                // count (read first, with acquire) shows the chunk complete
+                // the next chunk's rows, once it has been handed over: loads
+                // only, their values are first used after the barrier
+                int err = 0;
                 if (more) {
-                    const uint32_t hn = ld_acquire_cta_u32(&s_hand[sn]);
-                    load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
-                                      rhs + (size_t)sn * kThreads, w, lane, t, U, exps, nxt);
-                    pref = hn >= hneedn;
+                    if (!handed(sn, hneedn)) {
+                        err = 1;
+                        *verr = 1;
+                    } else {
+                        load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
+                                          rhs + (size_t)sn * kThreads, w, lane, t, U, exps, nxt);
+                    }
                 }
+                T out = T(0);
+                T *gout = nullptr;
                 if (rows) { // warps without rows issue no multiply-adds
                     T acc = cur.rhs;
 #pragma unroll
@@ -776,49 +778,35 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                         if (rm)
                             ring[pos & a.ring_mask] = acc;
                         else
-                            (U ? zsc : ysc_w)[pos] = acc; // read by later levels of this pass
+                            scr[pos] = acc; // read by later levels of this pass
                         if (U)
                             gout = cur.dst >= 0 ? z + cur.dst : nullptr;
                         else if (rm)
                             gout = ysc_w + pos;
                         if (cur.exp >= 0) // exports (-1 without export slots)
-                            st_cluster((U ? imp_prev : imp_next) +
-                                           (uint32_t)((cur.exp & (RI - 1)) * sizeof(T)),
-                                       acc);
+                            st_cluster(imp + (uint32_t)((cur.exp & (RI - 1)) * sizeof(T)), acc);
                         out = acc;
                     }
                 }
-            }
-            const int all = consumer_sync_and(pref && !err);
-            if (!all && *verr)
-                return true; // the feeding warps' own waits run out
-            // stages every thread is done with: chunk c (unless it was freed
-            // with the previous level), and chunk c + 1 when every thread
-            // holds its row of it
-            const bool free_next = all && more;
-            if (t == kThreads - 1) {
-                if (held)
-                    mbar_arrive(&empty[s]);
-                if (free_next)
-                    mbar_arrive(&empty[sn]);
-                if (signal)
-                    st_release_cta_u32(&s_done, (uint32_t)(c + 1));
-            }
-            if (gout)
-                *gout = out;
-            held = !free_next;
-            have = pref && more;
-            s = sn;
-            hneed = hneedn;
-            return false;
-        };
-        // one pass: chunks [c0, c1), two levels per trip (register sets swap)
-        auto run = [&](auto Ucst, int c0, int c1) -> bool {
-            have = false;
+                if (!consumer_sync_and(!err))
+                    return true; // a feeding warp's wait ran out
+                // every thread holds its row of chunk c + 1: its stage is free
+                if (t == kThreads - 1) {
+                    if (more)
+                        mbar_arrive(&empty[sn]);
+                    if (signal)
+                        st_release_cta_u32(&s_done, (uint32_t)(c + 1));
+                }
+                if (gout)
+                    *gout = out;
+                s = sn;
+                hneed = hneedn;
+                return false;
+            };
             for (int c = c0; c < c1; c += 2) {
-                if (step(Ucst, c, c1, A, B))
+                if (level(c, A, B))
                     return true;
-                if (c + 1 < c1 && step(Ucst, c + 1, c1, B, A))
+                if (c + 1 < c1 && level(c + 1, B, A))
                     return true;
             }
             return false;

@@ -397,9 +397,9 @@ bool plan_parts(const BlockFactor &B, BlockPlan &bp, int P, int stage_bytes, int
 }
 
 // Progress thresholds of every chunk for an import ring of RI slots, then a
-// host run of the parts against them: true if every part's program can run
-// to its end.  A part only waits for counters that never decrease, so if the
-// most eager run finishes, every interleaving does.
+// host run of the parts against them, by the kernel's rule: true if every
+// part's program can run to its end.  A part only waits for counters that
+// never decrease, so if the most eager run finishes, every interleaving does.
 bool set_thresholds(const BlockFactor &B, BlockPlan &bp, int RI)
 {
     const HostCSR &F = B.F;
@@ -434,15 +434,23 @@ bool set_thresholds(const BlockFactor &B, BlockPlan &bp, int RI)
             }
         }
     }
+    // The kernel completes chunk k only after chunk k + 1 of the same pass has
+    // been handed over too (its rows are loaded before chunk k's barrier), so
+    // completing k needs both chunks' thresholds met.
     std::vector<int> done(P, 0);
+    auto met = [&](int p, const ChunkPlan &ch) {
+        return ch.need_prev <= (p > 0 ? done[p - 1] : 0) &&
+               ch.need_next <= (p + 1 < P ? done[p + 1] : 0);
+    };
     for (bool moved = true; moved;) {
         moved = false;
         for (int p = 0; p < P; ++p) {
-            const std::vector<ChunkPlan> &cs = bp.parts[p].chunks;
+            const PartPlan &pp = bp.parts[p];
+            const std::vector<ChunkPlan> &cs = pp.chunks;
             while (done[p] < (int)cs.size()) {
-                const ChunkPlan &ch = cs[done[p]];
-                if (ch.need_prev > (p > 0 ? done[p - 1] : 0) ||
-                    ch.need_next > (p + 1 < P ? done[p + 1] : 0))
+                const int k = done[p];
+                const bool next_same_pass = k + 1 < (int)cs.size() && k + 1 != pp.nchunksL;
+                if (!met(p, cs[k]) || (next_same_pass && !met(p, cs[k + 1])))
                     break;
                 ++done[p];
                 moved = true;
