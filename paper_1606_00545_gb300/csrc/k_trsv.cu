@@ -332,8 +332,6 @@ __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rsl
     R.nwarps = hdr.y;
     R.base = hdr.z;
     R.flags = hdr.w;
-    if (w >= hdr.y)
-        return; // a warp without rows in this chunk needs its header only
     const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(upass, exps);
     const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
 #pragma unroll
@@ -371,15 +369,16 @@ __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v)
 //             reach the chunk's thresholds, every lane adds 1 to the stage's
 //             handover counter (release): 32 per chunk;
 //   consumers: fixed-slot chunks are software-pipelined by one chunk: after
-//             issuing chunk c's dependency loads, every thread waits until
-//             chunk c + 1 has been handed over (an acquire load of the
-//             counter; in the steady state it has) and copies its row of it
-//             into registers, then runs chunk c's multiply-add chain.  The
-//             level's results go to the ring (and, for exports, into the
-//             neighbour's import ring), the consumer barrier closes the
-//             level, and the last thread frees chunk c + 1's stage and
-//             publishes the completed count.  Generic chunks are solved from
-//             shared memory, one at a time;
+//             issuing chunk c's dependency loads, every thread copies its row
+//             of chunk c + 1 into registers, then runs chunk c's multiply-add
+//             chain.  The level's results go to the ring (and, for exports,
+//             into the neighbour's import ring).  Before the level's barrier
+//             the last thread -- whose warp holds the shortest rows --
+//             confirms that chunk c + 2 has been handed over (an acquire load
+//             of the counter; the barrier orders everybody's later loads
+//             after it), and after the barrier it frees chunk c + 1's stage
+//             and publishes the completed count.  Generic chunks are solved
+//             from shared memory, one at a time;
 //   signaller (warp 11): for a split block, forwards the completed count to
 //             the neighbouring parts (a release at cluster scope, then the
 //             count stored into their shared memory) as often as the fence
@@ -696,27 +695,38 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             const T *gdep = U ? zsc : ysc;
             T *scr = U ? zsc : ysc_w;
             const uint32_t imp = U ? imp_prev : imp_next;
-            // the pass's first chunk
-            if (!handed(s, hneed)) {
+            // stage and handover count of the chunk after a given one
+            auto next = [&](int &st, uint32_t &h) {
+                if (++st == S) {
+                    st = 0;
+                    h += 32;
+                }
+            };
+            // the last thread confirms the handovers (acquire) before a
+            // barrier, so the other threads' loads after it need no check:
+            // chunks c0 and c0 + 1 now, chunk c + 2 at level c
+            int s1 = s, s2;
+            uint32_t h1 = hneed, h2;
+            next(s1, h1);
+            s2 = s1;
+            h2 = h1;
+            next(s2, h2);
+            int err = 0;
+            if (t == kThreads - 1)
+                err = !handed(s, hneed) || (c0 + 1 < c1 && !handed(s1, h1));
+            if (!consumer_sync_and(!err)) {
                 *verr = 1;
                 return true;
             }
             load_fixed<T, FW>(stages + (size_t)s * a.stage_bytes, rhs + (size_t)s * kThreads, w,
                               lane, t, U, exps, A);
-            consumer_sync_and(1);
-            if (t == kThreads - 1)
-                mbar_arrive(&empty[s]);
 #ifdef HEC_DEBUG
             int xbase = 0; // position the program has reached in its pass
 #endif
+            // level c: cur holds chunk c, nxt receives chunk c + 1; s, s1, s2
+            // are the stages of chunks c, c + 1, c + 2
             auto level = [&](int c, RowRegs<T, FW> &cur, RowRegs<T, FW> &nxt) -> bool {
-                int sn = s + 1;
-                uint32_t hneedn = hneed;
-                if (sn == S) {
-                    sn = 0;
-                    hneedn += 32;
-                }
-                const bool more = c + 1 < c1;
+                const bool more = c + 1 < c1, more2 = c + 2 < c1;
                 bool rows = w < cur.nwarps; // warps past the chunk's last one hold no rows
 #ifdef HEC_DEBUG
                 rows = rows && HEC_CHECK(cur.base == xbase, 4, c, cur.base, xbase) &&
@@ -752,18 +762,11 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                             y[k] = cur.l(k) != T(0) ? gdep[cur.d(k)] : T(0);
                     }
                 }
-                // the next chunk's rows, once it has been handed over: loads
-                // only, their values are first used after the barrier
-                int err = 0;
-                if (more) {
-                    if (!handed(sn, hneedn)) {
-                        err = 1;
-                        *verr = 1;
-                    } else {
-                        load_fixed<T, FW>(stages + (size_t)sn * a.stage_bytes,
-                                          rhs + (size_t)sn * kThreads, w, lane, t, U, exps, nxt);
-                    }
-                }
+                // the next chunk's rows (handed over, confirmed before the
+                // previous barrier): loads only, first used after this barrier
+                if (more)
+                    load_fixed<T, FW>(stages + (size_t)s1 * a.stage_bytes,
+                                      rhs + (size_t)s1 * kThreads, w, lane, t, U, exps, nxt);
                 T out = T(0);
                 T *gout = nullptr;
                 if (rows) { // warps without rows issue no multiply-adds
@@ -788,29 +791,43 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                         out = acc;
                     }
                 }
-                if (!consumer_sync_and(!err))
+                int bad = 0;
+                if (t == kThreads - 1 && more2)
+                    bad = !handed(s2, h2);
+                if (!consumer_sync_and(!bad))
                     return true; // a feeding warp's wait ran out
-                // every thread holds its row of chunk c + 1: its stage is free
+                // every thread holds its rows of chunks c and c + 1: their
+                // stages are free (chunk c's only now at the pass's first level)
                 if (t == kThreads - 1) {
+                    if (c == c0)
+                        mbar_arrive(&empty[s]);
                     if (more)
-                        mbar_arrive(&empty[sn]);
+                        mbar_arrive(&empty[s1]);
                     if (signal)
                         st_release_cta_u32(&s_done, (uint32_t)(c + 1));
                 }
                 if (gout)
                     *gout = out;
-                s = sn;
-                hneed = hneedn;
+                s = s1;
+                hneed = h1;
+                s1 = s2;
+                h1 = h2;
+                next(s2, h2);
                 return false;
             };
             for (int c = c0; c < c1; c += 2) {
-                if (level(c, A, B))
+                if (level(c, A, B)) {
+                    *verr = 1;
                     return true;
-                if (c + 1 < c1 && level(c + 1, B, A))
+                }
+                if (c + 1 < c1 && level(c + 1, B, A)) {
+                    *verr = 1;
                     return true;
+                }
             }
             return false;
         };
+
         if (run(std::integral_constant<bool, false>(), 0, nL)) {
             failed = 1;
         } else {

@@ -434,9 +434,10 @@ bool set_thresholds(const BlockFactor &B, BlockPlan &bp, int RI)
             }
         }
     }
-    // The kernel completes chunk k only after chunk k + 1 of the same pass has
-    // been handed over too (its rows are loaded before chunk k's barrier), so
-    // completing k needs both chunks' thresholds met.
+    // The kernel completes chunk k only after chunks k + 1 and k + 2 of the
+    // same pass have been handed over too (the first is loaded, the second
+    // confirmed, before chunk k's barrier), so completing k needs all three
+    // chunks' thresholds met.
     std::vector<int> done(P, 0);
     auto met = [&](int p, const ChunkPlan &ch) {
         return ch.need_prev <= (p > 0 ? done[p - 1] : 0) &&
@@ -449,8 +450,11 @@ bool set_thresholds(const BlockFactor &B, BlockPlan &bp, int RI)
             const std::vector<ChunkPlan> &cs = pp.chunks;
             while (done[p] < (int)cs.size()) {
                 const int k = done[p];
-                const bool next_same_pass = k + 1 < (int)cs.size() && k + 1 != pp.nchunksL;
-                if (!met(p, cs[k]) || (next_same_pass && !met(p, cs[k + 1])))
+                const int pass_end = k < pp.nchunksL ? pp.nchunksL : (int)cs.size();
+                bool ok = true;
+                for (int j = k; j < std::min(k + 3, pass_end) && ok; ++j)
+                    ok = met(p, cs[j]);
+                if (!ok)
                     break;
                 ++done[p];
                 moved = true;
