@@ -305,24 +305,20 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "trsv_ras_c2.traffic.json")
+
+
 def profiled_traffic():
-    """DRAM bytes per launch of the triangular-solve kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "trsv_ras_c2.md")
+    """DRAM bytes per launch of the triangular-solve kernel from the recorded
+    ncu counters (profiles/trsv_ras_c2.traffic.json: source hash, bytes,
+    command), if they were taken on the current kernel source."""
     try:
-        txt = open(p).read()
-    except OSError:
+        with open(TRAFFIC_JSON) as f:
+            rec = json.load(f)
+        sha, bytes_ = rec["source_sha256_16"], float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
         return None
-    sha = bytes_ = None
-    for line in txt.splitlines():
-        if line.startswith("source_sha256_16:"):
-            sha = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            try:
-                bytes_ = float(line.split(":", 1)[1].strip())
-            except ValueError:
-                pass
-    if sha == kernel_source_sha() and bytes_:
+    if sha == kernel_source_sha() and bytes_ > 0:
         return bytes_
     return None
 

@@ -112,7 +112,7 @@ typedef struct {
                                 not fit the window and are read from global
                                 memory instead                                */
     int64_t apply_bytes_f32; /* the same for the FP32 layout (0 until built)   */
-    int32_t trsv_parts;      /* CTAs per RAS block of the triangular solve     */
+    int32_t trsv_parts;      /* CTAs per RAS block of the FP64 triangular solve */
     int32_t import_slots;    /* shared-memory window of values received from a
                                 neighbouring CTA (0: no block is split)        */
     int32_t split_blocks;    /* RAS blocks solved by more than one CTA         */
@@ -229,12 +229,6 @@ int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const doubl
                  void *stream);
 
 /* ---------------------------------------------------------------- preconditioner */
-/* Sections 2.4-2.5: partition the rows into nblocks contiguous owned ranges
- * W_b = [floor(b n / nblocks), floor((b+1) n / nblocks)), grow each by
- * `overlap` layers of matrix-graph neighbours (V_b), and factorise every
- * A[V_b, V_b] by ILU(k).  Factors are computed on the host and kept there
- * until level_schedule uploads them.  Returns HEC_ERR_ZERO_PIVOT if a pivot
- * is zero, HEC_ERR_INVALID if a diagonal entry is missing. */
 /* Damped Jacobi (Section 2.8 builds it, as a smoother, from the SpMV and
  * vector operations): the preconditioner z = omega D^{-1} r, D the diagonal
  * of A, usable wherever an ILU(k)/RAS handle is (apply calls, krylov_solve
@@ -246,6 +240,12 @@ int hec_multidot(int32_t n, int32_t k, const double *V, int64_t ldv, const doubl
  * Returns HEC_ERR_INVALID for omega <= 0 or not finite, HEC_ERR_ZERO_PIVOT
  * for a zero or missing diagonal entry. */
 int hec_jacobi_setup(hec_matrix_t A, double omega, void *stream, hec_precond_t *out);
+/* Sections 2.4-2.5: partition the rows into nblocks contiguous owned ranges
+ * W_b = [floor(b n / nblocks), floor((b+1) n / nblocks)), grow each by
+ * `overlap` layers of matrix-graph neighbours (V_b), and factorise every
+ * A[V_b, V_b] by ILU(k).  Factors are computed on the host and kept there
+ * until level_schedule uploads them.  Returns HEC_ERR_ZERO_PIVOT if a pivot
+ * is zero, HEC_ERR_INVALID if a diagonal entry is missing. */
 int ilu_k_setup(hec_matrix_t A, int32_t k, int32_t nblocks, int32_t overlap, void *stream,
                 hec_precond_t *out);
 /* Section 2.6 (Eq. 11, Algorithm 3): level of every row of every L_b and
@@ -316,8 +316,8 @@ int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, i
 /* CTAs that solve each RAS block's triangular systems (Section 2.6: the
  * rows of one level are independent, so they may be spread over several
  * SMs): 0 = automatic (split while the widest block's levels hold more than
- * 128 rows per CTA and nblocks * P CTAs fit on the device's SMs), or 1, 2, 4
- * or 8.  The CTAs of one block run as one thread-block cluster.  A block
+ * 128 rows per CTA in the FP64 layout, 256 in the FP32 one, and nblocks * P
+ * CTAs fit on the device's SMs), or 1, 2, 4 or 8 for both layouts.  The CTAs of one block run as one thread-block cluster.  A block
  * whose dependencies do not allow the split gets fewer parts.  Call it
  * between ilu_k_setup and level_schedule; HEC_ERR_INVALID afterwards, for a
  * damped-Jacobi handle or another value. */

@@ -337,11 +337,15 @@ int refresh_host_factors(hec_precond_s *M, cudaStream_t s)
 
 // CTAs per RAS block: the handle's choice, else split while levels are wide
 // and the CTAs fit on the device's SMs (host-only handles: 152, GB300's count).
-int layout_parts(const hec_precond_s *M)
+// FP64 (idx 0): split above 4 warps of rows per level and CTA -- each
+// warp's FP64 multiply-add chain occupies its SM sub-partition's FP64 pipe, so
+// fewer rows per SM shorten a level.  FP32 (idx 1): split only above one
+// chunk (8 warps) per level: an FP32 level costs the same with fewer rows.
+int layout_parts(const hec_precond_s *M, int idx)
 {
     if (M->trsv_parts > 0)
         return M->trsv_parts;
-    return trsv_auto_parts(M->blocks, M->host_only ? 152 : device_sms());
+    return trsv_auto_parts(M->blocks, M->host_only ? 152 : device_sms(), idx == 0 ? 128 : 256);
 }
 
 // Pack, upload and size the scratch of the layout with vb-byte values.
@@ -360,7 +364,7 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
                                                 max_factor_width(M->blocks, true)));
     std::string msg;
     int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg,
-                       L.fixed_width, layout_parts(M));
+                       L.fixed_width, layout_parts(M, idx));
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
     if (!M->host_only) {
@@ -546,7 +550,8 @@ int seq_norm_b(Solver &S, cudaStream_t cs)
     return run_vec(V_NRM2SQ, va, cs);
 }
 
-// Algorithm 4, first line: r0 = b - A x0, rho_0 = (r0, r0); shadow residual r0.
+// BiCGSTAB start (Section 2.7): ||b||, the residual r0 = b - A x0 and
+// rho_0 = (r0, r0); r0 is kept as the shadow residual.
 int seq_bicg_init(hec_matrix_s *A, Solver &S, cudaStream_t cs)
 {
     HEC_TRY(seq_norm_b(S, cs));
@@ -569,7 +574,9 @@ int seq_bicg_init(hec_matrix_s *A, Solver &S, cudaStream_t cs)
     return run_vec(V_COPY, cp, cs);
 }
 
-// One pass of the k loop of Algorithm 4.
+// One BiCGSTAB iteration (Section 2.7): direction update, two preconditioner
+// applies and SpMVs with the alpha and omega reductions fused into the SpMV
+// epilogues, then the x and r updates with the convergence tests.
 int seq_bicg_body(hec_matrix_s *A, hec_precond_s *M, Solver &S, cudaStream_t cs)
 {
     const int n = S.n;
@@ -1961,7 +1968,7 @@ int hec_workspace_bytes(hec_matrix_t A, hec_precond_t M, int32_t restart,
             const int fw = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
                                                        max_factor_width(M->blocks, true)));
             const int rc =
-                pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw, layout_parts(M));
+                pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw, layout_parts(M, 1));
             if (rc != HEC_OK)
                 return fail(rc, "%s", msg.c_str());
             total += dev((int64_t)P.pack.size()) + dev((int64_t)(P.chunks.size() * sizeof(uint2))) +

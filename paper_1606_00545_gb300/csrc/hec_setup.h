@@ -88,8 +88,8 @@ struct TrsvPack {
 int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,
               TrsvPack &out, std::string &msg, int uniform_width = 0, int parts = 1);
 // The parts per block worth launching: split while the widest block's levels
-// hold more than four warps of rows per part and the CTAs fit on sm_count SMs.
-int trsv_auto_parts(const std::vector<BlockFactor> &B, int sm_count);
+// hold more than rows_per_part rows per part and the CTAs fit on sm_count SMs.
+int trsv_auto_parts(const std::vector<BlockFactor> &B, int sm_count, int rows_per_part);
 // The longest off-diagonal row of any L_b (upass false) or U_b.
 int max_factor_width(const std::vector<BlockFactor> &B, bool upass);
 

@@ -39,7 +39,6 @@ constexpr int kMaxWarps = kThreads / kWarpRows;
 // offsets, [96,112) progress thresholds
 constexpr int kChunkHeader = 112;
 constexpr int kMaxParts = 8;
-constexpr int kRowsPerLevelPerPart = 128; // split while a level fills more than 4 warps
 constexpr int kNarrowRow = 8; // rows the kernel holds in registers (flag bit 2)
 
 constexpr int kFixedHeader = 32;
@@ -706,7 +705,7 @@ int max_factor_width(const std::vector<BlockFactor> &Bs, bool upass)
     return w;
 }
 
-int trsv_auto_parts(const std::vector<BlockFactor> &Bs, int sm_count)
+int trsv_auto_parts(const std::vector<BlockFactor> &Bs, int sm_count, int rows_per_part)
 {
     // rows per level of the widest block (L pass, all rows)
     double per_level = 0;
@@ -715,7 +714,7 @@ int trsv_auto_parts(const std::vector<BlockFactor> &Bs, int sm_count)
             per_level = std::max(per_level, (double)B.F.n / B.nlevL);
     int P = 1;
     while (2 * P <= kMaxParts && (int64_t)Bs.size() * 2 * P <= sm_count &&
-           per_level / P > kRowsPerLevelPerPart)
+           per_level / P > rows_per_part)
         P *= 2;
     return P;
 }

@@ -2,7 +2,10 @@
 timed region (median SM clock, throttle reasons, the rejection rule) and the
 traffic figure read from the committed ncu summary only while the kernel
 source it was taken on is unchanged."""
+import json
 import os
+
+import pytest
 
 import bench
 
@@ -35,23 +38,35 @@ def test_clock_summary_and_rejection_rule():
     assert c["reasons"] == ["unsampled"] and not bench.bad_clocks(c)
 
 
-def _recorded_sha():
-    p = os.path.join(bench.ROOT, "profiles", "trsv_ras_c2.md")
-    for line in open(p).read().splitlines():
-        if line.startswith("source_sha256_16:"):
-            return line.split(":", 1)[1].strip()
-    return None
-
-
-def test_profiled_traffic_follows_the_source_hash(monkeypatch):
-    # with the hash the summary records, its traffic is read back
-    monkeypatch.setattr(bench, "kernel_source_sha", lambda: _recorded_sha())
-    t = bench.profiled_traffic()
-    assert t is not None and t > 0
+def test_profiled_traffic_follows_the_source_hash(monkeypatch, tmp_path):
+    # a record taken on the current kernel source is read back
+    rec = tmp_path / "traffic.json"
+    rec.write_text(json.dumps({"source_sha256_16": bench.kernel_source_sha(),
+                               "dram_bytes_per_launch": 1.5e8, "command": "ncu ..."}))
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(rec))
+    assert bench.profiled_traffic() == 1.5e8
     # once the kernel source differs from the one the counters were taken on,
     # the traffic is reported as unknown
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "ffffffffffffffff")
     assert bench.profiled_traffic() is None
+    # a missing or malformed record is unknown too
+    rec.write_text("{}")
+    assert bench.profiled_traffic() is None
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(tmp_path / "absent.json"))
+    assert bench.profiled_traffic() is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    if not os.path.exists(bench.TRAFFIC_JSON):
+        pytest.skip("no traffic record committed")
+    with open(bench.TRAFFIC_JSON) as f:
+        rec = json.load(f)
+    assert len(rec["source_sha256_16"]) == 16
+    assert float(rec["dram_bytes_per_launch"]) > 0
+    assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+
+
+def test_source_hash_covers_the_layout_code():
     # the hash covers the kernel and the layout-deciding part of the setup only
     src = os.path.join(os.path.dirname(bench.__file__), "paper_1606_00545_gb300", "csrc",
                        "hec_setup.cpp")
