@@ -342,7 +342,9 @@ class Info:
 
 
 def bicgstab(A, b, M=None, x0=None, tol=1e-8, maxit=1000):
-    """Algorithm 4.  M: a RAS object or None.  Returns (x, Info)."""
+    """Right-preconditioned BiCGSTAB (Section 2.7; the van der Vorst 1992 /
+    Saad Section 7.4.2 recurrences on A M^{-1}).  M: a RAS object or None.
+    Returns (x, Info)."""
     rp, ci, va = _arrs(A)
     x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     info = _Info()

@@ -564,15 +564,25 @@ static void true_resid(int n, const int *rp, const int *ci, const double *va,
 }
 
 /*
- * Algorithm 4 (BiCGSTAB), right-preconditioned as written (p*, s*).
- * Readings where the paper is silent:
- *   - the shadow residual is the initial residual r_0 (Algorithm 4 names
- *     both r_0);
- *   - "is satisfied" means ||.||_2 <= tol * ||b||_2;
- *   - rho = 0 fails (status BREAKDOWN); (r_0, v) = 0 is treated the same way
- *     because alpha is undefined; omega = 0 stops with BREAKDOWN unless the
- *     residual test already passed;
- *   - one pass of the k loop is one iteration;
+ * BiCGSTAB (Section 2.7), written from the standard derivation: van der
+ * Vorst, SIAM J. Sci. Stat. Comput. 13 (1992), and Saad, "Iterative Methods
+ * for Sparse Linear Systems", 2nd ed., Section 7.4.2, applied to the right-
+ * preconditioned operator B = A M^{-1} (Saad, Section 9.3.2).  With u the
+ * iterate of B u = b, x = M^{-1} u is tracked directly, so that every
+ * direction p and every intermediate residual s pass through the
+ * preconditioner once: p^ = M^{-1} p, s^ = M^{-1} s.  One iteration j:
+ *   v = A p^,  alpha = (r, r~) / (v, r~),  s = r - alpha v,
+ *   t = A s^,  omega = (t, s) / (t, t),
+ *   x += alpha p^ + omega s^,  r = s - omega t,
+ *   beta = (r_new, r~) / (r_old, r~) * alpha / omega,
+ *   p = r + beta (p - omega v).
+ * Readings where the paper leaves a choice open:
+ *   - the shadow residual r~ is the initial residual r_0;
+ *   - convergence means ||.||_2 <= tol * ||b||_2, tested on s (then
+ *     x += alpha p^ alone) and on the new r;
+ *   - (r, r~) = 0 or (v, r~) = 0 is a breakdown (status BREAKDOWN); so is
+ *     omega = 0 ((t, t) = 0 gives omega = 0) unless r already converged;
+ *   - one iteration is one j above;
  *   - b = 0 returns x = 0 at once;
  *   - on exit the true residual ||b - A x|| / ||b|| is recomputed.
  */
@@ -581,9 +591,9 @@ int orc_bicgstab(int n, const int *rp, const int *ci, const double *va, const or
 {
     memset(info, 0, sizeof(*info));
     size_t sz = sizeof(double) * (size_t)n;
-    double *r = (double *)malloc(sz), *r0 = (double *)malloc(sz), *p = (double *)malloc(sz);
-    double *ps = (double *)malloc(sz), *v = (double *)malloc(sz), *s = (double *)malloc(sz);
-    double *ss = (double *)malloc(sz), *t = (double *)malloc(sz);
+    double *r = (double *)malloc(sz), *rt = (double *)malloc(sz), *p = (double *)malloc(sz);
+    double *ph = (double *)malloc(sz), *v = (double *)malloc(sz), *s = (double *)malloc(sz);
+    double *sh = (double *)malloc(sz), *t = (double *)malloc(sz);
     double bnorm = orc_nrm2(n, b);
     int status = ORC_MAXIT;
     int k = 0;
@@ -592,49 +602,37 @@ int orc_bicgstab(int n, const int *rp, const int *ci, const double *va, const or
         status = ORC_OK;
         goto finish;
     }
-    /* r_0 = b - A x_0 */
-    true_resid(n, rp, ci, va, b, x, r);
-    memcpy(r0, r, sz);
+    true_resid(n, rp, ci, va, b, x, r); /* r = b - A x_0 */
     if (orc_nrm2(n, r) <= tol * bnorm) {
         status = ORC_OK;
         goto finish;
     }
-    double rho_prev = 0.0, alpha = 0.0, omega = 0.0;
-    for (k = 1; k <= maxit; ++k) {
-        double rho = orc_dot(n, r0, r);
-        if (rho == 0.0) {
-            status = ORC_BREAKDOWN;
-            k--;
-            break;
-        }
-        if (k == 1) {
-            memcpy(p, r, sz);
-        } else {
-            double beta = (rho / rho_prev) * (alpha / omega);
-            for (int i = 0; i < n; ++i)
-                p[i] = r[i] + beta * (p[i] - omega * v[i]);
-        }
-        precond(M, n, p, ps);                 /* M p* = p */
-        orc_spmv(n, rp, ci, va, 1.0, ps, 0.0, v); /* v = A p* */
-        double r0v = orc_dot(n, r0, v);
-        if (r0v == 0.0) {
+    memcpy(rt, r, sz); /* shadow residual */
+    memcpy(p, r, sz);  /* first direction */
+    double rho = orc_dot(n, r, rt);
+    while (k < maxit) {
+        ++k;
+        precond(M, n, p, ph);
+        orc_spmv(n, rp, ci, va, 1.0, ph, 0.0, v);
+        double vr = orc_dot(n, v, rt);
+        if (vr == 0.0) {
             status = ORC_BREAKDOWN;
             break;
         }
-        alpha = rho / r0v;
-        orc_waxpby(n, 1.0, r, -alpha, v, s); /* s = r - alpha v */
+        double alpha = rho / vr;
+        orc_waxpby(n, 1.0, r, -alpha, v, s);
         if (orc_nrm2(n, s) <= tol * bnorm) {
-            orc_axpby(n, alpha, ps, 1.0, x); /* x = x + alpha p* */
+            orc_axpby(n, alpha, ph, 1.0, x);
             status = ORC_OK;
             break;
         }
-        precond(M, n, s, ss);                 /* M s* = s */
-        orc_spmv(n, rp, ci, va, 1.0, ss, 0.0, t); /* t = A s* */
+        precond(M, n, s, sh);
+        orc_spmv(n, rp, ci, va, 1.0, sh, 0.0, t);
         double tt = orc_dot(n, t, t);
-        omega = (tt == 0.0) ? 0.0 : orc_dot(n, t, s) / tt;
+        double omega = (tt == 0.0) ? 0.0 : orc_dot(n, t, s) / tt;
         for (int i = 0; i < n; ++i)
-            x[i] = x[i] + alpha * ps[i] + omega * ss[i];
-        orc_waxpby(n, 1.0, s, -omega, t, r); /* r = s - omega t */
+            x[i] += alpha * ph[i] + omega * sh[i];
+        orc_waxpby(n, 1.0, s, -omega, t, r);
         if (orc_nrm2(n, r) <= tol * bnorm) {
             status = ORC_OK;
             break;
@@ -643,10 +641,16 @@ int orc_bicgstab(int n, const int *rp, const int *ci, const double *va, const or
             status = ORC_BREAKDOWN;
             break;
         }
-        rho_prev = rho;
+        double rho_new = orc_dot(n, r, rt);
+        if (rho_new == 0.0) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double beta = (rho_new / rho) * (alpha / omega);
+        for (int i = 0; i < n; ++i)
+            p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        rho = rho_new;
     }
-    if (k > maxit)
-        k = maxit;
 finish:
     info->iters = k;
     info->status = status;
@@ -654,7 +658,7 @@ finish:
         true_resid(n, rp, ci, va, b, x, r);
         info->rel_resid = orc_nrm2(n, r) / bnorm;
     }
-    free(r); free(r0); free(p); free(ps); free(v); free(s); free(ss); free(t);
+    free(r); free(rt); free(p); free(ph); free(v); free(s); free(sh); free(t);
     return status;
 }
 

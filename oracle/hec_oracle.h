@@ -119,7 +119,8 @@ orc_ras *orc_jacobi_setup(int n, const int *rp, const int *ci, const double *va,
 int orc_cg(int n, const int *rp, const int *ci, const double *va, const orc_ras *M,
            const double *b, double *x, double tol, int maxit, orc_info *info);
 
-/* Algorithm 4: right-preconditioned BiCGSTAB.  M == NULL means no
+/* Right-preconditioned BiCGSTAB (Section 2.7; van der Vorst 1992, Saad
+ * Section 7.4.2 on A M^{-1}).  M == NULL means no
  * preconditioner.  x holds x0 on entry and the solution on exit. */
 int orc_bicgstab(int n, const int *rp, const int *ci, const double *va, const orc_ras *M,
                  const double *b, double *x, double tol, int maxit, orc_info *info);
