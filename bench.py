@@ -127,8 +127,10 @@ def run_kernel_only(args, local_rank):
         assert H.hec_precond_status(P) == H.OK
     ms = e0.elapsed_time(e1) / max(1, args.steps - 1) if args.steps > 1 else None
     inf = P.info()
-    nbytes = {"trsv": inf["apply_bytes"], "trsv32": inf["apply_bytes_f32"],
-              "spmv": A.nnz * 12 + A.n * 16, "spmv32": A.nnz * 8 + A.n * 8}[args.kernel]
+    nbytes = {"trsv": lambda: trsv_method_bytes(H, P, 8),
+              "trsv32": lambda: trsv_method_bytes(H, P, 4),
+              "spmv": lambda: A.nnz * 12 + A.n * 16, "spmv32": lambda: A.nnz * 8 + A.n * 8}[
+                  args.kernel]()
     print(json.dumps({"kernel": args.kernel, "launches": args.steps, "ms_per_launch": ms,
                       "alg_bytes": nbytes, "trsv_parts": inf["trsv_parts"],
                       "gbs": nbytes / (ms * 1e-3) / 1e9 if ms else None}))
@@ -323,6 +325,23 @@ def profiled_traffic():
     return None
 
 
+def trsv_method_bytes(H, P, vb):
+    """Algorithmic bytes of one RAS L+U apply as the method defines them, over
+    every row of every block: each stored factor entry (L_b strictly lower,
+    U_b with its diagonal) read once as value + int32 index, and per block
+    row r read, y written, y read back and z written (vb bytes each), plus
+    4 bytes per row and per level of the level arrays.  The kernel moves
+    fewer: it skips the rows that cannot reach an owned row of z, which
+    apply_bytes counts instead."""
+    inf = P.info()
+    levels = 0
+    for blk in range(inf["nblocks"]):
+        for which in (H.FACTOR_L, H.FACTOR_U):
+            levels += len(P.levels(blk, which)[0]) - 1
+    rows = inf["rows_total"]
+    return inf["factor_nnz"] * (vb + 4) + rows * 4 * vb + 4 * (rows + levels)
+
+
 # ------------------------------------------------------------------ CPU oracle
 def cpu_spmv_sample(A, reps=5):
     """The oracle's SpMV row loop on one host core and on every core (row
@@ -481,9 +500,13 @@ def c3_section(H, torch, dev, timed):
 
 
 def c4_bytes(Bs, per, nrhs, m_restart):
-    """Algorithmic bytes of one batched mixed solve from the per-system step
-    and cycle counts (stored nonzeros only, every vector counted once per
-    pass, cycles of equal length, second Gram-Schmidt passes not counted)."""
+    """Algorithmic bytes of one batched mixed solve from the per-system step,
+    cycle and re-orthogonalisation counts (stored nonzeros only, every vector
+    counted once per pass, cycles of equal length).  Gram-Schmidt step j reads
+    the j + 2 basis slots of the projection pass, the j + 2 of the fused
+    update-and-second-projection pass and writes one; a step whose second
+    projection lost too much takes a third pass of j + 2 reads and one write,
+    counted here at the cycle's mean j."""
     V, I, D = 4, 4, 8  # FP32 value, index, FP64
     total = 0.0
     rp, sp = Bs.row_ptr, Bs.sys_ptr
@@ -503,6 +526,7 @@ def c4_bytes(Bs, per, nrhs, m_restart):
         steps, cycles = per[s]["iters"], max(1, per[s]["cycles"])
         jlen = steps / cycles
         arn = cycles * sum((j + 2) * vec + (j + 3) * vec for j in range(int(round(jlen))))
+        arn += per[s].get("reorth", 0) * ((jlen - 1) / 2 + 3) * vec
         cyc = cycles * (nnz[s] * (D + I) + n * nrhs * (2 * D) + vec     # residual, v_0
                         + (jlen + 1) * vec + trsv + n * nrhs * (3 * D) + vec)  # u, M^-1 u, x += z
         grp = n * nrhs * D * 5  # b, x in; b, x staged; x out
@@ -547,7 +571,9 @@ def c4_section(H, torch, dev, timed, peak):
         d = {"solve_ms": ms, "solves_per_s": Bs.nsys * nrhs / (ms * 1e-3),
              "systems_per_s": Bs.nsys / (ms * 1e-3), "steps": inf["iters"],
              "steps_per_s": inf["iters"] / (ms * 1e-3), "max_rel_resid": inf["rel_resid"],
-             "converged_systems": ok, "kernel_launches": inf["kernel_launches"]}
+             "converged_systems": ok, "kernel_launches": inf["kernel_launches"],
+             "reorth_steps": int(sum(p["reorth"] for p in per)),
+             "fp64_finish": inf.get("fp64_finish", 0)}
         if name == "mixed":
             nbytes = c4_bytes(Bs, per, nrhs, C4_RESTART)
             d["roofline"] = {"bound": "hbm", "kernel": "k_batch<float,4> (whole batched solve)",
@@ -602,9 +628,17 @@ def c5_section(H):
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(C5_SEED + 1)
 
+    nstreams = [0]
+
     def stream(rate, nreq):
-        """A request stream: Poisson arrival offsets and pool picks."""
-        return np.cumsum(rng.exponential(1.0 / rate, nreq)), rng.integers(0, len(pool), nreq)
+        """A request stream: Poisson arrival offsets, pool picks and every
+        request's own right-hand side (uniform[-1, 1], seeded per request)."""
+        arr = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        picks = rng.integers(0, len(pool), nreq)
+        nstreams[0] += 1
+        own = [synth.rhs_uniform(pool[int(p)].n, C5_SEED * 10 ** 6 + nstreams[0] * 10 ** 4 + i)
+               for i, p in enumerate(picks)]
+        return arr, picks, own
 
     def register(S):
         t = time.perf_counter()
@@ -617,7 +651,7 @@ def c5_section(H):
         return time.perf_counter() - t
 
     def open_loop(S, rate, req, keyed):
-        arr, picks = req
+        arr, picks, own = req
         nreq = len(arr)
         res = []
         w0 = time.perf_counter()
@@ -628,7 +662,7 @@ def c5_section(H):
                     break
                 time.sleep(min(left, 0.002))
             p = int(picks[i])
-            S.submit(None if keyed else pool[p], rhs[p], ilu_k=specs[p]["k"],
+            S.submit(None if keyed else pool[p], own[i], ilu_k=specs[p]["k"],
                      key=p + 1 if keyed else 0, tag=i)
             res += S.poll(max_results=1024)
         while len(res) < nreq:
@@ -650,8 +684,9 @@ def c5_section(H):
                        "gmres30_tol1e-8_poisson_arrivals",
            "pool_unknowns": [A.n for A in pool], "generate_s": round(gen_s, 1),
            "lanes": C5_LANES, "note": "keyed runs: each pool system set up once and kept "
-                                     "resident, requests carry right-hand sides; cold run: "
-                                     "every request carries its matrix and is set up"}
+                                     "resident, every request carries its own right-hand side "
+                                     "(seeded per request); cold run: every request carries "
+                                     "its matrix and is set up"}
     req_lambda = stream(C5_LAMBDA, C5_REQUESTS)
     with H.Server(lanes=C5_LANES, flags=H.MIXED_FP32, keep_solutions=False) as S:
         out["register_s"] = round(register(S), 2)
@@ -787,7 +822,8 @@ def run_ours(args, rank, world, local_rank):
     assert H.hec_precond_status(P) == H.OK
     apply_s = ms_apply * 1e-3 / reps
     peak, peak_kind = measured_peaks()
-    achieved = pinf["apply_bytes"] / apply_s / 1e9
+    trsv_bytes = trsv_method_bytes(H, P, 8)
+    achieved = trsv_bytes / apply_s / 1e9
     # SpMV alone (second kernel of the path)
     y = torch.empty_like(r)
     for _ in range(5):
@@ -846,6 +882,7 @@ def run_ours(args, rank, world, local_rank):
                              flags=H.X0_ZERO)
     H.hec_refactor(Ah, P, v1)  # back to the benchmark's matrix
     pinf = P.info()
+    trsv_bytes32 = trsv_method_bytes(H, P, 4)
     skip = set(filter(None, args.skip.split(",")))
     c1 = (c1_section(H, torch, dev, rank == 0 and not args.no_cpu_baseline)
           if "c1" not in skip else None)
@@ -878,7 +915,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "k_trsv_ras (RAS L+U level-scheduled solve)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "alg_bytes_per_launch": pinf["apply_bytes"],
+                     "alg_bytes_per_launch": trsv_bytes,
+                     "alg_bytes_rule": "every block row: factor entries x (8 + 4) + rows x 4 x 8 "
+                                       "+ 4 x (rows + levels)",
+                     "needed_rows_bytes_per_launch": pinf["apply_bytes"],
                      "launch_ms": apply_s * 1e3},
         "spmv": {"achieved": spmv_gbs, "unit": "GB/s", "frac": spmv_gbs / peak,
                  "alg_bytes_per_launch": spmv_bytes, "launch_ms": ms_spmv / reps},
@@ -901,8 +941,10 @@ def run_ours(args, rank, world, local_rank):
                       "iters_per_s": cgi["iters"] / (ms_cg * 1e-3), "rel_resid": cgi["rel_resid"],
                       "solve_ms": ms_cg},
         "fp32_kernels": {"trsv_ms": ms_a32 / reps,
-                         "trsv_gbs": pinf["apply_bytes_f32"] / (ms_a32 * 1e-3 / reps) / 1e9,
-                         "trsv_alg_bytes": pinf["apply_bytes_f32"],
+                         "trsv_gbs": trsv_bytes32 / (ms_a32 * 1e-3 / reps) / 1e9,
+                         "trsv_frac": trsv_bytes32 / (ms_a32 * 1e-3 / reps) / 1e9 / peak,
+                         "trsv_alg_bytes": trsv_bytes32,
+                         "trsv_needed_rows_bytes": pinf["apply_bytes_f32"],
                          "spmv_ms": ms_s32 / reps,
                          "spmv_gbs": (A.nnz * 8 + A.n * 8) / (ms_s32 * 1e-3 / reps) / 1e9},
         "c1_latency": c1,

@@ -116,7 +116,8 @@ typedef struct {
     int32_t import_slots;    /* shared-memory window of values received from a
                                 neighbouring CTA (0: no block is split)        */
     int32_t split_blocks;    /* RAS blocks solved by more than one CTA         */
-    int32_t reserved;
+    int32_t trsv_resident;   /* 1: the FP64 triangular solves run the resident-
+                                vector kernel (hec_precond_set_trsv_kernel)    */
 } hec_precond_info_t;
 
 #define HEC_GMRES 0
@@ -211,7 +212,8 @@ int hec_spmv(hec_matrix_t A, double alpha, const double *x, double beta, const d
 /* The FP32 SpMV of the mixed-precision inner solves, Eq. 2 with FP32 values
  * (the matrix's values rounded once to FP32, kept beside the FP64 ones after
  * the first FP32 call), FP32 products and accumulation.  x, y_in, y_out:
- * device arrays of n floats, y_out 8-byte aligned; no fused dots. */
+ * device arrays of n floats, y_out 16-byte aligned (rows are stored four at
+ * a time; HEC_ERR_INVALID otherwise, before any device work); no fused dots. */
 int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const float *y_in,
                  float *y_out, void *stream);
 
@@ -306,9 +308,27 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
  * z[pos] = (y[src[t]] - sum_k val[k] z[dep[k]]) * dinv[t], written to
  * global row dst[t] when dst[t] >= 0 (an owned row).  exp[t] >= 0 is the
  * slot that row's value takes in the neighbour's ring (L: part p + 1, U:
- * part p - 1).  Padding entries have value 0.  The stream must be NULL or a
- * CUDA stream; a device handle's layout is read back on it (synchronously).
- * HEC_ERR_INVALID for a damped-Jacobi handle or before level_schedule. */
+ * part p - 1).  Padding entries have value 0.
+ *
+ * Layouts of the resident kernel (hec_precond_info_t.trsv_resident; chunk
+ * flag bit 5) have one program per block (*parts = 1) whose y scratch offset
+ * is the offset of the block's V_b in the kernel's row list and whose z
+ * scratch offset is its first group of consecutive chunks (the kernel
+ * streams a group of up to 16 KB with one bulk copy; flag bit 6 marks a
+ * group's last chunk), and chunks of 8 int32 (row count, warp count, first
+ * position, flags, 0, 0, FW, 0)
+ * followed, per warp of 32 rows, by val (ceil(FW / VW) vectors of 32 lanes
+ * x 16 bytes, VW = 16 / value bytes: lane l's entries k VW .. k VW + VW - 1
+ * in vector k), idx (ceil((FW + 1) / 8) vectors of 32 lanes x 8 uint16:
+ * lane l's FW dependency slots, then its own slot) and, for U, dinv[32].
+ * Slots are the block's local row indices; slot nv (the block's row count)
+ * holds 0 and pads short rows and the rows past the chunk's end.  Row t of
+ * the L pass computes x[own] -= sum_k val[k] x[dep[k]] with x = r on V_b at
+ * the start; of the U pass x[own] = (x[own] - sum_k val[k] x[dep[k]]) *
+ * dinv[t]; z on the owned rows is x at the end.  The stream must be NULL or
+ * a CUDA stream; a device handle's layout is read back on it
+ * (synchronously).  HEC_ERR_INVALID for a damped-Jacobi handle or before
+ * level_schedule. */
 int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, int32_t *nchunks,
                            int32_t *ring_slots, int32_t *import_slots, int32_t *parts,
                            int32_t *fixed_width, void *pack, uint32_t *chunks, int64_t *programs,
@@ -322,6 +342,32 @@ int hec_precond_get_layout(hec_precond_t M, int32_t fp32, int64_t *pack_bytes, i
  * between ilu_k_setup and level_schedule; HEC_ERR_INVALID afterwards, for a
  * damped-Jacobi handle or another value. */
 int hec_precond_set_trsv_parts(hec_precond_t M, int32_t parts);
+/* Which kernel applies the triangular solves (Section 2.6, Eq. 11: both walk
+ * the levels of L_b, then of U_b, and give the same z up to the rounding of
+ * the per-row sums, which are taken in the same order):
+ *   HEC_TRSV_STREAMED -- the level-major chunks stream through a shared-
+ *     memory ring of recent solved values; the right-hand sides are gathered
+ *     per chunk from r (L) and from a global y scratch (U); a block may be
+ *     split over the CTAs of a cluster (hec_precond_set_trsv_parts).  For
+ *     large blocks.
+ *   HEC_TRSV_RESIDENT -- one CTA per block keeps the block's whole vector in
+ *     shared memory and solves in place: a level's critical path is shared
+ *     memory, the row's multiply-adds and one barrier.  For blocks below
+ *     65535 rows whose factor rows hold at most 8 entries and whose vector
+ *     (rows + 1 values) fits in shared memory beside three chunk stages:
+ *     the latency-first form for small systems.
+ *   HEC_TRSV_AUTO (default) -- the streamed kernel (measured on GB300 the
+ *     resident kernel ties it on a single 64 x 64 ILU(0) block and is slower
+ *     on wider levels).
+ * The FP32 layout of the mixed-precision mode follows the same rule.  Call
+ * it between ilu_k_setup and level_schedule; HEC_ERR_INVALID afterwards,
+ * for a damped-Jacobi handle or another value; level_schedule returns
+ * HEC_ERR_INVALID when HEC_TRSV_RESIDENT is asked for and a block does not
+ * fit. */
+#define HEC_TRSV_AUTO 0
+#define HEC_TRSV_STREAMED 1
+#define HEC_TRSV_RESIDENT 2
+int hec_precond_set_trsv_kernel(hec_precond_t M, int32_t kernel);
 /* Debug builds (compiled with HEC_DEBUG; not a counterpart of anything in the
  * paper): the triangular-solve kernel checks every chunk header against the
  * position its program has reached, every gathered index against n, and
@@ -474,7 +520,9 @@ typedef struct {
     int32_t iters;      /* Arnoldi steps, summed over groups of 4 right-hand sides */
     int32_t cycles;     /* restart cycles                                         */
     int32_t status;     /* HEC_OK, HEC_MAXIT, HEC_BREAKDOWN                        */
-    int32_t reserved;
+    int32_t reorth;     /* Arnoldi steps whose classical Gram-Schmidt took a third
+                           (re-orthogonalising) pass: the second projection lost
+                           more than half of ||w||^2 for one of the right-hand sides */
     double rel_resid;   /* largest true ||b - A x|| / ||b|| over its right-hand sides */
 } hec_batch_sys_info_t;
 

@@ -57,7 +57,8 @@ struct BatchSys {
 
 // Per-system outcome, the layout of hec_batch_sys_info_t.
 struct BatchResult {
-    int iters, cycles, status, pad;
+    int iters, cycles, status;
+    int reorth; // Arnoldi steps that took the third (re-orthogonalising) pass
     double rel_resid;
 };
 

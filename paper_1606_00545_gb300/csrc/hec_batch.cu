@@ -861,6 +861,7 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
                 if (only[s]) {
                     res[s].iters += r64[s].iters;
                     res[s].cycles += r64[s].cycles;
+                    res[s].reorth += r64[s].reorth;
                     res[s].status = r64[s].status;
                     res[s].rel_resid = r64[s].rel_resid;
                 }
@@ -885,7 +886,7 @@ int krylov_solve_batched(hec_batch_t B, const double *b, double *x, int32_t nrhs
                 sys_info[s].iters = r.iters;
                 sys_info[s].cycles = r.cycles;
                 sys_info[s].status = r.status;
-                sys_info[s].reserved = 0;
+                sys_info[s].reorth = r.reorth;
                 sys_info[s].rel_resid = r.rel_resid;
             }
         }

@@ -171,7 +171,7 @@ struct hec_matrix_s {
 // triangular-solve kernel reads, and its scratch.
 struct TrsvLayout {
     TrsvPack pack;
-    DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc;
+    DevBuf d_pack, d_chunks, d_blocks, d_ysc, d_zsc, d_vrows, d_groups;
     DevBuf d_row0, d_rms, d_rml, d_rmd; // value maps of hec_refactor (uploaded on first use)
     int nstages = 8;
     int vbytes = 8;
@@ -180,7 +180,8 @@ struct TrsvLayout {
     int64_t device_bytes() const
     {
         return (int64_t)(d_pack.bytes + d_chunks.bytes + d_blocks.bytes + d_ysc.bytes +
-                         d_zsc.bytes + d_row0.bytes + d_rms.bytes + d_rml.bytes + d_rmd.bytes);
+                         d_zsc.bytes + d_vrows.bytes + d_groups.bytes + d_row0.bytes +
+                         d_rms.bytes + d_rml.bytes + d_rmd.bytes);
     }
 };
 
@@ -196,6 +197,7 @@ struct hec_precond_s {
     DevBuf d_err;
     int stage_bytes = 24576;
     int trsv_parts = 0; // CTAs per RAS block of the triangular solve (0: automatic)
+    int trsv_kernel = HEC_TRSV_AUTO; // triangular-solve kernel (hec_precond_set_trsv_kernel)
     std::vector<std::unique_ptr<Solver>> solvers;
     // hec_refactor: every block's factor on the device (entries numbered over
     // all blocks), its source map into A and the L level sets; the host copy
@@ -244,7 +246,13 @@ SpmvArgs spmv_args(const hec_matrix_s *A)
     return a;
 }
 
-int spmv_grid(const hec_matrix_s *A) { return grid_for((A->hec.n + kSpmvTile - 1) / kSpmvTile, 1, 8); }
+// CTAs of an SpMV launch: one per row block (one 512-row tile in FP64, two
+// in FP32, where a thread owns four rows), at most 8 per SM.
+int spmv_grid(const hec_matrix_s *A, bool fp32)
+{
+    const int64_t tiles = (A->hec.n + kSpmvTile - 1) / kSpmvTile;
+    return grid_for(fp32 ? (tiles + 1) / 2 : tiles, 1, 8);
+}
 
 int run_spmv(const hec_matrix_s *A, SpmvArgs a, int mode, int ndot, cudaStream_t s,
              bool fp32 = false)
@@ -253,7 +261,7 @@ int run_spmv(const hec_matrix_s *A, SpmvArgs a, int mode, int ndot, cudaStream_t
         a.ell_val = A->ell_val32.p;
         a.tail_val = A->tail_val32.p;
     }
-    if (launch_spmv(a, mode, ndot, !A->hec.tail_rows.empty(), spmv_grid(A), s, fp32) != 0)
+    if (launch_spmv(a, mode, ndot, !A->hec.tail_rows.empty(), spmv_grid(A, fp32), s, fp32) != 0)
         return fail(HEC_ERR_INVALID, "no SpMV variant for mode %d ndot %d", mode, ndot);
     return check_launch("spmv");
 }
@@ -306,6 +314,10 @@ TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
     a.spin_limit = spin;
     a.err = M->d_err.as<int>();
     a.n = M->n;
+    a.resident = L.pack.resident;
+    a.res_slots = L.pack.res_slots;
+    a.vrows = L.d_vrows.as<int>();
+    a.groups = L.d_groups.as<uint2>();
     return a;
 }
 
@@ -348,6 +360,56 @@ int layout_parts(const hec_precond_s *M, int idx)
     return trsv_auto_parts(M->blocks, M->host_only ? 152 : device_sms(), idx == 0 ? 128 : 256);
 }
 
+// The triangular-solve layout with (idx 0) FP64 or (idx 1) FP32 values: the
+// resident-vector kernel's when asked for (every block's vector must fit in
+// shared memory beside three stages); else the streamed kernel's.  (The
+// automatic choice streams: measured on GB300, the resident kernel ties the
+// streamed one on a single 64 x 64 ILU(0) block and is slower on wider
+// levels.)  Sets the row width of the
+// fixed-slot formats (0: generic) and, for the resident layout, the stage
+// count (the streamed kernel's is sized at upload).
+int pack_layout(const hec_precond_s *M, int idx, TrsvPack &P, int &fixed_width, int &nstages,
+                std::string &msg)
+{
+    const int vb = idx == 0 ? 8 : 4;
+    const int longest =
+        std::max(max_factor_width(M->blocks, false), max_factor_width(M->blocks, true));
+    if (M->trsv_kernel != HEC_TRSV_STREAMED) {
+        const int rw = trsv_resident_width(longest);
+        int maxnv = 0;
+        for (const BlockFactor &B : M->blocks)
+            maxnv = std::max(maxnv, B.F.n);
+        if (rw > 0 && maxnv < 65535 && M->trsv_kernel == HEC_TRSV_RESIDENT) {
+            const int rc = pack_trsv_resident(M->blocks, rw, vb, P, msg);
+            if (rc != HEC_OK)
+                return rc;
+            // shared memory of the stage count (host-only handles: 3 stages
+            // within GB300's 227 KB per block)
+            nstages = M->host_only
+                          ? (trsv_res_smem_bytes(P.stage_bytes, 3, P.res_slots, vb) <= 226 * 1024
+                                 ? 3
+                                 : 0)
+                          : trsv_res_stages_for(P.stage_bytes, P.res_slots, vb);
+            if (nstages > 0) {
+                fixed_width = rw;
+                return HEC_OK;
+            }
+        }
+        if (M->trsv_kernel == HEC_TRSV_RESIDENT) {
+            msg = "the resident triangular-solve kernel needs rows of at most 8 entries, blocks "
+                  "below 65535 rows and a block vector that fits in shared memory";
+            return HEC_ERR_INVALID;
+        }
+    }
+    // pad every row to one short width when the factors allow it: the
+    // fixed-slot chunks that the kernel streams from registers one chunk
+    // ahead (the padding costs multiply-adds only where a warp's rows are
+    // shorter than the width)
+    fixed_width = trsv_uniform_width(longest);
+    return pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, vb, P, msg, fixed_width,
+                     layout_parts(M, idx));
+}
+
 // Pack, upload and size the scratch of the layout with vb-byte values.
 int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
 {
@@ -356,21 +418,20 @@ int build_layout(hec_precond_s *M, int idx, cudaStream_t s)
         return HEC_OK;
     HEC_TRY(refresh_host_factors(M, s));
     L.vbytes = idx == 0 ? 8 : 4;
-    // pad every row to one short width when the factors allow it: the
-    // fixed-slot chunks that the kernel streams from registers one chunk ahead
-    // (the padding costs multiply-adds only where a warp's rows are shorter
-    // than the width)
-    L.fixed_width = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
-                                                max_factor_width(M->blocks, true)));
     std::string msg;
-    int rc = pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, L.vbytes, L.pack, msg,
-                       L.fixed_width, layout_parts(M, idx));
+    const int rc = pack_layout(M, idx, L.pack, L.fixed_width, L.nstages, msg);
     if (rc != HEC_OK)
         return fail(rc, "%s", msg.c_str());
+    const bool res = L.pack.resident != 0;
     if (!M->host_only) {
-        L.nstages = trsv_stages_for(L.pack.stage_bytes, L.pack.ring_slots + L.pack.import_slots,
-                                    L.vbytes);
+        if (!res)
+            L.nstages = trsv_stages_for(L.pack.stage_bytes,
+                                        L.pack.ring_slots + L.pack.import_slots, L.vbytes);
         HEC_TRY(upload(L.d_pack, L.pack.pack, s));
+        if (res) {
+            HEC_TRY(upload(L.d_vrows, L.pack.vrows, s));
+            HEC_TRY(upload(L.d_groups, L.pack.groups, s));
+        }
         HEC_TRY(upload(L.d_chunks, L.pack.chunks, s));
         HEC_TRY(upload(L.d_blocks, L.pack.blocks, s));
         HEC_TRY(L.d_ysc.alloc(std::max<int64_t>(L.pack.ysz, 1) * L.vbytes, s));
@@ -1440,9 +1501,9 @@ int hec_spmv_f32(hec_matrix_t A, float alpha, const float *x, float beta, const 
     return abi_guard(__func__, [&]() -> int {
         if (!A || !x || !y_out)
             return fail(HEC_ERR_INVALID, "null argument");
-        // a thread stores its two adjacent rows with one 8-byte store
-        if (reinterpret_cast<uintptr_t>(y_out) % (2 * sizeof(float)) != 0)
-            return fail(HEC_ERR_INVALID, "y_out must be 8-byte aligned");
+        // a thread stores its four adjacent rows with one 16-byte store
+        if (reinterpret_cast<uintptr_t>(y_out) % (4 * sizeof(float)) != 0)
+            return fail(HEC_ERR_INVALID, "y_out must be 16-byte aligned");
         if (A->host_only)
             return fail(HEC_ERR_INVALID, "host-only matrix has no device data");
         if (beta != 0.0f && !y_in)
@@ -1679,6 +1740,7 @@ int hec_precond_info(hec_precond_t M, hec_precond_info_t *info)
         for (const TrsvBlock &T : M->lay[0].pack.blocks)
             info->global_passes += (T.ring_L ? 0 : 1) + (T.ring_U ? 0 : 1);
         info->trsv_parts = M->scheduled && M->kind != kJacobi ? M->lay[0].pack.parts : 0;
+        info->trsv_resident = M->scheduled && M->kind != kJacobi ? M->lay[0].pack.resident : 0;
         info->import_slots = M->scheduled && M->kind != kJacobi ? M->lay[0].pack.import_slots : 0;
         {
             const TrsvPack &P = M->lay[0].pack;
@@ -1835,6 +1897,22 @@ int hec_precond_set_trsv_parts(hec_precond_t M, int32_t parts)
     });
 }
 
+int hec_precond_set_trsv_kernel(hec_precond_t M, int32_t kernel)
+{
+    return abi_guard(__func__, [&]() -> int {
+        if (!M || (kernel != HEC_TRSV_AUTO && kernel != HEC_TRSV_STREAMED &&
+                   kernel != HEC_TRSV_RESIDENT))
+            return fail(HEC_ERR_INVALID,
+                        "kernel must be HEC_TRSV_AUTO, HEC_TRSV_STREAMED or HEC_TRSV_RESIDENT");
+        if (M->kind == kJacobi)
+            return fail(HEC_ERR_INVALID, "a damped-Jacobi preconditioner has no triangular solve");
+        if (M->scheduled)
+            return fail(HEC_ERR_INVALID, "choose the kernel before level_schedule");
+        M->trsv_kernel = kernel;
+        return HEC_OK;
+    });
+}
+
 int hec_precond_apply(hec_precond_t M, const double *r, double *z, int64_t spin_limit, void *stream)
 {
     return abi_guard(__func__, [&]() -> int {
@@ -1965,15 +2043,16 @@ int hec_workspace_bytes(hec_matrix_t A, hec_precond_t M, int32_t restart,
             // here on the host to be counted
             TrsvPack P;
             std::string msg;
-            const int fw = trsv_uniform_width(std::max(max_factor_width(M->blocks, false),
-                                                       max_factor_width(M->blocks, true)));
-            const int rc =
-                pack_trsv(M->blocks, M->n, M->stage_bytes, kMaxRing, 4, P, msg, fw, layout_parts(M, 1));
+            int fw = 0, ns = 0;
+            const int rc = pack_layout(M, 1, P, fw, ns, msg);
             if (rc != HEC_OK)
                 return fail(rc, "%s", msg.c_str());
             total += dev((int64_t)P.pack.size()) + dev((int64_t)(P.chunks.size() * sizeof(uint2))) +
                      dev((int64_t)(P.blocks.size() * sizeof(TrsvBlock))) +
-                     std::max<int64_t>(P.ysz, 1) * 4 + std::max<int64_t>(P.zsz, 1) * 4;
+                     std::max<int64_t>(P.ysz, 1) * 4 + std::max<int64_t>(P.zsz, 1) * 4 +
+                     (P.resident ? dev((int64_t)(P.vrows.size() * sizeof(int))) +
+                                       dev((int64_t)(P.groups.size() * sizeof(uint2)))
+                                 : 0);
         }
         *bytes = total;
         return HEC_OK;

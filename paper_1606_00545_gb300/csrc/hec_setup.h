@@ -77,6 +77,12 @@ struct TrsvPack {
     // blocks in order (block b's entries start after those of blocks < b)
     std::vector<int64_t> chunk_row0; // per chunk: first index into the row maps
     std::vector<int> rm_start, rm_len, rm_diag; // first value's entry, count, diagonal (U; -1 for L)
+    // resident-vector layout (pack_trsv_resident): one CTA per block, the
+    // block's vector in shared memory
+    int resident = 0;
+    int res_slots = 0;          // largest block's rows + 1
+    std::vector<int> vrows;     // V_b of every block, concatenated (TrsvBlock::yoff)
+    std::vector<uint2> groups;  // bulk copies of consecutive chunks (TrsvBlock::zoff, ::pad)
 };
 // vb: bytes per stored value, 8 (FP64 layout) or 4 (FP32 layout).
 // uniform_width > 0 (at most 8): every row is padded to this width (value 0)
@@ -87,6 +93,13 @@ struct TrsvPack {
 // not allow that split gets fewer (its remaining programs are empty).
 int pack_trsv(const std::vector<BlockFactor> &B, int n, int stage_bytes, int max_ring, int vb,
               TrsvPack &out, std::string &msg, int uniform_width = 0, int parts = 1);
+// The resident-vector layout of k_trsv_res: every block one program, its rows
+// padded to `width` (2, 3, 4, 6 or 8: trsv_resident_width of the longest
+// row), dependencies as local row slots, every block below 65535 rows.
+int pack_trsv_resident(const std::vector<BlockFactor> &B, int width, int vb, TrsvPack &out,
+                       std::string &msg);
+// The resident width for rows of at most longest_row entries, 0 if none.
+int trsv_resident_width(int longest_row);
 // The parts per block worth launching: split while the widest block's levels
 // hold more than rows_per_part rows per part and the CTAs fit on sm_count SMs.
 int trsv_auto_parts(const std::vector<BlockFactor> &B, int sm_count, int rows_per_part);

@@ -626,7 +626,7 @@ template <class T, int NR> struct Batch {
     //   pass 1: h = V^T w, ||w||^2
     //   pass 2: w' = w - V h; h2 = V^T w', ||w'||^2       (one read of V)
     //   pass 3: w'' = w' - V h2, ||w''||^2; h += h2       (when needed)
-    __device__ bool orthogonalise(int j)
+    __device__ bool orthogonalise(int j, int &reorth_steps)
     {
         const int u4 = tid & 3;
         const int wi = (j + 1) << tshift;
@@ -677,6 +677,7 @@ template <class T, int NR> struct Batch {
             reorth |= v.sc[SC_ACTIVE] != 0.0 && v.sc[SC_W2] < 0.5 * v.sc[SC_WW];
         }
         if (reorth) {
+            ++reorth_steps;
             set_coef(j + 1, 1);
             T w2[4] = {T(0), T(0), T(0), T(0)};
             if (!stream(j + 2, [&](const T *st, int t) {
@@ -769,7 +770,7 @@ template <class T, int NR> struct Batch {
             __syncthreads();
         }
         const int m = a.m;
-        int steps = 0, cycles = 0, status = HEC_OK;
+        int steps = 0, cycles = 0, status = HEC_OK, reorth_steps = 0;
         double worst = 0.0;
         for (;;) {
             // ---- true residual in FP64; v_0 (unnormalised) in T
@@ -844,7 +845,7 @@ template <class T, int NR> struct Batch {
                 spmv_in(z, j + 1);
                 fence_proxy_async_global();
                 __syncthreads();
-                if (!orthogonalise(j))
+                if (!orthogonalise(j, reorth_steps))
                     return false;
                 // ---- Givens rotations and least-squares residual, FP64
                 if (tid < NR) {
@@ -939,6 +940,7 @@ template <class T, int NR> struct Batch {
         }
         res.iters += steps;
         res.cycles += cycles;
+        res.reorth += reorth_steps;
         if (status != HEC_OK && res.status == HEC_OK)
             res.status = status;
         res.rel_resid = worst > res.rel_resid ? worst : res.rel_resid;

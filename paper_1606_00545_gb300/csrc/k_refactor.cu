@@ -162,9 +162,10 @@ __global__ void __launch_bounds__(kThreads) k_iluk_numeric(RefactorArgs a)
 // The triangular-solve layout's value slots from the new factor values: one
 // CTA per chunk, thread t on row t.  Row t of chunk c takes the factor
 // entries [start, start + len) of its pass (L: the multipliers; U: the
-// entries right of the diagonal) and, for U, 1 / u_tt.  Both chunk formats
+// entries right of the diagonal) and, for U, 1 / u_tt.  The chunk formats
 // of trsv_layout.cpp: fixed-slot (flag bit 3: every row padded to FW entries,
-// 16-byte vectors per lane in per-warp blocks) and generic (per-warp widths).
+// 16-byte vectors per lane in per-warp blocks; bit 5: the resident kernel's
+// blocks, with 16-bit slots) and generic (per-warp widths).
 template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillArgs a)
 {
     const int c = blockIdx.x;
@@ -180,15 +181,24 @@ template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillA
     const int start = a.rm_start[q], len = a.rm_len[q];
     if (hdr[3] & 8) { // fixed-slot: 16-byte vectors of VW values per lane
         const int FW = hdr[6];
-        const bool exps = (hdr[3] & 16) != 0;
         constexpr int vb = (int)sizeof(T), VW = 16 / vb;
-        const int NV = (FW + VW - 1) / VW, ND = (FW + 3) / 4;
-        const int blk = (NV + ND) * 512 + 128 + (upass ? 32 * vb + 128 : 0) + (exps ? 128 : 0);
+        const int NV = (FW + VW - 1) / VW;
+        int blk, dinv_off;
+        if (hdr[3] & 32) { // resident format: index vectors of 8 uint16
+            const int NI = (FW + 1 + 7) / 8;
+            dinv_off = (NV + NI) * 512;
+            blk = dinv_off + (upass ? 32 * vb : 0);
+        } else {
+            const bool exps = (hdr[3] & 16) != 0;
+            const int ND = (FW + 3) / 4;
+            dinv_off = (NV + ND) * 512;
+            blk = dinv_off + 128 + (upass ? 32 * vb + 128 : 0) + (exps ? 128 : 0);
+        }
         T *val = reinterpret_cast<T *>(ch + 32 + (size_t)w * blk);
         for (int k = 0; k < NV * VW; ++k)
             val[(k / VW) * 32 * VW + lane * VW + k % VW] = k < len ? T(a.f[start + k]) : T(0);
         if (upass)
-            reinterpret_cast<T *>(ch + 32 + (size_t)w * blk + (NV + ND) * 512)[lane] =
+            reinterpret_cast<T *>(ch + 32 + (size_t)w * blk + dinv_off)[lane] =
                 T(__ddiv_rn(1.0, a.f[a.rm_diag[q]]));
         return;
     }

@@ -1,25 +1,53 @@
 // k_spmv.cu -- SpMV on the HEC format (Section 2.1-2.2, Algorithm 1, Eq. 2).
 //
 // The paper runs the ELL part with one thread per row and then the CSR part
-// with one thread per row.  Here one launch does both: every CTA walks tiles
-// of 512 consecutive rows; a thread owns two adjacent rows, so each slab
-// column is read with one vector load of values (double2 / float2) and one
-// 64-bit load of column indices (int2), coalesced across the warp because the
-// slab is column-major with a leading dimension that is a multiple of 256
-// rows.  Tail rows of a tile (rows longer than the slab width K) are summed
-// first, one warp per row with a shuffle reduction, into shared memory, then
-// added to the slab sum of their row.  The result goes through the Eq. 2
-// epilogue and, optionally, up to two dot products of the output are reduced
-// in the same launch (deterministic order, see reduce.cuh).  T = double is
-// the FP64 path; T = float is the FP32 inner solve of the mixed-precision
-// mode (FP32 products and accumulation; the dots' cross-CTA sums in FP64).
+// with one thread per row.  Here one launch does both.  A thread owns RPT
+// adjacent rows -- 2 in FP64, 4 in FP32 -- so each slab column is read with
+// one 16-byte load of values (double2 / float4) and one load of column
+// indices (int2 / int4), coalesced across the warp because the slab is
+// column-major with a leading dimension that is a multiple of 32 rows.  A CTA
+// walks row blocks of kThreads * RPT rows (one 512-row tile in FP64, two in
+// FP32).  Tail rows of a block (rows longer than the slab width K) are summed
+// first into shared memory, then added to the slab sum of their row: short
+// tail rows by groups of 4-32 lanes (the group size the setup chose for the
+// tile from its mean tail length) with xor-shuffle sums, rows longer than
+// kSpmvLongRow by the whole CTA in a fixed order.  The result goes through
+// the Eq. 2 epilogue and, optionally, up to two dot products of the output
+// are reduced in the same launch (deterministic order, see reduce.cuh).
+// T = double is the FP64 path; T = float is the FP32 inner solve of the
+// mixed-precision mode (FP32 products and accumulation; the dots' cross-CTA
+// sums in FP64).
 #include "reduce.cuh"
 
 namespace hec {
 
-template <class T> struct Vec2;
-template <> struct Vec2<double> { using type = double2; };
-template <> struct Vec2<float> { using type = float2; };
+// RPT adjacent rows per thread, read with 16-byte value vectors.
+template <class T> struct RowVec;
+template <> struct RowVec<double> {
+    static constexpr int RPT = 2;
+    using V = double2;
+    using C = int2;
+    __device__ static double get(const V &v, int j) { return j == 0 ? v.x : v.y; }
+    __device__ static int col(const C &c, int j) { return j == 0 ? c.x : c.y; }
+    __device__ static void put(double *p, const double *y) { *reinterpret_cast<V *>(p) = make_double2(y[0], y[1]); }
+};
+template <> struct RowVec<float> {
+    static constexpr int RPT = 4;
+    using V = float4;
+    using C = int4;
+    __device__ static float get(const V &v, int j)
+    {
+        return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    }
+    __device__ static int col(const C &c, int j)
+    {
+        return j == 0 ? c.x : j == 1 ? c.y : j == 2 ? c.z : c.w;
+    }
+    __device__ static void put(float *p, const float *y)
+    {
+        *reinterpret_cast<V *>(p) = make_float4(y[0], y[1], y[2], y[3]);
+    }
+};
 
 template <class T>
 __device__ __forceinline__ T warp_sum_t(T v)
@@ -30,58 +58,67 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
+// Row blocks of one CTA pass: kThreads * RPT rows, i.e. RPT / 2 SpMV tiles.
+template <class T> constexpr int spmv_tiles_per_block() { return RowVec<T>::RPT / 2; }
+
 template <int MODE, int NDOT, bool TAIL, class T>
 __global__ void __launch_bounds__(kThreads) k_spmv_hec(SpmvArgs a)
 {
-    using T2 = typename Vec2<T>::type;
+    using RV = RowVec<T>;
+    constexpr int RPT = RV::RPT, TPB = RPT / 2, BR = kThreads * RPT;
     count_launch(a.st);
     if (a.st && a.st->skip)
         return; // uniform across the grid: set before this launch
-    __shared__ T s_tail[TAIL ? kSpmvTile : 1];
+    __shared__ T s_tail[TAIL ? BR : 1];
     T acc[NDOT > 0 ? NDOT : 1];
 #pragma unroll
     for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
         acc[d] = T(0);
-    const T2 *__restrict__ val2 = reinterpret_cast<const T2 *>(a.ell_val);
-    const int2 *__restrict__ col2 = reinterpret_cast<const int2 *>(a.ell_col);
+    const typename RV::V *__restrict__ valv = reinterpret_cast<const typename RV::V *>(a.ell_val);
+    const typename RV::C *__restrict__ colv = reinterpret_cast<const typename RV::C *>(a.ell_col);
     const T *__restrict__ x = reinterpret_cast<const T *>(a.x);
     const T *y_in = reinterpret_cast<const T *>(a.y_in);
     T *y_out = reinterpret_cast<T *>(a.y_out);
     const T *tail_val = reinterpret_cast<const T *>(a.tail_val);
     const T alpha = T(a.alpha), beta = T(a.beta);
-    const int ld2 = a.ld >> 1;
+    const int ldv = a.ld / RPT; // the leading dimension is a multiple of 32 rows
+    const int nblk = (a.ntiles + TPB - 1) / TPB;
 
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int base = tile * kSpmvTile;
-        const int r0 = base + 2 * threadIdx.x;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const int base = blk * BR;
+        const int r0 = base + RPT * threadIdx.x;
         if (TAIL) {
-            s_tail[2 * threadIdx.x] = T(0);
-            s_tail[2 * threadIdx.x + 1] = T(0);
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+                s_tail[RPT * threadIdx.x + j] = T(0);
             __syncthreads();
-            const int t0 = a.tile_tail[tile], t1 = a.tile_tail[tile + 1];
             const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            // short rows: groups of g lanes, 32 / g rows per warp at a time,
-            // reduced by xor shuffles inside each aligned group of g lanes
-            const int g = a.tile_group[tile];
-            const int rpw = 32 / g, gid = lane / g, lig = lane % g;
-            for (int tb = t0 + wid * rpw; tb < t1; tb += (kThreads / 32) * rpw) {
-                const int t = tb + gid;
-                T s = T(0);
-                bool mine = false;
-                if (t < t1) {
-                    const int e0 = a.tail_ptr[t], e1 = a.tail_ptr[t + 1];
-                    mine = e1 - e0 <= kSpmvLongRow;
-                    if (mine)
-                        for (int e = e0 + lig; e < e1; e += g)
-                            s += tail_val[e] * __ldg(&x[a.tail_col[e]]);
+            const int tile0 = blk * TPB, tile1 = min(tile0 + TPB, a.ntiles);
+            for (int tile = tile0; tile < tile1; ++tile) {
+                // short rows: groups of g lanes, 32 / g rows per warp at a
+                // time, reduced by xor shuffles inside each aligned group
+                const int t0 = a.tile_tail[tile], t1 = a.tile_tail[tile + 1];
+                const int g = a.tile_group[tile];
+                const int rpw = 32 / g, gid = lane / g, lig = lane % g;
+                for (int tb = t0 + wid * rpw; tb < t1; tb += (kThreads / 32) * rpw) {
+                    const int t = tb + gid;
+                    T s = T(0);
+                    bool mine = false;
+                    if (t < t1) {
+                        const int e0 = a.tail_ptr[t], e1 = a.tail_ptr[t + 1];
+                        mine = e1 - e0 <= kSpmvLongRow;
+                        if (mine)
+                            for (int e = e0 + lig; e < e1; e += g)
+                                s += tail_val[e] * __ldg(&x[a.tail_col[e]]);
+                    }
+                    for (int o = g >> 1; o > 0; o >>= 1)
+                        s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (mine && lig == 0)
+                        s_tail[a.tail_rows[t] - base] = s;
                 }
-                for (int o = g >> 1; o > 0; o >>= 1)
-                    s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (mine && lig == 0)
-                    s_tail[a.tail_rows[t] - base] = s;
             }
             // long rows: the whole CTA, one row at a time, fixed-order sum
-            for (int q = a.tile_long[tile]; q < a.tile_long[tile + 1]; ++q) {
+            for (int q = a.tile_long[tile0]; q < a.tile_long[tile1]; ++q) {
                 const int t = a.tail_long[q];
                 T s = T(0);
                 for (int e = a.tail_ptr[t] + threadIdx.x; e < a.tail_ptr[t + 1]; e += kThreads)
@@ -102,57 +139,55 @@ __global__ void __launch_bounds__(kThreads) k_spmv_hec(SpmvArgs a)
             __syncthreads();
         }
         if (r0 < a.n) {
-            T s0 = T(0), s1 = T(0);
-            const int p0 = r0 >> 1;
+            T s[RPT];
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+                s[j] = T(0);
+            const int p0 = r0 / RPT;
 #pragma unroll 4
             for (int k = 0; k < a.K; ++k) {
-                const T2 v = __ldg(&val2[(size_t)k * ld2 + p0]);
-                const int2 c = __ldg(&col2[(size_t)k * ld2 + p0]);
-                s0 = fma(v.x, __ldg(&x[c.x]), s0);
-                s1 = fma(v.y, __ldg(&x[c.y]), s1);
+                const typename RV::V v = __ldg(&valv[(size_t)k * ldv + p0]);
+                const typename RV::C c = __ldg(&colv[(size_t)k * ldv + p0]);
+#pragma unroll
+                for (int j = 0; j < RPT; ++j)
+                    s[j] = fma(RV::get(v, j), __ldg(&x[RV::col(c, j)]), s[j]);
             }
-            if (TAIL) {
-                s0 += s_tail[2 * threadIdx.x];
-                s1 += s_tail[2 * threadIdx.x + 1];
+            const int nr = min(RPT, a.n - r0); // rows of this thread inside the matrix
+            T y[RPT];
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                if (TAIL)
+                    s[j] += s_tail[RPT * threadIdx.x + j];
+                if (MODE == 0)
+                    y[j] = s[j];
+                else if (MODE == 1)
+                    y[j] = alpha * s[j];
+                else
+                    y[j] = j < nr ? fma(alpha, s[j], beta * y_in[r0 + j]) : T(0);
             }
-            const bool two = (r0 + 1 < a.n);
-            T y0, y1;
-            if (MODE == 0) {
-                y0 = s0;
-                y1 = s1;
-            } else if (MODE == 1) {
-                y0 = alpha * s0;
-                y1 = alpha * s1;
+            if (nr == RPT) {
+                RV::put(&y_out[r0], y);
             } else {
-                y0 = fma(alpha, s0, beta * y_in[r0]);
-                y1 = two ? fma(alpha, s1, beta * y_in[r0 + 1]) : T(0);
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    if (j < nr)
+                        y_out[r0 + j] = y[j];
+                    else
+                        y[j] = T(0);
+                }
             }
-            if (two) {
-                T2 out;
-                out.x = y0;
-                out.y = y1;
-                *reinterpret_cast<T2 *>(&y_out[r0]) = out;
-            } else {
-                y_out[r0] = y0;
-                y1 = T(0);
-            }
-            if (NDOT >= 1) {
-                const T *w = reinterpret_cast<const T *>(a.w0);
-                T q0 = w ? w[r0] : y0;
-                T q1 = two ? (w ? w[r0 + 1] : y1) : T(0);
-                acc[0] = fma(q0, y0, acc[0]);
-                acc[0] = fma(q1, y1, acc[0]);
-            }
-            if (NDOT >= 2) {
-                const T *w = reinterpret_cast<const T *>(a.w1);
-                T q0 = w ? w[r0] : y0;
-                T q1 = two ? (w ? w[r0 + 1] : y1) : T(0);
-                acc[1] = fma(q0, y0, acc[1]);
-                acc[1] = fma(q1, y1, acc[1]);
+#pragma unroll
+            for (int d = 0; d < NDOT; ++d) {
+                const T *w = reinterpret_cast<const T *>(d == 0 ? a.w0 : a.w1);
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const T q = j < nr ? (w ? w[r0 + j] : y[j]) : T(0);
+                    acc[d] = fma(q, y[j], acc[d]);
+                }
             }
         }
         if (TAIL)
-            __syncthreads(); // s_tail is rewritten by the next tile
+            __syncthreads(); // s_tail is rewritten by the next row block
     }
     if constexpr (NDOT > 0) {
         double v[NDOT];

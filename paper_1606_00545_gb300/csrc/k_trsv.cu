@@ -59,6 +59,11 @@ size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
            (size_t)(2 * nstages + 1) * sizeof(uint64_t) + 2 * sizeof(uint32_t);
 }
 
+// Gatherer warps of a CTA: each takes every other chunk and keeps two
+// chunks' right-hand-side gathers in flight.  (Three and four gatherers
+// were measured on the 128^3 case: no faster.)
+constexpr int kGatherers = 2;
+
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes)
 {
     int dev = 0, optin = 0;
@@ -117,7 +122,7 @@ constexpr long long kDrainPolls = 1ll << 24;
 // imported ones from R on), else a position in the block's global scratch.
 constexpr int kWarpRows = 32;
 constexpr int kMaxWarps = kThreads / kWarpRows;
-constexpr int kFeedThreads = 128; // issuer, two gatherers and the signaller
+constexpr int kFeedThreads = 32 * (kGatherers + 2); // issuer, gatherers and the signaller
 constexpr int kMaxStages = 8;
 
 __device__ __forceinline__ int seg_stride(int w, int nrows)
@@ -349,6 +354,41 @@ __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rsl
     R.exp = exps ? reinterpret_cast<const int *>(blk + F::exp(upass))[lane] : -1;
 }
 
+// The issuer warp of both kernels: streams chunk c of the program into stage
+// c mod S once the consumers released chunk c - S.  Returns false when a
+// wait ran out.
+__device__ __forceinline__ bool issue_chunks(const uint2 *chunks, int nch, int S, int stage_bytes,
+                                             const unsigned char *pack, unsigned char *stages,
+                                             uint64_t *full, uint64_t *empty, long long limit,
+                                             int lane, int *s_issued)
+{
+    uint2 win = make_uint2(0, 0);
+    int wbase = -64;
+    int s = 0;
+    uint32_t par = 1; // parity of the release of the stage's previous chunk
+    for (int c = 0; c < nch; ++c) {
+        if (c >= wbase + 32) { // 32 descriptors per warp-wide load
+            wbase = c;
+            win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
+        }
+        const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
+        const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
+        // every wait decision is a warp vote: the lanes must stay converged
+        if (c >= S && __any_sync(0xffffffffu, !bounded_wait(&empty[s], par, limit)))
+            return false;
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_g2s(stages + (size_t)s * stage_bytes, pack + (size_t)off16 * 16, bytes, &full[s]);
+            *s_issued = c + 1;
+        }
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
+    }
+    return true;
+}
+
 // Release-add by one thread to a shared counter (the handover of a chunk).
 __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v)
 {
@@ -454,36 +494,10 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
 
     if (t >= kThreads && t < kThreads + 32 && !stall_test) {
         // ------------------------------------------------------------ issuer warp
-        // streams chunk c into stage c mod S once the consumers released it
-        const int lane = t - kThreads;
-        uint2 win = make_uint2(0, 0);
-        int wbase = -64;
-        int s = 0;
-        uint32_t par = 1; // parity of the release of the stage's previous chunk
-        for (int c = 0; c < nch; ++c) {
-            if (c >= wbase + 32) { // 32 descriptors per warp-wide load
-                wbase = c;
-                win = (c + lane < nch) ? chunks[c + lane] : make_uint2(0, 0);
-            }
-            const unsigned off16 = __shfl_sync(0xffffffffu, win.x, c - wbase);
-            const unsigned bytes = __shfl_sync(0xffffffffu, win.y, c - wbase);
-            // every wait decision is a warp vote: the lanes must stay converged
-            if (c >= S && __any_sync(0xffffffffu, !bounded_wait(&empty[s], par, limit))) {
-                failed = 1;
-                break;
-            }
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&full[s], bytes);
-                bulk_g2s(stages + (size_t)s * a.stage_bytes, a.pack + (size_t)off16 * 16, bytes,
-                         &full[s]);
-                s_issued = c + 1;
-            }
-            if (++s == S) {
-                s = 0;
-                par ^= 1u;
-            }
-        }
-    } else if (t >= kThreads + 32 && t < kThreads + 96 && !stall_test) {
+        if (!issue_chunks(chunks, nch, S, a.stage_bytes, a.pack, stages, full, empty, limit,
+                          t - kThreads, &s_issued))
+            failed = 1;
+    } else if (t >= kThreads + 32 && t < kThreads + 32 * (1 + kGatherers) && !stall_test) {
         // ------------------------------------------------------------ gatherer warps
         // follow the chunks as they land (even chunks: warp 9, odd: warp 10):
         // gather each one's right-hand sides as one cp.async group, and hand
@@ -522,7 +536,7 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             red_release_add(&s_hand[sgp], 1u); // this lane's gathers of chunk gp have landed
             return true;
         };
-        for (int g = gw; g < nch; g += 2) {
+        for (int g = gw; g < nch; g += kGatherers) {
             // a chunk in flight is handed over first when the next one has not landed
             if (gp >= 0 && !__all_sync(0xffffffffu, mbar_test_wait(&full[sg], par))) {
                 cp_async_wait_group<0>();
@@ -583,7 +597,7 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
             }
             gp = g;
             sgp = sg;
-            sg += 2;
+            sg += kGatherers;
             if (sg >= S) {
                 sg -= S;
                 par ^= 1u;
@@ -595,12 +609,12 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
                 failed = 1;
         }
         cp_async_wait_all();
-    } else if (t >= kThreads + 96) {
+    } else if (t >= kThreads + 32 * (1 + kGatherers)) {
         // ------------------------------------------------------------ signaller warp
         // publishes the completed-chunk count to the neighbours: the release
         // at cluster scope covers the consumers' stores into the neighbours'
         // import rings, ordered before the count by the consumer barrier
-        if (signal && t == kThreads + 96) {
+        if (signal && t == kThreads + 32 * (1 + kGatherers)) {
             const uint32_t to_prev = has_prev ? mapa_shared(smem_u32(&ctr[1]), part - 1) : 0;
             const uint32_t to_next = has_next ? mapa_shared(smem_u32(&ctr[0]), part + 1) : 0;
             uint32_t pub = 0;
@@ -894,10 +908,251 @@ __global__ void __launch_bounds__(kThreads + kFeedThreads, 1) k_trsv_ras(TrsvArg
         cluster_sync_all();
 }
 
+// ------------------------------------------------------------------ resident-vector kernel
+// A RAS block whose right-hand side fits in shared memory next to the chunk
+// stages is solved in place, by one CTA, with nothing on a level's critical
+// path but shared memory: xs[i] starts as r[V_b[i]] (all local rows, gathered
+// once at launch), the L pass overwrites it with y_i, the U pass with z_i, and
+// the owned rows are written to z at the end.  A row's right-hand side is its
+// own slot and its dependencies are the slots of its columns (local row
+// indices), so there are no gatherer warps, no global scratch and no handover
+// counters: one issuer warp streams the chunks (rows of one level) into the
+// stages S chunks ahead with cp.async.bulk, and the solving warps run
+//   level c: read the dependencies and the right-hand side of chunk c's rows
+//            from xs, copy chunk c + 1's rows into registers, run the
+//            multiply-add chain, store the results into xs; the last thread
+//            confirms that chunk c + 2 has landed; barrier; chunk c + 1's stage
+//            is released.
+// The per-level critical path is a shared-memory load, the row's dependent
+// multiply-adds (for U, the multiply by 1/u_ii) and a barrier of the solving
+// warps.  This is the latency-first form for small systems (a single ILU block
+// of a few thousand rows has hundreds of levels of a few dozen rows each).
+//
+// Chunk format (trsv_layout.cpp, flag bits 3 and 5): [0, 16) nrows, nwarps,
+// first position, flags (bit 0: U pass); [16, 32) 0, 0, FW, 0; then per warp
+// w < nwarps a block: val (ceil(FW / VW) 16-byte vectors of 32 lanes), idx
+// (ceil((FW + 1) / 8) 16-byte vectors of 32 lanes x 8 uint16: the FW
+// dependency slots, then the row's own slot), for U dinv[32].  Padding
+// entries have value 0 and slot nv (a slot that holds 0); padding rows have
+// row slot nv and are not stored.
+template <class T, int FW> struct Res {
+    static constexpr int VW = 16 / (int)sizeof(T);
+    static constexpr int NV = (FW + VW - 1) / VW; // value vectors per lane
+    static constexpr int NI = (FW + 1 + 7) / 8;   // index vectors per lane
+    __device__ static constexpr int idx() { return NV * 512; }
+    __device__ static constexpr int dinv() { return (NV + NI) * 512; }
+    __device__ static constexpr int block(bool u) { return dinv() + (u ? 32 * (int)sizeof(T) : 0); }
+};
+
+template <class T, int FW> struct ResRow {
+    int nrows, nwarps, flags;
+    typename Vec16<T>::type lv[Res<T, FW>::NV];
+    uint4 iv[Res<T, FW>::NI];
+    T dinv;
+    __device__ T l(int k) const { return Vec16<T>::get(lv[k / Res<T, FW>::VW], k % Res<T, FW>::VW); }
+    // uint16 k of the index vectors: dependency slot k < FW, the row's slot at FW
+    __device__ int slot(int k) const
+    {
+        const uint4 &v = iv[k / 8];
+        const int q = (k % 8) / 2;
+        const uint32_t word = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+        return (int)((word >> (16 * (k % 2))) & 0xffffu);
+    }
+};
+
+// A solving thread's row of a resident-format chunk.  Only warps that hold
+// rows of the chunk read past its header: a stage is sized for the largest
+// chunk of the layout, not for kThreads rows, so the block of a warp past the
+// chunk's last one may lie outside the stage (and outside shared memory).
+template <class T, int FW, bool U>
+__device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lane, ResRow<T, FW> &R)
+{
+    using F = Res<T, FW>;
+    const int4 hdr = *reinterpret_cast<const int4 *>(ch);
+    R.nrows = hdr.x;
+    R.nwarps = hdr.y;
+    R.flags = hdr.w;
+    if (w >= R.nwarps)
+        return;
+    const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(U);
+    const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
+#pragma unroll
+    for (int v = 0; v < F::NV; ++v)
+        R.lv[v] = val[v * 32];
+    const uint4 *idx = reinterpret_cast<const uint4 *>(blk + F::idx()) + lane;
+#pragma unroll
+    for (int v = 0; v < F::NI; ++v)
+        R.iv[v] = idx[v * 32];
+    if (U)
+        R.dinv = reinterpret_cast<const T *>(blk + F::dinv())[lane];
+}
+
+template <class T, int FW>
+__global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    count_launch(a.st);
+    if (a.st && a.st->skip)
+        return; // uniform over the grid
+    const T *r = reinterpret_cast<const T *>(a.r);
+    if (a.r_from_j)
+        r += (int64_t)a.st->j * a.ldv;
+    T *z = reinterpret_cast<T *>(a.z);
+    const TrsvBlock blk = a.blocks[blockIdx.x];
+    const int S = a.nstages;
+    unsigned char *stages = smem;
+    T *xs = reinterpret_cast<T *>(smem + (size_t)S * a.stage_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(xs) +
+                                                  (((size_t)a.res_slots * sizeof(T) + 7) & ~(size_t)7));
+    uint64_t *empty = full + S;
+    const int nch = blk.chunk_end - blk.chunk_begin;
+    const int nL = blk.chunk_mid - blk.chunk_begin;
+    const int *vrows = a.vrows + blk.yoff; // V_b: the global row of every local slot
+    const bool stall_test = a.spin_limit < 0; // fault injection: nothing is issued
+    const long long limit = stall_test ? -a.spin_limit : a.spin_limit;
+    const int t = threadIdx.x;
+    __shared__ int s_issued;
+    if (t == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        s_issued = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int failed = 0;
+    if (t >= kThreads) {
+        // ------------------------------------------------------------ issuer warp
+        if (!stall_test &&
+            !issue_chunks(a.groups + blk.zoff, blk.ngroups, S, a.stage_bytes, a.pack, stages,
+                          full, empty, limit, t - kThreads, &s_issued))
+            failed = 1;
+    } else {
+        // ------------------------------------------------------------ solving warps
+        // r on V_b into the resident vector; slot nv holds 0 (padding)
+        for (int i = t; i < blk.nv; i += kThreads) {
+            const int g = vrows[i];
+            xs[i] = HEC_CHECK(g >= 0 && g < a.n, 3, 0, g, a.n) ? r[g] : T(0);
+        }
+        if (t == 0)
+            xs[blk.nv] = T(0);
+        const int w = t / kWarpRows, lane = t % kWarpRows;
+        // Chunks arrive in groups (one bulk copy each): group g in stage
+        // g mod S, phase g / S; a chunk is found at a byte offset in its
+        // group's stage, the next one right after it unless flag bit 6 ends
+        // the group.
+        struct Loc {
+            int g, off;
+        };
+        auto landed = [&](int g) -> bool {
+            return bounded_wait(&full[g % S], (uint32_t)(g / S) & 1u, limit);
+        };
+        auto load = [&](int c, Loc l, ResRow<T, FW> &R) {
+            const unsigned char *ch = stages + (size_t)(l.g % S) * a.stage_bytes + l.off;
+            if (c < nL)
+                load_res<T, FW, false>(ch, w, lane, R);
+            else
+                load_res<T, FW, true>(ch, w, lane, R);
+        };
+        auto after = [&](int c, Loc l, const ResRow<T, FW> &R) -> Loc {
+            if (R.flags & 64)
+                return Loc{l.g + 1, 0};
+            const int blkb = c < nL ? Res<T, FW>::block(false) : Res<T, FW>::block(true);
+            return Loc{l.g, l.off + kFixedHeader + R.nwarps * blkb};
+        };
+        int bad = 0;
+        if (t == kThreads - 1 && nch > 0)
+            bad = !landed(0);
+        // the gather above is complete and the first group has landed
+        if (!consumer_sync_and(!bad)) {
+            failed = 1;
+        } else if (nch > 0) {
+            ResRow<T, FW> A, B;
+            load(0, Loc{0, 0}, A);
+            Loc ln = after(0, Loc{0, 0}, A); // chunk 1
+            bad = (t == kThreads - 1 && nch > 1 && ln.g > 0) ? !landed(ln.g) : 0;
+            if (!consumer_sync_and(!bad))
+                failed = 1;
+            // level c: cur holds chunk c's rows, nxt receives chunk c + 1's
+            // (found at ln)
+            auto level = [&](int c, ResRow<T, FW> &cur, ResRow<T, FW> &nxt) -> bool {
+                const bool U = c >= nL;
+                const bool rows = w < cur.nwarps; // warps past the chunk's last one idle
+                T y[FW];
+                T acc = T(0);
+                int me = blk.nv;
+                if (rows) {
+#pragma unroll
+                    for (int k = 0; k < FW; ++k) {
+                        const int d = cur.slot(k);
+                        y[k] = HEC_CHECK(d <= blk.nv, 5, c, d, blk.nv) ? xs[d] : T(0);
+                    }
+                    me = cur.slot(FW);
+                    if (!HEC_CHECK(me <= blk.nv, 7, c, me, blk.nv))
+                        me = blk.nv;
+                    acc = xs[me];
+                }
+                Loc l2 = ln;
+                if (c + 1 < nch) { // its group landed: confirmed before the previous barrier
+                    load(c + 1, ln, nxt);
+                    l2 = after(c + 1, ln, nxt);
+                }
+                if (rows) {
+#pragma unroll
+                    for (int k = 0; k < FW; ++k)
+                        acc = fma(-cur.l(k), y[k], acc);
+                    if (U)
+                        acc *= cur.dinv;
+                    if (t < cur.nrows && me < blk.nv)
+                        xs[me] = acc;
+                }
+                int late = 0;
+                if (t == kThreads - 1 && c + 2 < nch && l2.g != ln.g)
+                    late = !landed(l2.g);
+                if (!consumer_sync_and(!late))
+                    return false;
+                // every thread holds chunks up to c + 1 in registers: a group
+                // whose last chunk that is has a free stage
+                if (t == kThreads - 1) {
+                    if (c == 0 && (cur.flags & 64))
+                        mbar_arrive(&empty[0]);
+                    if (c + 1 < nch && (nxt.flags & 64))
+                        mbar_arrive(&empty[ln.g % S]);
+                }
+                ln = l2;
+                return true;
+            };
+            for (int c = 0; c < nch && !failed; c += 2) {
+                if (!level(c, A, B))
+                    failed = 1;
+                else if (c + 1 < nch && !level(c + 1, B, A))
+                    failed = 1;
+            }
+            if (!failed)
+                for (int i = blk.own0 + t; i < blk.own1; i += kThreads)
+                    z[vrows[i]] = xs[i];
+        }
+    }
+    // every role has left its loop: drain the copies still in flight, report
+    __syncthreads();
+    if (t == kThreads) {
+        const int issued = s_issued;
+        const int first = issued - S > 0 ? issued - S : 0;
+        for (int c = first; c < issued; ++c)
+            bounded_wait(&full[c % S], (uint32_t)(c / S) & 1u, kDrainPolls);
+    }
+    if (failed) {
+        atomicExch(a.err, HEC_ERR_TIMEOUT);
+        if (a.st)
+            a.st->err = HEC_ERR_TIMEOUT;
+    }
+}
+
 // The dynamic shared memory limit is a process-wide attribute of the kernel:
 // raised once to the device's opt-in maximum, so that launches of different
 // sizes from several host threads never race on it.
-template <class T, int FW> static cudaError_t prepare_trsv()
+template <class T, int FW, bool RES> static cudaError_t prepare_trsv()
 {
     static std::once_flag once;
     static cudaError_t e = cudaSuccess;
@@ -906,11 +1161,22 @@ template <class T, int FW> static cudaError_t prepare_trsv()
         cudaGetDevice(&dev);
         cudaFuncAttributes fa{};
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess)
-            e = cudaFuncGetAttributes(&fa, k_trsv_ras<T, FW>);
-        if (e == cudaSuccess)  // the opt-in limit covers static and dynamic shared memory
-            e = cudaFuncSetAttribute(k_trsv_ras<T, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     optin - (int)fa.sharedSizeBytes);
+        if (e == cudaSuccess) {
+            if constexpr (RES)
+                e = cudaFuncGetAttributes(&fa, k_trsv_res<T, FW>);
+            else
+                e = cudaFuncGetAttributes(&fa, k_trsv_ras<T, FW>);
+        }
+        if (e == cudaSuccess) { // the opt-in limit covers static and dynamic shared memory
+            if constexpr (RES)
+                e = cudaFuncSetAttribute(k_trsv_res<T, FW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes);
+            else
+                e = cudaFuncSetAttribute(k_trsv_ras<T, FW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes);
+        }
     });
     return e;
 }
@@ -919,7 +1185,7 @@ template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s
 {
     const size_t smem =
         trsv_smem_bytes(a.stage_bytes, a.nstages, a.ring_mask + 1 + a.import_slots, sizeof(T));
-    if (prepare_trsv<T, FW>() != cudaSuccess)
+    if (prepare_trsv<T, FW, false>() != cudaSuccess)
         return -1;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)a.nblocks);
@@ -934,6 +1200,34 @@ template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = a.parts > 1 ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k_trsv_ras<T, FW>, a) == cudaSuccess ? 0 : -1;
+}
+
+template <class T, int FW> static int launch_res(const TrsvArgs &a, cudaStream_t s)
+{
+    const size_t smem = trsv_res_smem_bytes(a.stage_bytes, a.nstages, a.res_slots, sizeof(T));
+    if (prepare_trsv<T, FW, true>() != cudaSuccess)
+        return -1;
+    k_trsv_res<T, FW><<<a.nblocks, kThreads + 32, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+size_t trsv_res_smem_bytes(int stage_bytes, int nstages, int res_slots, int vbytes)
+{
+    return (size_t)stage_bytes * nstages + (((size_t)res_slots * vbytes + 7) & ~(size_t)7) +
+           (size_t)2 * nstages * sizeof(uint64_t);
+}
+
+int trsv_res_stages_for(int stage_bytes, int res_slots, int vbytes)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    optin -= 1024; // static shared memory of the kernel
+    for (int S = 8; S >= 3; --S)
+        if (trsv_res_smem_bytes(stage_bytes, S, res_slots, vbytes) <= (size_t)optin)
+            return S;
+    return 0;
 }
 
 int trsv_debug_read(int *out, bool clear)
@@ -959,6 +1253,19 @@ bool trsv_debug_build()
 
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32)
 {
+    if (a.resident) {
+#define HEC_RES_CASE(W)                                                                          \
+    case W: return fp32 ? launch_res<float, W>(a, s) : launch_res<double, W>(a, s);
+        switch (a.fixed_width) {
+            HEC_RES_CASE(2)
+            HEC_RES_CASE(3)
+            HEC_RES_CASE(4)
+            HEC_RES_CASE(6)
+            HEC_RES_CASE(8)
+        default: return -1;
+        }
+#undef HEC_RES_CASE
+    }
     // fixed-slot layouts by their uniform width; generic layouts
     if (!fp32) {
         switch (a.fixed_width) {

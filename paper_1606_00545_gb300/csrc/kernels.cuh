@@ -163,7 +163,12 @@ struct TrsvBlock {
     int chunk_mid;              // first U chunk
     int links;                  // bit 0: part p - 1 of the same RAS block exists, bit 1: part p + 1
     int ring_L, ring_U;         // 1: dependencies read from the shared-memory ring
-    int64_t yoff, zoff;         // offsets of this program in the y / z scratch
+    int64_t yoff, zoff;         // offsets of this program in the y / z scratch (resident
+                                // kernel: yoff = offset of the block's V_b in vrows, zoff =
+                                // its first chunk group)
+    int nv;                     // resident kernel: the block's local rows
+    int own0, own1;             // resident kernel: its owned local rows [own0, own1)
+    int ngroups;                // resident kernel: its chunk groups
 };
 struct TrsvArgs {
     int nblocks;                // programs: RAS blocks x parts
@@ -185,6 +190,10 @@ struct TrsvArgs {
     int n;                      // rows of z (bounds checks of the debug build)
     int r_from_j;
     int64_t ldv;
+    int resident;               // 1: the resident-vector kernel (fixed_width: its row width)
+    int res_slots;              // resident kernel: shared-memory vector slots (largest nv + 1)
+    const int *vrows;           // resident kernel: V_b of every block, concatenated
+    const uint2 *groups;        // resident kernel: chunk groups {offset / 16, bytes}
 };
 // Shared memory of one CTA: stages, right-hand-side slots, own and import
 // ring, barriers and the two progress counters (vbytes: 8 for FP64, 4 for FP32).
@@ -192,6 +201,10 @@ size_t trsv_smem_bytes(int stage_bytes, int nstages, int ring_slots, int vbytes)
 // Largest stage count (3..8) that fits the device's shared memory per CTA
 // (ring_slots: own + import slots).
 int trsv_stages_for(int stage_bytes, int ring_slots, int vbytes);
+// The same for the resident-vector kernel: stages and a vector of res_slots values.
+size_t trsv_res_smem_bytes(int stage_bytes, int nstages, int res_slots, int vbytes);
+// Largest stage count (3..8) that fits, 0 if even 3 stages do not.
+int trsv_res_stages_for(int stage_bytes, int res_slots, int vbytes);
 int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32 = false);
 // The first violation a debug build (HEC_DEBUG) recorded: code, program,
 // chunk, thread, value, bound, 0, 0 (all 0: none); clear resets it.

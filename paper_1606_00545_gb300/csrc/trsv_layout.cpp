@@ -694,7 +694,220 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
     }
 }
 
+// ------------------------------------------------------------------ resident format
+// (k_trsv_res: the block's whole right-hand side stays in shared memory and is
+// overwritten in place, so dependencies are local row slots; see k_trsv.cu)
+//   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 3:
+//             fixed slots, bit 5: resident format)
+//   [16, 32)  0, 0, FW, 0
+//   per warp w < nwarps, a block of res_block() bytes, lane l = row 32w + l:
+//     val: ceil(FW / VW) vectors of 32 lanes x 16 bytes; idx: ceil((FW + 1) /
+//     8) vectors of 32 lanes x 8 uint16 (FW dependency slots, then the row's
+//     own slot); U: dinv[32] (value)
+// Padding entries have value 0 and slot nv (which holds 0); padding rows have
+// own slot nv.  Consecutive chunks of a block's program form groups of at
+// most kResGroupBytes (or one larger chunk), each streamed by one bulk copy
+// into one stage; flag bit 6 marks the last chunk of a group.
+inline int res_ni(int FW) { return (FW + 1 + 7) / 8; }
+constexpr size_t kResGroupBytes = 16384;
+
+size_t res_block(int FW, bool upass, int vb)
+{
+    return (size_t)(fixed_nv(FW, vb) + res_ni(FW)) * 512 + (upass ? (size_t)32 * vb : 0);
+}
+
+size_t chunk_bytes_res(int FW, int nrows, bool upass, int vb)
+{
+    return kFixedHeader + (size_t)((nrows + kWarpRows - 1) / kWarpRows) * res_block(FW, upass, vb);
+}
+
+struct ResOut {
+    std::vector<unsigned char> bytes;
+    std::vector<uint2> chunks; // offsets relative to this block
+    std::vector<uint2> groups; // the same for the groups of consecutive chunks
+    int nchunksL = 0, nL = 0, nU = 0, own0 = 0, own1 = 0;
+    std::vector<int> rows_per_chunk, rm_start, rm_len, rm_diag;
+    size_t largest = 0; // bytes of the largest group
+    int64_t alg = 0;
+};
+
+void emit_resident(const BlockFactor &B, int FW, int vb, ResOut &O)
+{
+    const HostCSR &F = B.F;
+    const int nv = F.n;
+    BlockPlan bp;
+    needed_rows(B, bp);
+    bp.part.assign(nv, 0);
+    bp.posL.assign(nv, -1);
+    bp.posU.assign(nv, -1);
+    PassOrder po[2];
+    order_pass(B, bp, 0, false, po[0], bp.posL);
+    order_pass(B, bp, 0, true, po[1], bp.posU);
+    O.nL = (int)po[0].order.size();
+    O.nU = (int)po[1].order.size();
+    O.own0 = (int)(std::lower_bound(B.rows.begin(), B.rows.end(), B.own_lo) - B.rows.begin());
+    O.own1 = (int)(std::lower_bound(B.rows.begin(), B.rows.end(), B.own_hi) - B.rows.begin());
+    const int VW = fixed_vw(vb), NV = fixed_nv(FW, vb), NI = res_ni(FW);
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool upass = pass == 1;
+        const PassOrder &P = po[pass];
+        const size_t blk = res_block(FW, upass, vb);
+        int start = 0;
+        for (int end : P.level_end) {
+            for (int q = start; q < end; q += kThreads) {
+                const int nr = std::min(kThreads, end - q), nw = (nr + kWarpRows - 1) / kWarpRows;
+                const size_t bytes = chunk_bytes_res(FW, nr, upass, vb);
+                const size_t off = O.bytes.size();
+                O.bytes.resize(off + bytes, 0);
+                O.largest = std::max(O.largest, bytes);
+                unsigned char *cb = O.bytes.data() + off;
+                const int hdr[kFixedHeader / 4] = {nr, nw, q, (upass ? 1 : 0) | 8 | 32, 0, 0, FW, 0};
+                std::memcpy(cb, hdr, kFixedHeader);
+                for (int w = 0; w < nw; ++w) {
+                    unsigned char *base = cb + kFixedHeader + w * blk;
+                    uint16_t *idx = reinterpret_cast<uint16_t *>(base + (size_t)NV * 512);
+                    unsigned char *dinv = base + (size_t)(NV + NI) * 512;
+                    auto at_val = [&](int k, int lane) {
+                        return (size_t)(k / VW) * 32 * VW + (size_t)lane * VW + k % VW;
+                    };
+                    auto at_idx = [&](int k, int lane) {
+                        return (size_t)(k / 8) * 256 + (size_t)lane * 8 + k % 8;
+                    };
+                    for (int lane = 0; lane < kWarpRows; ++lane) {
+                        const int t = w * kWarpRows + lane;
+                        const int i = t < nr ? P.order[q + t] : -1;
+                        const int e0 = i >= 0 ? row_first(B, upass, i) : 0;
+                        const int len = i >= 0 ? row_len(B, upass, i) : 0;
+                        for (int k = 0; k < NV * VW; ++k)
+                            put_value(base, at_val(k, lane), k < len ? F.va[e0 + k] : 0.0, vb);
+                        for (int k = 0; k < NI * 8; ++k)
+                            idx[at_idx(k, lane)] = (uint16_t)(k < len ? F.ci[e0 + k] : nv);
+                        idx[at_idx(FW, lane)] = (uint16_t)(i >= 0 ? i : nv);
+                        if (upass)
+                            put_value(dinv, lane, i >= 0 ? 1.0 / F.va[B.diag[i]] : 0.0, vb);
+                        if (i < 0)
+                            continue;
+                        O.rm_start.push_back(e0);
+                        O.rm_len.push_back(len);
+                        O.rm_diag.push_back(upass ? B.diag[i] : -1);
+                        if (upass)
+                            O.alg += (4ll + vb) * len + vb /*y*/ + vb /*dinv*/ + 4 /*src*/ +
+                                     4 /*dst*/ + (bp.owned[i] ? vb : 0);
+                        else
+                            O.alg += (4ll + vb) * len + vb /*r*/ + vb /*y*/ + 4 /*src*/;
+                    }
+                }
+                O.rows_per_chunk.push_back(nr);
+                O.chunks.push_back(make_uint2((unsigned)(off / 16), (unsigned)bytes));
+            }
+            start = end;
+        }
+        if (!upass)
+            O.nchunksL = (int)O.chunks.size();
+    }
+    // groups of consecutive chunks, one bulk copy each
+    size_t g0 = 0, gbytes = 0;
+    for (size_t c = 0; c < O.chunks.size(); ++c) {
+        const size_t b = O.chunks[c].y;
+        if (gbytes > 0 && gbytes + b > kResGroupBytes) {
+            O.groups.push_back(make_uint2((unsigned)(g0 / 16), (unsigned)gbytes));
+            reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks[c - 1].x * 16)[3] |= 64;
+            g0 += gbytes;
+            gbytes = 0;
+        }
+        gbytes += b;
+    }
+    if (gbytes > 0) {
+        O.groups.push_back(make_uint2((unsigned)(g0 / 16), (unsigned)gbytes));
+        reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks.back().x * 16)[3] |= 64;
+    }
+    O.largest = 0;
+    for (const uint2 &g : O.groups)
+        O.largest = std::max(O.largest, (size_t)g.y);
+}
+
 } // namespace
+
+int trsv_resident_width(int longest_row)
+{
+    for (int w : {2, 3, 4, 6, 8})
+        if (longest_row <= w)
+            return w;
+    return 0;
+}
+
+int pack_trsv_resident(const std::vector<BlockFactor> &Bs, int width, int vb, TrsvPack &P,
+                       std::string &msg)
+{
+    if ((vb != 8 && vb != 4) || trsv_resident_width(width) != width) {
+        msg = "resident layout: value size 8 or 4 and width 2, 3, 4, 6 or 8";
+        return HEC_ERR_INVALID;
+    }
+    const int nb = (int)Bs.size();
+    for (const BlockFactor &B : Bs)
+        if (B.F.n >= 65535) {
+            msg = "resident layout: a block has 65535 rows or more";
+            return HEC_ERR_INVALID;
+        }
+    std::vector<ResOut> outs(nb);
+    parallel_for(nb, [&](int b) { emit_resident(Bs[b], width, vb, outs[b]); });
+    P = TrsvPack();
+    P.resident = 1;
+    P.parts = 1;
+    P.ring_slots = 32;
+    size_t total = 0, largest = 16;
+    for (const ResOut &O : outs) {
+        total += O.bytes.size();
+        largest = std::max(largest, O.largest);
+    }
+    if (total / 16 > 0xffffffffull) {
+        msg = "factor layout exceeds 64 GiB";
+        return HEC_ERR_INVALID;
+    }
+    P.stage_bytes = (int)((largest + 127) & ~(size_t)127);
+    P.pack.resize(total);
+    P.blocks.assign(nb, TrsvBlock());
+    int64_t ent0 = 0, r0 = 0;
+    size_t off = 0;
+    for (int b = 0; b < nb; ++b) {
+        const ResOut &O = outs[b];
+        TrsvBlock &T = P.blocks[b];
+        T.chunk_begin = (int)P.chunks.size();
+        for (const uint2 &c : O.chunks)
+            P.chunks.push_back(make_uint2((unsigned)(c.x + off / 16), c.y));
+        T.chunk_end = (int)P.chunks.size();
+        T.chunk_mid = T.chunk_begin + O.nchunksL;
+        T.links = 0;
+        T.ring_L = T.ring_U = 1;
+        T.yoff = (int64_t)P.vrows.size();
+        T.zoff = (int64_t)P.groups.size();
+        T.ngroups = (int)O.groups.size();
+        for (const uint2 &g : O.groups)
+            P.groups.push_back(make_uint2((unsigned)(g.x + off / 16), g.y));
+        T.nv = Bs[b].F.n;
+        T.own0 = O.own0;
+        T.own1 = O.own1;
+        P.vrows.insert(P.vrows.end(), Bs[b].rows.begin(), Bs[b].rows.end());
+        P.res_slots = std::max(P.res_slots, T.nv + 1);
+        P.rows_L += O.nL;
+        P.rows_U += O.nU;
+        for (int nr : O.rows_per_chunk) {
+            P.chunk_row0.push_back(r0);
+            r0 += nr;
+        }
+        for (size_t k = 0; k < O.rm_start.size(); ++k) {
+            P.rm_start.push_back((int)(ent0 + O.rm_start[k]));
+            P.rm_len.push_back(O.rm_len[k]);
+            P.rm_diag.push_back(O.rm_diag[k] < 0 ? -1 : (int)(ent0 + O.rm_diag[k]));
+        }
+        ent0 += (int64_t)Bs[b].F.ci.size();
+        std::memcpy(P.pack.data() + off, O.bytes.data(), O.bytes.size());
+        off += O.bytes.size();
+        P.alg_bytes += O.alg;
+    }
+    P.chunk_row0.push_back(r0);
+    return HEC_OK;
+}
 
 int max_factor_width(const std::vector<BlockFactor> &Bs, bool upass)
 {

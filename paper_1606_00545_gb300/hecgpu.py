@@ -39,6 +39,9 @@ SOLVE_EAGER = 2
 MIXED_FP32 = 4
 FACTOR_L = 0
 FACTOR_U = 1
+TRSV_AUTO = 0
+TRSV_STREAMED = 1
+TRSV_RESIDENT = 2
 
 
 class HecError(RuntimeError):
@@ -77,7 +80,7 @@ class PrecondInfo_t(C.Structure):
                 ("ring_slots", C.c_int32), ("global_passes", C.c_int32),
                 ("apply_bytes_f32", C.c_int64), ("trsv_parts", C.c_int32),
                 ("import_slots", C.c_int32), ("split_blocks", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("trsv_resident", C.c_int32)]
 
 
 class SolveOpts_t(C.Structure):
@@ -110,7 +113,7 @@ class BatchInfo_t(C.Structure):
 
 class BatchSysInfo_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("status", C.c_int32),
-                ("reserved", C.c_int32), ("rel_resid", C.c_double)]
+                ("reorth", C.c_int32), ("rel_resid", C.c_double)]
 
 
 class ServerOpts_t(C.Structure):
@@ -166,6 +169,7 @@ _SIGS = {
                                 C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), _vp, _vp, _vp,
                                 _vp], C.c_int),
     "hec_precond_set_trsv_parts": ([_vp, _i32], C.c_int),
+    "hec_precond_set_trsv_kernel": ([_vp, _i32], C.c_int),
     "hec_debug_record": ([_vp, _i32], C.c_int),
     "hec_precond_apply": ([_vp, _vp, _vp, _i64, _vp], C.c_int),
     "hec_precond_status": ([_vp, _vp], C.c_int),
@@ -489,9 +493,13 @@ def ilu_k_setup(A: Matrix, k: int, nblocks: int, overlap: int, stream=None) -> P
     return Precond(h, A)
 
 
-def level_schedule(M: Precond, stream=None, parts: int = 0):
+def level_schedule(M: Precond, stream=None, parts: int = 0, kernel: int = 0):
     """Eq. 11 level sets and the triangular-solve layout.  parts: CTAs per
-    RAS block of the triangular solve (0: automatic; 1, 2, 4 or 8)."""
+    RAS block of the triangular solve (0: automatic; 1, 2, 4 or 8).  kernel:
+    TRSV_AUTO, TRSV_STREAMED or TRSV_RESIDENT."""
+    if kernel:
+        _check(load_library().hec_precond_set_trsv_kernel(M.handle, int(kernel)),
+               "hec_precond_set_trsv_kernel")
     if parts:
         _check(load_library().hec_precond_set_trsv_parts(M.handle, int(parts)),
                "hec_precond_set_trsv_parts")

@@ -1,9 +1,12 @@
 """The library compiled with HEC_DEBUG: the triangular-solve kernel checks every
 chunk header against the position its program has reached, every gathered
 index against n and every dependency slot against its ring, and records the
-first violation (hec_debug_record).  The small preconditioner parity cases,
-with 1, 2 and 8 CTAs per RAS block, in FP64 and FP32, must run with no
-violation and still match the oracle within the entry-wise rounding bound.
+first violation (hec_debug_record); the resident-vector kernel checks every
+dependency and row slot against the block's vector and every gathered index
+against n.  The small preconditioner parity cases, streamed with 1, 2 and 8
+CTAs per RAS block and resident where the blocks fit, in FP64 and FP32, must
+run with no violation and still match the oracle within the entry-wise
+rounding bound.
 
 A process loads one copy of the library, so the debug build runs in a child
 process."""
@@ -43,9 +46,12 @@ for name, (A, k, nb, ov) in cases.items():
     M = H.hec_build(A.row_ptr, A.col, A.val)
     R = orc.RAS(A, k, nb, ov)
     r = synth.rhs_uniform(A.n, 3)
-    for parts in (1, 2, 8):
+    modes = [(H.TRSV_STREAMED, 1), (H.TRSV_STREAMED, 2), (H.TRSV_STREAMED, 8)]
+    if name in ("poisson64_ilu0", "diffusion3d_16_ilu1_ras8", "many_blocks"):
+        modes.append((H.TRSV_RESIDENT, 0))
+    for kernel, parts in modes:
         P = H.ilu_k_setup(M, k, nb, ov)
-        H.level_schedule(P, parts=parts)
+        H.level_schedule(P, parts=parts, kernel=kernel)
         for fp32 in (False, True):
             dt = torch.float32 if fp32 else torch.float64
             ap = H.hec_precond_apply_f32 if fp32 else H.hec_precond_apply

@@ -162,33 +162,49 @@ PRECOND_CASES = {
 }
 
 
-@pytest.mark.parametrize("parts", [0, 2, 8])
+# cases whose blocks the resident-vector kernel takes (rows of at most 8
+# entries, the block's vector in shared memory)
+RESIDENT_FITS = {"c1_poisson64_ilu0", "diffusion3d_16_ilu1_ras8", "tridiag_exact", "many_blocks"}
+KERNEL_MODES = {"auto": (0, 0), "streamed1": (1, 1), "streamed2": (1, 2), "streamed8": (1, 8),
+                "resident": (2, 0)}
+
+
+@pytest.mark.parametrize("mode", sorted(KERNEL_MODES))
 @pytest.mark.parametrize("case", sorted(PRECOND_CASES))
-def test_precond_apply_parity(H, orc, case, parts):
-    """FP64 and FP32 applies against the oracle, entry by entry, with the
-    automatic number of CTAs per block and with blocks forced into chains of
-    2 and 8 thread-block-cluster CTAs (where the dependencies allow it)."""
+def test_precond_apply_parity(H, orc, case, mode):
+    """FP64 and FP32 applies against the oracle, entry by entry: the automatic
+    choice, the streamed kernel with one CTA per block and with blocks forced
+    into chains of 2 and 8 thread-block-cluster CTAs (where the dependencies
+    allow it), and the resident-vector kernel where the blocks fit."""
     import torch
+    kernel, parts = KERNEL_MODES[mode]
+    if kernel == H.TRSV_RESIDENT and case not in RESIDENT_FITS:
+        pytest.skip("rows too long or block too large for the resident kernel")
     A, k, nb, ov = PRECOND_CASES[case]()
     M = H.hec_build(A.row_ptr, A.col, A.val)
     P = H.ilu_k_setup(M, k, nb, ov)
-    H.level_schedule(P, parts=parts)
+    H.level_schedule(P, parts=parts, kernel=kernel)
+    inf = P.info()
+    assert inf["trsv_resident"] == (1 if kernel == H.TRSV_RESIDENT else
+                                    0 if kernel == H.TRSV_STREAMED else inf["trsv_resident"])
     R = orc.RAS(A, k, nb, ov)
     for seed in (1, 2):
         r = synth.rhs_uniform(A.n, seed)
         z = dev(np.full(A.n, np.nan))
         H.hec_precond_apply(P, dev(r), z)
         assert H.hec_precond_status(P) == H.OK
-        check_apply(orc, R, r, host(z), what="%s parts=%d" % (case, parts))
+        check_apply(orc, R, r, host(z), what="%s %s" % (case, mode))
         z32 = torch.full((A.n,), float("nan"), dtype=torch.float32, device="cuda:0")
         H.hec_precond_apply_f32(P, torch.tensor(r, dtype=torch.float32, device="cuda:0"), z32)
         assert H.hec_precond_status(P) == H.OK
-        check_apply(orc, R, r, host(z32), fp32=True, what="%s parts=%d fp32" % (case, parts))
+        check_apply(orc, R, r, host(z32), fp32=True, what="%s %s fp32" % (case, mode))
     inf = P.info()
-    if case == "wide_window_global":
+    if case == "wide_window_global" and kernel == H.TRSV_STREAMED:
         assert inf["global_passes"] > 0
     if case in ("c1_poisson64_ilu0", "diffusion3d_16_ilu1_ras8"):
         assert inf["global_passes"] == 0
+        if mode == "auto":
+            assert inf["trsv_resident"] == 0
     if parts > 1 and case in ("c1_poisson64_ilu0", "diffusion3d_16_ilu1_ras8"):
         assert inf["split_blocks"] == nb  # the chained path ran
 
@@ -205,13 +221,16 @@ def test_precond_exact_on_tridiagonal(H, orc):
     assert np.max(np.abs(host(z) - x)) <= 1e-13
 
 
-def test_precond_bounded_wait_reports_timeout(H, orc):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_precond_bounded_wait_reports_timeout(H, orc, kernel):
     """A wait on a barrier that nothing completes runs out, the kernel reports
-    HEC_ERR_TIMEOUT, and the context stays usable."""
+    HEC_ERR_TIMEOUT, and the context stays usable (streamed and resident
+    kernels)."""
     A = synth.poisson2d_5pt(32)
     M = H.hec_build(A.row_ptr, A.col, A.val)
     P = H.ilu_k_setup(M, 0, 2, 1)
-    H.level_schedule(P)
+    H.level_schedule(P, kernel=kernel)
+    assert P.info()["trsv_resident"] == (kernel == H.TRSV_RESIDENT)
     r = synth.rhs_uniform(A.n, 1)
     z = dev(np.zeros(A.n))
     H.hec_precond_apply(P, dev(r), z, spin_limit=-1000)  # stall: nothing issued

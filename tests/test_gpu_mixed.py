@@ -44,20 +44,29 @@ def host(t):
     return t.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("case", ["poisson2d", "irregular27", "random_tail"])
-def test_spmv_f32_within_fp32_bound(H, orc, case):
+@pytest.mark.parametrize("ab", [(1.0, 0.0), (-0.5, 0.0), (-1.0, 1.0)])
+@pytest.mark.parametrize("case", ["poisson2d", "irregular27", "random_tail", "ragged_tail"])
+def test_spmv_f32_within_fp32_bound(H, orc, case, ab):
+    """FP32 SpMV (four rows per thread) against the FP64 oracle, entry by
+    entry, within the first-order bound of a k-term FP32 dot product plus the
+    alpha/beta epilogue's roundings.  The ragged case has n = 5003 rows (not a
+    multiple of four, five row blocks) and a CSR tail."""
     import torch
+    alpha, beta = ab
     A, K = {"poisson2d": (synth.poisson2d_5pt(64), 0),
             "irregular27": (synth.stencil27_irregular(12, 4, 5), 0),
-            "random_tail": (synth.random_sparse(1200, 0.02, seed=2), 3)}[case]
+            "random_tail": (synth.random_sparse(1200, 0.02, seed=2), 3),
+            "ragged_tail": (synth.random_sparse(5003, 0.002, seed=3), 2)}[case]
     x = synth.rhs_uniform(A.n, 5)
+    yin = synth.rhs_uniform(A.n, 6).astype(np.float32).astype(np.float64)
     M = H.hec_build(A.row_ptr, A.col, A.val, ell_width=K)
-    y = torch.empty(A.n, dtype=torch.float32, device="cuda:0")
-    H.hec_spmv_f32(M, 1.0, dev(x, torch.float32), 0.0, None, y)
+    y = torch.tensor(yin, dtype=torch.float32, device="cuda:0")
+    H.hec_spmv_f32(M, alpha, dev(x, torch.float32), beta, y if beta else None, y)
     got = host(y)
-    ref = orc.spmv(A, x)
+    ref = alpha * orc.spmv(A, x) + beta * yin
     scale = orc.spmv(synth.CSR(A.row_ptr, A.col, np.abs(A.val)), np.abs(x))
-    bound = (A.row_lengths() + 2) * U32 * scale * 1.01 + 1e-300
+    bound = (A.row_lengths() + 4) * U32 * (abs(alpha) * scale + abs(beta) * np.abs(yin)) * 1.01 \
+        + 1e-300
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 

@@ -234,6 +234,103 @@ def parse_chunk(pack, chunks, c, vb):
     return out
 
 
+def parse_resident_chunk(pack, chunks, c, vb):
+    """One chunk of the resident kernel's format: per warp (rows, val, dep)
+    with dependency slots, and per row its own slot and (U) dinv."""
+    dt = np.float64 if vb == 8 else np.float32
+    base, h = _chunk(pack, chunks, c)
+    nr, nw, q, flags = (int(v) for v in h[:4])
+    upass = bool(flags & 1)
+    assert flags & 8 and flags & 32
+    assert 0 < nr <= 256 and nw == (nr + 31) // 32 and int(chunks[c, 1]) % 16 == 0
+    FW = int(h[6])
+    VW = 16 // vb
+    NV, NI = (FW + VW - 1) // VW, (FW + 1 + 7) // 8
+    blk = (NV + NI) * 512 + (32 * vb if upass else 0)
+    assert int(chunks[c, 1]) == 32 + nw * blk
+    out = dict(nr=nr, nw=nw, q=q, upass=upass, FW=FW, flags=flags, warps=[])
+    own, dinv = [], []
+    for w in range(nw):
+        o = base + 32 + w * blk
+        m = min(32, nr - 32 * w)
+        v = np.frombuffer(pack, dt, NV * 32 * VW, o).reshape(NV, 32, VW)
+        val = v.transpose(0, 2, 1).reshape(NV * VW, 32)[:FW]
+        ix = np.frombuffer(pack, np.uint16, NI * 256, o + NV * 512).reshape(NI, 32, 8)
+        ix = ix.transpose(0, 2, 1).reshape(NI * 8, 32).astype(np.int64)
+        dep = ix[:FW]
+        own.append(ix[FW])
+        if upass:
+            dinv.append(np.frombuffer(pack, dt, 32, o + (NV + NI) * 512))
+        out["warps"].append((w, val, dep, m))
+    out["own"] = np.concatenate(own)
+    out["dinv"] = np.concatenate(dinv) if upass else None
+    return out
+
+
+def run_resident(lay, P, n, r, nb):
+    """z = M^{-1} r by the resident kernel's programs, as it runs them: block
+    b's vector x starts as r on V_b with slot nv = 0; every chunk's rows
+    update their own slot in place from the slots of their dependencies
+    (which must hold values of this pass already), the U pass multiplies by
+    dinv; z on the owned rows is x at the end.  Padding entries must have
+    value 0 and slot nv, padding rows own slot nv.  Returns z and the writes
+    per row."""
+    pack, chunks, vb = lay["pack"], lay["chunks"], lay["vbytes"]
+    dt = np.float64 if vb == 8 else np.float32
+    z = np.full(n, np.nan, dt)
+    writes = np.zeros(n, np.int64)
+    rv = r.astype(dt)
+    progs = lay["programs"]
+    assert lay["parts"] == 1 and len(progs) == nb
+    voff = 0
+    for b in range(nb):
+        rows, lo, hi = P.block(b)
+        nv = len(rows)
+        c0, cm, c1, _, _, yoff, _, links = (int(v) for v in progs[b])
+        assert yoff == voff and links == 0
+        voff += nv
+        x = np.concatenate([rv[rows], [dt(0)]])
+        solved = [np.zeros(nv + 1, bool), np.zeros(nv + 1, bool)]
+        pos = [0, 0]
+        gbytes, gchunks = 0, 0  # the group of consecutive chunks being streamed
+        for c in range(c0, c1):
+            C = parse_resident_chunk(pack, chunks, c, vb)
+            gbytes += int(chunks[c, 1])
+            gchunks += 1
+            if C["flags"] & 64 or c == c1 - 1:  # one bulk copy of at most 16 KB
+                assert C["flags"] & 64 and (gbytes <= 16384 or gchunks == 1)
+                gbytes, gchunks = 0, 0
+            upass = C["upass"]
+            assert upass == (c >= cm) and C["q"] == pos[int(upass)]
+            pos[int(upass)] += C["nr"]
+            own = C["own"]
+            assert np.all(own[C["nr"]:] == nv) and np.all(own[:C["nr"]] < nv)
+            acc = x[own].copy()
+            done = solved[int(upass)]
+            for w, val, dep, m in C["warps"]:
+                assert np.all(val[:, m:] == 0) and np.all(dep[:, m:] == nv)
+                for k in range(val.shape[0]):
+                    d, live = dep[k], val[k] != 0
+                    assert np.all((d >= 0) & (d <= nv))
+                    # a dependency was solved by an earlier chunk of the pass
+                    assert np.all(done[d[:m][live[:m]]])
+                    acc[32 * w:32 * w + 32] -= val[k] * x[d]
+            if upass:
+                acc *= C["dinv"]
+            mine = own[:C["nr"]]
+            assert not np.any(done[mine])  # every row once per pass
+            if upass:  # a U row starts from its y: the L pass solved it
+                assert np.all(solved[0][mine])
+            x[mine] = acc[:C["nr"]]
+            done[mine] = True
+        o0 = int(np.searchsorted(rows, lo))
+        o1 = int(np.searchsorted(rows, hi))
+        assert solved[1][o0:o1].all() and solved[0][o0:o1].all()
+        z[rows[o0:o1]] = x[o0:o1]
+        writes[rows[o0:o1]] += 1
+    return z, writes
+
+
 def run_layout(lay, n, r, eager=True, who=None, sols=None):
     """z = M^{-1} r by the chunk programs of every RAS block, as the kernel
     runs them.  A block has P programs (its parts, one CTA each); each runs
@@ -406,11 +503,14 @@ LAYOUT_CASES = {
 @pytest.mark.parametrize("parts", [1, 2, 4, 8])
 @pytest.mark.parametrize("case", sorted(LAYOUT_CASES))
 def test_factor_layout_runs_to_the_oracle_apply(H, orc, case, parts):
+    """The streamed kernel's layout (ring of recent values, blocks split over
+    `parts` CTAs where the dependencies allow) run on the host."""
     make, k, nb, ov = LAYOUT_CASES[case]
     A = make()
     M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
     P = H.ilu_k_setup(M, k, nb, ov)
-    H.level_schedule(P, parts=parts)
+    H.level_schedule(P, parts=parts, kernel=H.TRSV_STREAMED)
+    assert P.info()["trsv_resident"] == 0
     R = orc.RAS(A, k, nb, ov)
     r = synth.rhs_uniform(A.n, 1)
     inf = P.info()
@@ -460,6 +560,62 @@ def test_factor_layout_runs_to_the_oracle_apply(H, orc, case, parts):
     if case in ("poisson2d_ilu0", "diffusion3d_ilu1_slab") and parts > 1:
         # dependencies reach only the next part: every block is split
         assert P.info()["split_blocks"] == nb
+
+
+RESIDENT_CASES = ["poisson2d_ilu0", "diffusion3d_ilu1_ras4", "diffusion3d_ilu1_slab",
+                  "random_ilu0_ras3_ov2", "poisson2d_64_ilu0"]
+
+
+@pytest.mark.parametrize("case", RESIDENT_CASES)
+def test_resident_layout_runs_to_the_oracle_apply(H, orc, case):
+    """The resident kernel's layout (one CTA per block, the block's vector in
+    shared memory, updated in place) run on the host, FP64 and FP32: every
+    owned row written once, the entry-wise rounding bound against the
+    oracle's RAS apply, the rows of every pass solved once in level order,
+    the algorithmic bytes counted as for the streamed layout."""
+    if case == "poisson2d_64_ilu0":  # the 64 x 64 single-block ILU(0) solve
+        A, k, nb, ov = synth.poisson2d_5pt(64), 0, 1, 0
+    elif case == "random_ilu0_ras3_ov2":  # irregular rows, 2 overlap layers
+        A, k, nb, ov = synth.random_sparse(600, 0.004, seed=5), 0, 3, 2
+    else:
+        make, k, nb, ov = LAYOUT_CASES[case]
+        A = make()
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P, kernel=H.TRSV_RESIDENT)
+    inf = P.info()
+    assert inf["trsv_resident"] == 1 and inf["trsv_parts"] == 1
+    R = orc.RAS(A, k, nb, ov)
+    r = synth.rhs_uniform(A.n, 1)
+    for fp32 in (False, True):
+        lay = H.Precond.layout(P, fp32=fp32)
+        assert lay["fixed_width"] in (2, 3, 4, 6, 8)
+        z, writes = run_resident(lay, P, A.n, r, nb)
+        assert np.all(writes == 1)
+        check_apply(orc, R, r, z, fp32=fp32, what="%s resident fp32=%d" % (case, fp32))
+    # the automatic choice streams; both count the same algorithmic bytes
+    P2 = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P2)
+    assert P2.info()["trsv_resident"] == 0
+    assert P2.info()["apply_bytes"] == inf["apply_bytes"]
+
+
+def test_resident_kernel_refused_where_it_does_not_fit(H):
+    """Rows longer than 8 entries (a random matrix with ILU(2) fill) cannot
+    take the resident kernel: asking for it fails at level_schedule, the
+    automatic choice streams."""
+    A = synth.random_sparse(600, 0.01, seed=2)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, 2, 3, 2)
+    with pytest.raises(H.HecError):
+        H.level_schedule(P, kernel=H.TRSV_RESIDENT)
+    P = H.ilu_k_setup(M, 2, 3, 2)
+    H.level_schedule(P)
+    assert P.info()["trsv_resident"] == 0
+    lib = H.load_library()
+    assert lib.hec_precond_set_trsv_kernel(P.handle, H.TRSV_RESIDENT) != H.OK  # too late
+    P = H.ilu_k_setup(M, 2, 3, 2)
+    assert lib.hec_precond_set_trsv_kernel(P.handle, 7) != H.OK
 
 
 def test_trsv_parts_choice(H):
@@ -518,13 +674,22 @@ def test_workspace_bytes_query(H):
     lay = P.layout(fp32=True)  # packs the FP32 layout (host-only: nothing uploaded)
     heads = [np.frombuffer(lay["pack"], np.int32, 4, int(c) * 16) for c in lay["chunks"][:, 0]]
     ysz = zsz = 0
+    resident = P.info()["trsv_resident"] == 1  # (the FP32 layout follows the FP64 choice)
     for c0, cm, c1, _, ring_u, _, _, _ in lay["programs"]:
+        if resident:  # no scratch; the kernel's row list holds every block's V_b
+            continue
         if cm > c0:
             ysz += int(heads[cm - 1][2] + heads[cm - 1][0])
         if not ring_u and c1 > cm:
             zsz += int(heads[c1 - 1][2] + heads[c1 - 1][0])
-    layout_bytes = (len(lay["pack"]) + 8 * len(lay["chunks"]) + 40 * len(lay["programs"]) +
-                    4 * max(ysz, 1) + 4 * max(zsz, 1))
+    rows = sum(len(P.block(b)[0]) for b in range(3)) if resident else 0
+    groups = 0
+    if resident:  # chunk groups: a group ends at every chunk with flag bit 6
+        groups = sum(1 for h in heads if h[3] & 64)
+    # per program 56 bytes (chunk range, ring flags, scratch offsets, links,
+    # the resident kernel's row count, owned range and group count)
+    layout_bytes = (len(lay["pack"]) + 8 * len(lay["chunks"]) + 56 * len(lay["programs"]) +
+                    4 * max(ysz, 1) + 4 * max(zsz, 1) + 4 * rows + (8 * groups if resident else 0))
     assert m30 - q(M, P, 30, H.GMRES, H.MIXED_FP32) == layout_bytes
     for bad in (dict(restart=0, method=H.GMRES), dict(restart=500, method=H.GMRES),
                 dict(restart=0, method=H.BICGSTAB, flags=H.MIXED_FP32), dict(restart=30, method=7)):
@@ -533,8 +698,8 @@ def test_workspace_bytes_query(H):
 
 
 def test_spmv_rejects_misaligned_output(H):
-    """The SpMV stores two adjacent rows per thread with one vector store, so
-    y_out must be 16-byte (FP64) or 8-byte (FP32) aligned; a misaligned
+    """The SpMV stores its adjacent rows (two in FP64, four in FP32) with one
+    16-byte vector store, so y_out must be 16-byte aligned; a misaligned
     output is rejected before any device work (the addresses below are
     never dereferenced)."""
     import ctypes
@@ -542,7 +707,7 @@ def test_spmv_rejects_misaligned_output(H):
     M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
     lib = H.load_library()
     x = ctypes.c_void_p(0x10000)
-    for y, f32 in ((0x20008, False), (0x20004, True)):
+    for y, f32 in ((0x20008, False), (0x20004, True), (0x20008, True)):
         if f32:
             rc = lib.hec_spmv_f32(M.handle, 1.0, x, 0.0, None, ctypes.c_void_p(y), None)
         else:
