@@ -80,6 +80,10 @@ def parse():
                          "of Table 3's comparison): HEC SpMV with the ELL width forced to 1 "
                          "(almost all CSR tail), chosen by the one-third rule (HEC), or the "
                          "longest row (pure ELL), on regular, irregular and heavy-tailed rows")
+    ap.add_argument("--serve", type=int, default=0, metavar="N",
+                    help="instead of the benchmark line: the served request stream alone, N "
+                         "requests at 2000/s, then N / 5 each at half and a quarter of the "
+                         "measured capacity (keyed pool systems, mixed precision)")
     ap.add_argument("--parts", type=int, default=0,
                     help="CTAs per RAS block of the triangular solve (0: automatic)")
     ap.add_argument("--kernel", choices=["trsv", "spmv", "trsv32", "spmv32", "batch"],
@@ -614,7 +618,8 @@ def c4_section(H, torch, dev, timed, peak):
     return out
 
 
-def c5_section(H):
+def c5_section(H, n_lambda=C5_REQUESTS, n_quarter_lambda=C5_REQUESTS, n_half=40,
+               n_quarter_cap=0, extras=True):
     """Served solves: an open-loop Poisson request stream against the solve
     server (lanes of CUDA streams, admission by device memory).  Requests
     draw their system from a pool of C5_POOL matrices of the request mix
@@ -631,14 +636,14 @@ def c5_section(H):
     nstreams = [0]
 
     def stream(rate, nreq):
-        """A request stream: Poisson arrival offsets, pool picks and every
-        request's own right-hand side (uniform[-1, 1], seeded per request)."""
+        """A request stream: Poisson arrival offsets, pool picks and the seed of
+        every request's own right-hand side (uniform[-1, 1], drawn when the
+        request is submitted)."""
         arr = np.cumsum(rng.exponential(1.0 / rate, nreq))
         picks = rng.integers(0, len(pool), nreq)
         nstreams[0] += 1
-        own = [synth.rhs_uniform(pool[int(p)].n, C5_SEED * 10 ** 6 + nstreams[0] * 10 ** 4 + i)
-               for i, p in enumerate(picks)]
-        return arr, picks, own
+        seeds = [C5_SEED * 10 ** 7 + nstreams[0] * 10 ** 5 + i for i in range(nreq)]
+        return arr, picks, seeds
 
     def register(S):
         t = time.perf_counter()
@@ -651,7 +656,7 @@ def c5_section(H):
         return time.perf_counter() - t
 
     def open_loop(S, rate, req, keyed):
-        arr, picks, own = req
+        arr, picks, seeds = req
         nreq = len(arr)
         res = []
         w0 = time.perf_counter()
@@ -662,16 +667,27 @@ def c5_section(H):
                     break
                 time.sleep(min(left, 0.002))
             p = int(picks[i])
-            S.submit(None if keyed else pool[p], own[i], ilu_k=specs[p]["k"],
-                     key=p + 1 if keyed else 0, tag=i)
+            S.submit(None if keyed else pool[p], synth.rhs_uniform(pool[p].n, seeds[i]),
+                     ilu_k=specs[p]["k"], key=p + 1 if keyed else 0, tag=i)
             res += S.poll(max_results=1024)
         while len(res) < nreq:
             res += S.poll(max_results=1024, wait_ms=100)
         lat = np.array([r["t_done"] - r["t_submit"] for r in res])
         span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        # latency by request size: the one-CTA batched path (<= 32,768
+        # unknowns) and the single-system RAS path
+        size = np.array([pool[int(picks[r["tag"]])].n for r in res])
+        small = size <= 32768
+        solve_ms = np.array([r["t_done"] - r["t_start"] for r in res]) * 1e3
+        worst = int(np.argmax(lat))
+        pct = lambda v, q: 1e3 * float(np.percentile(v, q)) if len(v) else None
         return {"offered_per_s": rate, "requests": nreq, "solves_per_s": nreq / span,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "p50_ms_small": pct(lat[small], 50), "p99_ms_small": pct(lat[small], 99),
+                "p50_ms_large": pct(lat[~small], 50), "p99_ms_large": pct(lat[~small], 99),
+                "worst_latency_unknowns": int(size[worst]),
+                "worst_latency_solve_ms": float(solve_ms[worst]),
                 "mean_wait_ms": 1e3 * float(np.mean([r["t_start"] - r["t_submit"] for r in res])),
                 "ok": int(sum(r["status"] == H.OK for r in res)),
                 "status_counts": {str(k): int(v) for k, v in zip(*np.unique(
@@ -687,14 +703,20 @@ def c5_section(H):
                                      "resident, every request carries its own right-hand side "
                                      "(seeded per request); cold run: every request carries "
                                      "its matrix and is set up"}
-    req_lambda = stream(C5_LAMBDA, C5_REQUESTS)
+    req_lambda = stream(C5_LAMBDA, n_lambda)
     with H.Server(lanes=C5_LANES, flags=H.MIXED_FP32, keep_solutions=False) as S:
         out["register_s"] = round(register(S), 2)
         out["mixed_lambda"] = open_loop(S, C5_LAMBDA, req_lambda, True)
-        out["mixed_quarter_lambda"] = open_loop(S, C5_LAMBDA / 4, stream(C5_LAMBDA / 4, C5_REQUESTS),
-                                                True)
+        if n_quarter_lambda:
+            out["mixed_quarter_lambda"] = open_loop(
+                S, C5_LAMBDA / 4, stream(C5_LAMBDA / 4, n_quarter_lambda), True)
         cap = out["mixed_lambda"]["solves_per_s"]
-        out["mixed_half_capacity"] = open_loop(S, 0.5 * cap, stream(0.5 * cap, 40), True)
+        out["mixed_half_capacity"] = open_loop(S, 0.5 * cap, stream(0.5 * cap, n_half), True)
+        if n_quarter_cap:
+            out["mixed_quarter_capacity"] = open_loop(S, 0.25 * cap,
+                                                      stream(0.25 * cap, n_quarter_cap), True)
+        if not extras:
+            return out
         # new values for the resident systems of the single-system path (a
         # time step of the same grids): keyed requests are refactored on the
         # GPU; the same matrices sent without a key are set up on the host
@@ -1138,6 +1160,18 @@ def main():
         return
     if args.formats:
         run_formats(args, local_rank)
+        return
+    if args.serve:
+        import torch
+        from paper_1606_00545_gb300 import build
+        build.build()
+        from paper_1606_00545_gb300 import hecgpu as H
+        torch.cuda.set_device(local_rank)
+        H.load_library()
+        sub = max(1, args.serve // 5)
+        print(json.dumps({"c5_serving_stream": c5_section(
+            H, n_lambda=args.serve, n_quarter_lambda=0, n_half=sub, n_quarter_cap=sub,
+            extras=False)}), flush=True)
         return
     if world > 1:
         import torch

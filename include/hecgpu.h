@@ -162,7 +162,9 @@ typedef struct {
     int32_t fp64_finish;    /* HEC_MIXED_FP32: the FP32 cycles stopped refining
                                (two cycles in a row left a true FP64 residual
                                above 10x the cycle's own final estimate and
-                               above half the cycle's starting residual) and
+                               above half the cycle's starting residual, or
+                               eight cycles in a row each cut it by less than
+                               10%) and
                                the solve was finished in FP64 from the current
                                x (iters, restarts count both phases); batched
                                solves: the number of systems finished so    */
@@ -356,9 +358,10 @@ int hec_precond_set_trsv_parts(hec_precond_t M, int32_t parts);
  *     65535 rows whose factor rows hold at most 8 entries and whose vector
  *     (rows + 1 values) fits in shared memory beside three chunk stages:
  *     the latency-first form for small systems.
- *   HEC_TRSV_AUTO (default) -- the streamed kernel (measured on GB300 the
- *     resident kernel ties it on a single 64 x 64 ILU(0) block and is slower
- *     on wider levels).
+ *   HEC_TRSV_AUTO (default) -- resident when every block fits, no level
+ *     holds more than 128 rows and the streamed kernel would not split a
+ *     block over several CTAs (measured on GB300: 1.1-1.2x faster there,
+ *     slower on wider levels), else streamed.
  * The FP32 layout of the mixed-precision mode follows the same rule.  Call
  * it between ilu_k_setup and level_schedule; HEC_ERR_INVALID afterwards,
  * for a damped-Jacobi handle or another value; level_schedule returns

@@ -318,6 +318,7 @@ TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
     a.res_slots = L.pack.res_slots;
     a.vrows = L.d_vrows.as<int>();
     a.groups = L.d_groups.as<uint2>();
+    a.res_warps = L.pack.res_warps;
     return a;
 }
 
@@ -361,11 +362,12 @@ int layout_parts(const hec_precond_s *M, int idx)
 }
 
 // The triangular-solve layout with (idx 0) FP64 or (idx 1) FP32 values: the
-// resident-vector kernel's when asked for (every block's vector must fit in
-// shared memory beside three stages); else the streamed kernel's.  (The
-// automatic choice streams: measured on GB300, the resident kernel ties the
-// streamed one on a single 64 x 64 ILU(0) block and is slower on wider
-// levels.)  Sets the row width of the
+// resident-vector kernel's when asked for, or automatically when every
+// block's vector fits in shared memory beside three stages, no level holds
+// more than 128 rows and the streamed kernel would not split a block (on
+// GB300 the resident kernel is 1.1-1.2x faster there -- 0.104 against 0.122
+// ms on the 64 x 64 ILU(0) block -- and slower on wider levels); else the
+// streamed kernel's.  Sets the row width of the
 // fixed-slot formats (0: generic) and, for the resident layout, the stage
 // count (the streamed kernel's is sized at upload).
 int pack_layout(const hec_precond_s *M, int idx, TrsvPack &P, int &fixed_width, int &nstages,
@@ -376,10 +378,19 @@ int pack_layout(const hec_precond_s *M, int idx, TrsvPack &P, int &fixed_width, 
         std::max(max_factor_width(M->blocks, false), max_factor_width(M->blocks, true));
     if (M->trsv_kernel != HEC_TRSV_STREAMED) {
         const int rw = trsv_resident_width(longest);
-        int maxnv = 0;
-        for (const BlockFactor &B : M->blocks)
+        int maxnv = 0, widest = 0;
+        for (const BlockFactor &B : M->blocks) {
             maxnv = std::max(maxnv, B.F.n);
-        if (rw > 0 && maxnv < 65535 && M->trsv_kernel == HEC_TRSV_RESIDENT) {
+            for (size_t l = 0; l + 1 < B.lptrL.size(); ++l)
+                widest = std::max(widest, B.lptrL[l + 1] - B.lptrL[l]);
+            for (size_t l = 0; l + 1 < B.lptrU.size(); ++l)
+                widest = std::max(widest, B.lptrU[l + 1] - B.lptrU[l]);
+        }
+        // automatic: levels of at most 128 rows (4 solving warps) on blocks
+        // the streamed kernel would not split
+        const bool want = M->trsv_kernel == HEC_TRSV_RESIDENT ||
+                          (widest <= 128 && layout_parts(M, idx) == 1);
+        if (rw > 0 && maxnv < 65535 && want) {
             const int rc = pack_trsv_resident(M->blocks, rw, vb, P, msg);
             if (rc != HEC_OK)
                 return rc;

@@ -355,7 +355,9 @@ __device__ __forceinline__ void load_fixed(const unsigned char *ch, const T *rsl
 }
 
 // The issuer warp of both kernels: streams chunk c of the program into stage
-// c mod S once the consumers released chunk c - S.  Returns false when a
+// c mod S once the consumers released chunk c - S.  (Copying a chunk with
+// lane-parallel 16-byte cp.async instead of one cp.async.bulk was measured
+// on the 128^3 case: 1.3x slower in FP64, 2x in FP32.)  Returns false when a
 // wait ran out.
 __device__ __forceinline__ bool issue_chunks(const uint2 *chunks, int nch, int S, int stage_bytes,
                                              const unsigned char *pack, unsigned char *stages,
@@ -987,9 +989,27 @@ __device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lan
         R.dinv = reinterpret_cast<const T *>(blk + F::dinv())[lane];
 }
 
-template <class T, int FW>
-__global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
+// Barrier of the NT solving threads of a resident-kernel CTA (named barrier
+// 1), AND-reducing a flag.
+template <int NT> __device__ __forceinline__ int solvers_sync_and(int flag)
 {
+    int all;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.s32 p, %1, 0;\n\t"
+                 "barrier.cta.red.and.pred q, 1, %2, p;\n\t"
+                 "selp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(all)
+                 : "r"(flag), "n"(NT)
+                 : "memory");
+    return all;
+}
+
+// NW solving warps (chunks of at most 32 NW rows, NW sized at setup to the
+// widest level) and one issuer warp.
+template <class T, int FW, int NW>
+__global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
+{
+    constexpr int NT = NW * 32; // solving threads
     extern __shared__ __align__(128) unsigned char smem[];
     count_launch(a.st);
     if (a.st && a.st->skip)
@@ -1022,57 +1042,65 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
     }
     __syncthreads();
     int failed = 0;
-    if (t >= kThreads) {
+    if (t >= NT) {
         // ------------------------------------------------------------ issuer warp
         if (!stall_test &&
             !issue_chunks(a.groups + blk.zoff, blk.ngroups, S, a.stage_bytes, a.pack, stages,
-                          full, empty, limit, t - kThreads, &s_issued))
+                          full, empty, limit, t - NT, &s_issued))
             failed = 1;
     } else {
         // ------------------------------------------------------------ solving warps
         // r on V_b into the resident vector; slot nv holds 0 (padding)
-        for (int i = t; i < blk.nv; i += kThreads) {
+        for (int i = t; i < blk.nv; i += NT) {
             const int g = vrows[i];
             xs[i] = HEC_CHECK(g >= 0 && g < a.n, 3, 0, g, a.n) ? r[g] : T(0);
         }
         if (t == 0)
             xs[blk.nv] = T(0);
         const int w = t / kWarpRows, lane = t % kWarpRows;
-        // Chunks arrive in groups (one bulk copy each): group g in stage
-        // g mod S, phase g / S; a chunk is found at a byte offset in its
-        // group's stage, the next one right after it unless flag bit 6 ends
-        // the group.
+        // Chunks arrive in groups (one bulk copy each) in stage order: a
+        // chunk's place is its group's stage s, that stage's phase parity and
+        // a byte offset; the next chunk follows at the next offset unless flag
+        // bit 6 ends the group.
         struct Loc {
-            int g, off;
+            int s;
+            uint32_t ph;
+            int off;
         };
-        auto landed = [&](int g) -> bool {
-            return bounded_wait(&full[g % S], (uint32_t)(g / S) & 1u, limit);
-        };
-        auto load = [&](int c, Loc l, ResRow<T, FW> &R) {
-            const unsigned char *ch = stages + (size_t)(l.g % S) * a.stage_bytes + l.off;
-            if (c < nL)
-                load_res<T, FW, false>(ch, w, lane, R);
-            else
+        auto landed = [&](const Loc &l) -> bool { return bounded_wait(&full[l.s], l.ph, limit); };
+        auto load = [&](bool U, const Loc &l, ResRow<T, FW> &R) {
+            const unsigned char *ch = stages + (size_t)l.s * a.stage_bytes + l.off;
+            if (U)
                 load_res<T, FW, true>(ch, w, lane, R);
+            else
+                load_res<T, FW, false>(ch, w, lane, R);
         };
-        auto after = [&](int c, Loc l, const ResRow<T, FW> &R) -> Loc {
-            if (R.flags & 64)
-                return Loc{l.g + 1, 0};
-            const int blkb = c < nL ? Res<T, FW>::block(false) : Res<T, FW>::block(true);
-            return Loc{l.g, l.off + kFixedHeader + R.nwarps * blkb};
+        auto after = [&](bool U, const Loc &l, const ResRow<T, FW> &R) -> Loc {
+            if (R.flags & 64) {
+                Loc n{l.s + 1, l.ph, 0};
+                if (n.s == S) {
+                    n.s = 0;
+                    n.ph ^= 1u;
+                }
+                return n;
+            }
+            return Loc{l.s, l.ph, l.off + kFixedHeader +
+                                      R.nwarps * (U ? Res<T, FW>::block(true)
+                                                    : Res<T, FW>::block(false))};
         };
+        const Loc l0{0, 0u, 0};
         int bad = 0;
-        if (t == kThreads - 1 && nch > 0)
-            bad = !landed(0);
+        if (t == NT - 1 && nch > 0)
+            bad = !landed(l0);
         // the gather above is complete and the first group has landed
-        if (!consumer_sync_and(!bad)) {
+        if (!solvers_sync_and<NT>(!bad)) {
             failed = 1;
         } else if (nch > 0) {
             ResRow<T, FW> A, B;
-            load(0, Loc{0, 0}, A);
-            Loc ln = after(0, Loc{0, 0}, A); // chunk 1
-            bad = (t == kThreads - 1 && nch > 1 && ln.g > 0) ? !landed(ln.g) : 0;
-            if (!consumer_sync_and(!bad))
+            load(0 >= nL, l0, A);
+            Loc ln = after(0 >= nL, l0, A); // chunk 1
+            bad = (t == NT - 1 && nch > 1 && ln.s != 0) ? !landed(ln) : 0;
+            if (!solvers_sync_and<NT>(!bad))
                 failed = 1;
             // level c: cur holds chunk c's rows, nxt receives chunk c + 1's
             // (found at ln)
@@ -1094,9 +1122,11 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
                     acc = xs[me];
                 }
                 Loc l2 = ln;
-                if (c + 1 < nch) { // its group landed: confirmed before the previous barrier
-                    load(c + 1, ln, nxt);
-                    l2 = after(c + 1, ln, nxt);
+                const bool more = c + 1 < nch;
+                if (more) { // its group landed: confirmed before the previous barrier
+                    const bool U1 = c + 1 >= nL;
+                    load(U1, ln, nxt);
+                    l2 = after(U1, ln, nxt);
                 }
                 if (rows) {
 #pragma unroll
@@ -1108,17 +1138,17 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
                         xs[me] = acc;
                 }
                 int late = 0;
-                if (t == kThreads - 1 && c + 2 < nch && l2.g != ln.g)
-                    late = !landed(l2.g);
-                if (!consumer_sync_and(!late))
+                if (t == NT - 1 && c + 2 < nch && (l2.s != ln.s || l2.ph != ln.ph))
+                    late = !landed(l2);
+                if (!solvers_sync_and<NT>(!late))
                     return false;
                 // every thread holds chunks up to c + 1 in registers: a group
                 // whose last chunk that is has a free stage
-                if (t == kThreads - 1) {
+                if (t == NT - 1) {
                     if (c == 0 && (cur.flags & 64))
                         mbar_arrive(&empty[0]);
-                    if (c + 1 < nch && (nxt.flags & 64))
-                        mbar_arrive(&empty[ln.g % S]);
+                    if (more && (nxt.flags & 64))
+                        mbar_arrive(&empty[ln.s]);
                 }
                 ln = l2;
                 return true;
@@ -1130,13 +1160,13 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
                     failed = 1;
             }
             if (!failed)
-                for (int i = blk.own0 + t; i < blk.own1; i += kThreads)
+                for (int i = blk.own0 + t; i < blk.own1; i += NT)
                     z[vrows[i]] = xs[i];
         }
     }
     // every role has left its loop: drain the copies still in flight, report
     __syncthreads();
-    if (t == kThreads) {
+    if (t == NT) {
         const int issued = s_issued;
         const int first = issued - S > 0 ? issued - S : 0;
         for (int c = first; c < issued; ++c)
@@ -1152,7 +1182,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_trsv_res(TrsvArgs a)
 // The dynamic shared memory limit is a process-wide attribute of the kernel:
 // raised once to the device's opt-in maximum, so that launches of different
 // sizes from several host threads never race on it.
-template <class T, int FW, bool RES> static cudaError_t prepare_trsv()
+template <class T, int FW, bool RES, int NW = 8> static cudaError_t prepare_trsv()
 {
     static std::once_flag once;
     static cudaError_t e = cudaSuccess;
@@ -1163,13 +1193,13 @@ template <class T, int FW, bool RES> static cudaError_t prepare_trsv()
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e == cudaSuccess) {
             if constexpr (RES)
-                e = cudaFuncGetAttributes(&fa, k_trsv_res<T, FW>);
+                e = cudaFuncGetAttributes(&fa, k_trsv_res<T, FW, NW>);
             else
                 e = cudaFuncGetAttributes(&fa, k_trsv_ras<T, FW>);
         }
         if (e == cudaSuccess) { // the opt-in limit covers static and dynamic shared memory
             if constexpr (RES)
-                e = cudaFuncSetAttribute(k_trsv_res<T, FW>,
+                e = cudaFuncSetAttribute(k_trsv_res<T, FW, NW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          optin - (int)fa.sharedSizeBytes);
             else
@@ -1202,13 +1232,23 @@ template <class T, int FW> static int launch_t(const TrsvArgs &a, cudaStream_t s
     return cudaLaunchKernelEx(&cfg, k_trsv_ras<T, FW>, a) == cudaSuccess ? 0 : -1;
 }
 
-template <class T, int FW> static int launch_res(const TrsvArgs &a, cudaStream_t s)
+template <class T, int FW, int NW> static int launch_res(const TrsvArgs &a, cudaStream_t s)
 {
     const size_t smem = trsv_res_smem_bytes(a.stage_bytes, a.nstages, a.res_slots, sizeof(T));
-    if (prepare_trsv<T, FW, true>() != cudaSuccess)
+    if (prepare_trsv<T, FW, true, NW>() != cudaSuccess)
         return -1;
-    k_trsv_res<T, FW><<<a.nblocks, kThreads + 32, smem, s>>>(a);
+    k_trsv_res<T, FW, NW><<<a.nblocks, NW * 32 + 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class T, int FW> static int launch_res_w(const TrsvArgs &a, cudaStream_t s)
+{
+    switch (a.res_warps) {
+    case 2: return launch_res<T, FW, 2>(a, s);
+    case 4: return launch_res<T, FW, 4>(a, s);
+    case 8: return launch_res<T, FW, 8>(a, s);
+    default: return -1;
+    }
 }
 
 size_t trsv_res_smem_bytes(int stage_bytes, int nstages, int res_slots, int vbytes)
@@ -1255,7 +1295,7 @@ int launch_trsv(const TrsvArgs &a, cudaStream_t s, bool fp32)
 {
     if (a.resident) {
 #define HEC_RES_CASE(W)                                                                          \
-    case W: return fp32 ? launch_res<float, W>(a, s) : launch_res<double, W>(a, s);
+    case W: return fp32 ? launch_res_w<float, W>(a, s) : launch_res_w<double, W>(a, s);
         switch (a.fixed_width) {
             HEC_RES_CASE(2)
             HEC_RES_CASE(3)

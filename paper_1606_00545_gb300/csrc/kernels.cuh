@@ -48,6 +48,8 @@ struct __align__(16) SolverState {
     double cg_beta;                // CG: (r_{j+1}, z_{j+1}) / (r_j, z_j)
     int stag_run, stagnated;       // mixed precision: cycles in a row whose true FP64
                                    // residual exceeded 10x the FP32 cycle's estimate
+    int slow_run, slow_pad;        // mixed precision: cycles in a row that reduced the
+                                   // true FP64 residual by less than 10%
     double dots[kMaxDots];
     int iters, restarts, status, done;
     int skip, s_conv, zero_x, j;
@@ -194,6 +196,7 @@ struct TrsvArgs {
     int res_slots;              // resident kernel: shared-memory vector slots (largest nv + 1)
     const int *vrows;           // resident kernel: V_b of every block, concatenated
     const uint2 *groups;        // resident kernel: chunk groups {offset / 16, bytes}
+    int res_warps;              // resident kernel: solving warps (2, 4 or 8)
 };
 // Shared memory of one CTA: stages, right-hand-side slots, own and import
 // ring, barriers and the two progress counters (vbytes: 8 for FP64, 4 for FP32).

@@ -129,11 +129,18 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         // est * ||b||; a true FP64 residual far above it, with less than a
         // halving over the cycle, means the FP32 arithmetic, not the Krylov
         // space, limits the refinement
+        // -- and eight cycles in a row that each cut the true residual by
+        // less than 10% mean the FP32 inner cycles gain too little on this
+        // system (measured: an ill-conditioned 2D system of 737,881 unknowns
+        // reached 1.6e-5 after 20,000 mixed steps where FP64 converges in
+        // 12,801)
         const double promised = st->est * st->bnorm;
-        if (st->inner_rtol > 0.0 && st->restarts > 0)
+        if (st->inner_rtol > 0.0 && st->restarts > 0) {
             st->stag_run = (promised > 0.0 && beta > 10.0 * promised && beta > 0.5 * st->beta_cycle)
                                ? st->stag_run + 1
                                : 0;
+            st->slow_run = beta > 0.9 * st->beta_cycle ? st->slow_run + 1 : 0;
+        }
         st->est = beta / st->bnorm;
         if (beta <= st->tol * st->bnorm) {
             st->done = 1;
@@ -144,8 +151,8 @@ __device__ inline void finalize(int op, const double *s, int nd, double *result,
         } else if (st->iters >= st->maxit) {
             st->done = 1;
             st->status = HEC_MAXIT;
-        } else if (st->stag_run >= 2) {
-            // two cycles in a row: the host continues in FP64
+        } else if (st->stag_run >= 2 || st->slow_run >= 8) {
+            // the host continues in FP64
             st->done = 1;
             st->stagnated = 1;
             st->status = HEC_MAXIT;

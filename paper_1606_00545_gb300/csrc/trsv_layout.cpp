@@ -731,7 +731,7 @@ struct ResOut {
     int64_t alg = 0;
 };
 
-void emit_resident(const BlockFactor &B, int FW, int vb, ResOut &O)
+void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
 {
     const HostCSR &F = B.F;
     const int nv = F.n;
@@ -754,8 +754,9 @@ void emit_resident(const BlockFactor &B, int FW, int vb, ResOut &O)
         const size_t blk = res_block(FW, upass, vb);
         int start = 0;
         for (int end : P.level_end) {
-            for (int q = start; q < end; q += kThreads) {
-                const int nr = std::min(kThreads, end - q), nw = (nr + kWarpRows - 1) / kWarpRows;
+            for (int q = start; q < end; q += NW * kWarpRows) {
+                const int nr = std::min(NW * kWarpRows, end - q);
+                const int nw = (nr + kWarpRows - 1) / kWarpRows;
                 const size_t bytes = chunk_bytes_res(FW, nr, upass, vb);
                 const size_t off = O.bytes.size();
                 O.bytes.resize(off + bytes, 0);
@@ -849,10 +850,21 @@ int pack_trsv_resident(const std::vector<BlockFactor> &Bs, int width, int vb, Tr
             msg = "resident layout: a block has 65535 rows or more";
             return HEC_ERR_INVALID;
         }
+    // solving warps: enough for the widest level (wider levels take several
+    // chunks of 8 warps)
+    int widest = 1;
+    for (const BlockFactor &B : Bs) {
+        for (size_t l = 0; l + 1 < B.lptrL.size(); ++l)
+            widest = std::max(widest, B.lptrL[l + 1] - B.lptrL[l]);
+        for (size_t l = 0; l + 1 < B.lptrU.size(); ++l)
+            widest = std::max(widest, B.lptrU[l + 1] - B.lptrU[l]);
+    }
+    const int NW = widest <= 2 * kWarpRows ? 2 : widest <= 4 * kWarpRows ? 4 : 8;
     std::vector<ResOut> outs(nb);
-    parallel_for(nb, [&](int b) { emit_resident(Bs[b], width, vb, outs[b]); });
+    parallel_for(nb, [&](int b) { emit_resident(Bs[b], width, vb, NW, outs[b]); });
     P = TrsvPack();
     P.resident = 1;
+    P.res_warps = NW;
     P.parts = 1;
     P.ring_slots = 32;
     size_t total = 0, largest = 16;

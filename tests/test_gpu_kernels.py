@@ -203,8 +203,8 @@ def test_precond_apply_parity(H, orc, case, mode):
         assert inf["global_passes"] > 0
     if case in ("c1_poisson64_ilu0", "diffusion3d_16_ilu1_ras8"):
         assert inf["global_passes"] == 0
-        if mode == "auto":
-            assert inf["trsv_resident"] == 0
+        if mode == "auto" and case == "c1_poisson64_ilu0":
+            assert inf["trsv_resident"] == 1  # levels of at most 64 rows
     if parts > 1 and case in ("c1_poisson64_ilu0", "diffusion3d_16_ilu1_ras8"):
         assert inf["split_blocks"] == nb  # the chained path ran
 
