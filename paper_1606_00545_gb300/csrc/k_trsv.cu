@@ -948,6 +948,7 @@ template <class T, int FW> struct Res {
 
 template <class T, int FW> struct ResRow {
     int nrows, nwarps, flags;
+    int next_off, next_nw; // the next chunk's offset in its group's stage and its warps
     typename Vec16<T>::type lv[Res<T, FW>::NV];
     uint4 iv[Res<T, FW>::NI];
     T dinv;
@@ -962,19 +963,24 @@ template <class T, int FW> struct ResRow {
     }
 };
 
-// A solving thread's row of a resident-format chunk.  Only warps that hold
-// rows of the chunk read past its header: a stage is sized for the largest
-// chunk of the layout, not for kThreads rows, so the block of a warp past the
+// A solving thread's row of a resident-format chunk of nw warps (known from
+// the previous chunk's header, so the row loads do not wait for this one's).
+// Only warps that hold rows of the chunk read past its header: a stage is
+// sized for the largest group of chunks, so the block of a warp past the
 // chunk's last one may lie outside the stage (and outside shared memory).
 template <class T, int FW, bool U>
-__device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lane, ResRow<T, FW> &R)
+__device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lane, int nw,
+                                         ResRow<T, FW> &R)
 {
     using F = Res<T, FW>;
     const int4 hdr = *reinterpret_cast<const int4 *>(ch);
+    const int4 nxt = *reinterpret_cast<const int4 *>(ch + 16);
     R.nrows = hdr.x;
     R.nwarps = hdr.y;
     R.flags = hdr.w;
-    if (w >= R.nwarps)
+    R.next_off = nxt.x;
+    R.next_nw = nxt.y;
+    if (w >= nw)
         return;
     const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(U);
     const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
@@ -1068,14 +1074,15 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
             int off;
         };
         auto landed = [&](const Loc &l) -> bool { return bounded_wait(&full[l.s], l.ph, limit); };
-        auto load = [&](bool U, const Loc &l, ResRow<T, FW> &R) {
+        auto load = [&](bool U, const Loc &l, int nw, ResRow<T, FW> &R) {
             const unsigned char *ch = stages + (size_t)l.s * a.stage_bytes + l.off;
             if (U)
-                load_res<T, FW, true>(ch, w, lane, R);
+                load_res<T, FW, true>(ch, w, lane, nw, R);
             else
-                load_res<T, FW, false>(ch, w, lane, R);
+                load_res<T, FW, false>(ch, w, lane, nw, R);
         };
-        auto after = [&](bool U, const Loc &l, const ResRow<T, FW> &R) -> Loc {
+        // the place of the chunk after the one R holds
+        auto after = [&](const Loc &l, const ResRow<T, FW> &R) -> Loc {
             if (R.flags & 64) {
                 Loc n{l.s + 1, l.ph, 0};
                 if (n.s == S) {
@@ -1084,9 +1091,7 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
                 }
                 return n;
             }
-            return Loc{l.s, l.ph, l.off + kFixedHeader +
-                                      R.nwarps * (U ? Res<T, FW>::block(true)
-                                                    : Res<T, FW>::block(false))};
+            return Loc{l.s, l.ph, R.next_off};
         };
         const Loc l0{0, 0u, 0};
         int bad = 0;
@@ -1097,8 +1102,8 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
             failed = 1;
         } else if (nch > 0) {
             ResRow<T, FW> A, B;
-            load(0 >= nL, l0, A);
-            Loc ln = after(0 >= nL, l0, A); // chunk 1
+            load(0 >= nL, l0, reinterpret_cast<const int *>(stages)[1], A);
+            Loc ln = after(l0, A); // chunk 1
             bad = (t == NT - 1 && nch > 1 && ln.s != 0) ? !landed(ln) : 0;
             if (!solvers_sync_and<NT>(!bad))
                 failed = 1;
@@ -1124,9 +1129,10 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
                 Loc l2 = ln;
                 const bool more = c + 1 < nch;
                 if (more) { // its group landed: confirmed before the previous barrier
-                    const bool U1 = c + 1 >= nL;
-                    load(U1, ln, nxt);
-                    l2 = after(U1, ln, nxt);
+                    load(c + 1 >= nL, ln, cur.next_nw, nxt);
+                    l2 = after(ln, nxt);
+                    if (!HEC_CHECK(nxt.nwarps == cur.next_nw, 2, c + 1, nxt.nwarps, cur.next_nw))
+                        nxt.nwarps = 0; // its rows are not used
                 }
                 if (rows) {
 #pragma unroll

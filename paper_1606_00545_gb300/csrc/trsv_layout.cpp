@@ -699,7 +699,8 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
 // overwritten in place, so dependencies are local row slots; see k_trsv.cu)
 //   [0, 16)   nrows, nwarps, first position, flags (bit 0: U pass, bit 3:
 //             fixed slots, bit 5: resident format)
-//   [16, 32)  0, 0, FW, 0
+//   [16, 32)  the next chunk's byte offset in its group's stage and its warp
+//             count (0, 0 for the last chunk), FW, 0
 //   per warp w < nwarps, a block of res_block() bytes, lane l = row 32w + l:
 //     val: ceil(FW / VW) vectors of 32 lanes x 16 bytes; idx: ceil((FW + 1) /
 //     8) vectors of 32 lanes x 8 uint16 (FW dependency slots, then the row's
@@ -821,6 +822,21 @@ void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
     if (gbytes > 0) {
         O.groups.push_back(make_uint2((unsigned)(g0 / 16), (unsigned)gbytes));
         reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks.back().x * 16)[3] |= 64;
+    }
+    // every chunk names the next one's byte offset in its group's stage and
+    // its warp count, so the kernel loads it without waiting for its header
+    size_t gstart = 0;
+    for (size_t c = 0; c < O.chunks.size(); ++c) {
+        int *h = reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks[c].x * 16);
+        const size_t end = (size_t)O.chunks[c].x * 16 + O.chunks[c].y;
+        if (h[3] & 64)
+            gstart = end; // the next chunk opens a group
+        if (c + 1 < O.chunks.size()) {
+            const int *hn = reinterpret_cast<const int *>(O.bytes.data() +
+                                                          (size_t)O.chunks[c + 1].x * 16);
+            h[4] = (int)((size_t)O.chunks[c + 1].x * 16 - gstart);
+            h[5] = hn[1];
+        }
     }
     O.largest = 0;
     for (const uint2 &g : O.groups)

@@ -293,13 +293,19 @@ def run_resident(lay, P, n, r, nb):
         solved = [np.zeros(nv + 1, bool), np.zeros(nv + 1, bool)]
         pos = [0, 0]
         gbytes, gchunks = 0, 0  # the group of consecutive chunks being streamed
+        gstart = int(chunks[c0, 0]) * 16
         for c in range(c0, c1):
             C = parse_resident_chunk(pack, chunks, c, vb)
             gbytes += int(chunks[c, 1])
             gchunks += 1
+            h = _chunk(pack, chunks, c)[1]
             if C["flags"] & 64 or c == c1 - 1:  # one bulk copy of at most 16 KB
                 assert C["flags"] & 64 and (gbytes <= 16384 or gchunks == 1)
                 gbytes, gchunks = 0, 0
+                gstart = int(chunks[c, 0]) * 16 + int(chunks[c, 1])
+            if c + 1 < c1:  # the next chunk's place in its group's stage and its warps
+                hn = _chunk(pack, chunks, c + 1)[1]
+                assert int(h[4]) == int(chunks[c + 1, 0]) * 16 - gstart and int(h[5]) == int(hn[1])
             upass = C["upass"]
             assert upass == (c >= cm) and C["q"] == pos[int(upass)]
             pos[int(upass)] += C["nr"]
