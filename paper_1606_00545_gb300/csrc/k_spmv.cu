@@ -5,7 +5,8 @@
 // adjacent rows -- 2 in FP64, 4 in FP32 -- so each slab column is read with
 // one 16-byte load of values (double2 / float4) and one load of column
 // indices (int2 / int4), coalesced across the warp because the slab is
-// column-major with a leading dimension that is a multiple of 32 rows.  A CTA
+// column-major with a leading dimension that is a multiple of 32 rows, and
+// streamed with an evict-first L2 policy so that x stays in L2.  A CTA
 // walks row blocks of kThreads * RPT rows (one 512-row tile in FP64, two in
 // FP32).  Tail rows of a block (rows longer than the slab width K) are summed
 // first into shared memory, then added to the slab sum of their row: short
@@ -20,6 +21,45 @@
 #include "reduce.cuh"
 
 namespace hec {
+
+// Loads of the slab stream: no L1 allocation and an evict-first L2 policy,
+// so the slab (read once per SpMV) does not push x -- gathered at random,
+// and small enough to stay in L2 -- out of it.  Measured on the 128^3 and
+// 96^3 cases: 9-12% faster in FP64, 17% in FP32.
+__device__ __forceinline__ uint64_t evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p, uint64_t pol)
+{
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *p, uint64_t pol)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int2 ld_stream(const int2 *p, uint64_t pol)
+{
+    int2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int4 ld_stream(const int4 *p, uint64_t pol)
+{
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
 
 // RPT adjacent rows per thread, read with 16-byte value vectors.
 template <class T> struct RowVec;
@@ -144,10 +184,11 @@ __global__ void __launch_bounds__(kThreads) k_spmv_hec(SpmvArgs a)
             for (int j = 0; j < RPT; ++j)
                 s[j] = T(0);
             const int p0 = r0 / RPT;
+            const uint64_t pol = evict_first_policy();
 #pragma unroll 4
             for (int k = 0; k < a.K; ++k) {
-                const typename RV::V v = __ldg(&valv[(size_t)k * ldv + p0]);
-                const typename RV::C c = __ldg(&colv[(size_t)k * ldv + p0]);
+                const typename RV::V v = ld_stream(&valv[(size_t)k * ldv + p0], pol);
+                const typename RV::C c = ld_stream(&colv[(size_t)k * ldv + p0], pol);
 #pragma unroll
                 for (int j = 0; j < RPT; ++j)
                     s[j] = fma(RV::get(v, j), __ldg(&x[RV::col(c, j)]), s[j]);
