@@ -1,7 +1,8 @@
 """CPU tests of bench.py's host logic: the clock record taken during the
-timed region (median SM clock, throttle reasons, the rejection rule) and the
-traffic figure read from the committed ncu summary only while the kernel
-source it was taken on is unchanged."""
+timed region (median SM clock, throttle reasons, the rejection rule), the
+traffic figure read from the committed ncu record only while the kernel
+source it was taken on is unchanged, and the algorithmic byte counts behind
+the roofline figures."""
 import json
 import os
 
@@ -71,3 +72,41 @@ def test_source_hash_covers_the_layout_code():
     src = os.path.join(os.path.dirname(bench.__file__), "paper_1606_00545_gb300", "csrc",
                        "hec_setup.cpp")
     assert bench.LAYOUT_MARKER in open(src, "rb").read()
+
+
+def test_trsv_method_bytes_counts_every_block_row():
+    """The triangular-solve roofline's byte count: every stored factor entry
+    (strict L, U with its diagonal) as value + int32 index, 4 values per block
+    row (r read, y written and read back, z written) and 4 bytes per row and
+    per level, recounted here from the factor and level queries of a small
+    host-only preconditioner."""
+    import numpy as np
+    from paper_1606_00545_gb300 import hecgpu as H, synth
+    A = synth.diffusion3d_7pt_lognormal(10, 2.0, 2)
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, 1, 4, 1)
+    H.level_schedule(P)
+    for vb in (8, 4):
+        want = 0
+        for b in range(4):
+            rp, ci, _, _ = P.factor(b)
+            rows = len(rp) - 1
+            levels = sum(len(P.levels(b, w)[0]) - 1 for w in (H.FACTOR_L, H.FACTOR_U))
+            want += len(ci) * (vb + 4) + rows * 4 * vb + 4 * (rows + levels)
+        assert bench.trsv_method_bytes(H, P, vb) == want
+    # it counts every row; the kernel's own count covers the needed rows only
+    assert bench.trsv_method_bytes(H, P, 8) >= P.info()["apply_bytes"]
+
+
+def test_c4_bytes_charges_the_third_gram_schmidt_pass():
+    """Each Arnoldi step that took the third (re-orthogonalising) pass adds
+    j + 3 vector passes at the cycle's mean j: with every step of a 30-step
+    cycle re-orthogonalised, 30 * (14.5 + 3) vectors of n * nrhs FP32 values."""
+    from paper_1606_00545_gb300 import synth
+    Bs = synth.batch_diffusion2d(3, 16, 20, 2.0, 7)
+    base = [{"iters": 30, "cycles": 1, "reorth": 0} for _ in range(3)]
+    full = [{"iters": 30, "cycles": 1, "reorth": 30} for _ in range(3)]
+    extra = bench.c4_bytes(Bs, full, 4, 30) - bench.c4_bytes(Bs, base, 4, 30)
+    want = sum(30 * (29 / 2 + 3) * float(Bs.sys_ptr[s + 1] - Bs.sys_ptr[s]) * 4 * 4
+               for s in range(3))
+    assert abs(extra - want) <= 1e-9 * want
