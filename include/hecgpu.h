@@ -318,11 +318,13 @@ int hec_precond_get_levels(hec_precond_t M, int32_t b, int32_t which, int32_t *n
  * scratch offset is its first group of consecutive chunks (the kernel
  * streams a group of up to 16 KB with one bulk copy; flag bit 6 marks a
  * group's last chunk), and chunks of 8 int32 (row count, warp count, first
- * position, flags, 0, 0, FW, 0)
- * followed, per warp of 32 rows, by val (ceil(FW / VW) vectors of 32 lanes
- * x 16 bytes, VW = 16 / value bytes: lane l's entries k VW .. k VW + VW - 1
- * in vector k), idx (ceil((FW + 1) / 8) vectors of 32 lanes x 8 uint16:
- * lane l's FW dependency slots, then its own slot) and, for U, dinv[32].
+ * position, flags, the next chunk's offset in its group's stage and its
+ * warp count, FW, 0) followed, for each of the kernel's solving warps (every
+ * chunk has the same size; warps past the row count hold padding), by val
+ * (ceil(FW / VW) vectors of 32 lanes x 16 bytes, VW = 16 / value bytes: lane
+ * l's entries k VW .. k VW + VW - 1 in vector k), idx (ceil((FW + 1) / 8)
+ * vectors of 32 lanes x 8 uint16: lane l's FW dependency slots, then its own
+ * slot) and dinv[32] (read in the U pass).
  * Slots are the block's local row indices; slot nv (the block's row count)
  * holds 0 and pads short rows and the rows past the chunk's end.  Row t of
  * the L pass computes x[own] -= sum_k val[k] x[dep[k]] with x = r on V_b at

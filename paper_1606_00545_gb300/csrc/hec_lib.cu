@@ -319,6 +319,7 @@ TrsvArgs trsv_args(const hec_precond_s *M, const TrsvLayout &L, long long spin)
     a.vrows = L.d_vrows.as<int>();
     a.groups = L.d_groups.as<uint2>();
     a.res_warps = L.pack.res_warps;
+    a.res_group = L.pack.res_group;
     return a;
 }
 

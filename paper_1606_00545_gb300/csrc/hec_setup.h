@@ -82,6 +82,7 @@ struct TrsvPack {
     int resident = 0;
     int res_slots = 0;          // largest block's rows + 1
     int res_warps = 0;          // solving warps of the kernel (2, 4 or 8): chunks of 32 x that rows
+    int res_group = 1;          // chunks per group (one bulk copy; every chunk the same size)
     std::vector<int> vrows;     // V_b of every block, concatenated (TrsvBlock::yoff)
     std::vector<uint2> groups;  // bulk copies of consecutive chunks (TrsvBlock::zoff, ::pad)
 };

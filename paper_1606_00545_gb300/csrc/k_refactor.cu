@@ -184,10 +184,10 @@ template <class T> __global__ void __launch_bounds__(kThreads) k_fill_pack(FillA
         constexpr int vb = (int)sizeof(T), VW = 16 / vb;
         const int NV = (FW + VW - 1) / VW;
         int blk, dinv_off;
-        if (hdr[3] & 32) { // resident format: index vectors of 8 uint16
+        if (hdr[3] & 32) { // resident format: index vectors of 8 uint16, every block with dinv
             const int NI = (FW + 1 + 7) / 8;
             dinv_off = (NV + NI) * 512;
-            blk = dinv_off + (upass ? 32 * vb : 0);
+            blk = dinv_off + 32 * vb;
         } else {
             const bool exps = (hdr[3] & 16) != 0;
             const int ND = (FW + 3) / 4;

@@ -948,7 +948,7 @@ template <class T, int FW> struct Res {
     static constexpr int NI = (FW + 1 + 7) / 8;   // index vectors per lane
     __device__ static constexpr int idx() { return NV * 512; }
     __device__ static constexpr int dinv() { return (NV + NI) * 512; }
-    __device__ static constexpr int block(bool u) { return dinv() + (u ? 32 * (int)sizeof(T) : 0); }
+    __device__ static constexpr int block() { return dinv() + 32 * (int)sizeof(T); }
 };
 
 template <class T, int FW> struct ResRow {
@@ -968,11 +968,10 @@ template <class T, int FW> struct ResRow {
     }
 };
 
-// A solving thread's row of a resident-format chunk of nw warps (known from
-// the previous chunk's header, so the row loads do not wait for this one's).
-// Only warps that hold rows of the chunk read past its header: a stage is
-// sized for the largest group of chunks, so the block of a warp past the
-// chunk's last one may lie outside the stage (and outside shared memory).
+// A solving thread's row of a resident-format chunk.  Every chunk has a block
+// for each of the kernel's NW solving warps (padding rows beyond its rows), so
+// a warp reads its block without waiting for the chunk's header; nw limits
+// the reads all the same (the header's warp count of a chunk is at most NW).
 template <class T, int FW, bool U>
 __device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lane, int nw,
                                          ResRow<T, FW> &R)
@@ -987,7 +986,7 @@ __device__ __forceinline__ void load_res(const unsigned char *ch, int w, int lan
     R.next_nw = nxt.y;
     if (w >= nw)
         return;
-    const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block(U);
+    const unsigned char *blk = ch + kFixedHeader + (size_t)w * F::block();
     const typename Vec16<T>::type *val = reinterpret_cast<const typename Vec16<T>::type *>(blk) + lane;
 #pragma unroll
     for (int v = 0; v < F::NV; ++v)
@@ -1069,34 +1068,33 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
         if (t == 0)
             xs[blk.nv] = T(0);
         const int w = t / kWarpRows, lane = t % kWarpRows;
-        // Chunks arrive in groups (one bulk copy each) in stage order: a
-        // chunk's place is its group's stage s, that stage's phase parity and
-        // a byte offset; the next chunk follows at the next offset unless flag
-        // bit 6 ends the group.
+        // Chunks arrive in groups of G (one bulk copy each) in stage order, all
+        // of one size CB: chunk k of a group sits at k CB in its group's stage.
+        // A chunk's place is that stage s, the stage's phase parity and k.
+        constexpr int CB = kFixedHeader + NW * Res<T, FW>::block();
+        const int G = a.res_group;
         struct Loc {
             int s;
             uint32_t ph;
-            int off;
+            int k;
+        };
+        auto next = [&](Loc l) -> Loc {
+            if (++l.k == G) {
+                l.k = 0;
+                if (++l.s == S) {
+                    l.s = 0;
+                    l.ph ^= 1u;
+                }
+            }
+            return l;
         };
         auto landed = [&](const Loc &l) -> bool { return bounded_wait(&full[l.s], l.ph, limit); };
-        auto load = [&](bool U, const Loc &l, int nw, ResRow<T, FW> &R) {
-            const unsigned char *ch = stages + (size_t)l.s * a.stage_bytes + l.off;
+        auto load = [&](bool U, const Loc &l, ResRow<T, FW> &R) {
+            const unsigned char *ch = stages + (size_t)l.s * a.stage_bytes + (size_t)l.k * CB;
             if (U)
-                load_res<T, FW, true>(ch, w, lane, nw, R);
+                load_res<T, FW, true>(ch, w, lane, NW, R);
             else
-                load_res<T, FW, false>(ch, w, lane, nw, R);
-        };
-        // the place of the chunk after the one R holds
-        auto after = [&](const Loc &l, const ResRow<T, FW> &R) -> Loc {
-            if (R.flags & 64) {
-                Loc n{l.s + 1, l.ph, 0};
-                if (n.s == S) {
-                    n.s = 0;
-                    n.ph ^= 1u;
-                }
-                return n;
-            }
-            return Loc{l.s, l.ph, R.next_off};
+                load_res<T, FW, false>(ch, w, lane, NW, R);
         };
         const Loc l0{0, 0u, 0};
         int bad = 0;
@@ -1107,13 +1105,13 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
             failed = 1;
         } else if (nch > 0) {
             ResRow<T, FW> A, B;
-            load(0 >= nL, l0, reinterpret_cast<const int *>(stages)[1], A);
-            Loc ln = after(l0, A); // chunk 1
-            bad = (t == NT - 1 && nch > 1 && ln.s != 0) ? !landed(ln) : 0;
+            load(0 >= nL, l0, A);
+            Loc ln = next(l0); // chunk 1
+            bad = (t == NT - 1 && nch > 1 && ln.k == 0) ? !landed(ln) : 0;
             if (!solvers_sync_and<NT>(!bad))
                 failed = 1;
             // level c: cur holds chunk c's rows, nxt receives chunk c + 1's
-            // (found at ln)
+            // (found at ln); every place is known without reading a header
             auto level = [&](int c, ResRow<T, FW> &cur, ResRow<T, FW> &nxt) -> bool {
                 const bool U = c >= nL;
                 const bool rows = w < cur.nwarps; // warps past the chunk's last one idle
@@ -1131,14 +1129,14 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
                         me = blk.nv;
                     acc = xs[me];
                 }
-                Loc l2 = ln;
+                const Loc l2 = next(ln); // chunk c + 2
                 const bool more = c + 1 < nch;
-                if (more) { // its group landed: confirmed before the previous barrier
-                    load(c + 1 >= nL, ln, cur.next_nw, nxt);
-                    l2 = after(ln, nxt);
-                    if (!HEC_CHECK(nxt.nwarps == cur.next_nw, 2, c + 1, nxt.nwarps, cur.next_nw))
-                        nxt.nwarps = 0; // its rows are not used
-                }
+                if (more) // its group landed: confirmed before the previous barrier
+                    load(c + 1 >= nL, ln, nxt);
+                // chunk c + 2 opens a group: the last thread confirms it landed
+                int late = 0;
+                if (t == NT - 1 && c + 2 < nch && l2.k == 0)
+                    late = !landed(l2);
                 if (rows) {
 #pragma unroll
                     for (int k = 0; k < FW; ++k)
@@ -1148,17 +1146,14 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) k_trsv_res(TrsvArgs a)
                     if (t < cur.nrows && me < blk.nv)
                         xs[me] = acc;
                 }
-                int late = 0;
-                if (t == NT - 1 && c + 2 < nch && (l2.s != ln.s || l2.ph != ln.ph))
-                    late = !landed(l2);
                 if (!solvers_sync_and<NT>(!late))
                     return false;
-                // every thread holds chunks up to c + 1 in registers: a group
-                // whose last chunk that is has a free stage
+                // every thread holds chunks up to c + 1 in registers: the group
+                // that chunk closes has a free stage
                 if (t == NT - 1) {
-                    if (c == 0 && (cur.flags & 64))
+                    if (c == 0 && (G == 1 || nch == 1))
                         mbar_arrive(&empty[0]);
-                    if (more && (nxt.flags & 64))
+                    if (more && (ln.k == G - 1 || c + 1 == nch - 1))
                         mbar_arrive(&empty[ln.s]);
                 }
                 ln = l2;

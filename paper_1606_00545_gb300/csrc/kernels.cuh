@@ -197,6 +197,7 @@ struct TrsvArgs {
     const int *vrows;           // resident kernel: V_b of every block, concatenated
     const uint2 *groups;        // resident kernel: chunk groups {offset / 16, bytes}
     int res_warps;              // resident kernel: solving warps (2, 4 or 8)
+    int res_group;              // resident kernel: chunks per group of one bulk copy
 };
 // Shared memory of one CTA: stages, right-hand-side slots, own and import
 // ring, barriers and the two progress counters (vbytes: 8 for FP64, 4 for FP32).

@@ -701,25 +701,28 @@ void emit_block(const BlockFactor &B, const BlockPlan &bp, int R, int RI, int vb
 //             fixed slots, bit 5: resident format)
 //   [16, 32)  the next chunk's byte offset in its group's stage and its warp
 //             count (0, 0 for the last chunk), FW, 0
-//   per warp w < nwarps, a block of res_block() bytes, lane l = row 32w + l:
+//   per warp w < NW (the kernel's solving warps: every chunk has the same
+//   size, so the kernel finds chunk k of a group at k times that size), a
+//   block of res_block() bytes, lane l = row 32w + l:
 //     val: ceil(FW / VW) vectors of 32 lanes x 16 bytes; idx: ceil((FW + 1) /
 //     8) vectors of 32 lanes x 8 uint16 (FW dependency slots, then the row's
-//     own slot); U: dinv[32] (value)
-// Padding entries have value 0 and slot nv (which holds 0); padding rows have
-// own slot nv.  Consecutive chunks of a block's program form groups of at
-// most kResGroupBytes (or one larger chunk), each streamed by one bulk copy
-// into one stage; flag bit 6 marks the last chunk of a group.
+//     own slot); dinv[32] (value; used by the U pass)
+// Padding entries have value 0 and slot nv (which holds 0); padding rows and
+// the warps past the chunk's rows have own slot nv.  Every group of G =
+// kResGroupBytes / (chunk size) consecutive chunks of a block's program (at
+// least one) is streamed by one bulk copy into one stage; flag bit 6 marks
+// the last chunk of a group.
 inline int res_ni(int FW) { return (FW + 1 + 7) / 8; }
 constexpr size_t kResGroupBytes = 16384;
 
-size_t res_block(int FW, bool upass, int vb)
+size_t res_block(int FW, int vb)
 {
-    return (size_t)(fixed_nv(FW, vb) + res_ni(FW)) * 512 + (upass ? (size_t)32 * vb : 0);
+    return (size_t)(fixed_nv(FW, vb) + res_ni(FW)) * 512 + (size_t)32 * vb;
 }
 
-size_t chunk_bytes_res(int FW, int nrows, bool upass, int vb)
+size_t chunk_bytes_res(int FW, int NW, int vb)
 {
-    return kFixedHeader + (size_t)((nrows + kWarpRows - 1) / kWarpRows) * res_block(FW, upass, vb);
+    return kFixedHeader + (size_t)NW * res_block(FW, vb);
 }
 
 struct ResOut {
@@ -729,6 +732,7 @@ struct ResOut {
     int nchunksL = 0, nL = 0, nU = 0, own0 = 0, own1 = 0;
     std::vector<int> rows_per_chunk, rm_start, rm_len, rm_diag;
     size_t largest = 0; // bytes of the largest group
+    int group = 1;      // chunks per group
     int64_t alg = 0;
 };
 
@@ -752,20 +756,20 @@ void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
     for (int pass = 0; pass < 2; ++pass) {
         const bool upass = pass == 1;
         const PassOrder &P = po[pass];
-        const size_t blk = res_block(FW, upass, vb);
+        const size_t blk = res_block(FW, vb);
         int start = 0;
         for (int end : P.level_end) {
             for (int q = start; q < end; q += NW * kWarpRows) {
                 const int nr = std::min(NW * kWarpRows, end - q);
                 const int nw = (nr + kWarpRows - 1) / kWarpRows;
-                const size_t bytes = chunk_bytes_res(FW, nr, upass, vb);
+                const size_t bytes = chunk_bytes_res(FW, NW, vb);
                 const size_t off = O.bytes.size();
                 O.bytes.resize(off + bytes, 0);
                 O.largest = std::max(O.largest, bytes);
                 unsigned char *cb = O.bytes.data() + off;
                 const int hdr[kFixedHeader / 4] = {nr, nw, q, (upass ? 1 : 0) | 8 | 32, 0, 0, FW, 0};
                 std::memcpy(cb, hdr, kFixedHeader);
-                for (int w = 0; w < nw; ++w) {
+                for (int w = 0; w < NW; ++w) {
                     unsigned char *base = cb + kFixedHeader + w * blk;
                     uint16_t *idx = reinterpret_cast<uint16_t *>(base + (size_t)NV * 512);
                     unsigned char *dinv = base + (size_t)(NV + NI) * 512;
@@ -785,8 +789,7 @@ void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
                         for (int k = 0; k < NI * 8; ++k)
                             idx[at_idx(k, lane)] = (uint16_t)(k < len ? F.ci[e0 + k] : nv);
                         idx[at_idx(FW, lane)] = (uint16_t)(i >= 0 ? i : nv);
-                        if (upass)
-                            put_value(dinv, lane, i >= 0 ? 1.0 / F.va[B.diag[i]] : 0.0, vb);
+                        put_value(dinv, lane, upass && i >= 0 ? 1.0 / F.va[B.diag[i]] : 0.0, vb);
                         if (i < 0)
                             continue;
                         O.rm_start.push_back(e0);
@@ -807,21 +810,14 @@ void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
         if (!upass)
             O.nchunksL = (int)O.chunks.size();
     }
-    // groups of consecutive chunks, one bulk copy each
-    size_t g0 = 0, gbytes = 0;
-    for (size_t c = 0; c < O.chunks.size(); ++c) {
-        const size_t b = O.chunks[c].y;
-        if (gbytes > 0 && gbytes + b > kResGroupBytes) {
-            O.groups.push_back(make_uint2((unsigned)(g0 / 16), (unsigned)gbytes));
-            reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks[c - 1].x * 16)[3] |= 64;
-            g0 += gbytes;
-            gbytes = 0;
-        }
-        gbytes += b;
-    }
-    if (gbytes > 0) {
-        O.groups.push_back(make_uint2((unsigned)(g0 / 16), (unsigned)gbytes));
-        reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks.back().x * 16)[3] |= 64;
+    // groups of G consecutive chunks, one bulk copy each
+    const size_t cbytes = chunk_bytes_res(FW, NW, vb);
+    O.group = std::max<int>(1, (int)(kResGroupBytes / cbytes));
+    const int nch = (int)O.chunks.size();
+    for (int g0 = 0; g0 < nch; g0 += O.group) {
+        const int g1 = std::min(nch, g0 + O.group);
+        O.groups.push_back(make_uint2(O.chunks[g0].x, (unsigned)((size_t)(g1 - g0) * cbytes)));
+        reinterpret_cast<int *>(O.bytes.data() + (size_t)O.chunks[g1 - 1].x * 16)[3] |= 64;
     }
     // every chunk names the next one's byte offset in its group's stage and
     // its warp count, so the kernel loads it without waiting for its header
@@ -838,9 +834,7 @@ void emit_resident(const BlockFactor &B, int FW, int vb, int NW, ResOut &O)
             h[5] = hn[1];
         }
     }
-    O.largest = 0;
-    for (const uint2 &g : O.groups)
-        O.largest = std::max(O.largest, (size_t)g.y);
+    O.largest = (size_t)O.group * cbytes;
 }
 
 } // namespace
@@ -893,6 +887,7 @@ int pack_trsv_resident(const std::vector<BlockFactor> &Bs, int width, int vb, Tr
         return HEC_ERR_INVALID;
     }
     P.stage_bytes = (int)((largest + 127) & ~(size_t)127);
+    P.res_group = nb > 0 ? outs[0].group : 1;
     P.pack.resize(total);
     P.blocks.assign(nb, TrsvBlock());
     int64_t ent0 = 0, r0 = 0;

@@ -246,9 +246,14 @@ def parse_resident_chunk(pack, chunks, c, vb):
     FW = int(h[6])
     VW = 16 // vb
     NV, NI = (FW + VW - 1) // VW, (FW + 1 + 7) // 8
-    blk = (NV + NI) * 512 + (32 * vb if upass else 0)
-    assert int(chunks[c, 1]) == 32 + nw * blk
-    out = dict(nr=nr, nw=nw, q=q, upass=upass, FW=FW, flags=flags, warps=[])
+    blk = (NV + NI) * 512 + 32 * vb  # every chunk has a block per solving warp of the kernel
+    assert (int(chunks[c, 1]) - 32) % blk == 0 and (int(chunks[c, 1]) - 32) // blk >= nw
+    pad_slots = []  # warps past the rows: values 0, every slot padding
+    for w in range(nw, (int(chunks[c, 1]) - 32) // blk):
+        o = base + 32 + w * blk
+        assert not np.any(np.frombuffer(pack, dt, NV * 32 * VW, o))
+        pad_slots.append(np.frombuffer(pack, np.uint16, NI * 256, o + NV * 512))
+    out = dict(nr=nr, nw=nw, q=q, upass=upass, FW=FW, flags=flags, warps=[], pad_slots=pad_slots)
     own, dinv = [], []
     for w in range(nw):
         o = base + 32 + w * blk
@@ -311,6 +316,7 @@ def run_resident(lay, P, n, r, nb):
             pos[int(upass)] += C["nr"]
             own = C["own"]
             assert np.all(own[C["nr"]:] == nv) and np.all(own[:C["nr"]] < nv)
+            assert all(np.all(p == nv) for p in C["pad_slots"])
             acc = x[own].copy()
             done = solved[int(upass)]
             for w, val, dep, m in C["warps"]:
