@@ -642,12 +642,20 @@ def test_trsv_parts_choice(H):
     M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
     P = H.ilu_k_setup(M, 0, 1, 0)
     H.level_schedule(P)
-    assert P.info()["trsv_parts"] == 1
+    # levels of at most 24 rows on an unsplit block: the resident kernel
+    assert P.info()["trsv_parts"] == 1 and P.info()["trsv_resident"] == 1
     A = synth.poisson2d_5pt(400)  # 160,000 rows, 799 levels: 200 rows per level
     M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
     P = H.ilu_k_setup(M, 0, 1, 0)
     H.level_schedule(P)
+    # split over 2 CTAs (and too large for shared memory anyway): streamed
     assert P.info()["trsv_parts"] == 2 and P.info()["split_blocks"] == 1
+    assert P.info()["trsv_resident"] == 0
+    A = synth.poisson2d_5pt(160)  # 25,600 rows, levels up to 160 rows: streamed, 1 CTA
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, 0, 1, 0)
+    H.level_schedule(P)
+    assert P.info()["trsv_parts"] == 1 and P.info()["trsv_resident"] == 0
     A = synth.random_sparse(600, 0.01, seed=2)
     M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
     P = H.ilu_k_setup(M, 2, 1, 0)
