@@ -439,7 +439,6 @@ def test_bicgstab_unpreconditioned_and_breakdown(orc):
     assert info.status == orc.OK
     assert np.allclose(x, np.linalg.solve(A.to_dense(), b), atol=1e-8)
     # skew-symmetric: (r0, A r0) = 0, so alpha is undefined at the first step
-    S = synth.CSR(np.array([0, 1, 2]), np.array([1, 0]), np.array([1.0, -1.0]))
     S = synth.CSR(np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([0.0, 1.0, -1.0, 0.0]))
     x, info = orc.bicgstab(S, np.array([1.0, 2.0]), tol=1e-10)
     assert info.status == orc.BREAKDOWN
@@ -451,7 +450,91 @@ def test_bicgstab_zero_rhs(orc):
     assert info.iters == 0 and np.all(x == 0)
 
 
+def diag_inverse(A):
+    d = np.zeros(A.n)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    on = rows == A.col
+    d[rows[on]] = A.val[on]
+    return 1.0 / d
+
+
+@pytest.mark.parametrize("prec", ["none", "jacobi", "ras"])
+def test_bicgstab_iterates_match_scipy(orc, prec):
+    """The first iterates equal SciPy's BiCGSTAB (van der Vorst's right-preconditioned
+    recurrences, shadow residual r0) with the same preconditioner: a wrong sign or a
+    swapped alpha/omega in any update moves x_k off SciPy's x_k at once."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    A = synth.diffusion2d_5pt_lognormal(14, 1.0, seed=6)
+    b = synth.rhs_uniform(A.n, 4)
+    As = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n))
+    if prec == "none":
+        M, Ms = None, None
+    elif prec == "jacobi":
+        dinv = diag_inverse(A)
+        M = orc.Jacobi(A, 1.0)
+        Ms = spla.LinearOperator((A.n, A.n), matvec=lambda r: dinv * r)
+    else:
+        M = orc.RAS(A, 0, 3, 1)
+        Ms = spla.LinearOperator((A.n, A.n), matvec=M.apply)
+    hist = []
+    spla.bicgstab(As, b, rtol=1e-300, atol=0.0, maxiter=6, M=Ms,
+                  callback=lambda xk: hist.append(xk.copy()))
+    assert len(hist) == 6
+    for k in range(1, 7):
+        x, info = orc.bicgstab(A, b, M=M, tol=1e-300, maxit=k)
+        assert info.iters == k
+        xs = hist[k - 1]
+        assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs), k
+
+
 # --------------------------------------------------------------------------- O8: GMRES
+def min_residual_iterate(Ad, Minv, b, x0, k):
+    """argmin ||b - A x|| over x in x0 + M^{-1} K_k(A M^{-1}, r0), by dense least squares
+    over an orthonormalised power basis (the defining property of GMRES)."""
+    B = Ad @ Minv
+    r0 = b - Ad @ x0
+    K = np.empty((len(b), k))
+    v = r0 / np.linalg.norm(r0)
+    for j in range(k):
+        K[:, j] = v
+        v = B @ v
+        v /= np.linalg.norm(v)
+    W, _ = np.linalg.qr(K)
+    c = np.linalg.lstsq(B @ W, r0, rcond=None)[0]
+    return x0 + Minv @ (W @ c)
+
+
+@pytest.mark.parametrize("prec", ["none", "ras"])
+def test_gmres_iterates_minimise_the_residual_over_the_krylov_space(orc, prec):
+    """Each x_k (k steps inside one cycle) is the minimal-residual point of the
+    right-preconditioned Krylov space; after a restart the same holds from the
+    restart point. A dropped Givens term, a wrong back substitution or a missing
+    M^{-1} in the update each give a larger residual than the minimum."""
+    A = synth.diffusion2d_5pt_lognormal(12, 1.5, seed=8)
+    b = synth.rhs_uniform(A.n, 5)
+    Ad = A.to_dense()
+    if prec == "none":
+        M, Minv = None, np.eye(A.n)
+    else:
+        M = orc.RAS(A, 0, 2, 1)
+        Minv = np.column_stack([M.apply(e) for e in np.eye(A.n)])
+    for k in range(1, 7):
+        x, info = orc.gmres(A, b, M=M, tol=1e-300, maxit=k, restart=8)
+        assert info.iters == k and info.restarts == 1
+        xr = min_residual_iterate(Ad, Minv, b, np.zeros(A.n), k)
+        res, res_ref = np.linalg.norm(b - Ad @ x), np.linalg.norm(b - Ad @ xr)
+        assert res <= res_ref * (1 + 1e-9), k
+        assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr), k
+        assert abs(info.est_resid - res / np.linalg.norm(b)) <= 1e-10
+    # two cycles of GMRES(3): the second minimises from the first cycle's end point
+    x3, _ = orc.gmres(A, b, M=M, tol=1e-300, maxit=3, restart=3)
+    x5, info = orc.gmres(A, b, M=M, tol=1e-300, maxit=5, restart=3)
+    assert info.restarts == 2
+    xr = min_residual_iterate(Ad, Minv, b, x3, 2)
+    assert np.linalg.norm(x5 - xr) <= 1e-8 * np.linalg.norm(xr)
+
+
 def test_gmres_finite_termination(orc):
     A = synth.poisson2d_5pt(6)
     b = synth.rhs_uniform(A.n, 1)
