@@ -623,7 +623,10 @@ typedef struct {
                          level, refactored
                          on the GPU with the new values (hec_refactor); with
                          another pattern (or for a one-CTA batched system), set
-                         up again                                                  */
+                         up again.  If that refactor or new set-up fails, the
+                         key's resident system is dropped (the error is the
+                         request's status): the next request with the key
+                         must carry a matrix                                       */
     uint64_t tag;     /* returned with the result                                   */
 } hec_request_t;
 

@@ -240,6 +240,7 @@ void lane_main(hec_server_s *S, int lane)
         Resident local;
         Resident *R = &local;
         int rc = HEC_OK;
+        bool broken = false;  // a cached system's refactor or new set-up failed part-way
         if (reuse) {
             {
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -256,10 +257,12 @@ void lane_main(hec_server_s *S, int lane)
                 // exactly the resident matrix's count of values
                 rc = hec_refactor(R->A, R->M, q.va.data(), st);
                 r.refactored = 1;
+                broken = rc < 0;
             } else if (q.has_matrix) {
                 // another pattern, or a one-CTA batched system: set it up again
                 R->destroy();
                 rc = abi_guard("hec_server set-up", [&]() { return setup(S, q, st, *R); });
+                broken = rc < 0;
             }
         } else if (!q.has_matrix) {
             rc = fail(HEC_ERR_INVALID, "key %llu is not resident and the request has no matrix",
@@ -317,7 +320,15 @@ void lane_main(hec_server_s *S, int lane)
             S->reserved -= need;
             if (q.key)
                 S->busy.erase(q.key);
-            if (reuse) {
+            if (reuse && broken) {
+                // its handles may hold part of the old and part of the new
+                // system: drop the entry, so that the key must come back
+                // with a matrix
+                Resident &c = S->cache[q.key];
+                S->reserved -= c.bytes;
+                c.destroy();
+                S->cache.erase(q.key);
+            } else if (reuse) {
                 Resident &c = S->cache[q.key];
                 c.users = 0;
                 S->reserved += used - c.bytes; // refactor maps or a new set-up
@@ -417,7 +428,8 @@ int hec_server_submit(hec_server_t S, const hec_request_t *req, uint64_t *ticket
         if (has && (!req->A.col || !req->A.val))
             return fail(HEC_ERR_INVALID, "invalid request matrix");
         const int n = req->A.n;
-        if (n < 1 || req->ilu_k < 0 || (has && (req->A.row_ptr[0] != 0 || req->A.row_ptr[n] != req->A.nnz)))
+        if (n < 1 || req->ilu_k < 0 ||
+            (has && (req->A.nnz < 0 || req->A.row_ptr[0] != 0 || req->A.row_ptr[n] != req->A.nnz)))
             return fail(HEC_ERR_INVALID, "invalid request matrix");
         Request q;
         q.tag = req->tag;

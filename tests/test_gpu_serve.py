@@ -170,3 +170,39 @@ def test_serve_keyed_new_values_refactor_on_device(H, orc):
         assert r["status"] == H.OK and rc["status"] == H.OK
         assert np.array_equal(x, xc)
         assert np.linalg.norm(b - orc.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_serve_failed_refactor_drops_the_resident_system(H, orc):
+    """New values of the resident pattern with a zero first pivot: the
+    refactor fails (the request's status), the key's system is dropped
+    rather than kept half-updated, a request with the key alone then finds
+    nothing resident, and the key set up again from a matrix solves."""
+    A = synth.serving_matrix({"stencil": 7, "side": 36, "k": 1, "seed": 5})
+    b = synth.rhs_uniform(A.n, 4)
+    r0, r1 = int(A.row_ptr[0]), int(A.row_ptr[1])
+    bad_val = A.val.copy()
+    bad_val[r0 + int(np.flatnonzero(A.col[r0:r1] == 0)[0])] = 0.0
+    bad = synth.CSR(A.row_ptr, A.col, bad_val)
+
+    def one(S, M, key, tag):
+        t = S.submit(M, b, ilu_k=1, key=key, tag=tag)
+        r = []
+        while not r:
+            r = S.poll(wait_ms=200)
+        return t, r[0]
+
+    with H.Server(lanes=1, flags=H.MIXED_FP32) as S:
+        t, r = one(S, A, 92, 0)
+        assert r["status"] == H.OK and r["reused"] == 0
+        S.solution(t, A.n)
+        assert S.stats()["reserved"] > 0
+        _, r = one(S, bad, 92, 1)
+        assert r["reused"] == 1 and r["refactored"] == 1
+        assert r["status"] == H.ERR_ZERO_PIVOT
+        assert S.stats()["reserved"] == 0
+        _, r = one(S, None, 92, 2)
+        assert r["status"] == H.ERR_INVALID
+        t, r = one(S, A, 92, 3)
+        assert r["status"] == H.OK and r["reused"] == 0
+        x = S.solution(t, A.n)
+        assert np.linalg.norm(b - orc.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
