@@ -615,6 +615,64 @@ def test_resident_layout_runs_to_the_oracle_apply(H, orc, case):
     assert P2.info()["apply_bytes"] == inf["apply_bytes"]
 
 
+def _diagonal(n):
+    return synth.CSR(np.arange(n + 1), np.arange(n), 1.5 + np.arange(n) % 3)
+
+
+def _lower_bidiagonal(n):
+    rows = np.concatenate([np.arange(n), np.arange(1, n)])
+    cols = np.concatenate([np.arange(n), np.arange(n - 1)])
+    vals = np.concatenate([np.full(n, 2.0), np.full(n - 1, -1.0)])
+    o = np.lexsort((cols, rows))
+    return synth.CSR(np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]),
+                     cols[o], vals[o])
+
+
+DEGENERATE_CASES = {
+    "n1": (lambda: _diagonal(1), 0, 1, 0),                    # one row, one level
+    "diagonal_3_blocks": (lambda: _diagonal(300), 0, 3, 1),   # no dependencies at all
+    "bidiagonal_chain": (lambda: _lower_bidiagonal(300), 0, 1, 0),  # L: 300 levels of 1 row
+    "one_row_per_block": (lambda: synth.tridiagonal(16, 3), 0, 16, 1),
+    "overlap_covers_all": (lambda: synth.tridiagonal(40, 4), 1, 4, 50),
+}
+
+
+@pytest.mark.parametrize("kernel", ["streamed", "resident"])
+@pytest.mark.parametrize("case", sorted(DEGENERATE_CASES))
+def test_degenerate_layouts_run_to_the_oracle_apply(H, orc, case, kernel):
+    """The edge cases of the method: a single row, rows with no dependency,
+    a chain with one row per level, blocks of one owned row, and an overlap
+    that covers the whole matrix; both kernels' layouts run on the host,
+    FP64 and FP32, every owned row written once and within the rounding bound
+    of the oracle's RAS apply."""
+    make, k, nb, ov = DEGENERATE_CASES[case]
+    A = make()
+    M = H.hec_build(A.row_ptr, A.col, A.val, host_only=True)
+    P = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P, kernel=H.TRSV_RESIDENT if kernel == "resident" else H.TRSV_STREAMED)
+    assert P.info()["trsv_resident"] == (1 if kernel == "resident" else 0)
+    R = orc.RAS(A, k, nb, ov)
+    r = synth.rhs_uniform(A.n, 2)
+    for fp32 in (False, True):
+        lay = H.Precond.layout(P, fp32=fp32)
+        if kernel == "resident":
+            z, writes = run_resident(lay, P, A.n, r, nb)
+        else:
+            z, writes = run_layout(lay, A.n, r)
+            z2, _ = run_layout(lay, A.n, r, eager=False)
+            assert np.array_equal(z, z2)
+        assert np.all(writes == 1)
+        check_apply(orc, R, r, z, fp32=fp32, what="%s %s fp32=%d" % (case, kernel, fp32))
+    # the automatic choice: resident unless a level holds more than 128 rows
+    # (the chain's U is diagonal: one level of 300 rows)
+    widest = max(int(np.max(np.diff(P.levels(b, which)[0])))
+                 for b in range(nb) for which in (H.FACTOR_L, H.FACTOR_U))
+    P2 = H.ilu_k_setup(M, k, nb, ov)
+    H.level_schedule(P2)
+    assert P2.info()["trsv_resident"] == (1 if widest <= 128 else 0)
+    assert (widest > 128) == (case == "bidiagonal_chain")
+
+
 def test_resident_kernel_refused_where_it_does_not_fit(H):
     """Rows longer than 8 entries (a random matrix with ILU(2) fill) cannot
     take the resident kernel: asking for it fails at level_schedule, the
